@@ -1,0 +1,399 @@
+#!/usr/bin/env python3
+"""Benchmark of the evaluate-and-stamp hot path (one JSON line on stdout).
+
+A step is one Newton-iteration eval_stamp of the whole workload: every MOSFET evaluated (currents,
+charges, conductances) and stamped into A and b. Default workload: the 256 x 256 6T SRAM array
+(393,216 MOSFETs, 131,840 unknowns), node voltages U[0, 1] V, sizes W ~ U[0.5, 5] um,
+L ~ U[0.1, 1] um, all from the fixed seed. Inputs are resident in HBM; a 256 MiB buffer is
+written between timed steps so every step starts with a cold L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (under torchrun): every rank evaluates its own replica of the workload (weak scaling, no
+collective on the data path); rank 0 prints the aggregate. ``--impl reference`` times the serial
+CPU oracle on the host cores on the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MOSFET eval+stamp/s per NR iter (FP64, 1xGB300)"
+UNIT = "device evals+stamps/s"
+# FP64 floating-point operations per device of the evaluate kernel (DADD + DMUL + 2 DFMA thread
+# instructions per device, from the ncu instruction counters of the kernel; see profiles/).
+FP64_FLOP_PER_DEVICE = None
+# GB300: 152 SMs x 2 FP64 FMA per clock per SM x 2 flop x 2070 MHz maximum SM clock.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["sram", "logic", "logic1m", "batch", "chain"],
+                    default="sram")
+    ap.add_argument("--variant", default="auto")
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--quick", action="store_true",
+                    help="timed steps only (no autotune, e2e, extras, probes, baseline): for ncu")
+    return ap.parse_args()
+
+
+def workload(name):
+    import netgen
+    if name == "sram":
+        return netgen.config(2), "sram_256x256_6T (393216 MOSFETs)"
+    if name == "logic":
+        return netgen.config(3), "random_logic_200k_gates"
+    if name == "logic1m":
+        return netgen.random_logic(277_778), "random_logic_277778_gates (~1M MOSFETs)"
+    if name == "batch":
+        return netgen.config(4), "batch_4096_circuits_merged"
+    return netgen.config(1), "inverter_chain_64"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region (SM clock, reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.3)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(net, x, budget_s=10.0):
+    """The oracle as it stands, single-threaded, on the host: full workload, repeated."""
+    import netgen
+    import oracle
+    o = oracle.Oracle(net, netgen.default_cards())
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        o.eval_stamp(x, want_q=True)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or (reps >= 1 and el * (reps + 1) / reps > 3 * budget_s):
+            break
+    return {"value": net.n_dev * reps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"whole workload ({net.n_dev} devices) x {reps} eval_stamp calls, "
+                      f"{el:.1f} s, 1 thread"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import netgen
+    import oracle
+    net, wname = workload(args.workload)
+    x = netgen.random_x(net)
+    o = oracle.Oracle(net, netgen.default_cards())
+    # bounded steps: the oracle takes about a second per step on this workload
+    steps = max(1, min(args.steps, 20))
+    warm = max(0, min(args.warmup, 2))
+    for _ in range(warm):
+        o.eval_stamp(x, want_q=True)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        o.eval_stamp(x, want_q=True)
+    el = time.perf_counter() - t0
+    v = net.n_dev * steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0,
+            "steps": steps, "warmup": warm, "ms_per_step": 1e3 * el / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wname, "sample": "whole workload"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"whole workload ({net.n_dev} devices) x {steps} steps"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    from paper_2604_03079_gb300 import build as _build
+    _build.build()
+    import netgen
+    import paper_2604_03079_gb300 as eec
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    net, wname = workload(args.workload)
+    x = netgen.random_x(net)
+    cards = netgen.default_cards()
+    circ = eec.Circuit(net, cards, color=True)
+    xt = torch.as_tensor(x, device=dev)
+    A, b, q = circ.new_outputs(want_q=True)
+    ms_variants = [] if args.quick else eec.eec_autotune(circ.ctx, xt, A, b, q, reps=5)
+    if args.variant != "auto":
+        eec.eec_set_variant(circ.ctx, int(args.variant))
+    variant = eec.eec_get_variant(circ.ctx)
+    graphed = variant in (eec.EEC_VARIANT_COLOR_FUSED, eec.EEC_VARIANT_COLOR_BUFFERED)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        circ.eval_stamp(xt, A, b, q)
+    torch.cuda.synchronize()
+    assert circ.status() == 0
+
+    clocks = Clocks(torch.cuda.current_device()) if (rank == 0 and not args.quick) else None
+    if clocks:
+        clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if not graphed:
+        eec.eec_profile_enable(circ.ctx, True)
+    eec.eec_profile_read(circ.ctx)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        circ.eval_stamp(xt, A, b, q)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop() if clocks else None
+    prof = eec.eec_profile_read(circ.ctx)
+    eec.eec_profile_enable(circ.ctx, False)
+    step_ms = [a.elapsed_time(bb) for a, bb in ev]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    assert circ.status() == 0
+    ms_per_step = total_ms / args.steps
+    value = world * net.n_dev / (ms_per_step * 1e-3)
+    launches = prof["kernels"]
+
+    if graphed:   # per-kernel times of the graph-replayed schedules: one profiled pass
+        eec.eec_profile_enable(circ.ctx, True)
+        for _ in range(args.steps):
+            flush.zero_()
+            circ.eval_stamp(xt, A, b, q)
+        prof = eec.eec_profile_read(circ.ctx)
+        eec.eec_profile_enable(circ.ctx, False)
+    eval_ms = prof["ms_eval"] / max(prof["calls"], 1)
+    stamp_ms = prof["ms_stamp"] / max(prof["calls"], 1)
+    init_ms = prof["ms_init"] / max(prof["calls"], 1)
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded netlist generators, random-init node voltages)",
+           "config": {"workload": wname, "n_dev": net.n_dev, "n_unknowns": circ.n,
+                      "nnz": circ.nnz, "colors": circ.n_colors,
+                      "variant": eec.VARIANT_NAMES[variant],
+                      "l2": "flushed (256 MiB write) before every timed step",
+                      "parallelism": f"replica x{world}" if world > 1 else "single GPU"},
+           "gpu_launches": launches,
+           "phases_ms": {"init": init_ms, "eval": eval_ms, "stamp": stamp_ms}}
+    if clk:
+        out["clocks"] = clk
+
+    if rank == 0 and args.quick:
+        print(json.dumps(out))
+    elif rank == 0:
+        # roofline of the dominant kernel (the evaluate kernel; FP64-pipe bound)
+        flop = FP64_FLOP_PER_DEVICE
+        ach = (flop * net.n_dev / (eval_ms * 1e-3) / 1e12) if (flop and eval_ms > 0) else None
+        out["roofline"] = {"bound": "alu", "kernel": "k_eval (evaluate)",
+                           "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                           "frac": (ach / FP64_PEAK_TFLOPS) if ach else None, "traffic": None,
+                           "peak_source": "152 SM x 2 DFMA/clk x 2 flop x 2070 MHz (recipe unit "
+                                          "counts; nominal 1.25 TFLOP/s FP64)"}
+        out["fp64_probe_tflops"] = eec.eec_fp64_peak(4096, 8) / 1e12
+        out["variants_ms"] = {eec.VARIANT_NAMES[i]: m for i, m in enumerate(ms_variants)}
+
+        # end to end through the public API with host buffers (pinned), copies inside the timing
+        xh = torch.as_tensor(x).pin_memory()
+        Ah = torch.empty(circ.nnz, dtype=torch.float64).pin_memory()
+        bh = torch.empty(circ.n, dtype=torch.float64).pin_memory()
+        qh = torch.empty(4 * circ.n_dev, dtype=torch.float64).pin_memory()
+        e2e_steps = max(10, min(args.steps, 200))
+        for _ in range(3):
+            xt.copy_(xh, non_blocking=True)
+            circ.eval_stamp(xt, A, b, q)
+            Ah.copy_(A, non_blocking=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(e2e_steps):
+            xt.copy_(xh, non_blocking=True)
+            circ.eval_stamp(xt, A, b, q)
+            Ah.copy_(A, non_blocking=True)
+            bh.copy_(b, non_blocking=True)
+            qh.copy_(q, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = e0.elapsed_time(e1) / e2e_steps
+        out["e2e"] = {"value": world * net.n_dev / (e2e_ms * 1e-3), "unit": UNIT,
+                      "h2d_bytes_per_step": 8 * circ.n,
+                      "d2h_bytes_per_step": 8 * (circ.nnz + circ.n + 4 * circ.n_dev),
+                      "ms_per_step": e2e_ms}
+
+        if world == 1 and not args.no_extras:
+            out["extras"] = extras(eec, circ, net, x, xt, A, b, q, args, dev)
+        if world == 1:
+            out["cpu_baseline"] = cpu_baseline(net, x)
+            out["gpu_over_oracle"] = value / out["cpu_baseline"]["value"]
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def _time(fn, reps, stream):
+    import torch
+    for _ in range(2):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def extras(eec, circ, net, x, xt, A, b, q, args, dev):
+    """Backward vs plain forward, per-variant phase split (t_calc / t_stamp), batched vs
+    4096 separate calls."""
+    import torch
+    import netgen
+    stream = torch.cuda.current_stream()
+    res = {}
+    rng = netgen.Rng(netgen.DEFAULT_SEED, 12)
+    gA = torch.as_tensor(rng.normal(circ.nnz), device=dev)
+    gb = torch.as_tensor(rng.normal(circ.n), device=dev)
+    gx = torch.empty(circ.n, dtype=torch.float64, device=dev)
+    gW = torch.empty(circ.n_dev, dtype=torch.float64, device=dev)
+    gL = torch.empty(circ.n_dev, dtype=torch.float64, device=dev)
+    fwd_ms = _time(lambda: circ.eval_stamp(xt, A, b, q), 50, stream)
+    bwd_ms = _time(lambda: eec.eec_eval_stamp_bwd(circ.ctx, xt, gA, gb, gx, gW, gL), 20, stream)
+    res["bwd"] = {"devices_per_s": net.n_dev / (bwd_ms * 1e-3), "ms": bwd_ms,
+                  "fwd_ms": fwd_ms, "bwd_over_fwd_time": bwd_ms / fwd_ms,
+                  "workload": "config 5: SRAM 256x256, gA, gb ~ N(0, 1)"}
+    phases = {}
+    v0 = eec.eec_get_variant(circ.ctx)
+    for v in range(eec.EEC_N_VARIANTS):
+        eec.eec_set_variant(circ.ctx, v)
+        eec.eec_profile_enable(circ.ctx, True)
+        eec.eec_profile_read(circ.ctx)
+        for _ in range(10):
+            circ.eval_stamp(xt, A, b, q)
+        p = eec.eec_profile_read(circ.ctx)
+        eec.eec_profile_enable(circ.ctx, False)
+        n = max(p["calls"], 1)
+        phases[eec.VARIANT_NAMES[v]] = {"init_ms": p["ms_init"] / n, "eval_ms": p["ms_eval"] / n,
+                                        "stamp_ms": p["ms_stamp"] / n}
+    eec.eec_set_variant(circ.ctx, v0)
+    res["phases_ungraphed"] = phases
+
+    # batched (config 4): one context for 4096 circuits vs 4096 plain per-circuit calls
+    nets = netgen.batch_circuits(4096)
+    cards = netgen.default_cards()
+    bc = eec.Circuit(None, cards, color=True, batch=nets)
+    xb = torch.as_tensor(netgen.random_x(netgen.concat(nets)), device=dev)
+    Ab, bb_, qb = bc.new_outputs()
+    ms_b = eec.eec_autotune(bc.ctx, xb, Ab, bb_, qb, reps=5)
+    vb = eec.eec_get_variant(bc.ctx)
+    eec.eec_graph_capture(bc.ctx, xb, Ab, bb_, qb)
+    t_graph = _time(lambda: eec.eec_graph_launch(bc.ctx), 20, stream)
+    t_batch = _time(lambda: bc.eval_stamp(xb, Ab, bb_, qb), 20, stream)
+    ro, no, do = eec.eec_get_batch_offsets(bc.ctx, len(nets))
+    plain = [eec.Circuit(m, cards, color=True, variant=vb) for m in nets]
+    views = []
+    for k, c in enumerate(plain):
+        views.append((xb[ro[k]:ro[k + 1]], Ab[no[k]:no[k + 1]], bb_[ro[k]:ro[k + 1]],
+                      torch.empty(4 * c.n_dev, dtype=torch.float64, device=dev)))
+
+    def all_plain():
+        for c, (xv, av, bv, qv) in zip(plain, views):
+            c.eval_stamp(xv, av, bv, qv)
+    t_plain = _time(all_plain, 3, stream)
+    nd = bc.n_dev
+    res["batched"] = {"circuits": len(nets), "devices": nd, "colors_merged": bc.n_colors,
+                      "variant": eec.VARIANT_NAMES[vb],
+                      "batched_devices_per_s": nd / (t_batch * 1e-3),
+                      "graph_devices_per_s": nd / (t_graph * 1e-3),
+                      "plain_4096_calls_devices_per_s": nd / (t_plain * 1e-3),
+                      "batched_ms": t_batch, "graph_ms": t_graph, "plain_4096_calls_ms": t_plain,
+                      "speedup_vs_plain": t_plain / t_graph,
+                      "variants_ms": {eec.VARIANT_NAMES[i]: m for i, m in enumerate(ms_b)}}
+    del plain
+    return res
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,269 @@
+/*
+ * eec.h — C ABI of the GB300 (sm_103a) MOSFET evaluate-and-stamp library.
+ *
+ * The library implements the per-Newton-iteration hot path of EEspice (arXiv 2604.03079): every
+ * MOSFET instance is evaluated at the present node voltages (terminal currents, charges and
+ * linearised conductances: the "compute phase" of Sec. II (i)) and its contributions are
+ * accumulated into the shared sparse MNA matrix A and right-hand side b (the "stamp phase" of
+ * Sec. II (ii)). Stamping is made lock-free by the paper's conflict graph and greedy colouring
+ * (Sec. I, Sec. II): devices that share a non-ground node get different colours, colours run one
+ * after another, and the devices of one colour stamp concurrently.
+ *
+ * Conventions shared by every entry point
+ *  - Return value: 0 on success, a negative EEC_E* code on failure. No C++ exception crosses the
+ *    ABI. eec_last_error() returns a message for the last failure on that context.
+ *  - Pointers named *_dev are CUDA device pointers; all others are host pointers. The caller owns
+ *    every pointer it passes; the library copies host inputs during the call and keeps no pointer
+ *    to them, never frees caller memory, and owns only the device arrays it allocates itself
+ *    (released by eec_destroy).
+ *  - cuda_stream is a cudaStream_t (NULL = legacy default stream). Calls that take a stream are
+ *    asynchronous and stream-ordered unless stated otherwise.
+ *  - Unknowns are the free (not source-held) nodes in increasing node order. A is stored in CSR
+ *    with sorted column indices; its pattern comes from eec_get_pattern().
+ *  - The context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef EEC_H_
+#define EEC_H_
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define EEC_API __attribute__((visibility("default")))
+#else
+#define EEC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Error codes. */
+#define EEC_OK 0
+#define EEC_EINVAL (-1)   /* bad argument: size, index, pointer, enum value */
+#define EEC_ESTATE (-2)   /* call out of order (e.g. eval before eec_build_scatter) */
+#define EEC_ECUDA (-3)    /* a CUDA runtime call failed; message has the CUDA error string */
+#define EEC_ETIMEOUT (-4) /* a device-side wait ran past its limit (status word) */
+#define EEC_ENUMERIC (-5) /* non-finite value detected by the debug checks (status word) */
+#define EEC_ENOMEM (-7)   /* device allocation failed */
+
+/* Evaluation/stamp schedules (Table I analogues). */
+#define EEC_VARIANT_AUTO (-1)          /* the autotuner's choice (SEGREDUCE until tuned) */
+#define EEC_VARIANT_COLOR_FUSED 0      /* "ColorFused": one fused launch per colour */
+#define EEC_VARIANT_PERSISTENT 1       /* one persistent launch, grid barrier between colours */
+#define EEC_VARIANT_ATOMIC 2           /* uncoloured, FP64 atomicAdd stamping */
+#define EEC_VARIANT_SEGREDUCE 3        /* evaluate to buffer, then per-entry gather (no colours) */
+#define EEC_VARIANT_COLOR_BUFFERED 4   /* "Color": evaluate to buffer, then one stamp per colour */
+#define EEC_N_VARIANTS 5
+
+/* Conflict rules for the colouring. */
+#define EEC_CONFLICT_FREE_NODE 0   /* share a free node (rails are not unknowns)  [default] */
+#define EEC_CONFLICT_ANY_NONGROUND 1 /* share any node but ground (the paper's literal rule) */
+#define EEC_CONFLICT_WRITE_ROWS 2  /* share a free node both write as a DC row (d, s or b) */
+
+/* Colouring algorithms. */
+#define EEC_COLOR_GREEDY_SEQ 0  /* host greedy in the given order */
+#define EEC_COLOR_JP_INDEX 1    /* GPU Jones-Plassmann, priority = position in the order */
+#define EEC_COLOR_JP_RANDOM 2   /* GPU Jones-Plassmann, hashed priorities (valid, not greedy) */
+
+/* Model card of the EES-L1 level: EEC_CARD_LEN doubles in this order.
+ * VTH0 K1 PHI NFACT U0 UA UB VSAT TOX ETA0 DELTA LAMBDA LREF JS HDIF CGSO CGDO XPART D1 GMIN TEMP */
+#define EEC_CARD_LEN 21
+
+typedef struct eec_ctx eec_ctx; /* opaque, library-owned */
+
+typedef struct {
+  int32_t variant;       /* EEC_VARIANT_*; default EEC_VARIANT_AUTO */
+  int32_t block;         /* threads per block of the evaluate kernels; 0 = library default */
+  int32_t conflict_rule; /* EEC_CONFLICT_*; default EEC_CONFLICT_FREE_NODE */
+  int32_t debug_checks;  /* nonzero: kernels flag non-finite outputs in the status word */
+} eec_options;
+
+/* eec_options with every field at its default. */
+EEC_API eec_options eec_default_options(void);
+
+/* Create a context. opt may be NULL (defaults). *out receives the handle. */
+EEC_API int eec_create(eec_ctx** out, const eec_options* opt);
+
+/* Release the context and every device array it owns. Accepts NULL. Synchronises the device. */
+EEC_API void eec_destroy(eec_ctx* ctx);
+
+/* Message for the last failure on ctx ("" if none); valid until the next call on ctx. */
+EEC_API const char* eec_last_error(const eec_ctx* ctx);
+
+/*
+ * Upload a netlist (Sec. I: the MNA system A x = b of the circuit; Sec. II: FET instances).
+ *  n_nodes      nodes 0..n_nodes-1; node 0 is ground.
+ *  node_fixed   [n_nodes] 1 = node held by an ideal source at node_vfix[i] volts (ground is
+ *               always fixed at 0 V), 0 = free node (an unknown).
+ *  dev_nodes    [n_dev*4] terminals d, g, s, b of each MOSFET.
+ *  dev_type     [n_dev] +1 NMOS, -1 PMOS.
+ *  W, L         [n_dev] channel width and length in metres (> 0).
+ *  model_id     [n_dev] row of the card table (eec_set_model_cards).
+ *  res_nodes    [n_res*2], res_G [n_res] siemens: linear conductances.
+ *  isrc_nodes   [n_isrc*2] (a, b), isrc_val [n_isrc] amperes flowing from a to b through the source.
+ *  gshunt       conductance from every free node to ground (keeps gate-only nodes regular).
+ * Host arrays, copied. Replaces any previous netlist and resets the colouring and scatter map.
+ */
+EEC_API int eec_upload_netlist(eec_ctx* ctx, int32_t n_nodes, const uint8_t* node_fixed,
+                       const double* node_vfix, int32_t n_dev, const int32_t* dev_nodes,
+                       const int8_t* dev_type, const double* W, const double* L,
+                       const int32_t* model_id, int32_t n_res, const int32_t* res_nodes,
+                       const double* res_G, int32_t n_isrc, const int32_t* isrc_nodes,
+                       const double* isrc_val, double gshunt);
+
+/* Model-card table [n_cards*EEC_CARD_LEN] (host, copied). Every model_id must be < n_cards. */
+EEC_API int eec_set_model_cards(eec_ctx* ctx, int32_t n_cards, const double* cards);
+
+/*
+ * Colour the conflict graph (Sec. I; Sec. II: an edge joins two FETs that share at least one
+ * non-ground node; greedy colouring gives each vertex, in visiting order, the smallest colour not
+ * used by its already coloured neighbours). The edge rule is opt.conflict_rule.
+ *  order       [n_dev] visiting order (a permutation of 0..n_dev-1), NULL = natural order.
+ *  algo        EEC_COLOR_*: GREEDY_SEQ (host) and JP_INDEX (GPU) give the same colours for the
+ *              same order; JP_RANDOM gives a valid colouring with hashed priorities.
+ *  colors_out  [n_dev] host, nullable: colour of each device.
+ *  n_colors    host, out: number of colours C.
+ * Synchronous. Resets the scatter map.
+ */
+EEC_API int eec_color(eec_ctx* ctx, const int32_t* order, int32_t algo, int32_t* colors_out,
+              int32_t* n_colors);
+
+/*
+ * Build the MNA pattern and the per-device scatter map (Sec. II: every device's contributions
+ * go to fixed entries of A and b). The pattern holds, over free nodes: the diagonal, resistor
+ * pairs, and every (t, u) terminal pair of every device, the gate row included (symmetric).
+ * Devices are laid out colour-major on the device (natural order when not coloured).
+ * Out: *n_unknowns, *nnz. Synchronous.
+ */
+EEC_API int eec_build_scatter(eec_ctx* ctx, int32_t* n_unknowns, int64_t* nnz);
+
+/* Copy the pattern to caller arrays: row_ptr [n+1], col_idx [nnz], unk_of_node [n_nodes]
+ * (unknown index of each node, -1 when fixed). Any of them may be NULL. */
+EEC_API int eec_get_pattern(const eec_ctx* ctx, int32_t* row_ptr, int32_t* col_idx,
+                    int32_t* unk_of_node);
+
+/* Colour offsets [C+1] (host) of the device layout; colour c holds positions
+ * off[c] .. off[c+1]-1. Fails with EEC_ESTATE when not coloured. */
+EEC_API int eec_get_color_offsets(const eec_ctx* ctx, int32_t* off);
+
+/*
+ * Replace W and L of every device (original device order, length n_dev) without touching the
+ * topology; sizing loops call this between evaluations. W_dev, L_dev: device pointers.
+ */
+EEC_API int eec_update_params(eec_ctx* ctx, const double* W_dev, const double* L_dev, void* cuda_stream);
+
+/* Select the schedule (EEC_VARIANT_*) used by eec_eval_stamp. */
+EEC_API int eec_set_variant(eec_ctx* ctx, int32_t variant);
+EEC_API int eec_get_variant(const eec_ctx* ctx, int32_t* variant);
+
+/*
+ * One Newton-iteration evaluate-and-stamp (Sec. II (i) compute phase, (ii) stamp phase):
+ *   A = A_lin + sum_dev G_dev,   b = b_lin + sum_dev (-I_dev + G_dev V_dev)
+ * where I_dev[t] is the current from node t into the device, G_dev[t][u] = dI_t/dV_u over free
+ * terminals, A_lin / b_lin hold gshunt, resistors, current sources and source-held nodes.
+ *  x_dev        [n] node voltages of the unknowns.
+ *  A_values_dev [nnz] out: values of A in the CSR pattern of eec_get_pattern().
+ *  b_dev        [n] out.
+ *  q_dev        [4*n_dev] out, nullable: terminal charges, terminal-major (q[t*n_dev + k],
+ *               t = d, g, s, b), original device order.
+ * Asynchronous on cuda_stream. Device errors land in the status word (eec_status).
+ */
+EEC_API int eec_eval_stamp(eec_ctx* ctx, const double* x_dev, double* A_values_dev, double* b_dev,
+                   double* q_dev, void* cuda_stream);
+
+/*
+ * Gradient of s = sum_e gA[e] A[e] + sum_i gb[i] b[i], with A, b formed at x, with respect to
+ * x and to every device's W and L. Read-only gathers (the transpose of the scatter): one pass
+ * per device produces terminal and parameter gradients, one pass per unknown gathers them.
+ *  gA_dev [nnz], gb_dev [n] in; gx_dev [n], gW_dev [n_dev], gL_dev [n_dev] out (original order).
+ */
+EEC_API int eec_eval_stamp_bwd(eec_ctx* ctx, const double* x_dev, const double* gA_dev,
+                       const double* gb_dev, double* gx_dev, double* gW_dev, double* gL_dev,
+                       void* cuda_stream);
+
+/*
+ * Capture the current variant's eval_stamp on these buffers into a CUDA graph owned by ctx
+ * (replacing any previous one); eec_graph_launch() then replays it on any stream.
+ */
+EEC_API int eec_graph_capture(eec_ctx* ctx, const double* x_dev, double* A_values_dev, double* b_dev,
+                      double* q_dev, void* cuda_stream);
+EEC_API int eec_graph_launch(eec_ctx* ctx, void* cuda_stream);
+
+/*
+ * Time every variant on these buffers (CUDA events, `reps` launches each after one warm-up) and
+ * select the fastest for eec_eval_stamp; ms_out [EEC_N_VARIANTS] (nullable) receives the mean
+ * time per call, negative for a variant that does not apply (e.g. colour schedules when the
+ * context is not coloured). Synchronous.
+ */
+EEC_API int eec_autotune(eec_ctx* ctx, const double* x_dev, double* A_values_dev, double* b_dev,
+                 double* q_dev, int32_t reps, void* cuda_stream, float* ms_out);
+
+/*
+ * Synchronise cuda_stream, read and clear the device status word. Returns 0 when no device-side
+ * error was recorded, else EEC_ETIMEOUT (a grid barrier gave up waiting) or EEC_ENUMERIC.
+ */
+EEC_API int eec_status(eec_ctx* ctx, void* cuda_stream);
+
+/*
+ * Phase timing, the t_calc / t_stamp split of the paper's Fig. 4. While enabled, every
+ * eec_eval_stamp records CUDA events on the caller's stream around its three phases (copy of the
+ * linear part into A/b, evaluate — which includes the store-add in the fused schedules — and the
+ * separate stamp pass of the buffered schedules) and launches without CUDA graphs.
+ * eec_profile_read synchronises the recorded events, returns the accumulated milliseconds per
+ * phase over the calls since the last read (any pointer may be NULL) and resets the sums.
+ * n_kernels counts the library's kernel launches (graph replays count their kernel nodes) since
+ * the last read, whether or not timing is enabled.
+ */
+EEC_API int eec_profile_enable(eec_ctx* ctx, int32_t enable);
+EEC_API int eec_profile_read(eec_ctx* ctx, double* ms_init, double* ms_eval, double* ms_stamp,
+                             int64_t* n_calls, int64_t* n_kernels);
+
+/* Sizes of the built context: devices, unknowns, nnz, colours (0 when not coloured). */
+EEC_API int eec_get_sizes(const eec_ctx* ctx, int32_t* n_dev, int32_t* n_unknowns, int64_t* nnz,
+                  int32_t* n_colors);
+
+/*
+ * Batched form: the disjoint union of n_circ netlists as one context whose A is block diagonal
+ * (circuit k owns unknowns circ_row_off[k] .. circ_row_off[k+1]-1 and CSR values
+ * circ_nnz_off[k] .. circ_nnz_off[k+1]-1). Each circuit is described by the same arrays as
+ * eec_upload_netlist, passed as arrays of per-circuit pointers; node 0 of every circuit is the
+ * shared ground. Greedy colouring of the union in natural order colours every circuit on its own
+ * and merges colour c of all circuits into one phase.
+ */
+typedef struct {
+  int32_t n_nodes;
+  const uint8_t* node_fixed;
+  const double* node_vfix;
+  int32_t n_dev;
+  const int32_t* dev_nodes;
+  const int8_t* dev_type;
+  const double* W;
+  const double* L;
+  const int32_t* model_id;
+  int32_t n_res;
+  const int32_t* res_nodes;
+  const double* res_G;
+  int32_t n_isrc;
+  const int32_t* isrc_nodes;
+  const double* isrc_val;
+} eec_netlist;
+
+EEC_API int eec_upload_batch(eec_ctx* ctx, int32_t n_circ, const eec_netlist* nets, double gshunt);
+
+/* After eec_build_scatter on a batch: circ_row_off [n_circ+1], circ_nnz_off [n_circ+1],
+ * circ_dev_off [n_circ+1] (first device of each circuit in original order). */
+EEC_API int eec_get_batch_offsets(const eec_ctx* ctx, int32_t* circ_row_off, int64_t* circ_nnz_off,
+                          int32_t* circ_dev_off);
+
+/*
+ * FP64 fused-multiply-add throughput probe: `iters` iterations of 8 independent DFMA chains per
+ * thread over a grid of blocks_per_sm * SMs blocks. Writes the measured DFMA rate (FLOP/s,
+ * 2 per DFMA) to *flops. Synchronous; used to report the FP64 roofline.
+ */
+EEC_API int eec_fp64_peak(int32_t iters, int32_t blocks_per_sm, double* flops);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EEC_H_ */

@@ -1,0 +1,1089 @@
+// Host side of the C ABI declared in include/eec.h: netlist storage, greedy colouring (host),
+// MNA pattern and scatter-map construction, device uploads, schedule dispatch, CUDA graphs,
+// autotuning and the device status word.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "eec_internal.h"
+
+using namespace eec;
+
+struct eec_ctx {
+  eec_options opt{};
+  std::string err;
+  bool has_net = false, has_cards = false, colored = false, built = false;
+  bool pattern_ready = false;  // host pattern and layout exist (device upload may be missing)
+  // netlist (original device order)
+  int n_nodes = 0;
+  std::vector<uint8_t> fixed;
+  std::vector<double> vfix;
+  int n_dev = 0;
+  std::vector<int> dn;
+  std::vector<int8_t> type;
+  std::vector<double> W, L;
+  std::vector<int> mid;
+  std::vector<int> rn;
+  std::vector<double> rG;
+  std::vector<int> sn;
+  std::vector<double> sI;
+  double gshunt = 0.0;
+  // batch bookkeeping (n_circ == 0: not a batch)
+  int n_circ = 0;
+  std::vector<int> circ_node_off, circ_dev_off;
+  std::vector<int> circ_row_off;
+  std::vector<int64_t> circ_nnz_off;
+  // cards
+  int n_cards = 0;
+  std::vector<double> cards;
+  std::vector<CardK> cardk;
+  // colouring
+  std::vector<int> color;
+  int C = 0;
+  // pattern and layout
+  int n = 0;
+  long long nnz = 0;
+  std::vector<int> unk, row_ptr, col, perm, color_off;
+  // device state
+  DevTopo d{};
+  int* d_coff = nullptr;
+  std::vector<void*> dmem;
+  int* d_status = nullptr;  // [0] status, [1..2] barrier
+  bool params_dirty = false;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t auto_exec = nullptr;
+  const void* auto_key[4] = {nullptr, nullptr, nullptr, nullptr};
+  int auto_variant = -100;
+  cudaGraphExec_t user_exec = nullptr;
+  int tuned_variant = EEC_VARIANT_SEGREDUCE;
+  int sms = 0;
+  int persist_grid = 0;
+  // phase timing and launch counting
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  long long prof_calls = 0;
+  long long n_kernels = 0;
+  long long auto_kernels = 0;  // kernel nodes of the cached graph
+  long long user_kernels = 0;  // kernel nodes of the user graph
+};
+
+namespace {
+
+int fail(eec_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+#define CUDA_TRY(ctx, expr)                                                              \
+  do {                                                                                   \
+    cudaError_t e_ = (expr);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(ctx, EEC_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_));   \
+  } while (0)
+
+template <class T>
+int dalloc(eec_ctx* c, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, EEC_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  c->dmem.push_back(*p);
+  return EEC_OK;
+}
+
+template <class T>
+int dupload(eec_ctx* c, T** p, const std::vector<T>& h) {
+  int rc = dalloc(c, p, h.size());
+  if (rc) return rc;
+  if (!h.empty()) CUDA_TRY(c, cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return EEC_OK;
+}
+
+void drop_graphs(eec_ctx* c) {
+  if (c->auto_exec) cudaGraphExecDestroy(c->auto_exec);
+  if (c->user_exec) cudaGraphExecDestroy(c->user_exec);
+  c->auto_exec = nullptr;
+  c->user_exec = nullptr;
+  c->auto_variant = -100;
+}
+
+void free_topology(eec_ctx* c) {
+  drop_graphs(c);
+  if (!c->dmem.empty()) cudaDeviceSynchronize();
+  for (void* p : c->dmem) cudaFree(p);
+  c->dmem.clear();
+  int* st = c->d_status;
+  c->d = DevTopo{};
+  c->d_coff = nullptr;
+  c->d_status = st;
+  c->built = false;
+}
+
+// Pull sizes changed by eec_update_params back into the host copy before a rebuild.
+int sync_params_to_host(eec_ctx* c) {
+  if (!c->built || !c->params_dirty) return EEC_OK;
+  std::vector<double> Wp(c->n_dev), Lp(c->n_dev);
+  CUDA_TRY(c, cudaMemcpy(Wp.data(), c->d.W, sizeof(double) * c->n_dev, cudaMemcpyDeviceToHost));
+  CUDA_TRY(c, cudaMemcpy(Lp.data(), c->d.L, sizeof(double) * c->n_dev, cudaMemcpyDeviceToHost));
+  for (int k = 0; k < c->n_dev; ++k) {
+    c->W[c->perm[k]] = Wp[k];
+    c->L[c->perm[k]] = Lp[k];
+  }
+  c->params_dirty = false;
+  return EEC_OK;
+}
+
+bool conflict_node(const eec_ctx* c, int node, int term, int rule) {
+  if (rule == EEC_CONFLICT_ANY_NONGROUND) return node != 0;
+  if (c->fixed[node]) return false;
+  if (rule == EEC_CONFLICT_WRITE_ROWS && term == 1) return false;
+  return true;
+}
+
+// Device -> conflict-node lists and node -> device lists (CSR), duplicates removed per device.
+void conflict_incidence(const eec_ctx* c, int rule, std::vector<int>& dev_ptr,
+                        std::vector<int>& dev_node, std::vector<int>& node_ptr,
+                        std::vector<int>& node_dev) {
+  const int N = c->n_dev;
+  dev_ptr.assign(N + 1, 0);
+  dev_node.clear();
+  dev_node.reserve(4 * (size_t)N);
+  for (int k = 0; k < N; ++k) {
+    int got[4];
+    int m = 0;
+    for (int t = 0; t < 4; ++t) {
+      const int node = c->dn[4 * k + t];
+      if (!conflict_node(c, node, t, rule)) continue;
+      bool dup = false;
+      for (int i = 0; i < m; ++i) dup = dup || got[i] == node;
+      if (!dup) got[m++] = node;
+    }
+    for (int i = 0; i < m; ++i) dev_node.push_back(got[i]);
+    dev_ptr[k + 1] = (int)dev_node.size();
+  }
+  node_ptr.assign(c->n_nodes + 1, 0);
+  for (int v : dev_node) node_ptr[v + 1]++;
+  for (int i = 0; i < c->n_nodes; ++i) node_ptr[i + 1] += node_ptr[i];
+  node_dev.assign(dev_node.size(), 0);
+  std::vector<int> fill(node_ptr.begin(), node_ptr.end() - 1);
+  for (int k = 0; k < N; ++k)
+    for (int p = dev_ptr[k]; p < dev_ptr[k + 1]; ++p) node_dev[fill[dev_node[p]]++] = k;
+}
+
+// Greedy colouring in `order`: mark the colours of already-coloured neighbours with the
+// visiting device's id, then take the first unmarked colour.
+void greedy_host(int N, const std::vector<int>& order, const std::vector<int>& dev_ptr,
+                 const std::vector<int>& dev_node, const std::vector<int>& node_ptr,
+                 const std::vector<int>& node_dev, std::vector<int>& col, int* n_colors) {
+  col.assign(N, -1);
+  std::vector<int> mark(64, -1);
+  int C = 0;
+  for (int i = 0; i < N; ++i) {
+    const int v = order[i];
+    for (int p = dev_ptr[v]; p < dev_ptr[v + 1]; ++p) {
+      const int node = dev_node[p];
+      for (int q = node_ptr[node]; q < node_ptr[node + 1]; ++q) {
+        const int w = node_dev[q];
+        const int cw = col[w];
+        if (cw >= 0) {
+          if (cw >= (int)mark.size()) mark.resize(2 * cw + 2, -1);
+          mark[cw] = v;
+        }
+      }
+    }
+    int m = 0;
+    while (m < (int)mark.size() && mark[m] == v) ++m;
+    col[v] = m;
+    C = std::max(C, m + 1);
+  }
+  *n_colors = C;
+}
+
+CardK derive_card(const double* a) {
+  const double kB = 1.380649e-23, q = 1.602176634e-19, eps0 = 8.8541878128e-12;
+  const double VTH0 = a[0], K1 = a[1], PHI = a[2], NFACT = a[3], U0 = a[4], UA = a[5],
+               UB = a[6], VSAT = a[7], TOX = a[8], ETA0 = a[9], DELTA = a[10],
+               LAMBDA = a[11], LREF = a[12], JS = a[13], HDIF = a[14], CGSO = a[15],
+               CGDO = a[16], XPART = a[17], D1 = a[18], GMIN = a[19], TEMP = a[20];
+  CardK k{};
+  const double Vt = kB * TEMP / q;
+  const double Cox = 3.9 * eps0 / TOX;
+  k.VTH0 = VTH0; k.K1 = K1; k.PHI = PHI; k.sqrtPHI = std::sqrt(PHI);
+  k.Vt = Vt; k.inv_Vt = 1.0 / Vt; k.twoVt = 2.0 * Vt;
+  k.nVt = NFACT * Vt; k.inv_nVt = 1.0 / k.nVt;
+  k.UA = UA; k.UB = UB; k.ETA0 = ETA0;
+  k.DELTA = DELTA; k.twoDELTA = 2.0 * DELTA; k.fourDELTA = 4.0 * DELTA;
+  k.fourD1sq = 4.0 * D1 * D1; k.twoD1sq = 2.0 * D1 * D1;
+  k.XPART = XPART; k.GMIN = GMIN;
+  k.U0Cox = U0 * Cox; k.twoVSAT_U0 = 2.0 * VSAT / U0; k.LAMBDA_LREF = LAMBDA * LREF;
+  k.JS_HDIF = JS * HDIF; k.Cox = Cox; k.CGSO = CGSO; k.CGDO = CGDO;
+  return k;
+}
+
+bool valid_card(const double* a) {
+  for (int i = 0; i < EEC_CARD_LEN; ++i)
+    if (!std::isfinite(a[i])) return false;
+  // TOX, U0, VSAT, NFACT, PHI, TEMP must be positive; the rest non-negative except VTH0/ETA0.
+  return a[8] > 0 && a[4] > 0 && a[7] > 0 && a[3] > 0 && a[2] > 0 && a[20] > 0 && a[1] >= 0 &&
+         a[10] >= 0 && a[18] >= 0 && a[13] >= 0 && a[14] >= 0;
+}
+
+int ensure_buf(eec_ctx* c) {
+  if (c->d.buf) return EEC_OK;
+  return dalloc(c, &c->d.buf, (size_t)kNContrib * c->n_dev);
+}
+
+int ensure_gv(eec_ctx* c) {
+  if (c->d.gv) return EEC_OK;
+  return dalloc(c, &c->d.gv, (size_t)4 * c->n_dev);
+}
+
+// Next free profiling event (pool grows on demand, reset by eec_profile_read).
+cudaEvent_t prof_event(eec_ctx* c) {
+  if (c->ev_used == c->ev_pool.size()) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    c->ev_pool.push_back(e);
+  }
+  return c->ev_pool[c->ev_used++];
+}
+
+void prof_mark(eec_ctx* c, cudaStream_t s) {
+  if (!c->prof) return;
+  cudaEvent_t e = prof_event(c);
+  if (e) cudaEventRecord(e, s);
+}
+
+bool variant_needs_colors(int v) {
+  return v == EEC_VARIANT_COLOR_FUSED || v == EEC_VARIANT_PERSISTENT ||
+         v == EEC_VARIANT_COLOR_BUFFERED;
+}
+
+// Enqueue one evaluate-and-stamp with schedule v on stream s. Returns the number of kernels
+// launched in *nk. With profiling on, four events bracket the phases init | evaluate | stamp.
+int run_variant(eec_ctx* c, int v, const double* x, double* A, double* b, double* q,
+                cudaStream_t s, long long* nk) {
+  const DevTopo& T = c->d;
+  const int dbg = c->opt.debug_checks ? 1 : 0;
+  const int blk = c->opt.block;
+  *nk = 0;
+  if (variant_needs_colors(v) && !c->colored)
+    return fail(c, EEC_ESTATE, "colour schedules need eec_color before eec_build_scatter");
+  auto init_Ab = [&]() -> int {
+    CUDA_TRY(c, cudaMemcpyAsync(A, T.Alin, sizeof(double) * c->nnz, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(c, cudaMemcpyAsync(b, T.blin, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, s));
+    return EEC_OK;
+  };
+  int rc;
+  if (v == EEC_VARIANT_SEGREDUCE || v == EEC_VARIANT_COLOR_BUFFERED) {
+    if ((rc = ensure_buf(c))) return rc;
+  }
+  prof_mark(c, s);
+  switch (v) {
+    case EEC_VARIANT_COLOR_FUSED:
+      if ((rc = init_Ab())) return rc;
+      prof_mark(c, s);
+      for (int k = 0; k < c->C; ++k) {
+        if (c->color_off[k + 1] <= c->color_off[k]) continue;
+        CUDA_TRY(c, launch_eval(T, MODE_RMW, c->color_off[k], c->color_off[k + 1], x, A, b, q,
+                                blk, dbg, s));
+        ++*nk;
+      }
+      prof_mark(c, s);
+      break;
+    case EEC_VARIANT_PERSISTENT:
+      if ((rc = init_Ab())) return rc;
+      prof_mark(c, s);
+      CUDA_TRY(c, launch_persistent(T, c->d_coff, c->C, x, A, b, q, blk, c->persist_grid, dbg, s));
+      *nk = 1;
+      prof_mark(c, s);
+      break;
+    case EEC_VARIANT_ATOMIC:
+      if ((rc = init_Ab())) return rc;
+      prof_mark(c, s);
+      CUDA_TRY(c, launch_eval(T, MODE_ATOMIC, 0, c->n_dev, x, A, b, q, blk, dbg, s));
+      *nk = c->n_dev > 0;
+      prof_mark(c, s);
+      break;
+    case EEC_VARIANT_SEGREDUCE:
+      prof_mark(c, s);
+      CUDA_TRY(c, launch_eval(c->d, MODE_BUFFER, 0, c->n_dev, x, A, b, q, blk, dbg, s));
+      prof_mark(c, s);
+      CUDA_TRY(c, launch_gather(c->d, A, b, s));
+      *nk = (c->n_dev > 0) + (c->nnz + c->n > 0);
+      break;
+    case EEC_VARIANT_COLOR_BUFFERED:
+      if ((rc = init_Ab())) return rc;
+      prof_mark(c, s);
+      CUDA_TRY(c, launch_eval(c->d, MODE_BUFFER, 0, c->n_dev, x, A, b, q, blk, dbg, s));
+      prof_mark(c, s);
+      *nk = c->n_dev > 0;
+      for (int k = 0; k < c->C; ++k) {
+        if (c->color_off[k + 1] <= c->color_off[k]) continue;
+        CUDA_TRY(c, launch_stamp_buffer(c->d, c->color_off[k], c->color_off[k + 1], A, b, blk, s));
+        ++*nk;
+      }
+      break;
+    default:
+      return fail(c, EEC_EINVAL, "unknown variant");
+  }
+  prof_mark(c, s);
+  if (c->prof) ++c->prof_calls;
+  return EEC_OK;
+}
+
+int effective_variant(const eec_ctx* c) {
+  return c->opt.variant == EEC_VARIANT_AUTO ? c->tuned_variant : c->opt.variant;
+}
+
+int capture(eec_ctx* c, int v, const double* x, double* A, double* b, double* q,
+            cudaGraphExec_t* out, long long* nk) {
+  if (!c->cap_stream)
+    CUDA_TRY(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  // Buffers allocated lazily must exist before capture (no allocation inside a capture).
+  if (v == EEC_VARIANT_SEGREDUCE || v == EEC_VARIANT_COLOR_BUFFERED) {
+    int rc = ensure_buf(c);
+    if (rc) return rc;
+  }
+  CUDA_TRY(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+  const bool prof = c->prof;
+  c->prof = false;  // no profiling events inside a graph
+  int rc = run_variant(c, v, x, A, b, q, c->cap_stream, nk);
+  c->prof = prof;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return fail(c, EEC_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(c, EEC_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+  return EEC_OK;
+}
+
+// eval_stamp with schedule v; the per-colour schedules replay a cached CUDA graph unless
+// phase timing is on.
+int eval_with(eec_ctx* c, int v, const double* x, double* A, double* b, double* q,
+              cudaStream_t s) {
+  if (!c->prof && (v == EEC_VARIANT_COLOR_FUSED || v == EEC_VARIANT_COLOR_BUFFERED)) {
+    const void* key[4] = {x, A, b, q};
+    bool hit = c->auto_exec && c->auto_variant == v;
+    for (int i = 0; i < 4 && hit; ++i) hit = key[i] == c->auto_key[i];
+    if (!hit) {
+      if (c->auto_exec) cudaGraphExecDestroy(c->auto_exec);
+      c->auto_exec = nullptr;
+      c->auto_variant = -100;
+      int rc = capture(c, v, x, A, b, q, &c->auto_exec, &c->auto_kernels);
+      if (rc) return rc;
+      c->auto_variant = v;
+      for (int i = 0; i < 4; ++i) c->auto_key[i] = key[i];
+    }
+    CUDA_TRY(c, cudaGraphLaunch(c->auto_exec, s));
+    c->n_kernels += c->auto_kernels;
+    return EEC_OK;
+  }
+  long long nk = 0;
+  int rc = run_variant(c, v, x, A, b, q, s, &nk);
+  c->n_kernels += nk;
+  return rc;
+}
+
+int check_pattern(eec_ctx* c) {
+  if (!c) return EEC_EINVAL;
+  if (!c->pattern_ready) return fail(c, EEC_ESTATE, "call eec_build_scatter first");
+  return EEC_OK;
+}
+
+int check_built(eec_ctx* c) {
+  if (!c) return EEC_EINVAL;
+  if (!c->built) return fail(c, EEC_ESTATE, "call eec_build_scatter first");
+  return EEC_OK;
+}
+
+int store_netlist(eec_ctx* c, int32_t n_nodes, const uint8_t* node_fixed, const double* node_vfix,
+                  int32_t n_dev, const int32_t* dev_nodes, const int8_t* dev_type,
+                  const double* W, const double* L, const int32_t* model_id, int32_t n_res,
+                  const int32_t* res_nodes, const double* res_G, int32_t n_isrc,
+                  const int32_t* isrc_nodes, const double* isrc_val, double gshunt) {
+  if (n_nodes < 1 || n_dev < 0 || n_res < 0 || n_isrc < 0)
+    return fail(c, EEC_EINVAL, "negative size or no ground node");
+  if (!node_fixed || !node_vfix || (n_dev && (!dev_nodes || !dev_type || !W || !L || !model_id)) ||
+      (n_res && (!res_nodes || !res_G)) || (n_isrc && (!isrc_nodes || !isrc_val)))
+    return fail(c, EEC_EINVAL, "NULL array with nonzero size");
+  if (!(gshunt >= 0.0) || !std::isfinite(gshunt)) return fail(c, EEC_EINVAL, "gshunt must be >= 0");
+  for (long long i = 0; i < 4LL * n_dev; ++i)
+    if (dev_nodes[i] < 0 || dev_nodes[i] >= n_nodes) return fail(c, EEC_EINVAL, "device node index out of range");
+  for (long long i = 0; i < 2LL * n_res; ++i)
+    if (res_nodes[i] < 0 || res_nodes[i] >= n_nodes) return fail(c, EEC_EINVAL, "resistor node index out of range");
+  for (long long i = 0; i < 2LL * n_isrc; ++i)
+    if (isrc_nodes[i] < 0 || isrc_nodes[i] >= n_nodes) return fail(c, EEC_EINVAL, "source node index out of range");
+  for (int k = 0; k < n_dev; ++k) {
+    if (dev_type[k] != 1 && dev_type[k] != -1) return fail(c, EEC_EINVAL, "dev_type must be +1 or -1");
+    if (!(W[k] > 0) || !(L[k] > 0) || !std::isfinite(W[k]) || !std::isfinite(L[k]))
+      return fail(c, EEC_EINVAL, "W and L must be positive and finite");
+    if (model_id[k] < 0) return fail(c, EEC_EINVAL, "negative model_id");
+  }
+  for (int i = 0; i < n_nodes; ++i)
+    if (node_fixed[i] && !std::isfinite(node_vfix[i])) return fail(c, EEC_EINVAL, "non-finite fixed voltage");
+  free_topology(c);
+  c->n_nodes = n_nodes;
+  c->fixed.assign(node_fixed, node_fixed + n_nodes);
+  for (auto& f : c->fixed) f = f ? 1 : 0;
+  c->vfix.assign(node_vfix, node_vfix + n_nodes);
+  c->fixed[0] = 1;
+  c->vfix[0] = 0.0;
+  c->n_dev = n_dev;
+  c->dn.assign(dev_nodes, dev_nodes + 4LL * n_dev);
+  c->type.assign(dev_type, dev_type + n_dev);
+  c->W.assign(W, W + n_dev);
+  c->L.assign(L, L + n_dev);
+  c->mid.assign(model_id, model_id + n_dev);
+  c->rn.assign(res_nodes, res_nodes + 2LL * n_res);
+  c->rG.assign(res_G, res_G + n_res);
+  c->sn.assign(isrc_nodes, isrc_nodes + 2LL * n_isrc);
+  c->sI.assign(isrc_val, isrc_val + n_isrc);
+  c->gshunt = gshunt;
+  c->has_net = true;
+  c->pattern_ready = false;
+  c->colored = false;
+  c->C = 0;
+  c->color.clear();
+  c->params_dirty = false;
+  c->n_circ = 0;
+  return EEC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+eec_options eec_default_options(void) {
+  eec_options o;
+  o.variant = EEC_VARIANT_AUTO;
+  o.block = 0;
+  o.conflict_rule = EEC_CONFLICT_FREE_NODE;
+  o.debug_checks = 0;
+  return o;
+}
+
+int eec_create(eec_ctx** out, const eec_options* opt) {
+  if (!out) return EEC_EINVAL;
+  *out = nullptr;
+  eec_ctx* c = new (std::nothrow) eec_ctx;
+  if (!c) return EEC_ENOMEM;
+  c->opt = opt ? *opt : eec_default_options();
+  if (c->opt.variant < EEC_VARIANT_AUTO || c->opt.variant >= EEC_N_VARIANTS ||
+      c->opt.conflict_rule < 0 || c->opt.conflict_rule > 2 || c->opt.block < 0) {
+    delete c;
+    return EEC_EINVAL;
+  }
+  *out = c;  // no CUDA call: host-side steps work without a device
+  return EEC_OK;
+}
+
+void eec_destroy(eec_ctx* c) {
+  if (!c) return;
+  free_topology(c);
+  if (c->d_status) cudaFree(c->d_status);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  delete c;
+}
+
+const char* eec_last_error(const eec_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int eec_upload_netlist(eec_ctx* c, int32_t n_nodes, const uint8_t* node_fixed,
+                       const double* node_vfix, int32_t n_dev, const int32_t* dev_nodes,
+                       const int8_t* dev_type, const double* W, const double* L,
+                       const int32_t* model_id, int32_t n_res, const int32_t* res_nodes,
+                       const double* res_G, int32_t n_isrc, const int32_t* isrc_nodes,
+                       const double* isrc_val, double gshunt) {
+  if (!c) return EEC_EINVAL;
+  return store_netlist(c, n_nodes, node_fixed, node_vfix, n_dev, dev_nodes, dev_type, W, L,
+                       model_id, n_res, res_nodes, res_G, n_isrc, isrc_nodes, isrc_val, gshunt);
+}
+
+int eec_upload_batch(eec_ctx* c, int32_t n_circ, const eec_netlist* nets, double gshunt) {
+  if (!c) return EEC_EINVAL;
+  if (n_circ < 1 || !nets) return fail(c, EEC_EINVAL, "empty batch");
+  long long nodes = 1, devs = 0, res = 0, src = 0;
+  for (int k = 0; k < n_circ; ++k) {
+    const eec_netlist& m = nets[k];
+    if (m.n_nodes < 1 || m.n_dev < 0 || m.n_res < 0 || m.n_isrc < 0)
+      return fail(c, EEC_EINVAL, "bad circuit sizes");
+    nodes += m.n_nodes - 1;
+    devs += m.n_dev;
+    res += m.n_res;
+    src += m.n_isrc;
+  }
+  if (nodes > 0x7fffffffLL || devs > 0x7fffffffLL) return fail(c, EEC_EINVAL, "batch too large");
+  std::vector<uint8_t> fx(nodes, 0);
+  std::vector<double> vf(nodes, 0.0);
+  std::vector<int32_t> dnod(4 * devs), rnod(2 * res), snod(2 * src), mids(devs);
+  std::vector<int8_t> typ(devs);
+  std::vector<double> Wv(devs), Lv(devs), rg(res), sv(src);
+  std::vector<int> node_off(n_circ + 1), dev_off(n_circ + 1);
+  fx[0] = 1;
+  long long nn = 1, nd = 0, nr = 0, ns = 0;
+  for (int k = 0; k < n_circ; ++k) {
+    const eec_netlist& m = nets[k];
+    if (!m.node_fixed || !m.node_vfix || (m.n_dev && (!m.dev_nodes || !m.dev_type || !m.W || !m.L || !m.model_id)) ||
+        (m.n_res && (!m.res_nodes || !m.res_G)) || (m.n_isrc && (!m.isrc_nodes || !m.isrc_val)))
+      return fail(c, EEC_EINVAL, "NULL array in batch circuit");
+    node_off[k] = (int)nn;
+    dev_off[k] = (int)nd;
+    auto mapn = [&](int v) -> int32_t { return v <= 0 ? 0 : (int32_t)(nn + v - 1); };
+    for (int i = 1; i < m.n_nodes; ++i) {
+      fx[nn + i - 1] = m.node_fixed[i] ? 1 : 0;
+      vf[nn + i - 1] = m.node_vfix[i];
+    }
+    for (long long i = 0; i < 4LL * m.n_dev; ++i) {
+      if (m.dev_nodes[i] < 0 || m.dev_nodes[i] >= m.n_nodes) return fail(c, EEC_EINVAL, "batch device node out of range");
+      dnod[4 * nd + i] = mapn(m.dev_nodes[i]);
+    }
+    for (int i = 0; i < m.n_dev; ++i) {
+      typ[nd + i] = m.dev_type[i];
+      Wv[nd + i] = m.W[i];
+      Lv[nd + i] = m.L[i];
+      mids[nd + i] = m.model_id[i];
+    }
+    for (long long i = 0; i < 2LL * m.n_res; ++i) {
+      if (m.res_nodes[i] < 0 || m.res_nodes[i] >= m.n_nodes) return fail(c, EEC_EINVAL, "batch resistor node out of range");
+      rnod[2 * nr + i] = mapn(m.res_nodes[i]);
+    }
+    for (int i = 0; i < m.n_res; ++i) rg[nr + i] = m.res_G[i];
+    for (long long i = 0; i < 2LL * m.n_isrc; ++i) {
+      if (m.isrc_nodes[i] < 0 || m.isrc_nodes[i] >= m.n_nodes) return fail(c, EEC_EINVAL, "batch source node out of range");
+      snod[2 * ns + i] = mapn(m.isrc_nodes[i]);
+    }
+    for (int i = 0; i < m.n_isrc; ++i) sv[ns + i] = m.isrc_val[i];
+    nn += m.n_nodes - 1;
+    nd += m.n_dev;
+    nr += m.n_res;
+    ns += m.n_isrc;
+  }
+  node_off[n_circ] = (int)nn;
+  dev_off[n_circ] = (int)nd;
+  int rc = store_netlist(c, (int32_t)nodes, fx.data(), vf.data(), (int32_t)devs, dnod.data(),
+                         typ.data(), Wv.data(), Lv.data(), mids.data(), (int32_t)res,
+                         rnod.data(), rg.data(), (int32_t)src, snod.data(), sv.data(), gshunt);
+  if (rc) return rc;
+  c->n_circ = n_circ;
+  c->circ_node_off = node_off;
+  c->circ_dev_off = dev_off;
+  return EEC_OK;
+}
+
+int eec_set_model_cards(eec_ctx* c, int32_t n_cards, const double* cards) {
+  if (!c) return EEC_EINVAL;
+  if (n_cards < 1 || !cards) return fail(c, EEC_EINVAL, "need at least one card");
+  for (int i = 0; i < n_cards; ++i)
+    if (!valid_card(cards + (size_t)i * EEC_CARD_LEN)) return fail(c, EEC_EINVAL, "invalid model card " + std::to_string(i));
+  c->n_cards = n_cards;
+  c->cards.assign(cards, cards + (size_t)n_cards * EEC_CARD_LEN);
+  c->cardk.resize(n_cards);
+  for (int i = 0; i < n_cards; ++i) c->cardk[i] = derive_card(cards + (size_t)i * EEC_CARD_LEN);
+  c->has_cards = true;
+  if (c->built) {
+    int rc = sync_params_to_host(c);
+    if (rc) return rc;
+    free_topology(c);
+  }
+  return EEC_OK;
+}
+
+int eec_color(eec_ctx* c, const int32_t* order, int32_t algo, int32_t* colors_out,
+              int32_t* n_colors) {
+  if (!c) return EEC_EINVAL;
+  if (!c->has_net) return fail(c, EEC_ESTATE, "upload a netlist first");
+  if (!n_colors) return fail(c, EEC_EINVAL, "n_colors is NULL");
+  if (algo < EEC_COLOR_GREEDY_SEQ || algo > EEC_COLOR_JP_RANDOM) return fail(c, EEC_EINVAL, "unknown colouring algorithm");
+  const int N = c->n_dev;
+  std::vector<int> ord(N);
+  if (order) {
+    std::vector<char> seen(N, 0);
+    for (int i = 0; i < N; ++i) {
+      const int v = order[i];
+      if (v < 0 || v >= N || seen[v]) return fail(c, EEC_EINVAL, "order is not a permutation");
+      seen[v] = 1;
+      ord[i] = v;
+    }
+  } else {
+    std::iota(ord.begin(), ord.end(), 0);
+  }
+  int rc = sync_params_to_host(c);
+  if (rc) return rc;
+  std::vector<int> dev_ptr, dev_node, node_ptr, node_dev;
+  conflict_incidence(c, c->opt.conflict_rule, dev_ptr, dev_node, node_ptr, node_dev);
+  std::vector<int> col;
+  int C = 0;
+  if (algo == EEC_COLOR_GREEDY_SEQ) {
+    greedy_host(N, ord, dev_ptr, dev_node, node_ptr, node_dev, col, &C);
+  } else {
+    std::vector<uint32_t> prio(N);
+    if (algo == EEC_COLOR_JP_INDEX) {
+      for (int i = 0; i < N; ++i) prio[ord[i]] = (uint32_t)(N - i);
+    } else {
+      // Hashed priorities (SplitMix64 finaliser of the device index), ties broken by index.
+      std::vector<std::pair<uint64_t, int>> h(N);
+      for (int v = 0; v < N; ++v) {
+        uint64_t z = (uint64_t)v + 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        h[v] = {z ^ (z >> 31), v};
+      }
+      std::sort(h.begin(), h.end());
+      for (int i = 0; i < N; ++i) prio[h[i].second] = (uint32_t)(i + 1);
+    }
+    std::string err;
+    rc = jp_color(N, node_ptr, node_dev, dev_ptr, dev_node, prio, col, &C, err);
+    if (rc) return fail(c, rc, err);
+  }
+  free_topology(c);
+  c->pattern_ready = false;
+  c->color = col;
+  c->C = C;
+  c->colored = true;
+  if (colors_out) std::copy(col.begin(), col.end(), colors_out);
+  *n_colors = C;
+  return EEC_OK;
+}
+
+int eec_build_scatter(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_out) {
+  if (!c) return EEC_EINVAL;
+  if (!c->has_net || !c->has_cards) return fail(c, EEC_ESTATE, "upload a netlist and model cards first");
+  for (int k = 0; k < c->n_dev; ++k)
+    if (c->mid[k] >= c->n_cards) return fail(c, EEC_EINVAL, "model_id beyond the card table");
+  int rc = sync_params_to_host(c);
+  if (rc) return rc;
+  free_topology(c);
+  const int N = c->n_dev;
+  // unknowns and the fixed-voltage table
+  c->unk.assign(c->n_nodes, -1);
+  std::vector<int> fidx(c->n_nodes, -1);
+  std::vector<double> vtab;
+  int n = 0;
+  for (int i = 0; i < c->n_nodes; ++i) {
+    if (c->fixed[i]) {
+      fidx[i] = (int)vtab.size();
+      vtab.push_back(c->vfix[i]);
+    } else {
+      c->unk[i] = n++;
+    }
+  }
+  c->n = n;
+  // pattern: sorted unique (row, col) keys
+  std::vector<uint64_t> keys;
+  keys.reserve((size_t)n + 4 * c->rG.size() + 9 * (size_t)N);
+  auto key = [](int r, int cc) { return ((uint64_t)(uint32_t)r << 32) | (uint32_t)cc; };
+  for (int i = 0; i < n; ++i) keys.push_back(key(i, i));
+  for (size_t r = 0; r < c->rG.size(); ++r) {
+    const int a = c->unk[c->rn[2 * r]], bb = c->unk[c->rn[2 * r + 1]];
+    if (a >= 0 && bb >= 0) { keys.push_back(key(a, bb)); keys.push_back(key(bb, a)); }
+  }
+  for (int k = 0; k < N; ++k)
+    for (int t = 0; t < 4; ++t) {
+      const int a = c->unk[c->dn[4 * k + t]];
+      if (a < 0) continue;
+      for (int u = 0; u < 4; ++u) {
+        const int bb = c->unk[c->dn[4 * k + u]];
+        if (bb >= 0) keys.push_back(key(a, bb));
+      }
+    }
+  std::sort(keys.begin(), keys.end());
+  keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+  c->nnz = (long long)keys.size();
+  if (c->nnz > 0x7fffffffLL) return fail(c, EEC_EINVAL, "nnz beyond 2^31 is not supported");
+  c->row_ptr.assign(n + 1, 0);
+  c->col.resize(keys.size());
+  for (size_t i = 0; i < keys.size(); ++i) {
+    c->row_ptr[(keys[i] >> 32) + 1]++;
+    c->col[i] = (int)(keys[i] & 0xffffffffu);
+  }
+  for (int i = 0; i < n; ++i) c->row_ptr[i + 1] += c->row_ptr[i];
+  auto find = [&](int r, int cc) -> int {
+    const int* b0 = c->col.data() + c->row_ptr[r];
+    const int* b1 = c->col.data() + c->row_ptr[r + 1];
+    const int* p = std::lower_bound(b0, b1, cc);
+    return (int)(p - c->col.data());
+  };
+  // layout: colour-major, then card/polarity, then original index
+  std::vector<long long> sk(N);
+  for (int k = 0; k < N; ++k) {
+    const long long colr = c->colored ? c->color[k] : 0;
+    const long long meta = ((long long)c->mid[k] << 1) | (c->type[k] < 0 ? 1 : 0);
+    sk[k] = (colr << 32) | meta;
+  }
+  c->perm.resize(N);
+  std::iota(c->perm.begin(), c->perm.end(), 0);
+  std::stable_sort(c->perm.begin(), c->perm.end(), [&](int a, int bb) { return sk[a] < sk[bb]; });
+  std::vector<int> pos_of(N);
+  for (int p = 0; p < N; ++p) pos_of[c->perm[p]] = p;
+  const int C = c->colored ? c->C : 1;
+  c->color_off.assign(C + 1, 0);
+  for (int k = 0; k < N; ++k) c->color_off[(c->colored ? c->color[k] : 0) + 1]++;
+  for (int i = 0; i < C; ++i) c->color_off[i + 1] += c->color_off[i];
+  // per-position arrays
+  std::vector<int4> tidx(N);
+  std::vector<int> meta(N), slot((size_t)kNSlot * N, -1);
+  std::vector<double> Wp(N), Lp(N);
+  const int rows_t[3] = {0, 2, 3};
+  for (int p = 0; p < N; ++p) {
+    const int k = c->perm[p];
+    int ti[4];
+    for (int t = 0; t < 4; ++t) {
+      const int node = c->dn[4 * k + t];
+      ti[t] = c->unk[node] >= 0 ? c->unk[node] : ~fidx[node];
+    }
+    tidx[p] = make_int4(ti[0], ti[1], ti[2], ti[3]);
+    meta[p] = (c->mid[k] << 1) | (c->type[k] < 0 ? 1 : 0);
+    Wp[p] = c->W[k];
+    Lp[p] = c->L[k];
+    for (int r = 0; r < 3; ++r) {
+      if (ti[rows_t[r]] < 0) continue;
+      for (int u = 0; u < 4; ++u)
+        if (ti[u] >= 0) slot[(size_t)(4 * r + u) * N + p] = find(ti[rows_t[r]], ti[u]);
+    }
+  }
+  // linear part, summed in the natural element order: gshunt, resistors, current sources
+  std::vector<double> Alin(c->nnz, 0.0), blin(n, 0.0);
+  for (int i = 0; i < n; ++i) Alin[find(i, i)] += c->gshunt;
+  for (size_t r = 0; r < c->rG.size(); ++r) {
+    const int ni = c->rn[2 * r], nj = c->rn[2 * r + 1];
+    const int a = c->unk[ni], bb = c->unk[nj];
+    const double G = c->rG[r];
+    if (a >= 0) {
+      Alin[find(a, a)] += G;
+      if (bb >= 0) Alin[find(a, bb)] -= G;
+      else blin[a] += G * c->vfix[nj];
+    }
+    if (bb >= 0) {
+      Alin[find(bb, bb)] += G;
+      if (a >= 0) Alin[find(bb, a)] -= G;
+      else blin[bb] += G * c->vfix[ni];
+    }
+  }
+  for (size_t s = 0; s < c->sI.size(); ++s) {
+    const int a = c->unk[c->sn[2 * s]], bb = c->unk[c->sn[2 * s + 1]];
+    if (a >= 0) blin[a] -= c->sI[s];
+    if (bb >= 0) blin[bb] += c->sI[s];
+  }
+  // segmented-reduction map: contributions per entry in original device order
+  const long long E = c->nnz + n;
+  std::vector<long long> gptr(E + 1, 0);
+  for (int k = 0; k < N; ++k) {
+    const int p = pos_of[k];
+    const int4 t4 = tidx[p];
+    const int ti[4] = {t4.x, t4.y, t4.z, t4.w};
+    for (int r = 0; r < 3; ++r) {
+      const int row = ti[rows_t[r]];
+      if (row < 0) continue;
+      for (int u = 0; u < 4; ++u) {
+        const int s = slot[(size_t)(4 * r + u) * N + p];
+        if (s >= 0) gptr[s + 1]++;
+      }
+      gptr[c->nnz + row + 1]++;
+    }
+  }
+  for (long long e = 0; e < E; ++e) gptr[e + 1] += gptr[e];
+  std::vector<int> gsrc(gptr[E]);
+  {
+    std::vector<long long> fill(gptr.begin(), gptr.end() - 1);
+    for (int k = 0; k < N; ++k) {
+      const int p = pos_of[k];
+      const int4 t4 = tidx[p];
+      const int ti[4] = {t4.x, t4.y, t4.z, t4.w};
+      for (int r = 0; r < 3; ++r) {
+        const int row = ti[rows_t[r]];
+        if (row < 0) continue;
+        for (int u = 0; u < 4; ++u) {
+          const int s = slot[(size_t)(4 * r + u) * N + p];
+          if (s >= 0) gsrc[fill[s]++] = (4 * r + u) * N + p;
+        }
+        gsrc[fill[c->nnz + row]++] = (kNSlot + r) * N + p;
+      }
+    }
+  }
+  // backward incidence: unknown -> (terminal, position) in original device order
+  std::vector<int> iptr(n + 1, 0);
+  for (int k = 0; k < N; ++k)
+    for (int t = 0; t < 4; ++t) {
+      const int a = c->unk[c->dn[4 * k + t]];
+      if (a >= 0) iptr[a + 1]++;
+    }
+  for (int i = 0; i < n; ++i) iptr[i + 1] += iptr[i];
+  std::vector<int> isrc(iptr[n]);
+  {
+    std::vector<int> fill(iptr.begin(), iptr.end() - 1);
+    for (int k = 0; k < N; ++k)
+      for (int t = 0; t < 4; ++t) {
+        const int a = c->unk[c->dn[4 * k + t]];
+        if (a >= 0) isrc[fill[a]++] = t * N + pos_of[k];
+      }
+  }
+  if ((long long)N * kNContrib > 0x7fffffffLL) return fail(c, EEC_EINVAL, "too many devices");
+  // batch offsets
+  if (c->n_circ > 0) {
+    c->circ_row_off.assign(c->n_circ + 1, 0);
+    c->circ_nnz_off.assign(c->n_circ + 1, 0);
+    int u = 0;
+    for (int k = 0; k < c->n_circ; ++k) {
+      c->circ_row_off[k] = u;
+      for (int i = c->circ_node_off[k]; i < c->circ_node_off[k + 1]; ++i)
+        if (c->unk[i] >= 0) ++u;
+    }
+    c->circ_row_off[c->n_circ] = u;
+    for (int k = 0; k <= c->n_circ; ++k) c->circ_nnz_off[k] = c->row_ptr[c->circ_row_off[k]];
+  }
+  c->pattern_ready = true;
+  if (n_unknowns) *n_unknowns = n;
+  if (nnz_out) *nnz_out = c->nnz;
+  // device part
+  if (!c->d_status) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaError_t e = cudaGetLastError();
+      return fail(c, EEC_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+    }
+    CUDA_TRY(c, cudaMalloc(&c->d_status, 4 * sizeof(int)));
+    CUDA_TRY(c, cudaMemset(c->d_status, 0, 4 * sizeof(int)));
+  }
+  DevTopo& d = c->d;
+  d.N = N;
+  d.n = n;
+  d.nnz = c->nnz;
+  std::vector<int> orig(c->perm.begin(), c->perm.end());
+  if ((rc = dupload(c, &d.tidx, tidx)) || (rc = dupload(c, &d.meta, meta)) ||
+      (rc = dupload(c, &d.orig, orig)) || (rc = dupload(c, &d.slot, slot)) ||
+      (rc = dupload(c, &d.W, Wp)) || (rc = dupload(c, &d.L, Lp)) ||
+      (rc = dalloc(c, &d.prm, (size_t)kNPrm * N)) || (rc = dupload(c, &d.vfix, vtab)) ||
+      (rc = dupload(c, &d.cards, c->cardk)) || (rc = dupload(c, &d.Alin, Alin)) ||
+      (rc = dupload(c, &d.blin, blin)) || (rc = dupload(c, &d.gat_ptr, gptr)) ||
+      (rc = dupload(c, &d.gat_src, gsrc)) || (rc = dupload(c, &d.inc_ptr, iptr)) ||
+      (rc = dupload(c, &d.inc_src, isrc)) || (rc = dupload(c, &c->d_coff, c->color_off))) {
+    free_topology(c);
+    return rc;
+  }
+  d.status = c->d_status;
+  d.bar = reinterpret_cast<unsigned*>(c->d_status + 1);
+  CUDA_TRY(c, launch_params(d, 0));
+  CUDA_TRY(c, cudaDeviceSynchronize());
+  const int bps = persistent_max_blocks_per_sm(0, false);
+  const int bpsq = persistent_max_blocks_per_sm(0, true);
+  c->persist_grid = std::max(1, std::min(std::min(bps, bpsq), 4)) * c->sms;
+  c->built = true;
+  return EEC_OK;
+}
+
+int eec_get_pattern(const eec_ctx* cc, int32_t* row_ptr, int32_t* col_idx, int32_t* unk_of_node) {
+  eec_ctx* c = const_cast<eec_ctx*>(cc);
+  int rc = check_pattern(c);
+  if (rc) return rc;
+  if (row_ptr) std::copy(c->row_ptr.begin(), c->row_ptr.end(), row_ptr);
+  if (col_idx) std::copy(c->col.begin(), c->col.end(), col_idx);
+  if (unk_of_node) std::copy(c->unk.begin(), c->unk.end(), unk_of_node);
+  return EEC_OK;
+}
+
+int eec_get_color_offsets(const eec_ctx* cc, int32_t* off) {
+  eec_ctx* c = const_cast<eec_ctx*>(cc);
+  int rc = check_pattern(c);
+  if (rc) return rc;
+  if (!c->colored) return fail(c, EEC_ESTATE, "not coloured");
+  if (!off) return fail(c, EEC_EINVAL, "off is NULL");
+  std::copy(c->color_off.begin(), c->color_off.end(), off);
+  return EEC_OK;
+}
+
+int eec_get_sizes(const eec_ctx* cc, int32_t* n_dev, int32_t* n_unknowns, int64_t* nnz,
+                  int32_t* n_colors) {
+  eec_ctx* c = const_cast<eec_ctx*>(cc);
+  int rc = check_pattern(c);
+  if (rc) return rc;
+  if (n_dev) *n_dev = c->n_dev;
+  if (n_unknowns) *n_unknowns = c->n;
+  if (nnz) *nnz = c->nnz;
+  if (n_colors) *n_colors = c->colored ? c->C : 0;
+  return EEC_OK;
+}
+
+int eec_get_batch_offsets(const eec_ctx* cc, int32_t* row_off, int64_t* nnz_off, int32_t* dev_off) {
+  eec_ctx* c = const_cast<eec_ctx*>(cc);
+  int rc = check_pattern(c);
+  if (rc) return rc;
+  if (c->n_circ == 0) return fail(c, EEC_ESTATE, "context was not uploaded as a batch");
+  if (row_off) std::copy(c->circ_row_off.begin(), c->circ_row_off.end(), row_off);
+  if (nnz_off) std::copy(c->circ_nnz_off.begin(), c->circ_nnz_off.end(), nnz_off);
+  if (dev_off) std::copy(c->circ_dev_off.begin(), c->circ_dev_off.end(), dev_off);
+  return EEC_OK;
+}
+
+int eec_update_params(eec_ctx* c, const double* W_dev, const double* L_dev, void* stream) {
+  int rc = check_built(c);
+  if (rc) return rc;
+  if (!W_dev || !L_dev) return fail(c, EEC_EINVAL, "NULL W or L");
+  CUDA_TRY(c, launch_update_params(c->d, W_dev, L_dev, static_cast<cudaStream_t>(stream)));
+  c->params_dirty = true;
+  return EEC_OK;
+}
+
+int eec_set_variant(eec_ctx* c, int32_t v) {
+  if (!c) return EEC_EINVAL;
+  if (v < EEC_VARIANT_AUTO || v >= EEC_N_VARIANTS) return fail(c, EEC_EINVAL, "unknown variant");
+  c->opt.variant = v;
+  return EEC_OK;
+}
+
+int eec_get_variant(const eec_ctx* c, int32_t* v) {
+  if (!c || !v) return EEC_EINVAL;
+  *v = effective_variant(c);
+  return EEC_OK;
+}
+
+int eec_eval_stamp(eec_ctx* c, const double* x, double* A, double* b, double* q, void* stream) {
+  int rc = check_built(c);
+  if (rc) return rc;
+  if (!x || !A || !b) return fail(c, EEC_EINVAL, "NULL x, A or b");
+  return eval_with(c, effective_variant(c), x, A, b, q, static_cast<cudaStream_t>(stream));
+}
+
+int eec_eval_stamp_bwd(eec_ctx* c, const double* x, const double* gA, const double* gb,
+                       double* gx, double* gW, double* gL, void* stream) {
+  int rc = check_built(c);
+  if (rc) return rc;
+  if (!x || !gA || !gb || !gx || !gW || !gL) return fail(c, EEC_EINVAL, "NULL argument");
+  if ((rc = ensure_gv(c))) return rc;
+  CUDA_TRY(c, launch_bwd(c->d, x, gA, gb, gx, gW, gL, c->opt.block, static_cast<cudaStream_t>(stream)));
+  return EEC_OK;
+}
+
+int eec_graph_capture(eec_ctx* c, const double* x, double* A, double* b, double* q, void* stream) {
+  int rc = check_built(c);
+  if (rc) return rc;
+  if (!x || !A || !b) return fail(c, EEC_EINVAL, "NULL x, A or b");
+  if (c->user_exec) cudaGraphExecDestroy(c->user_exec);
+  c->user_exec = nullptr;
+  // Order the capture after the caller's pending work on `stream` (nothing runs during capture).
+  if (stream) CUDA_TRY(c, cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  return capture(c, effective_variant(c), x, A, b, q, &c->user_exec, &c->user_kernels);
+}
+
+int eec_graph_launch(eec_ctx* c, void* stream) {
+  int rc = check_built(c);
+  if (rc) return rc;
+  if (!c->user_exec) return fail(c, EEC_ESTATE, "no graph captured");
+  CUDA_TRY(c, cudaGraphLaunch(c->user_exec, static_cast<cudaStream_t>(stream)));
+  c->n_kernels += c->user_kernels;
+  return EEC_OK;
+}
+
+int eec_profile_enable(eec_ctx* c, int32_t enable) {
+  if (!c) return EEC_EINVAL;
+  if (c->prof && !enable && c->ev_used) cudaDeviceSynchronize();
+  c->prof = enable != 0;
+  c->ev_used = 0;
+  c->prof_calls = 0;
+  return EEC_OK;
+}
+
+int eec_profile_read(eec_ctx* c, double* ms_init, double* ms_eval, double* ms_stamp,
+                     int64_t* n_calls, int64_t* n_kernels) {
+  if (!c) return EEC_EINVAL;
+  double t[3] = {0.0, 0.0, 0.0};
+  if (c->ev_used) {
+    CUDA_TRY(c, cudaEventSynchronize(c->ev_pool[c->ev_used - 1]));
+    // every call recorded exactly four events: init | evaluate | stamp
+    for (size_t i = 0; i + 3 < c->ev_used; i += 4) {
+      for (int ph = 0; ph < 3; ++ph) {
+        float ms = 0.f;
+        CUDA_TRY(c, cudaEventElapsedTime(&ms, c->ev_pool[i + ph], c->ev_pool[i + ph + 1]));
+        t[ph] += ms;
+      }
+    }
+  }
+  if (ms_init) *ms_init = t[0];
+  if (ms_eval) *ms_eval = t[1];
+  if (ms_stamp) *ms_stamp = t[2];
+  if (n_calls) *n_calls = c->prof_calls;
+  if (n_kernels) *n_kernels = c->n_kernels;
+  c->ev_used = 0;
+  c->prof_calls = 0;
+  c->n_kernels = 0;
+  return EEC_OK;
+}
+
+int eec_autotune(eec_ctx* c, const double* x, double* A, double* b, double* q, int32_t reps,
+                 void* stream, float* ms_out) {
+  int rc = check_built(c);
+  if (rc) return rc;
+  if (!x || !A || !b || reps < 1) return fail(c, EEC_EINVAL, "bad autotune arguments");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  CUDA_TRY(c, cudaEventCreate(&e0));
+  CUDA_TRY(c, cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_v = EEC_VARIANT_SEGREDUCE;
+  for (int v = 0; v < EEC_N_VARIANTS; ++v) {
+    float ms = -1.0f;
+    if (!variant_needs_colors(v) || c->colored) {
+      rc = eval_with(c, v, x, A, b, q, s);
+      if (rc == EEC_OK) {
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && rc == EEC_OK; ++r) rc = eval_with(c, v, x, A, b, q, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) == cudaSuccess && rc == EEC_OK) {
+          cudaEventElapsedTime(&ms, e0, e1);
+          ms /= reps;
+        } else {
+          ms = -1.0f;
+        }
+      }
+      if (rc != EEC_OK) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return rc;
+      }
+    }
+    if (ms_out) ms_out[v] = ms;
+    if (ms >= 0.0f && ms < best) {
+      best = ms;
+      best_v = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->tuned_variant = best_v;
+  return EEC_OK;
+}
+
+int eec_status(eec_ctx* c, void* stream) {
+  if (!c) return EEC_EINVAL;
+  if (!c->d_status) return fail(c, EEC_ESTATE, "no device state yet");
+  CUDA_TRY(c, cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  int st = 0;
+  CUDA_TRY(c, cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  CUDA_TRY(c, cudaMemset(c->d_status, 0, sizeof(int)));
+  if (st & kStatusTimeout) return fail(c, EEC_ETIMEOUT, "a grid barrier wait ran past its limit");
+  if (st & kStatusNumeric) return fail(c, EEC_ENUMERIC, "non-finite value in an evaluated device");
+  return EEC_OK;
+}
+
+int eec_fp64_peak(int32_t iters, int32_t blocks_per_sm, double* flops) {
+  if (iters < 1 || blocks_per_sm < 1 || !flops) return EEC_EINVAL;
+  return fp64_peak(iters, blocks_per_sm, flops) == cudaSuccess ? EEC_OK : EEC_ECUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,94 @@
+// Internal declarations shared by the library's translation units (host and device).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/eec.h"
+
+namespace eec {
+
+// Per-card constants of the EES-L1 level, derived on the host from the EEC_CARD_LEN card.
+struct CardK {
+  double VTH0, K1, PHI, sqrtPHI;
+  double nVt, inv_nVt, Vt, inv_Vt, twoVt;
+  double UA, UB, ETA0;
+  double DELTA, twoDELTA, fourDELTA;
+  double fourD1sq, twoD1sq;
+  double XPART, GMIN;
+  // factors of the per-device parameters (eval_params)
+  double U0Cox, twoVSAT_U0, LAMBDA_LREF, JS_HDIF, Cox, CGSO, CGDO;
+};
+
+// Per-device derived parameters, stored structure-of-arrays [kNPrm][N] by layout position.
+enum Prm : int { P_BETA0 = 0, P_CE, P_INV_CE, P_LAML, P_ISAT, P_COXT, P_COVS, P_COVD, kNPrm };
+
+// Contribution slots of one device: rows (d, s, b) x columns (d, g, s, b) -> j = 4 r + u,
+// then the three right-hand-side rows j = 12 + r.
+constexpr int kNSlot = 12;
+constexpr int kNContrib = 15;
+
+// Device-side topology and parameters, indexed by layout position k (colour-major when coloured).
+struct DevTopo {
+  int N;            // devices
+  int n;            // unknowns
+  long long nnz;    // CSR nonzeros
+  int4* tidx;       // [N] terminal -> unknown (>= 0) or ~fixed-table index (< 0)
+  int* meta;        // [N] (card << 1) | (type < 0)
+  int* orig;        // [N] original device index of each position
+  int* slot;        // [kNSlot][N] CSR value index or -1
+  double* W;        // [N]
+  double* L;        // [N]
+  double* prm;      // [kNPrm][N]
+  double* vfix;     // [n_fixed] voltages of source-held nodes
+  CardK* cards;     // [n_cards]
+  double* Alin;     // [nnz]
+  double* blin;     // [n]
+  // segmented reduction: entry e (A entries 0..nnz-1, then b rows) sums buf[src] over
+  // gat_src[gat_ptr[e] .. gat_ptr[e+1]) in original-device order
+  long long* gat_ptr;  // [nnz + n + 1]
+  int* gat_src;        // [total contributions], flat index j * N + k into buf
+  double* buf;         // [kNContrib][N] (allocated on first use)
+  // backward: unknown u gathers gv[src] over inc_src[inc_ptr[u] .. inc_ptr[u+1])
+  int* inc_ptr;     // [n + 1]
+  int* inc_src;     // flat index t * N + k into gv
+  double* gv;       // [4][N] (allocated on first use)
+  int* status;      // device status word: bit 0 timeout, bit 1 non-finite
+  unsigned* bar;    // grid barrier: [0] arrival count, [1] generation
+};
+
+constexpr int kStatusTimeout = 1;
+constexpr int kStatusNumeric = 2;
+
+// ---- kernels (eec_kernels.cu) ----
+enum StampMode : int { MODE_RMW = 0, MODE_ATOMIC = 1, MODE_BUFFER = 2 };
+
+cudaError_t launch_params(const DevTopo& T, cudaStream_t s);
+// W_dev, L_dev in original device order -> per-position W, L and derived parameters.
+cudaError_t launch_update_params(const DevTopo& T, const double* W_dev, const double* L_dev,
+                                 cudaStream_t s);
+cudaError_t launch_eval(const DevTopo& T, int mode, int begin, int end, const double* x,
+                        double* A, double* b, double* q, int block, int dbg, cudaStream_t s);
+cudaError_t launch_persistent(const DevTopo& T, const int* color_off_dev, int n_colors,
+                              const double* x, double* A, double* b, double* q, int block,
+                              int grid, int dbg, cudaStream_t s);
+int persistent_max_blocks_per_sm(int block, bool want_q);
+cudaError_t launch_gather(const DevTopo& T, double* A, double* b, cudaStream_t s);
+cudaError_t launch_stamp_buffer(const DevTopo& T, int begin, int end, double* A, double* b,
+                                int block, cudaStream_t s);
+cudaError_t launch_bwd(const DevTopo& T, const double* x, const double* gA, const double* gb,
+                       double* gx, double* gW, double* gL, int block, cudaStream_t s);
+cudaError_t fp64_peak(int iters, int blocks_per_sm, double* flops);
+
+// ---- GPU colouring (eec_color.cu) ----
+// Jones-Plassmann colouring of the conflict graph given as node -> device incidence (CSR over
+// conflict nodes). prio[v] = priority (higher colours first). Returns colours in col (host).
+int jp_color(int n_dev, const std::vector<int>& node_ptr, const std::vector<int>& node_dev,
+             const std::vector<int>& dev_ptr, const std::vector<int>& dev_node,
+             const std::vector<uint32_t>& prio, std::vector<int>& col, int* n_colors,
+             std::string& err);
+
+}  // namespace eec

@@ -1,0 +1,366 @@
+// Evaluate-and-stamp kernels (sm_103a).
+//
+// Sec. II (i)/(ii): per Newton iteration every device is evaluated at the present bias and its
+// contributions are accumulated into A and b. Sec. I / Sec. II: devices of one colour share no
+// non-ground node, so their stamps touch disjoint rows and may be plain store-adds; colours run
+// one after another. Schedules (Table I analogues):
+//   MODE_RMW    one fused evaluate + store-add per device; one launch per colour ("ColorFused")
+//               or one persistent launch with a grid barrier between colours ("Color", single
+//               parallel region);
+//   MODE_ATOMIC uncoloured, FP64 atomicAdd (the lock-based stamping the paper avoids, in its
+//               GPU form);
+//   MODE_BUFFER evaluate into a per-device buffer ("loadomp"/"Color" buffer), then either a
+//               per-entry gather (segmented reduction, deterministic, no colours) or one store-add
+//               launch per colour.
+// The evaluation is FP64-pipe bound on GB300 (FP64 issues at about 1/64 of the FP32 rate), so
+// the kernels aim at a saturated FP64 pipe: one device per thread, few warps per SM suffice;
+// parameters are precomputed per device so that no division on W or L is repeated per call.
+#include <cuda_runtime.h>
+
+#include "eec_model.cuh"
+
+namespace eec {
+
+namespace {
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+constexpr unsigned long long kBarrierLimitNs = 1000000000ull;  // 1 s
+
+// Grid-wide barrier for a co-resident (cooperative) grid. Every wait is bounded: after
+// kBarrierLimitNs the waiting block records kStatusTimeout and the whole grid returns false.
+__device__ __forceinline__ bool grid_sync(unsigned* bar, int* status) {
+  __shared__ int fail;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    fail = 0;
+    const unsigned nblocks = gridDim.x * gridDim.y * gridDim.z;
+    const unsigned gen = ld_acquire_u32(bar + 1);
+    __threadfence();
+    const unsigned prev = atomicAdd(bar, 1u);
+    if (prev == nblocks - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (ld_acquire_u32(bar + 1) == gen) {
+        if (*((volatile int*)status) & kStatusTimeout) { fail = 1; break; }
+        if (global_ns() - t0 > kBarrierLimitNs) {
+          atomicOr(status, kStatusTimeout);
+          fail = 1;
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return fail == 0;
+}
+
+__device__ __forceinline__ PrmS<double> load_prm(const DevTopo& T, int k) {
+  const double* p = T.prm;
+  const long long N = T.N;
+  PrmS<double> P;
+  P.beta0 = __ldg(p + P_BETA0 * N + k);
+  P.cE = __ldg(p + P_CE * N + k);
+  P.inv_cE = __ldg(p + P_INV_CE * N + k);
+  P.lamL = __ldg(p + P_LAML * N + k);
+  P.Isat = __ldg(p + P_ISAT * N + k);
+  P.Coxt = __ldg(p + P_COXT * N + k);
+  P.CovS = __ldg(p + P_COVS * N + k);
+  P.CovD = __ldg(p + P_COVD * N + k);
+  return P;
+}
+
+// Evaluate device at layout position k and stamp (MODE_RMW / MODE_ATOMIC) or buffer it.
+template <int MODE, bool WANT_Q>
+__device__ __forceinline__ void eval_one(const DevTopo& T, int k, const double* __restrict__ x,
+                                         double* A, double* b, double* __restrict__ q,
+                                         int dbg) {
+  const int4 ti = __ldg(T.tidx + k);
+  const int idx[4] = {ti.x, ti.y, ti.z, ti.w};
+  double V[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t)
+    V[t] = idx[t] >= 0 ? __ldg(x + idx[t]) : __ldg(T.vfix + ~idx[t]);
+  const int meta = __ldg(T.meta + k);
+  const CardK& c = T.cards[meta >> 1];
+  const double pp = (meta & 1) ? -1.0 : 1.0;
+  const PrmS<double> P = load_prm(T, k);
+  EvalOut<double> o;
+  ees_l1<double, WANT_Q>(c, pp, P, V, o);
+
+  const int term[3] = {0, 2, 3};
+  double bc[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    double s = -o.I[term[r]];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (idx[u] >= 0) s = fma(o.G[r][u], V[u], s);
+    bc[r] = s;
+  }
+  const long long N = T.N;
+  if (MODE == MODE_BUFFER) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) T.buf[(4 * r + u) * N + k] = o.G[r][u];
+      T.buf[(kNSlot + r) * N + k] = bc[r];
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const int row = idx[term[r]];
+      if (row < 0) continue;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int s = __ldg(T.slot + (4 * r + u) * N + k);
+        if (s < 0) continue;
+        if (MODE == MODE_ATOMIC) atomicAdd(A + s, o.G[r][u]);
+        else A[s] += o.G[r][u];
+      }
+      if (MODE == MODE_ATOMIC) atomicAdd(b + row, bc[r]);
+      else b[row] += bc[r];
+    }
+  }
+  if (WANT_Q) {
+    const int od = __ldg(T.orig + k);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) q[t * N + od] = o.Q[t];
+  }
+  if (dbg) {
+    bool ok = isfinite(bc[0]) && isfinite(bc[1]) && isfinite(bc[2]);
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) ok = ok && isfinite(o.G[r][u]);
+    if (!ok) atomicOr(T.status, kStatusNumeric);
+  }
+}
+
+constexpr int kEvalBlock = 128;
+
+template <int MODE, bool WANT_Q>
+__global__ void __launch_bounds__(kEvalBlock) k_eval(DevTopo T, int begin, int end,
+                                                     const double* __restrict__ x, double* A,
+                                                     double* b, double* q, int dbg) {
+  for (int k = begin + blockIdx.x * blockDim.x + threadIdx.x; k < end;
+       k += gridDim.x * blockDim.x)
+    eval_one<MODE, WANT_Q>(T, k, x, A, b, q, dbg);
+}
+
+template <bool WANT_Q>
+__global__ void __launch_bounds__(kEvalBlock) k_persistent(DevTopo T, const int* __restrict__ coff,
+                                                           int C, const double* __restrict__ x,
+                                                           double* A, double* b, double* q,
+                                                           int dbg) {
+  for (int c = 0; c < C; ++c) {
+    const int end = __ldg(coff + c + 1);
+    for (int k = __ldg(coff + c) + blockIdx.x * blockDim.x + threadIdx.x; k < end;
+         k += gridDim.x * blockDim.x)
+      eval_one<MODE_RMW, WANT_Q>(T, k, x, A, b, q, dbg);
+    if (c + 1 < C && !grid_sync(T.bar, T.status)) return;
+  }
+}
+
+__global__ void k_params(DevTopo T, const double* __restrict__ Wo, const double* __restrict__ Lo) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= T.N) return;
+  if (Wo) {  // new sizes in original device order
+    const int od = T.orig[k];
+    T.W[k] = Wo[od];
+    T.L[k] = Lo[od];
+  }
+  const CardK& c = T.cards[T.meta[k] >> 1];
+  const PrmS<double> P = derive_params<double>(c, T.W[k], T.L[k]);
+  const long long N = T.N;
+  T.prm[P_BETA0 * N + k] = P.beta0;
+  T.prm[P_CE * N + k] = P.cE;
+  T.prm[P_INV_CE * N + k] = P.inv_cE;
+  T.prm[P_LAML * N + k] = P.lamL;
+  T.prm[P_ISAT * N + k] = P.Isat;
+  T.prm[P_COXT * N + k] = P.Coxt;
+  T.prm[P_COVS * N + k] = P.CovS;
+  T.prm[P_COVD * N + k] = P.CovD;
+}
+
+// Segmented reduction: entry e of [A ; b] = linear part + contributions in original-device
+// order (deterministic, no colours needed).
+__global__ void k_gather(DevTopo T, double* A, double* b) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long total = T.nnz + T.n;
+  if (e >= total) return;
+  double s = e < T.nnz ? __ldg(T.Alin + e) : __ldg(T.blin + (e - T.nnz));
+  const long long p0 = __ldg(T.gat_ptr + e), p1 = __ldg(T.gat_ptr + e + 1);
+  for (long long p = p0; p < p1; ++p) s += __ldg(T.buf + __ldg(T.gat_src + p));
+  if (e < T.nnz) A[e] = s;
+  else b[e - T.nnz] = s;
+}
+
+// One colour's stamp from the buffer (positions begin..end-1 share no row).
+__global__ void __launch_bounds__(kEvalBlock) k_stamp_buffer(DevTopo T, int begin, int end,
+                                                             double* A, double* b) {
+  const long long N = T.N;
+  for (int k = begin + blockIdx.x * blockDim.x + threadIdx.x; k < end;
+       k += gridDim.x * blockDim.x) {
+    const int4 ti = __ldg(T.tidx + k);
+    const int rows[3] = {ti.x, ti.z, ti.w};
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      if (rows[r] < 0) continue;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int s = __ldg(T.slot + (4 * r + u) * N + k);
+        if (s >= 0) A[s] += __ldg(T.buf + (4 * r + u) * N + k);
+      }
+      b[rows[r]] += __ldg(T.buf + (kNSlot + r) * N + k);
+    }
+  }
+}
+
+__global__ void k_dfma(double* out, int iters, double a, double c) {
+  double x0 = threadIdx.x * 1e-3, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3;
+  double x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6, x7 = x0 + 7;
+  for (int i = 0; i < iters; ++i) {
+    x0 = fma(x0, a, c); x1 = fma(x1, a, c); x2 = fma(x2, a, c); x3 = fma(x3, a, c);
+    x4 = fma(x4, a, c); x5 = fma(x5, a, c); x6 = fma(x6, a, c); x7 = fma(x7, a, c);
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+}
+
+int grid_for(long long n, int block) {
+  long long g = (n + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > 0x7fffffffLL) g = 0x7fffffffLL;
+  return (int)g;
+}
+
+}  // namespace
+
+cudaError_t launch_params(const DevTopo& T, cudaStream_t s) {
+  if (T.N == 0) return cudaSuccess;
+  k_params<<<grid_for(T.N, 256), 256, 0, s>>>(T, nullptr, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_params(const DevTopo& T, const double* W_dev, const double* L_dev,
+                                 cudaStream_t s) {
+  if (T.N == 0) return cudaSuccess;
+  k_params<<<grid_for(T.N, 256), 256, 0, s>>>(T, W_dev, L_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eval(const DevTopo& T, int mode, int begin, int end, const double* x,
+                        double* A, double* b, double* q, int block, int dbg, cudaStream_t s) {
+  if (end <= begin) return cudaSuccess;
+  (void)block;
+  const int g = grid_for(end - begin, kEvalBlock);
+  const bool wq = q != nullptr;
+  switch (mode) {
+    case MODE_RMW:
+      if (wq) k_eval<MODE_RMW, true><<<g, kEvalBlock, 0, s>>>(T, begin, end, x, A, b, q, dbg);
+      else k_eval<MODE_RMW, false><<<g, kEvalBlock, 0, s>>>(T, begin, end, x, A, b, q, dbg);
+      break;
+    case MODE_ATOMIC:
+      if (wq) k_eval<MODE_ATOMIC, true><<<g, kEvalBlock, 0, s>>>(T, begin, end, x, A, b, q, dbg);
+      else k_eval<MODE_ATOMIC, false><<<g, kEvalBlock, 0, s>>>(T, begin, end, x, A, b, q, dbg);
+      break;
+    default:
+      if (wq) k_eval<MODE_BUFFER, true><<<g, kEvalBlock, 0, s>>>(T, begin, end, x, A, b, q, dbg);
+      else k_eval<MODE_BUFFER, false><<<g, kEvalBlock, 0, s>>>(T, begin, end, x, A, b, q, dbg);
+      break;
+  }
+  return cudaGetLastError();
+}
+
+int persistent_max_blocks_per_sm(int block, bool want_q) {
+  (void)block;
+  int nb = 0;
+  cudaError_t e;
+  if (want_q)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent<true>, kEvalBlock, 0);
+  else
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent<false>, kEvalBlock, 0);
+  return e == cudaSuccess ? nb : 0;
+}
+
+cudaError_t launch_persistent(const DevTopo& T, const int* color_off_dev, int n_colors,
+                              const double* x, double* A, double* b, double* q, int block,
+                              int grid, int dbg, cudaStream_t s) {
+  (void)block;
+  cudaError_t e = cudaMemsetAsync(T.bar, 0, 2 * sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  DevTopo Tc = T;
+  const int* coff = color_off_dev;
+  int C = n_colors;
+  const double* xx = x;
+  double* AA = A;
+  double* bb = b;
+  double* qq = q;
+  int d = dbg;
+  void* args[] = {&Tc, &coff, &C, &xx, &AA, &bb, &qq, &d};
+  if (q)
+    return cudaLaunchCooperativeKernel((const void*)k_persistent<true>, dim3(grid),
+                                       dim3(kEvalBlock), args, 0, s);
+  return cudaLaunchCooperativeKernel((const void*)k_persistent<false>, dim3(grid),
+                                     dim3(kEvalBlock), args, 0, s);
+}
+
+cudaError_t launch_gather(const DevTopo& T, double* A, double* b, cudaStream_t s) {
+  const long long total = T.nnz + T.n;
+  if (total == 0) return cudaSuccess;
+  k_gather<<<grid_for(total, 256), 256, 0, s>>>(T, A, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stamp_buffer(const DevTopo& T, int begin, int end, double* A, double* b,
+                                int block, cudaStream_t s) {
+  (void)block;
+  if (end <= begin) return cudaSuccess;
+  k_stamp_buffer<<<grid_for(end - begin, kEvalBlock), kEvalBlock, 0, s>>>(T, begin, end, A, b);
+  return cudaGetLastError();
+}
+
+cudaError_t fp64_peak(int iters, int blocks_per_sm, double* flops) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int blocks = sms * blocks_per_sm, threads = 256;
+  double* out = nullptr;
+  e = cudaMalloc(&out, sizeof(double) * blocks * threads);
+  if (e != cudaSuccess) return e;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  k_dfma<<<blocks, threads>>>(out, iters / 8 + 1, 0.999999, 1e-9);  // warm-up
+  cudaEventRecord(e0);
+  k_dfma<<<blocks, threads>>>(out, iters, 0.999999, 1e-9);
+  cudaEventRecord(e1);
+  e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  if (e != cudaSuccess) return e;
+  *flops = 2.0 * 8.0 * iters * (double)blocks * threads / (ms * 1e-3);
+  return cudaGetLastError();
+}
+
+}  // namespace eec

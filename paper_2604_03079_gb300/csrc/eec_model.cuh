@@ -1,0 +1,227 @@
+// EES-L1 device model on the GPU with a hand-derived Jacobian.
+//
+// The paper evaluates BSIM4 v4.82 per device in the compute phase of every Newton iteration
+// (Sec. II (i): terminal currents, charges and linearised conductances at the present bias) but
+// prints no model equations. This file implements the documented BSIM-style level EES-L1:
+//   (1) source/drain mode swap, (2) smooth body effect with DIBL, (3) softplus effective
+//   overdrive, (4) bulk-charge factor, (5) mobility degradation, (6) velocity saturation,
+//   (7) smooth min(vds, Vdsat), (8) drain current with length modulation, (9) channel current
+//   into the terminals, (10) body-drain / body-source junctions with exponent limiting above
+//   40 Vt, (11) charge partition with overlaps, (12) the analytic Jacobian dI_t/dV_u.
+//
+// The code is written once for a scalar type S: S = double for the forward kernels, and S = a
+// tangent (forward-mode) type for the backward kernel, which needs derivatives of the Jacobian.
+// Every division and square root goes through rcp()/rsqrt() overloads so that one reciprocal is
+// shared between a quotient and its derivatives.
+#pragma once
+
+#include "eec_internal.h"
+
+namespace eec {
+
+// ---- scalar helpers for S = double ----
+__device__ __forceinline__ double sval(double x) { return x; }
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ double rsqrt_(double x) { return ::rsqrt(x); }
+__device__ __forceinline__ double exp_(double x) { return ::exp(x); }
+__device__ __forceinline__ double expm1_(double x) { return ::expm1(x); }
+__device__ __forceinline__ double log1p_(double x) { return ::log1p(x); }
+
+template <class S>
+struct PrmS {
+  S beta0;   // U0 Cox W / L
+  S cE;      // 2 VSAT L / U0 (EsatL = cE * mobility denominator)
+  S inv_cE;  // 1 / cE
+  S lamL;    // LAMBDA LREF / L
+  S Isat;    // JS W HDIF
+  S Coxt;    // Cox W L
+  S CovS;    // CGSO W
+  S CovD;    // CGDO W
+};
+
+// Per-device parameters from W and L (the forward stores these per position; the backward
+// recomputes them in tangent arithmetic so that W and L derivatives flow through).
+template <class S>
+__device__ __forceinline__ PrmS<S> derive_params(const CardK& c, const S& W, const S& L) {
+  PrmS<S> P;
+  const S iL = rcp(L);
+  P.beta0 = c.U0Cox * W * iL;
+  P.cE = c.twoVSAT_U0 * L;
+  P.inv_cE = iL * (1.0 / c.twoVSAT_U0);
+  P.lamL = c.LAMBDA_LREF * iL;
+  P.Isat = c.JS_HDIF * W;
+  P.Coxt = c.Cox * W * L;
+  P.CovS = c.CGSO * W;
+  P.CovD = c.CGDO * W;
+  return P;
+}
+
+template <class S>
+struct EvalOut {
+  S I[4];      // current from node t into the device, t = d, g, s, b (I[1] == 0)
+  S G[3][4];   // rows d, s, b of dI_t / dV_u, u = d, g, s, b (gate row is zero in DC)
+  S Q[4];      // terminal charges (only when requested)
+};
+
+template <class S>
+__device__ __forceinline__ S sel(bool c, const S& a, const S& b) { return c ? a : b; }
+
+// Junction current and conductance: Ij(v) = Isat (explim(v/Vt) - 1) + GMIN v with
+// explim(z) = exp(z) for z <= 40 and e^40 (1 + z - 40) above.
+template <class S>
+__device__ __forceinline__ void junction(const CardK& c, const S& Isat, const S& v, S& Ij, S& gj) {
+  const S z = v * c.inv_Vt;
+  const bool over = sval(z) > 40.0;
+  const S zc = over ? S(40.0) : z;
+  const S em1 = expm1_(zc);
+  const S ez = em1 + 1.0;
+  const S lin = over ? (z - 40.0) : S(0.0);
+  Ij = Isat * (em1 + ez * lin) + c.GMIN * v;
+  gj = Isat * c.inv_Vt * ez + c.GMIN;
+}
+
+template <class S, bool WANT_Q>
+__device__ __forceinline__ void ees_l1(const CardK& c, double pp, const PrmS<S>& P,
+                                       const S V[4], EvalOut<S>& o) {
+  // (1) mode
+  const S vds0 = pp * (V[0] - V[2]);
+  const bool fwd = sval(vds0) >= 0.0;
+  const S VD = fwd ? V[0] : V[2];
+  const S VS = fwd ? V[2] : V[0];
+  const S vgs = pp * (V[1] - VS);
+  const S vds = pp * (VD - VS);
+  const S vbs = pp * (V[3] - VS);
+
+  // (2) body effect: phis = (u + R1)/2, R1 = sqrt(u^2 + 4 D1^2), u = PHI - vbs
+  //     d phis / d u = phis / R1, d sqs / d vbs = -sqs / (2 R1)
+  const S u = c.PHI - vbs;
+  const S R1sq = u * u + c.fourD1sq;
+  const S inv_R1 = rsqrt_(R1sq);
+  const S R1 = R1sq * inv_R1;
+  S phis;
+  if (sval(u) >= 0.0) phis = 0.5 * (u + R1);
+  else phis = c.twoD1sq * rcp(R1 - u);
+  const S inv_sqs = rsqrt_(phis);
+  const S sqs = phis * inv_sqs;
+  const S Vth = c.VTH0 + c.K1 * (sqs - c.sqrtPHI) - c.ETA0 * vds;
+  const S hK1R = (0.5 * c.K1) * inv_R1;
+  const S dVth_dvbs = -(hK1R * sqs);            // K1 d sqs / d vbs
+  const S Ab = 1.0 + (0.5 * c.K1) * inv_sqs;     // (4)
+  const S dAb_dvbs = 0.5 * hK1R * inv_sqs;       // K1 / (4 sqs R1)
+
+  // (3) Vgsteff = nVt softplus(z), dVgsteff/dz = nVt sigmoid(z)
+  const S z = (vgs - Vth) * c.inv_nVt;
+  const bool zpos = sval(z) >= 0.0;
+  const S e = exp_(zpos ? -z : z);               // exp(-|z|)
+  const S lg = log1p_(e);
+  const S Vg = c.nVt * (zpos ? z + lg : lg);
+  const S inv_1pe = rcp(1.0 + e);
+  const S sig = zpos ? inv_1pe : e * inv_1pe;
+
+  // (5) mobility denominator, (6) velocity saturation
+  const S den = 1.0 + Vg * (c.UA + c.UB * Vg);
+  const S dden = c.UA + 2.0 * c.UB * Vg;
+  const S inv_den = rcp(den);
+  const S beta = P.beta0 * inv_den;
+  const S EsatL = P.cE * den;
+  const S inv_EsatL = P.inv_cE * inv_den;
+  const S EsatL_Vg = P.cE * dden;
+  const S Vgst2 = Vg + c.twoVt;
+  const S inv_Vgst2 = rcp(Vgst2);
+  const S Dd = Ab * EsatL + Vgst2;
+  const S inv_Dd = rcp(Dd);
+  const S r1 = Vgst2 * inv_Dd;
+  const S r2 = EsatL * inv_Dd;
+  const S Vdsat = EsatL * r1;
+  const S Vdsat_Vg = r1 * r1 * EsatL_Vg + Ab * (r2 * r2);   // dVgst2/dVg = 1
+  const S Vdsat_Ab = -(r2 * r2) * Vgst2;
+
+  // (7) Vdseff = 2 Vdsat vds / (Vdsat + vds + DELTA + R2), R2 = sqrt(t^2 + 4 DELTA Vdsat)
+  const S t = Vdsat - vds - c.DELTA;
+  const S R2sq = t * t + c.fourDELTA * Vdsat;
+  const S inv_R2 = rsqrt_(R2sq);
+  const S R2 = R2sq * inv_R2;
+  const S E = Vdsat + vds + c.DELTA + R2;
+  const S inv_E = rcp(E);
+  const S Vdseff = 2.0 * Vdsat * vds * inv_E;
+  const S dE_dVdsat = 1.0 + (t + c.twoDELTA) * inv_R2;
+  const S dE_dvds = 1.0 - t * inv_R2;
+  const S Vde_Vdsat = (2.0 * vds - Vdseff * dE_dVdsat) * inv_E;
+  const S Vde_vds = (2.0 * Vdsat - Vdseff * dE_dvds) * inv_E;
+
+  // (8) Ids = beta Vg Vdseff F1 F3 / F2
+  const S h = 0.5 * inv_Vgst2;
+  const S F1 = 1.0 - Ab * Vdseff * h;
+  const S F2 = 1.0 + Vdseff * inv_EsatL;
+  const S inv_F2 = rcp(F2);
+  const S F3 = 1.0 + P.lamL * (vds - Vdseff);
+  const S Pb = beta * Vg;
+  const S F13 = F1 * F3;
+  const S VF13 = Vdseff * F13;
+  const S Ids = Pb * VF13 * inv_F2;
+
+  // partial derivatives with Vg, Ab and vds as independent variables
+  const S Vde_Vg = Vde_Vdsat * Vdsat_Vg;
+  const S Vde_Ab = Vde_Vdsat * Vdsat_Ab;
+  const S F1_Vg = -(Ab * h) * (Vde_Vg - Vdseff * inv_Vgst2);
+  const S F1_Ab = -h * (Vdseff + Ab * Vde_Ab);
+  const S F1_vds = -(Ab * h) * Vde_vds;
+  const S F2_Vg = inv_EsatL * (Vde_Vg - Vdseff * dden * inv_den);
+  const S F2_Ab = inv_EsatL * Vde_Ab;
+  const S F2_vds = inv_EsatL * Vde_vds;
+  const S F3_Vg = -(P.lamL * Vde_Vg);
+  const S F3_Ab = -(P.lamL * Vde_Ab);
+  const S F3_vds = P.lamL * (1.0 - Vde_vds);
+  const S Pb_Vg = beta * (1.0 - Vg * dden * inv_den);
+  const S dV_Vg = Vde_Vg * F13 + Vdseff * (F1_Vg * F3 + F1 * F3_Vg);
+  const S dV_Ab = Vde_Ab * F13 + Vdseff * (F1_Ab * F3 + F1 * F3_Ab);
+  const S dV_vds = Vde_vds * F13 + Vdseff * (F1_vds * F3 + F1 * F3_vds);
+  const S Ids_Vg = (Pb_Vg * VF13 + Pb * dV_Vg - Ids * F2_Vg) * inv_F2;
+  const S Ids_Ab = (Pb * dV_Ab - Ids * F2_Ab) * inv_F2;
+  const S Ids_vds = (Pb * dV_vds - Ids * F2_vds) * inv_F2;
+
+  // chain to the mode-frame voltages: dVg/dvgs = sig, dVg/dvds = sig ETA0,
+  // dVg/dvbs = -sig dVth/dvbs
+  const S gm = Ids_Vg * sig;
+  const S gds = gm * c.ETA0 + Ids_vds;
+  const S gmb = Ids_Ab * dAb_dvbs - gm * dVth_dvbs;
+  const S gsum = gm + gds + gmb;
+
+  // (9) channel current into physical d (into s is the negative), and its Jacobian row
+  const double m = fwd ? 1.0 : -1.0;
+  const S Ichd = (pp * m) * Ids;
+  const S cdd = fwd ? gds : gsum;
+  const S cdg = fwd ? gm : -gm;
+  const S cds = fwd ? -gsum : -gds;
+  const S cdb = fwd ? gmb : -gmb;
+
+  // (10) junctions on the physical terminals
+  S Ijd, gjd, Ijs, gjs;
+  junction<S>(c, P.Isat, pp * (V[3] - V[0]), Ijd, gjd);
+  junction<S>(c, P.Isat, pp * (V[3] - V[2]), Ijs, gjs);
+
+  o.I[0] = Ichd - pp * Ijd;
+  o.I[1] = S(0.0);
+  o.I[2] = -Ichd - pp * Ijs;
+  o.I[3] = pp * (Ijd + Ijs);
+  o.G[0][0] = cdd + gjd;  o.G[0][1] = cdg;   o.G[0][2] = cds;        o.G[0][3] = cdb - gjd;
+  o.G[1][0] = -cdd;       o.G[1][1] = -cdg;  o.G[1][2] = gjs - cds;  o.G[1][3] = -cdb - gjs;
+  o.G[2][0] = -gjd;       o.G[2][1] = S(0.0); o.G[2][2] = -gjs;      o.G[2][3] = gjd + gjs;
+
+  if (WANT_Q) {
+    // (11) charges: depletion, inversion partitioned XPART to the mode drain, overlaps
+    const S Qb = -(P.Coxt * c.K1 * sqs);
+    const S Qinv = -(P.Coxt * Vg * F1);
+    const S Qg0 = -(Qb + Qinv);
+    const S QD = c.XPART * Qinv;
+    const S QS = (1.0 - c.XPART) * Qinv;
+    const S Qovs = P.CovS * (pp * (V[1] - V[2]));
+    const S Qovd = P.CovD * (pp * (V[1] - V[0]));
+    o.Q[1] = pp * (Qg0 + Qovs + Qovd);
+    o.Q[0] = pp * ((fwd ? QD : QS) - Qovd);
+    o.Q[2] = pp * ((fwd ? QS : QD) - Qovs);
+    o.Q[3] = pp * Qb;
+  }
+}
+
+}  // namespace eec
