@@ -27,7 +27,8 @@ def build(force: bool = False) -> str:
     """Compile the oracle with the host compiler (portable flags: it runs on x86 and Arm)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-o", tmp, _SRC],
+        subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp,
+                        _SRC],
                        check=True)
         os.replace(tmp, _LIB)
     return _LIB

@@ -45,7 +45,7 @@ def check_against_oracle(eec, circ, o, x, variant, want_q=True, ref=None):
     eb = rel_err(host(b), r["b"], r["b_scale"])
     assert eA.max() <= TOL, (variant, eA.max(), int(eA.argmax()))
     assert eb.max() <= TOL, (variant, eb.max(), int(eb.argmax()))
-    if want_q:
+    if want_q and r["q"].size:
         qg = host(q).reshape(4, -1)
         scale = np.maximum(np.abs(r["q"]).max(axis=0, keepdims=True), 1e-300)
         assert (np.abs(qg - r["q"]) / scale).max() <= 1e-13
