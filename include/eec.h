@@ -182,6 +182,33 @@ EEC_API int eec_eval_stamp_bwd(eec_ctx* ctx, const double* x_dev, const double* 
                        void* cuda_stream);
 
 /*
+ * eec_eval_stamp_bwd_noalloc: the same gradients as eec_eval_stamp_bwd, computed by the same
+ * kernels, for callers that cannot allocate device memory. Typical callers: an application whose
+ * GPU memory is entirely reserved by its own allocator (a framework's caching pool, a fixed
+ * arena), so a cudaMalloc from inside this library would fail or break its accounting; and a
+ * latency-critical loop that cannot afford the device-wide synchronisation cudaMalloc and cudaFree
+ * can cause. The paper has no counterpart; this is a property of the library interface only.
+ *
+ * The backward's per-device scratch (four terminal gradients per device, written by the first
+ * pass and gathered by the second) lives in one fixed array compiled into the library instead of
+ * a buffer allocated on first use. The call makes no cudaMalloc, cudaFree or other allocating
+ * call; the caller passes every input and output as in eec_eval_stamp_bwd.
+ *  - Limit: the context may hold at most EEC_NOALLOC_MAX_DEV devices (the array is
+ *    4 * EEC_NOALLOC_MAX_DEV doubles = 16 MiB); larger contexts are rejected with EEC_EINVAL.
+ *  - The array exists on every GPU on which the library is loaded and stays allocated until the
+ *    process exits.
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress with
+ *    that device current) and caches it; make that first call before any stream capture.
+ *  - Every call, from any context, shares the array, and it keeps the last call's contents. Each
+ *    call writes every entry it later reads, so nothing needs clearing, but calls whose work
+ *    overlaps on the GPU (e.g. on two streams without ordering between them) race on it.
+ */
+#define EEC_NOALLOC_MAX_DEV 524288
+EEC_API int eec_eval_stamp_bwd_noalloc(eec_ctx* ctx, const double* x_dev, const double* gA_dev,
+                                       const double* gb_dev, double* gx_dev, double* gW_dev,
+                                       double* gL_dev, void* cuda_stream);
+
+/*
  * Capture the current variant's eval_stamp on these buffers into a CUDA graph owned by ctx
  * (replacing any previous one); eec_graph_launch() then replays it on any stream.
  */

@@ -68,6 +68,7 @@ _SIG = {
     "eec_get_variant": (ctypes.c_int, [_P, ctypes.POINTER(_I32)]),
     "eec_eval_stamp": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "eec_eval_stamp_bwd": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "eec_eval_stamp_bwd_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "eec_graph_capture": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "eec_graph_launch": (ctypes.c_int, [_P, _P]),
     "eec_autotune": (ctypes.c_int, [_P, _P, _P, _P, _P, _I32, _P, _P]),
@@ -285,6 +286,16 @@ def eec_eval_stamp_bwd(ctx, x, gA, gb, gx, gW, gL, stream=None):
     _check(ctx, _load().eec_eval_stamp_bwd(ctx, _d(x, name="x"), _d(gA, name="gA"), _d(gb, name="gb"),
                                        _d(gx, name="gx"), _d(gW, name="gW"), _d(gL, name="gL"),
                                        _stream(stream)))
+
+
+def eec_eval_stamp_bwd_noalloc(ctx, x, gA, gb, gx, gW, gL, stream=None):
+    """Backward with the library's fixed scratch array: allocates nothing (see include/eec.h)."""
+    _check(ctx, _load().eec_eval_stamp_bwd_noalloc(
+        ctx, _d(x, name="x"), _d(gA, name="gA"), _d(gb, name="gb"), _d(gx, name="gx"),
+        _d(gW, name="gW"), _d(gL, name="gL"), _stream(stream)))
+
+
+EEC_NOALLOC_MAX_DEV = 524288
 
 
 def eec_graph_capture(ctx, x, A, b, q=None, stream=None):

@@ -13,11 +13,19 @@
 // arithmetic with six directions (Vd, Vg, Vs, Vb, W, L).
 #include <cuda_runtime.h>
 
+#include <map>
+#include <mutex>
+
 #include "eec_model.cuh"
 
 namespace eec {
 
 namespace {
+
+// Fixed scratch of eec_eval_stamp_bwd_noalloc: four terminal gradients per device for up to
+// EEC_NOALLOC_MAX_DEV devices (16 MiB on every GPU that loads the library). Host code must not
+// use this name as an address; noalloc_scratch() resolves the device address.
+static __device__ __align__(256) double g_noalloc_gv[4 * (size_t)EEC_NOALLOC_MAX_DEV];
 
 constexpr int kT = 6;
 
@@ -176,7 +184,45 @@ __global__ void k_bwd_gather(DevTopo T, double* __restrict__ gx) {
   gx[u] = s;
 }
 
+// Device address of g_noalloc_gv on the current device, looked up once per device (set-up on the
+// first call there) and cached; no allocation.
+cudaError_t noalloc_scratch(double** out) {
+  static std::mutex mu;
+  static std::map<int, double*> cache;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(dev);
+  if (it == cache.end()) {
+    double* ptr = nullptr;
+    e = cudaGetSymbolAddress((void**)&ptr, g_noalloc_gv);
+    if (e != cudaSuccess) return e;
+    it = cache.emplace(dev, ptr).first;
+  }
+  *out = it->second;
+  return cudaSuccess;
+}
+
 }  // namespace
+
+cudaError_t launch_bwd_noalloc(const DevTopo& T, const double* x, const double* gA,
+                               const double* gb, double* gx, double* gW, double* gL,
+                               cudaStream_t s) {
+  if (T.N > EEC_NOALLOC_MAX_DEV) return cudaErrorInvalidValue;
+  double* scratch = nullptr;
+  cudaError_t e = noalloc_scratch(&scratch);
+  if (e != cudaSuccess) return e;
+  DevTopo Ts = T;
+  Ts.gv = scratch;
+  if (Ts.N > 0) {
+    k_bwd_device<<<(Ts.N + kBwdBlock - 1) / kBwdBlock, kBwdBlock, 0, s>>>(Ts, x, gA, gb, gW, gL);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (Ts.n > 0) k_bwd_gather<<<(Ts.n + 255) / 256, 256, 0, s>>>(Ts, gx);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_bwd(const DevTopo& T, const double* x, const double* gA, const double* gb,
                        double* gx, double* gW, double* gL, int block, cudaStream_t s) {

@@ -970,6 +970,19 @@ int eec_eval_stamp_bwd(eec_ctx* c, const double* x, const double* gA, const doub
   return EEC_OK;
 }
 
+int eec_eval_stamp_bwd_noalloc(eec_ctx* c, const double* x, const double* gA, const double* gb,
+                               double* gx, double* gW, double* gL, void* stream) {
+  int rc = check_built(c);
+  if (rc) return rc;
+  if (!x || !gA || !gb || !gx || !gW || !gL) return fail(c, EEC_EINVAL, "NULL argument");
+  if (c->n_dev > EEC_NOALLOC_MAX_DEV)
+    return fail(c, EEC_EINVAL, "eec_eval_stamp_bwd_noalloc: " + std::to_string(c->n_dev) +
+                                   " devices exceed the fixed scratch of EEC_NOALLOC_MAX_DEV = " +
+                                   std::to_string(EEC_NOALLOC_MAX_DEV) + " devices");
+  CUDA_TRY(c, launch_bwd_noalloc(c->d, x, gA, gb, gx, gW, gL, static_cast<cudaStream_t>(stream)));
+  return EEC_OK;
+}
+
 int eec_graph_capture(eec_ctx* c, const double* x, double* A, double* b, double* q, void* stream) {
   int rc = check_built(c);
   if (rc) return rc;

@@ -82,6 +82,10 @@ cudaError_t launch_stamp_buffer(const DevTopo& T, int begin, int end, double* A,
 cudaError_t launch_bwd(const DevTopo& T, const double* x, const double* gA, const double* gb,
                        double* gx, double* gW, double* gL, int block, cudaStream_t s);
 cudaError_t fp64_peak(int iters, int blocks_per_sm, double* flops);
+// Backward with its terminal-gradient scratch in the library's fixed array (no allocation).
+cudaError_t launch_bwd_noalloc(const DevTopo& T, const double* x, const double* gA,
+                               const double* gb, double* gx, double* gW, double* gL,
+                               cudaStream_t s);
 
 // ---- GPU colouring (eec_color.cu) ----
 // Jones-Plassmann colouring of the conflict graph given as node -> device incidence (CSR over
