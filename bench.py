@@ -31,9 +31,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MOSFET eval+stamp/s per NR iter (FP64, 1xGB300)"
 UNIT = "device evals+stamps/s"
-# FP64 floating-point operations per device of the evaluate kernel (DADD + DMUL + 2 DFMA thread
-# instructions per device, from the ncu instruction counters of the kernel; see profiles/).
-FP64_FLOP_PER_DEVICE = None
+# Per-device work of the evaluate kernel on this workload, from ncu's counters of the kernel
+# (profiles/k_eval_atomic_sram_256x256.md): FP64 flop = 2 DFMA + DADD + DMUL thread instructions
+# per device, and DRAM bytes read + written per device.
+FP64_FLOP_PER_DEVICE = 348.7
+DRAM_BYTES_PER_DEVICE = 181.3
 # GB300: 152 SMs x 2 FP64 FMA per clock per SM x 2 flop x 2070 MHz maximum SM clock.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
@@ -112,6 +114,23 @@ class Clocks:
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows)}
+
+
+def reduce_max(value, device=None):
+    """Max of a per-rank number over the default process group (identity on one rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(world, n_dev_per_rank, ms_per_step):
+    """Whole-job throughput: every rank evaluates its own replica of n_dev_per_rank devices
+    (weak scaling); the step time is the slowest rank's."""
+    return world * n_dev_per_rank / (ms_per_step * 1e-3)
 
 
 def cpu_baseline(net, x, budget_s=10.0):
@@ -218,14 +237,10 @@ def run_ours(args):
     prof = eec.eec_profile_read(circ.ctx)
     eec.eec_profile_enable(circ.ctx, False)
     step_ms = [a.elapsed_time(bb) for a, bb in ev]
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = reduce_max(float(sum(step_ms)), dev)
     assert circ.status() == 0
     ms_per_step = total_ms / args.steps
-    value = world * net.n_dev / (ms_per_step * 1e-3)
+    value = aggregate_value(world, net.n_dev, ms_per_step)
     launches = prof["kernels"]
 
     if graphed:   # per-kernel times of the graph-replayed schedules: one profiled pass
@@ -257,42 +272,21 @@ def run_ours(args):
         print(json.dumps(out))
     elif rank == 0:
         # roofline of the dominant kernel (the evaluate kernel; FP64-pipe bound)
-        flop = FP64_FLOP_PER_DEVICE
+        flop = FP64_FLOP_PER_DEVICE if args.workload == "sram" else None
         ach = (flop * net.n_dev / (eval_ms * 1e-3) / 1e12) if (flop and eval_ms > 0) else None
+        traffic = DRAM_BYTES_PER_DEVICE * net.n_dev if args.workload == "sram" else None
         out["roofline"] = {"bound": "alu", "kernel": "k_eval (evaluate)",
                            "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                           "frac": (ach / FP64_PEAK_TFLOPS) if ach else None, "traffic": None,
+                           "frac": (ach / FP64_PEAK_TFLOPS) if ach else None, "traffic": traffic,
                            "peak_source": "152 SM x 2 DFMA/clk x 2 flop x 2070 MHz (recipe unit "
                                           "counts; nominal 1.25 TFLOP/s FP64)"}
         out["fp64_probe_tflops"] = eec.eec_fp64_peak(4096, 8) / 1e12
         out["variants_ms"] = {eec.VARIANT_NAMES[i]: m for i, m in enumerate(ms_variants)}
 
-        # end to end through the public API with host buffers (pinned), copies inside the timing
-        xh = torch.as_tensor(x).pin_memory()
-        Ah = torch.empty(circ.nnz, dtype=torch.float64).pin_memory()
-        bh = torch.empty(circ.n, dtype=torch.float64).pin_memory()
-        qh = torch.empty(4 * circ.n_dev, dtype=torch.float64).pin_memory()
-        e2e_steps = max(10, min(args.steps, 200))
-        for _ in range(3):
-            xt.copy_(xh, non_blocking=True)
-            circ.eval_stamp(xt, A, b, q)
-            Ah.copy_(A, non_blocking=True)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(e2e_steps):
-            xt.copy_(xh, non_blocking=True)
-            circ.eval_stamp(xt, A, b, q)
-            Ah.copy_(A, non_blocking=True)
-            bh.copy_(b, non_blocking=True)
-            qh.copy_(q, non_blocking=True)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        e2e_ms = e0.elapsed_time(e1) / e2e_steps
-        out["e2e"] = {"value": world * net.n_dev / (e2e_ms * 1e-3), "unit": UNIT,
-                      "h2d_bytes_per_step": 8 * circ.n,
-                      "d2h_bytes_per_step": 8 * (circ.nnz + circ.n + 4 * circ.n_dev),
-                      "ms_per_step": e2e_ms}
+        # end to end through the public API with host buffers (pinned): every step copies its
+        # x in and its A, b, q out inside the timed region; copies run on a second stream and
+        # the device buffers are doubled, so step i's copies overlap step i+1's evaluation
+        out["e2e"] = e2e(eec, circ, x, args, dev, world, net.n_dev)
 
         if world == 1 and not args.no_extras:
             out["extras"] = extras(eec, circ, net, x, xt, A, b, q, args, dev)
@@ -303,6 +297,54 @@ def run_ours(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def e2e(eec, circ, x, args, dev, world, n_dev):
+    import torch
+    cs = torch.cuda.current_stream()
+    ts = torch.cuda.Stream()
+    xh = torch.as_tensor(x).pin_memory()
+    xd = [torch.empty(circ.n, dtype=torch.float64, device=dev) for _ in range(2)]
+    outs = [circ.new_outputs(want_q=True) for _ in range(2)]
+    hosts = [tuple(torch.empty(t.numel(), dtype=torch.float64).pin_memory() for t in o)
+             for o in outs]
+    ev = {k: [torch.cuda.Event() for _ in range(2)] for k in ("h2d", "eval", "d2h")}
+    steps = max(10, min(args.steps, 400))
+
+    def step(i):
+        s = i & 1
+        A, b, q = outs[s]
+        with torch.cuda.stream(ts):
+            if i >= 2:
+                ts.wait_event(ev["eval"][s])      # x buffer s free again
+            xd[s].copy_(xh, non_blocking=True)
+            ev["h2d"][s].record(ts)
+        cs.wait_event(ev["h2d"][s])
+        if i >= 2:
+            cs.wait_event(ev["d2h"][s])           # outputs of step i-2 are on the host
+        eec.eec_eval_stamp(circ.ctx, xd[s], A, b, q, cs)
+        ev["eval"][s].record(cs)
+        with torch.cuda.stream(ts):
+            ts.wait_event(ev["eval"][s])
+            for hdst, dsrc in zip(hosts[s], (A, b, q)):
+                hdst.copy_(dsrc, non_blocking=True)
+            ev["d2h"][s].record(ts)
+
+    for i in range(4):
+        step(i)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(cs)
+    for i in range(steps):
+        step(i)
+    cs.wait_stream(ts)
+    e1.record(cs)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return {"value": world * n_dev / (ms * 1e-3), "unit": UNIT,
+            "h2d_bytes_per_step": 8 * circ.n,
+            "d2h_bytes_per_step": 8 * (circ.nnz + circ.n + 4 * circ.n_dev),
+            "ms_per_step": ms, "pipelined": "copies on a second stream, double-buffered"}
 
 
 def _time(fn, reps, stream):

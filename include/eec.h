@@ -73,7 +73,9 @@ typedef struct eec_ctx eec_ctx; /* opaque, library-owned */
 
 typedef struct {
   int32_t variant;       /* EEC_VARIANT_*; default EEC_VARIANT_AUTO */
-  int32_t block;         /* threads per block of the evaluate kernels; 0 = library default */
+  int32_t block;         /* threads per block of the evaluate kernels: 0 = library choice (one
+                            warp per block for launches under 152 x 128 devices, else 128),
+                            or 8, 16, 32, 64, 96, 128 */
   int32_t conflict_rule; /* EEC_CONFLICT_*; default EEC_CONFLICT_FREE_NODE */
   int32_t debug_checks;  /* nonzero: kernels flag non-finite outputs in the status word */
 } eec_options;
@@ -288,6 +290,26 @@ EEC_API int eec_get_batch_offsets(const eec_ctx* ctx, int32_t* circ_row_off, int
  * 2 per DFMA) to *flops. Synchronous; used to report the FP64 roofline.
  */
 EEC_API int eec_fp64_peak(int32_t iters, int32_t blocks_per_sm, double* flops);
+
+/*
+ * Test hook for the failure path of the persistent schedule's grid barrier (the paper has no
+ * counterpart): launches the persistent kernel on these buffers with one block that never
+ * arrives at the barriers, so the other blocks' waits run out after their 1 s limit and the
+ * status word records EEC_ETIMEOUT (read it with eec_status). Nothing faults or hangs; A and b
+ * are left partially stamped. Needs a coloured context with at least two colours.
+ */
+EEC_API int eec_test_barrier_timeout(eec_ctx* ctx, const double* x_dev, double* A_values_dev,
+                                     double* b_dev, void* cuda_stream);
+
+/*
+ * Validation hook for the library's own FP64 elementary functions (the table-driven exp, expm1
+ * and log1p the model evaluation uses in place of CUDA's). The paper has no counterpart.
+ *  fn      0 = exp, 1 = expm1, 2 = log1p (argument in [0, 1], the only range the model uses).
+ *  x_dev   [n] arguments; ours_dev [n] the library's results; cuda_dev [n] CUDA's exp / expm1 /
+ *          log1p of the same arguments. Asynchronous on cuda_stream.
+ */
+EEC_API int eec_math_check(int32_t fn, int64_t n, const double* x_dev, double* ours_dev,
+                           double* cuda_dev, void* cuda_stream);
 
 #ifdef __cplusplus
 }

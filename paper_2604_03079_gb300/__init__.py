@@ -78,6 +78,8 @@ _SIG = {
     "eec_upload_batch": (ctypes.c_int, [_P, _I32, ctypes.POINTER(eec_netlist), _F64]),
     "eec_get_batch_offsets": (ctypes.c_int, [_P, _P, _P, _P]),
     "eec_fp64_peak": (ctypes.c_int, [_I32, _I32, ctypes.POINTER(_F64)]),
+    "eec_math_check": (ctypes.c_int, [_I32, _I64, _P, _P, _P, _P]),
+    "eec_test_barrier_timeout": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "eec_profile_enable": (ctypes.c_int, [_P, _I32]),
     "eec_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(_F64), ctypes.POINTER(_F64),
                                         ctypes.POINTER(_F64), ctypes.POINTER(_I64),
@@ -329,6 +331,23 @@ def eec_profile_read(ctx):
                                      ctypes.byref(n), ctypes.byref(k)))
     return dict(ms_init=a.value, ms_eval=b.value, ms_stamp=c.value, calls=int(n.value),
                 kernels=int(k.value))
+
+
+def eec_test_barrier_timeout(ctx, x, A, b, stream=None):
+    _check(ctx, _load().eec_test_barrier_timeout(ctx, _d(x, name="x"), _d(A, name="A"),
+                                                 _d(b, name="b"), _stream(stream)))
+
+
+def eec_math_check(fn, x, stream=None):
+    """-> (library result, CUDA result) of exp (0), expm1 (1) or log1p on [0, 1] (2) at x."""
+    import torch
+    ours = torch.empty_like(x)
+    ref = torch.empty_like(x)
+    rc = _load().eec_math_check(int(fn), x.numel(), _d(x, name="x"), _d(ours), _d(ref),
+                                _stream(stream))
+    if rc != EEC_OK:
+        raise EECError(rc, "eec_math_check failed")
+    return ours, ref
 
 
 def eec_fp64_peak(iters=4096, blocks_per_sm=8) -> float:

@@ -8,9 +8,17 @@
 // devices attached to that node (the transpose of the stamp scatter). No two threads write the
 // same location, so neither colours nor atomics are needed.
 //
-// The device term needs derivatives of the Jacobian G (second derivatives of the currents).
-// They come from running the same hand-derived model (eec_model.cuh) in forward-mode tangent
-// arithmetic with six directions (Vd, Vg, Vs, Vb, W, L).
+// The device term is s_k = sum_{r,u} c_ru G_ru - sum_r wb_r I_r with c_ru = gA[slot] + wb_r V_u
+// over free rows r and free columns u, wb_r = gb[row r]. Its gradient needs second derivatives
+// of the currents; they come in three pieces:
+//  * channel: I_d = -I_s = p m Ids(vgs, vds, vbs), so its part of s_k is m (g . w) - p m omega Ids
+//    with g = dIds/d(vgs, vds, vbs), w the mode-frame weights and omega = wb_d - wb_s. Its
+//    gradient needs only the Hessian-vector product H w and the L-derivatives of g and Ids: one
+//    forward pass of the hand-derived channel code (eec_model.cuh) in 2-direction tangent
+//    arithmetic (direction w in (vgs, vds, vbs), direction L);
+//  * junctions: Ij(v), gj(v) and dgj/dv in closed form;
+//  * W: the channel current is proportional to W (through U0 Cox W / L only) and the junction
+//    currents minus their GMIN part are proportional to W, so d/dW is exact division by W.
 #include <cuda_runtime.h>
 
 #include <map>
@@ -27,94 +35,118 @@ namespace {
 // use this name as an address; noalloc_scratch() resolves the device address.
 static __device__ __align__(256) double g_noalloc_gv[4 * (size_t)EEC_NOALLOC_MAX_DEV];
 
-constexpr int kT = 6;
-
-struct T6 {
+// Value plus K forward-mode tangents.
+template <int K>
+struct Tan {
   double v;
-  double d[kT];
-  __device__ __forceinline__ T6() : v(0.0) {
+  double d[K];
+  __device__ __forceinline__ Tan() : v(0.0) {
 #pragma unroll
-    for (int i = 0; i < kT; ++i) d[i] = 0.0;
+    for (int i = 0; i < K; ++i) d[i] = 0.0;
   }
-  __device__ __forceinline__ T6(double c) : v(c) {  // NOLINT: constants convert implicitly
+  __device__ __forceinline__ Tan(double c) : v(c) {  // NOLINT: constants convert implicitly
 #pragma unroll
-    for (int i = 0; i < kT; ++i) d[i] = 0.0;
+    for (int i = 0; i < K; ++i) d[i] = 0.0;
   }
 };
 
-__device__ __forceinline__ double sval(const T6& a) { return a.v; }
+template <int K>
+__device__ __forceinline__ double sval(const Tan<K>& a) { return a.v; }
 
-__device__ __forceinline__ T6 operator+(const T6& a, const T6& b) {
-  T6 r; r.v = a.v + b.v;
+template <int K>
+__device__ __forceinline__ Tan<K> operator+(const Tan<K>& a, const Tan<K>& b) {
+  Tan<K> r; r.v = a.v + b.v;
 #pragma unroll
-  for (int i = 0; i < kT; ++i) r.d[i] = a.d[i] + b.d[i];
+  for (int i = 0; i < K; ++i) r.d[i] = a.d[i] + b.d[i];
   return r;
 }
-__device__ __forceinline__ T6 operator-(const T6& a, const T6& b) {
-  T6 r; r.v = a.v - b.v;
+template <int K>
+__device__ __forceinline__ Tan<K> operator-(const Tan<K>& a, const Tan<K>& b) {
+  Tan<K> r; r.v = a.v - b.v;
 #pragma unroll
-  for (int i = 0; i < kT; ++i) r.d[i] = a.d[i] - b.d[i];
+  for (int i = 0; i < K; ++i) r.d[i] = a.d[i] - b.d[i];
   return r;
 }
-__device__ __forceinline__ T6 operator-(const T6& a) {
-  T6 r; r.v = -a.v;
+template <int K>
+__device__ __forceinline__ Tan<K> operator-(const Tan<K>& a) {
+  Tan<K> r; r.v = -a.v;
 #pragma unroll
-  for (int i = 0; i < kT; ++i) r.d[i] = -a.d[i];
+  for (int i = 0; i < K; ++i) r.d[i] = -a.d[i];
   return r;
 }
-__device__ __forceinline__ T6 operator*(const T6& a, const T6& b) {
-  T6 r; r.v = a.v * b.v;
+template <int K>
+__device__ __forceinline__ Tan<K> operator*(const Tan<K>& a, const Tan<K>& b) {
+  Tan<K> r; r.v = a.v * b.v;
 #pragma unroll
-  for (int i = 0; i < kT; ++i) r.d[i] = fma(a.d[i], b.v, a.v * b.d[i]);
+  for (int i = 0; i < K; ++i) r.d[i] = fma(a.d[i], b.v, a.v * b.d[i]);
   return r;
 }
-__device__ __forceinline__ T6 operator+(const T6& a, double b) { T6 r = a; r.v += b; return r; }
-__device__ __forceinline__ T6 operator+(double a, const T6& b) { T6 r = b; r.v += a; return r; }
-__device__ __forceinline__ T6 operator-(const T6& a, double b) { T6 r = a; r.v -= b; return r; }
-__device__ __forceinline__ T6 operator-(double a, const T6& b) { return -(b - a); }
-__device__ __forceinline__ T6 operator*(const T6& a, double b) {
-  T6 r; r.v = a.v * b;
+template <int K>
+__device__ __forceinline__ Tan<K> operator+(const Tan<K>& a, double b) { Tan<K> r = a; r.v += b; return r; }
+template <int K>
+__device__ __forceinline__ Tan<K> operator+(double a, const Tan<K>& b) { Tan<K> r = b; r.v += a; return r; }
+template <int K>
+__device__ __forceinline__ Tan<K> operator-(const Tan<K>& a, double b) { Tan<K> r = a; r.v -= b; return r; }
+template <int K>
+__device__ __forceinline__ Tan<K> operator-(double a, const Tan<K>& b) { return -(b - a); }
+template <int K>
+__device__ __forceinline__ Tan<K> operator*(const Tan<K>& a, double b) {
+  Tan<K> r; r.v = a.v * b;
 #pragma unroll
-  for (int i = 0; i < kT; ++i) r.d[i] = a.d[i] * b;
+  for (int i = 0; i < K; ++i) r.d[i] = a.d[i] * b;
   return r;
 }
-__device__ __forceinline__ T6 operator*(double a, const T6& b) { return b * a; }
+template <int K>
+__device__ __forceinline__ Tan<K> operator*(double a, const Tan<K>& b) { return b * a; }
 
 // d(1/a) = -da / a^2
-__device__ __forceinline__ T6 rcp(const T6& a) {
-  T6 r; r.v = 1.0 / a.v;
+template <int K>
+__device__ __forceinline__ Tan<K> rcp(const Tan<K>& a) {
+  Tan<K> r; r.v = 1.0 / a.v;
   const double m = -r.v * r.v;
 #pragma unroll
-  for (int i = 0; i < kT; ++i) r.d[i] = m * a.d[i];
+  for (int i = 0; i < K; ++i) r.d[i] = m * a.d[i];
   return r;
 }
 // d(a^-1/2) = -a^-3/2 da / 2
-__device__ __forceinline__ T6 rsqrt_(const T6& a) {
-  T6 r; r.v = ::rsqrt(a.v);
+template <int K>
+__device__ __forceinline__ Tan<K> rsqrt_(const Tan<K>& a) {
+  Tan<K> r; r.v = ::rsqrt(a.v);
   const double m = -0.5 * r.v * r.v * r.v;
 #pragma unroll
-  for (int i = 0; i < kT; ++i) r.d[i] = m * a.d[i];
+  for (int i = 0; i < K; ++i) r.d[i] = m * a.d[i];
   return r;
 }
-__device__ __forceinline__ T6 exp_(const T6& a) {
-  T6 r; r.v = ::exp(a.v);
+template <int K>
+__device__ __forceinline__ Tan<K> exp_(const Tan<K>& a) {
+  Tan<K> r; r.v = fm_exp(a.v);
 #pragma unroll
-  for (int i = 0; i < kT; ++i) r.d[i] = r.v * a.d[i];
+  for (int i = 0; i < K; ++i) r.d[i] = r.v * a.d[i];
   return r;
 }
-__device__ __forceinline__ T6 expm1_(const T6& a) {
-  T6 r; r.v = ::expm1(a.v);
-  const double e = r.v + 1.0;
+// log(1 + a) for a in [0, 1], given inv_y = 1 / (1 + a)
+template <int K>
+__device__ __forceinline__ Tan<K> log1p_(const Tan<K>& a, const Tan<K>& inv_y) {
+  Tan<K> r; r.v = fm_log1p01(a.v, inv_y.v);
 #pragma unroll
-  for (int i = 0; i < kT; ++i) r.d[i] = e * a.d[i];
+  for (int i = 0; i < K; ++i) r.d[i] = inv_y.v * a.d[i];
   return r;
 }
-__device__ __forceinline__ T6 log1p_(const T6& a) {
-  T6 r; r.v = ::log1p(a.v);
-  const double m = 1.0 / (1.0 + a.v);
-#pragma unroll
-  for (int i = 0; i < kT; ++i) r.d[i] = m * a.d[i];
-  return r;
+
+using T2 = Tan<2>;
+
+// Junction pieces without the GMIN leak: IjI = Isat (explim(z) - 1), gjI = dIjI/dv, and
+// gj2 = d^2 IjI / dv^2 (zero on the linear continuation above z = 40).
+__device__ __forceinline__ void junction2(const CardK& c, double Isat, double v, double& IjI,
+                                          double& gjI, double& gj2) {
+  const double z = v * c.inv_Vt;
+  const bool over = z > 40.0;
+  const double zc = over ? 40.0 : z;
+  const double em1 = fm_expm1(zc);
+  const double ez = em1 + 1.0;
+  IjI = Isat * (em1 + ez * (over ? z - 40.0 : 0.0));
+  gjI = Isat * c.inv_Vt * ez;
+  gj2 = over ? 0.0 : gjI * c.inv_Vt;
 }
 
 constexpr int kBwdBlock = 128;
@@ -129,50 +161,102 @@ __global__ void __launch_bounds__(kBwdBlock) k_bwd_device(DevTopo T, const doubl
   const long long N = T.N;
   const int4 ti = __ldg(T.tidx + k);
   const int idx[4] = {ti.x, ti.y, ti.z, ti.w};
-  double Vv[4];
-  T6 V[4];
+  double V[4];
 #pragma unroll
-  for (int t = 0; t < 4; ++t) {
-    Vv[t] = idx[t] >= 0 ? __ldg(x + idx[t]) : __ldg(T.vfix + ~idx[t]);
-    V[t] = T6(Vv[t]);
-    V[t].d[t] = 1.0;
-  }
+  for (int t = 0; t < 4; ++t) V[t] = idx[t] >= 0 ? __ldg(x + idx[t]) : __ldg(T.vfix + ~idx[t]);
   const int meta = __ldg(T.meta + k);
-  const CardK& c = T.cards[meta >> 1];
-  const double pp = (meta & 1) ? -1.0 : 1.0;
-  T6 W(__ldg(T.W + k)), L(__ldg(T.L + k));
-  W.d[4] = 1.0;
-  L.d[5] = 1.0;
-  const PrmS<T6> P = derive_params<T6>(c, W, L);
-  EvalOut<T6> o;
-  ees_l1<T6, false>(c, pp, P, V, o);
-  double ds[kT];
-#pragma unroll
-  for (int j = 0; j < kT; ++j) ds[j] = 0.0;
+  const CardK& c = T.cards[meta >> 2];
+  const double p = (meta & 1) ? -1.0 : 1.0;
+  const double W = __ldg(T.W + k), L = __ldg(T.L + k);
+
+  // weights: wb by terminal (rows d, s, b), cw[t][u] = gA[slot] + wb_t V_u over free (t, u)
   const int term[3] = {0, 2, 3};
+  double wb[4] = {0.0, 0.0, 0.0, 0.0};
+  double cw[4][4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) cw[t][u] = 0.0;
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
-    const int row = idx[term[r]];
-    if (row < 0) continue;
-    const double wb = __ldg(gb + row);
+    const int t = term[r];
+    if (idx[t] < 0) continue;
+    wb[t] = __ldg(gb + idx[t]);
 #pragma unroll
-    for (int j = 0; j < kT; ++j) ds[j] -= wb * o.I[term[r]].d[j];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      if (idx[u] < 0) continue;
-      const int s = __ldg(T.slot + (4 * r + u) * N + k);
-      const double wa = __ldg(gA + s);
-      const double wv = wa + wb * Vv[u];
-#pragma unroll
-      for (int j = 0; j < kT; ++j) ds[j] = fma(wv, o.G[r][u].d[j], ds[j]);
-      ds[u] = fma(wb, o.G[r][u].v, ds[u]);
-    }
+    for (int u = 0; u < 4; ++u)
+      if (idx[u] >= 0) cw[t][u] = fma(wb[t], V[u], __ldg(gA + __ldg(T.slot + (4 * r + u) * N + k)));
   }
+
+  // (1) mode frame
+  const bool fwd = p * (V[0] - V[2]) >= 0.0;
+  const int iD = fwd ? 0 : 2, iS = fwd ? 2 : 0;
+  const double m = fwd ? 1.0 : -1.0;
+  const double vgs = p * (V[1] - V[iS]), vds = p * (V[iD] - V[iS]), vbs = p * (V[3] - V[iS]);
+
+  // channel: s_ch = m (g . w) - p m omega Ids with w in mode-frame coordinates
+  double wt[4];
 #pragma unroll
-  for (int t = 0; t < 4; ++t) T.gv[t * N + k] = ds[t];
+  for (int u = 0; u < 4; ++u) wt[u] = cw[0][u] - cw[2][u];
+  const double omega = wb[0] - wb[2];
+  const double w0 = wt[1] - wt[iS], w1 = wt[iD] - wt[iS], w2 = wt[3] - wt[iS];
+  T2 Lt(L);
+  Lt.d[1] = 1.0;
+  const PrmS<T2> P = derive_params<T2>(c, T2(W), Lt);
+  T2 vgs2(vgs), vds2(vds), vbs2(vbs);
+  vgs2.d[0] = w0;
+  vds2.d[0] = w1;
+  vbs2.d[0] = w2;
+  T2 sqs, Vthb, dVth, Ab, dAb;
+  body_terms<T2>(c, vbs2, sqs, Vthb, dVth, Ab, dAb);
+  Chan<T2> ch;
+  channel<T2>(c, P, vgs2, vds2, Vthb, dVth, Ab, dAb, ch);
+  const double gm = ch.gm.v, gds = ch.gds.v, gmb = ch.gmb.v, Ids = ch.Ids.v;
+  const double pmw = p * m * omega;
+  const double s_ch = m * (gm * w0 + gds * w1 + gmb * w2) - pmw * Ids;
+  const double dv0 = m * ch.gm.d[0] - pmw * gm;    // d s_ch / d vgs (H w is symmetric in w)
+  const double dv1 = m * ch.gds.d[0] - pmw * gds;  // d s_ch / d vds
+  const double dv2 = m * ch.gmb.d[0] - pmw * gmb;  // d s_ch / d vbs
+  double dW = s_ch / W;
+  const double dL = m * (ch.gm.d[1] * w0 + ch.gds.d[1] * w1 + ch.gmb.d[1] * w2) - pmw * ch.Ids.d[1];
+  double g[4];
+  g[1] = p * dv0;
+  g[3] = p * dv2;
+  g[iD] = p * dv1;
+  g[iS] = -p * (dv0 + dv1 + dv2);
+
+  // junctions (physical d-b and s-b): s_j = kappa gj - rho Ij
+  const double Isat = P.Isat.v;
+  double IjdI, gjdI, gjd2, IjsI, gjsI, gjs2;
+  const double vbd = p * (V[3] - V[0]), vbsj = p * (V[3] - V[2]);
+  junction2(c, Isat, vbd, IjdI, gjdI, gjd2);
+  junction2(c, Isat, vbsj, IjsI, gjsI, gjs2);
+  const double gjd = gjdI + c.GMIN, gjs = gjsI + c.GMIN;
+  const double kd = cw[0][0] - cw[0][3] - cw[3][0] + cw[3][3];
+  const double rd = p * (wb[3] - wb[0]);
+  const double ddv = kd * gjd2 - rd * gjd;
+  g[0] -= p * ddv;
+  g[3] += p * ddv;
+  const double ks = cw[2][2] - cw[2][3] - cw[3][2] + cw[3][3];
+  const double rs = p * (wb[3] - wb[2]);
+  const double dsv = ks * gjs2 - rs * gjs;
+  g[2] -= p * dsv;
+  g[3] += p * dsv;
+  dW += (kd * gjdI - rd * IjdI + ks * gjsI - rs * IjsI) / W;
+
+  // direct term d(sum_r wb_r G_ru V_u)/dV_u = sum_r wb_r G_ru
+  const double gsum = gm + gds + gmb;
+  const double cd[4] = {fwd ? gds : gsum, fwd ? gm : -gm, fwd ? -gsum : -gds, fwd ? gmb : -gmb};
+  const double Gd[4] = {cd[0] + gjd, cd[1], cd[2], cd[3] - gjd};
+  const double Gs[4] = {-cd[0], -cd[1], gjs - cd[2], -cd[3] - gjs};
+  const double Gb[4] = {-gjd, 0.0, -gjs, gjd + gjs};
+#pragma unroll
+  for (int u = 0; u < 4; ++u) g[u] += wb[0] * Gd[u] + wb[2] * Gs[u] + wb[3] * Gb[u];
+
+#pragma unroll
+  for (int t = 0; t < 4; ++t) T.gv[t * N + k] = g[t];
   const int od = __ldg(T.orig + k);
-  gW[od] = ds[4];
-  gL[od] = ds[5];
+  gW[od] = dW;
+  gL[od] = dL;
 }
 
 __global__ void k_bwd_gather(DevTopo T, double* __restrict__ gx) {

@@ -485,7 +485,9 @@ int eec_create(eec_ctx** out, const eec_options* opt) {
   if (!c) return EEC_ENOMEM;
   c->opt = opt ? *opt : eec_default_options();
   if (c->opt.variant < EEC_VARIANT_AUTO || c->opt.variant >= EEC_N_VARIANTS ||
-      c->opt.conflict_rule < 0 || c->opt.conflict_rule > 2 || c->opt.block < 0) {
+      c->opt.conflict_rule < 0 || c->opt.conflict_rule > 2 ||
+      !(c->opt.block == 0 || c->opt.block == 8 || c->opt.block == 16 ||
+        (c->opt.block % 32 == 0 && c->opt.block <= 128))) {
     delete c;
     return EEC_EINVAL;
   }
@@ -723,7 +725,8 @@ int eec_build_scatter(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_out) {
   std::vector<long long> sk(N);
   for (int k = 0; k < N; ++k) {
     const long long colr = c->colored ? c->color[k] : 0;
-    const long long meta = ((long long)c->mid[k] << 1) | (c->type[k] < 0 ? 1 : 0);
+    const long long sbf = (c->fixed[c->dn[4 * k + 2]] && c->fixed[c->dn[4 * k + 3]]) ? 1 : 0;
+    const long long meta = ((long long)c->mid[k] << 2) | (sbf << 1) | (c->type[k] < 0 ? 1 : 0);
     sk[k] = (colr << 32) | meta;
   }
   c->perm.resize(N);
@@ -748,7 +751,8 @@ int eec_build_scatter(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_out) {
       ti[t] = c->unk[node] >= 0 ? c->unk[node] : ~fidx[node];
     }
     tidx[p] = make_int4(ti[0], ti[1], ti[2], ti[3]);
-    meta[p] = (c->mid[k] << 1) | (c->type[k] < 0 ? 1 : 0);
+    const int sbf = (c->fixed[c->dn[4 * k + 2]] && c->fixed[c->dn[4 * k + 3]]) ? 1 : 0;
+    meta[p] = (c->mid[k] << 2) | (sbf << 1) | (c->type[k] < 0 ? 1 : 0);
     Wp[p] = c->W[k];
     Lp[p] = c->L[k];
     for (int r = 0; r < 3; ++r) {
@@ -869,7 +873,8 @@ int eec_build_scatter(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_out) {
   if ((rc = dupload(c, &d.tidx, tidx)) || (rc = dupload(c, &d.meta, meta)) ||
       (rc = dupload(c, &d.orig, orig)) || (rc = dupload(c, &d.slot, slot)) ||
       (rc = dupload(c, &d.W, Wp)) || (rc = dupload(c, &d.L, Lp)) ||
-      (rc = dalloc(c, &d.prm, (size_t)kNPrm * N)) || (rc = dupload(c, &d.vfix, vtab)) ||
+      (rc = dalloc(c, &d.prm, (size_t)kNPrm * N)) || (rc = dalloc(c, &d.bodyk, (size_t)7 * N)) ||
+      (rc = dupload(c, &d.vfix, vtab)) ||
       (rc = dupload(c, &d.cards, c->cardk)) || (rc = dupload(c, &d.Alin, Alin)) ||
       (rc = dupload(c, &d.blin, blin)) || (rc = dupload(c, &d.gat_ptr, gptr)) ||
       (rc = dupload(c, &d.gat_src, gsrc)) || (rc = dupload(c, &d.inc_ptr, iptr)) ||
@@ -1091,6 +1096,27 @@ int eec_status(eec_ctx* c, void* stream) {
   CUDA_TRY(c, cudaMemset(c->d_status, 0, sizeof(int)));
   if (st & kStatusTimeout) return fail(c, EEC_ETIMEOUT, "a grid barrier wait ran past its limit");
   if (st & kStatusNumeric) return fail(c, EEC_ENUMERIC, "non-finite value in an evaluated device");
+  return EEC_OK;
+}
+
+int eec_math_check(int32_t fn, int64_t n, const double* x, double* ours, double* ref,
+                   void* stream) {
+  if (fn < 0 || fn > 2 || n < 0 || (n > 0 && (!x || !ours || !ref))) return EEC_EINVAL;
+  return math_check(fn, n, x, ours, ref, static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? EEC_OK
+             : EEC_ECUDA;
+}
+
+int eec_test_barrier_timeout(eec_ctx* c, const double* x, double* A, double* b, void* stream) {
+  int rc = check_built(c);
+  if (rc) return rc;
+  if (!c->colored || c->C < 2) return fail(c, EEC_ESTATE, "needs a coloured context with >= 2 colours");
+  if (!x || !A || !b) return fail(c, EEC_EINVAL, "NULL x, A or b");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CUDA_TRY(c, cudaMemcpyAsync(A, c->d.Alin, sizeof(double) * c->nnz, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(c, cudaMemcpyAsync(b, c->d.blin, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(c, launch_persistent(c->d, c->d_coff, c->C, x, A, b, nullptr, 0, c->persist_grid, 0, s,
+                                /*absent_block=*/0));
   return EEC_OK;
 }
 

@@ -1,0 +1,105 @@
+// Table-driven FP64 elementary functions for the model evaluation.
+//
+// On GB300 every FP64 instruction costs about 64 FP32 instruction slots, and the evaluation is
+// bound by the FP64 pipe, so the three transcendental calls of a device (exp and log1p in the
+// effective overdrive, expm1 in each junction) are worth specialising. The methods are P. T. P.
+// Tang's table-driven algorithms:
+//   exp   — "Table-driven implementation of the exponential function in IEEE floating-point
+//           arithmetic", ACM TOMS 15(2), 1989: x = (64 m + j) ln2/64 + r with |r| <= ln2/128
+//           (Cody–Waite reduction with a two-part ln2/64), exp(x) = 2^m 2^(j/64) e^r, e^r - 1 by
+//           its Taylor polynomial;
+//   expm1 — "Table-driven implementation of the expm1 function ...", ACM TOMS 18(2), 1992: a
+//           Taylor polynomial for small |x|, otherwise the exp reduction with 2^(j/64) held as a
+//           double-double so that (2^m T - 1) is formed without losing the leading bits;
+//   log1p — "Table-driven implementation of the logarithm function ...", ACM TOMS 16(4), 1990,
+//           specialised to 1 + e with e in [0, 1]: y = 1 + e, F = 1 + j/128 nearest to y,
+//           u = (y - F)/F, log y = log F + log1p(u) by its Taylor polynomial, plus the rounding
+//           error of 1 + e carried as c / y.
+// Polynomial coefficients are Taylor coefficients; tables come from gen_tables.py. Accuracy
+// (checked against CUDA's functions by the GPU tests through eec_math_check) is within a few
+// units in the last place over the domains used here.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "eec_tables.h"
+
+namespace eec {
+
+// y * 2^m by adding m to the exponent field (y and the result must be normal, y != 0).
+__device__ __forceinline__ double fm_scale2(double y, int m) {
+  return __hiloint2double(__double2hiint(y) + (m << 20), __double2loint(y));
+}
+
+// Argument reduction shared by exp and expm1: x = (64 m + j) ln2/64 + r.
+__device__ __forceinline__ double fm_reduce(double x, int& j, int& m) {
+  const double s = fma(x, kInvLn2x64, 0x1.8p52);   // 1.5 * 2^52 shifter: rounds x*64/ln2
+  const int n = __double2loint(s);
+  const double nf = s - 0x1.8p52;
+  j = n & 63;
+  m = n >> 6;
+  return fma(-nf, kLn2o64Lo, fma(-nf, kLn2o64Hi, x));
+}
+
+// e^r - 1 for |r| <= ln2/128: Taylor polynomial through r^5 (truncation 1.7e-17, below 0.3 ulp
+// of e^r; enough for exp, whose result is near 1).
+__device__ __forceinline__ double fm_em1_small(double r) {
+  const double q = fma(r, fma(r, fma(r, fma(r, 1.0 / 120.0, 1.0 / 24.0), 1.0 / 6.0), 0.5), 1.0);
+  return r * q;
+}
+
+// The same through r^6 (truncation 3e-20): expm1 results can be as small as 2^-6, so the
+// polynomial error must stay below their ulp.
+__device__ __forceinline__ double fm_em1_small6(double r) {
+  const double q = fma(r, fma(r, fma(r, fma(r, fma(r, 1.0 / 720.0, 1.0 / 120.0), 1.0 / 24.0),
+                                       1.0 / 6.0), 0.5), 1.0);
+  return r * q;
+}
+
+__device__ __forceinline__ double fm_exp(double x) {
+  if (!(x > -707.0 && x < 709.0)) return ::exp(x);   // subnormal / overflow range, NaN
+  int j, m;
+  const double r = fm_reduce(x, j, m);
+  const double p = fm_em1_small(r);
+  const double th = __ldg(kExp2Hi + j);
+  const double y = fma(th, p, __ldg(kExp2Lo + j)) + th;   // 2^(j/64) e^r in [0.99, 2)
+  return fm_scale2(y, m);
+}
+
+__device__ __forceinline__ double fm_expm1(double x) {
+  if (fabs(x) < 0x1p-6) {
+    // x + x^2/2 + ... + x^7/5040 (truncation below 2^-59 relative)
+    const double q = fma(x, fma(x, fma(x, fma(x, fma(x, 1.0 / 5040.0, 1.0 / 720.0), 1.0 / 120.0),
+                                       1.0 / 24.0), 1.0 / 6.0), 0.5);
+    return fma(x * x, q, x);
+  }
+  if (x < -38.0) return -1.0;   // e^x < 2^-54: -1 + e^x rounds to -1
+  if (!(x < 709.0)) return ::expm1(x);
+  int j, m;
+  const double r = fm_reduce(x, j, m);
+  const double p = fm_em1_small6(r);
+  const double T = fm_scale2(__ldg(kExp2Hi + j), m);
+  const double tl = __ldg(kExp2Lo + j);
+  const double Tl = (__double2hiint(tl) == 0 && __double2loint(tl) == 0) ? 0.0 : fm_scale2(tl, m);
+  return (T - 1.0) + fma(T, p, Tl);
+}
+
+// log(1 + e) for e in [0, 1]; inv_y must be 1 / (1 + e) rounded (the caller needs it anyway).
+__device__ __forceinline__ double fm_log1p01(double e, double inv_y) {
+  if (e < 0x1p-7) {
+    // e - e^2/2 + ... + e^7/7 (truncation below 2^-52 relative)
+    const double q = fma(e, fma(e, fma(e, fma(e, fma(e, 1.0 / 7.0, -1.0 / 6.0), 0.2), -0.25),
+                                1.0 / 3.0), -0.5);
+    return fma(e * e, q, e);
+  }
+  const double y = 1.0 + e;                        // (1, 2]
+  const double c = e - (y - 1.0);                  // rounding error of y, exact
+  const double s = fma(y, 128.0, 0x1.8p52);        // round(128 y) in [129, 256]
+  const int jj = __double2loint(s) - 128;          // F = 1 + jj/128, jj in [1, 128]
+  const double u = (y - __ldg(kF + jj)) * __ldg(kInvF + jj);   // |u| <= 2^-8; y - F exact
+  const double q = fma(u, fma(u, fma(u, fma(u, -1.0 / 6.0, 0.2), -0.25), 1.0 / 3.0), -0.5);
+  const double pu = fma(u * u, q, u);              // log1p(u), truncation below 2^-59
+  return __ldg(kLogFHi + jj) + fma(c, inv_y, __ldg(kLogFLo + jj) + pu);
+}
+
+}  // namespace eec

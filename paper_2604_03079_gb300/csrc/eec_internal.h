@@ -37,12 +37,13 @@ struct DevTopo {
   int n;            // unknowns
   long long nnz;    // CSR nonzeros
   int4* tidx;       // [N] terminal -> unknown (>= 0) or ~fixed-table index (< 0)
-  int* meta;        // [N] (card << 1) | (type < 0)
+  int* meta;        // [N] (card << 2) | (source and body source-held) << 1 | (type < 0)
   int* orig;        // [N] original device index of each position
   int* slot;        // [kNSlot][N] CSR value index or -1
   double* W;        // [N]
   double* L;        // [N]
   double* prm;      // [kNPrm][N]
+  double* bodyk;    // [kNBody][N] x-independent body/source-junction terms (flagged devices)
   double* vfix;     // [n_fixed] voltages of source-held nodes
   CardK* cards;     // [n_cards]
   double* Alin;     // [nnz]
@@ -72,9 +73,11 @@ cudaError_t launch_update_params(const DevTopo& T, const double* W_dev, const do
                                  cudaStream_t s);
 cudaError_t launch_eval(const DevTopo& T, int mode, int begin, int end, const double* x,
                         double* A, double* b, double* q, int block, int dbg, cudaStream_t s);
+// absent_block >= 0 is a test hook: that block skips every grid barrier, so the other blocks'
+// bounded waits expire and the status word records a timeout.
 cudaError_t launch_persistent(const DevTopo& T, const int* color_off_dev, int n_colors,
                               const double* x, double* A, double* b, double* q, int block,
-                              int grid, int dbg, cudaStream_t s);
+                              int grid, int dbg, cudaStream_t s, int absent_block = -1);
 int persistent_max_blocks_per_sm(int block, bool want_q);
 cudaError_t launch_gather(const DevTopo& T, double* A, double* b, cudaStream_t s);
 cudaError_t launch_stamp_buffer(const DevTopo& T, int begin, int end, double* A, double* b,
@@ -82,6 +85,8 @@ cudaError_t launch_stamp_buffer(const DevTopo& T, int begin, int end, double* A,
 cudaError_t launch_bwd(const DevTopo& T, const double* x, const double* gA, const double* gb,
                        double* gx, double* gW, double* gL, int block, cudaStream_t s);
 cudaError_t fp64_peak(int iters, int blocks_per_sm, double* flops);
+cudaError_t math_check(int fn, long long n, const double* x, double* ours, double* ref,
+                       cudaStream_t s);
 // Backward with its terminal-gradient scratch in the library's fixed array (no allocation).
 cudaError_t launch_bwd_noalloc(const DevTopo& T, const double* x, const double* gA,
                                const double* gb, double* gx, double* gW, double* gL,

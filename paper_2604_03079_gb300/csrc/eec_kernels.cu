@@ -39,9 +39,10 @@ constexpr unsigned long long kBarrierLimitNs = 1000000000ull;  // 1 s
 
 // Grid-wide barrier for a co-resident (cooperative) grid. Every wait is bounded: after
 // kBarrierLimitNs the waiting block records kStatusTimeout and the whole grid returns false.
-__device__ __forceinline__ bool grid_sync(unsigned* bar, int* status) {
+__device__ __forceinline__ bool grid_sync(unsigned* bar, int* status, int absent_block) {
   __shared__ int fail;
   __syncthreads();
+  if (absent_block == (int)blockIdx.x) return true;  // test hook: this block never arrives
   if (threadIdx.x == 0) {
     fail = 0;
     const unsigned nblocks = gridDim.x * gridDim.y * gridDim.z;
@@ -90,6 +91,7 @@ template <int MODE, bool WANT_Q>
 __device__ __forceinline__ void eval_one(const DevTopo& T, int k, const double* __restrict__ x,
                                          double* A, double* b, double* __restrict__ q,
                                          int dbg) {
+  const long long N = T.N;
   const int4 ti = __ldg(T.tidx + k);
   const int idx[4] = {ti.x, ti.y, ti.z, ti.w};
   double V[4];
@@ -97,11 +99,23 @@ __device__ __forceinline__ void eval_one(const DevTopo& T, int k, const double* 
   for (int t = 0; t < 4; ++t)
     V[t] = idx[t] >= 0 ? __ldg(x + idx[t]) : __ldg(T.vfix + ~idx[t]);
   const int meta = __ldg(T.meta + k);
-  const CardK& c = T.cards[meta >> 1];
-  const double pp = (meta & 1) ? -1.0 : 1.0;
+  const CardK& c = T.cards[meta >> 2];
+  const unsigned long long psb = (meta & 1) ? kSignBit : 0ull;
+  const bool sbf = (meta >> 1) & 1;
   const PrmS<double> P = load_prm(T, k);
+  BodyK bk;
+  if (sbf) {
+    const double* q0 = T.bodyk + k;
+    bk.sqs = __ldg(q0);
+    bk.Vthb = __ldg(q0 + N);
+    bk.dVth_dvbs = __ldg(q0 + 2 * N);
+    bk.Ab = __ldg(q0 + 3 * N);
+    bk.dAb_dvbs = __ldg(q0 + 4 * N);
+    bk.Ijs = __ldg(q0 + 5 * N);
+    bk.gjs = __ldg(q0 + 6 * N);
+  }
   EvalOut<double> o;
-  ees_l1<double, WANT_Q>(c, pp, P, V, o);
+  ees_l1<double, WANT_Q>(c, psb, P, V, o, sbf, &bk);
 
   const int term[3] = {0, 2, 3};
   double bc[3];
@@ -113,7 +127,6 @@ __device__ __forceinline__ void eval_one(const DevTopo& T, int k, const double* 
       if (idx[u] >= 0) s = fma(o.G[r][u], V[u], s);
     bc[r] = s;
   }
-  const long long N = T.N;
   if (MODE == MODE_BUFFER) {
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
@@ -163,17 +176,26 @@ __global__ void __launch_bounds__(kEvalBlock) k_eval(DevTopo T, int begin, int e
     eval_one<MODE, WANT_Q>(T, k, x, A, b, q, dbg);
 }
 
+// One co-resident grid walks the colours; a colour's devices are dealt out in 32-device chunks
+// round-robin over the blocks first (chunk i -> block i mod grid, then the next warp of that
+// block), so a small colour occupies one warp on each of many SMs instead of whole blocks on a
+// few. The FP64 pipe of an SM is narrow; spreading the warps is what shortens a colour.
 template <bool WANT_Q>
 __global__ void __launch_bounds__(kEvalBlock) k_persistent(DevTopo T, const int* __restrict__ coff,
                                                            int C, const double* __restrict__ x,
                                                            double* A, double* b, double* q,
-                                                           int dbg) {
+                                                           int dbg, int absent_block) {
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int wpb = blockDim.x >> 5;
   for (int c = 0; c < C; ++c) {
-    const int end = __ldg(coff + c + 1);
-    for (int k = __ldg(coff + c) + blockIdx.x * blockDim.x + threadIdx.x; k < end;
-         k += gridDim.x * blockDim.x)
-      eval_one<MODE_RMW, WANT_Q>(T, k, x, A, b, q, dbg);
-    if (c + 1 < C && !grid_sync(T.bar, T.status)) return;
+    const int begin = __ldg(coff + c), end = __ldg(coff + c + 1);
+    const int nch = (end - begin + 31) >> 5;
+    for (int ch = blockIdx.x + gridDim.x * warp; ch < nch; ch += gridDim.x * wpb) {
+      const int k = begin + (ch << 5) + lane;
+      if (k < end) eval_one<MODE_RMW, WANT_Q>(T, k, x, A, b, q, dbg);
+    }
+    if (c + 1 < C && !grid_sync(T.bar, T.status, absent_block)) return;
   }
 }
 
@@ -185,9 +207,26 @@ __global__ void k_params(DevTopo T, const double* __restrict__ Wo, const double*
     T.W[k] = Wo[od];
     T.L[k] = Lo[od];
   }
-  const CardK& c = T.cards[T.meta[k] >> 1];
+  const int meta = T.meta[k];
+  const CardK& c = T.cards[meta >> 2];
   const PrmS<double> P = derive_params<double>(c, T.W[k], T.L[k]);
   const long long N = T.N;
+  if ((meta >> 1) & 1) {  // source and body source-held: hoist the x-independent terms
+    const int4 ti = T.tidx[k];
+    const unsigned long long psb = (meta & 1) ? kSignBit : 0ull;
+    const double vbs = flip(T.vfix[~ti.w] - T.vfix[~ti.z], psb);
+    double sqs, Vthb, dVth, Ab, dAb, Ijs, gjs;
+    body_terms<double>(c, vbs, sqs, Vthb, dVth, Ab, dAb);
+    junction<double>(c, P.Isat, vbs, Ijs, gjs);
+    double* q0 = T.bodyk + k;
+    q0[0] = sqs;
+    q0[N] = Vthb;
+    q0[2 * N] = dVth;
+    q0[3 * N] = Ab;
+    q0[4 * N] = dAb;
+    q0[5 * N] = Ijs;
+    q0[6 * N] = gjs;
+  }
   T.prm[P_BETA0 * N + k] = P.beta0;
   T.prm[P_CE * N + k] = P.cE;
   T.prm[P_INV_CE * N + k] = P.inv_cE;
@@ -242,6 +281,23 @@ __global__ void k_dfma(double* out, int iters, double a, double c) {
   out[blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
 }
 
+__global__ void k_math_check(int fn, long long n, const double* __restrict__ x, double* ours,
+                             double* ref) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = x[i];
+  if (fn == 0) {
+    ours[i] = fm_exp(v);
+    ref[i] = ::exp(v);
+  } else if (fn == 1) {
+    ours[i] = fm_expm1(v);
+    ref[i] = ::expm1(v);
+  } else {
+    ours[i] = fm_log1p01(v, 1.0 / (1.0 + v));
+    ref[i] = ::log1p(v);
+  }
+}
+
 int grid_for(long long n, int block) {
   long long g = (n + block - 1) / block;
   if (g < 1) g = 1;
@@ -264,24 +320,31 @@ cudaError_t launch_update_params(const DevTopo& T, const double* W_dev, const do
   return cudaGetLastError();
 }
 
+// Block size for a launch over n devices: small launches (one colour of a high-conflict circuit)
+// use one warp per block so the blocks spread over many SMs; large ones use kEvalBlock.
+int eval_block(long long n, int block) {
+  if (block > 0) return block;
+  return n < 152LL * kEvalBlock ? 32 : kEvalBlock;
+}
+
 cudaError_t launch_eval(const DevTopo& T, int mode, int begin, int end, const double* x,
                         double* A, double* b, double* q, int block, int dbg, cudaStream_t s) {
   if (end <= begin) return cudaSuccess;
-  (void)block;
-  const int g = grid_for(end - begin, kEvalBlock);
+  const int B = eval_block(end - begin, block);
+  const int g = grid_for(end - begin, B);
   const bool wq = q != nullptr;
   switch (mode) {
     case MODE_RMW:
-      if (wq) k_eval<MODE_RMW, true><<<g, kEvalBlock, 0, s>>>(T, begin, end, x, A, b, q, dbg);
-      else k_eval<MODE_RMW, false><<<g, kEvalBlock, 0, s>>>(T, begin, end, x, A, b, q, dbg);
+      if (wq) k_eval<MODE_RMW, true><<<g, B, 0, s>>>(T, begin, end, x, A, b, q, dbg);
+      else k_eval<MODE_RMW, false><<<g, B, 0, s>>>(T, begin, end, x, A, b, q, dbg);
       break;
     case MODE_ATOMIC:
-      if (wq) k_eval<MODE_ATOMIC, true><<<g, kEvalBlock, 0, s>>>(T, begin, end, x, A, b, q, dbg);
-      else k_eval<MODE_ATOMIC, false><<<g, kEvalBlock, 0, s>>>(T, begin, end, x, A, b, q, dbg);
+      if (wq) k_eval<MODE_ATOMIC, true><<<g, B, 0, s>>>(T, begin, end, x, A, b, q, dbg);
+      else k_eval<MODE_ATOMIC, false><<<g, B, 0, s>>>(T, begin, end, x, A, b, q, dbg);
       break;
     default:
-      if (wq) k_eval<MODE_BUFFER, true><<<g, kEvalBlock, 0, s>>>(T, begin, end, x, A, b, q, dbg);
-      else k_eval<MODE_BUFFER, false><<<g, kEvalBlock, 0, s>>>(T, begin, end, x, A, b, q, dbg);
+      if (wq) k_eval<MODE_BUFFER, true><<<g, B, 0, s>>>(T, begin, end, x, A, b, q, dbg);
+      else k_eval<MODE_BUFFER, false><<<g, B, 0, s>>>(T, begin, end, x, A, b, q, dbg);
       break;
   }
   return cudaGetLastError();
@@ -300,7 +363,7 @@ int persistent_max_blocks_per_sm(int block, bool want_q) {
 
 cudaError_t launch_persistent(const DevTopo& T, const int* color_off_dev, int n_colors,
                               const double* x, double* A, double* b, double* q, int block,
-                              int grid, int dbg, cudaStream_t s) {
+                              int grid, int dbg, cudaStream_t s, int absent_block) {
   (void)block;
   cudaError_t e = cudaMemsetAsync(T.bar, 0, 2 * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
@@ -312,7 +375,8 @@ cudaError_t launch_persistent(const DevTopo& T, const int* color_off_dev, int n_
   double* bb = b;
   double* qq = q;
   int d = dbg;
-  void* args[] = {&Tc, &coff, &C, &xx, &AA, &bb, &qq, &d};
+  int ab = absent_block;
+  void* args[] = {&Tc, &coff, &C, &xx, &AA, &bb, &qq, &d, &ab};
   if (q)
     return cudaLaunchCooperativeKernel((const void*)k_persistent<true>, dim3(grid),
                                        dim3(kEvalBlock), args, 0, s);
@@ -329,9 +393,16 @@ cudaError_t launch_gather(const DevTopo& T, double* A, double* b, cudaStream_t s
 
 cudaError_t launch_stamp_buffer(const DevTopo& T, int begin, int end, double* A, double* b,
                                 int block, cudaStream_t s) {
-  (void)block;
   if (end <= begin) return cudaSuccess;
-  k_stamp_buffer<<<grid_for(end - begin, kEvalBlock), kEvalBlock, 0, s>>>(T, begin, end, A, b);
+  const int B = eval_block(end - begin, block);
+  k_stamp_buffer<<<grid_for(end - begin, B), B, 0, s>>>(T, begin, end, A, b);
+  return cudaGetLastError();
+}
+
+cudaError_t math_check(int fn, long long n, const double* x, double* ours, double* ref,
+                       cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_math_check<<<grid_for(n, 256), 256, 0, s>>>(fn, n, x, ours, ref);
   return cudaGetLastError();
 }
 

@@ -15,6 +15,7 @@
 // shared between a quotient and its derivatives.
 #pragma once
 
+#include "eec_fastmath.cuh"
 #include "eec_internal.h"
 
 namespace eec {
@@ -23,9 +24,15 @@ namespace eec {
 __device__ __forceinline__ double sval(double x) { return x; }
 __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 __device__ __forceinline__ double rsqrt_(double x) { return ::rsqrt(x); }
-__device__ __forceinline__ double exp_(double x) { return ::exp(x); }
-__device__ __forceinline__ double expm1_(double x) { return ::expm1(x); }
-__device__ __forceinline__ double log1p_(double x) { return ::log1p(x); }
+__device__ __forceinline__ double exp_(double x) { return fm_exp(x); }
+__device__ __forceinline__ double expm1_(double x) { return fm_expm1(x); }
+// log(1 + e) for e in [0, 1], given inv_y = 1 / (1 + e)
+__device__ __forceinline__ double log1p_(double e, double inv_y) { return fm_log1p01(e, inv_y); }
+// x * (+1 or -1) as a sign-bit flip on the integer pipe (sb is 0 or the sign bit).
+__device__ __forceinline__ double flip(double x, unsigned long long sb) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (long long)sb);
+}
+constexpr unsigned long long kSignBit = 0x8000000000000000ull;
 
 template <class S>
 struct PrmS {
@@ -80,20 +87,12 @@ __device__ __forceinline__ void junction(const CardK& c, const S& Isat, const S&
   gj = Isat * c.inv_Vt * ez + c.GMIN;
 }
 
-template <class S, bool WANT_Q>
-__device__ __forceinline__ void ees_l1(const CardK& c, double pp, const PrmS<S>& P,
-                                       const S V[4], EvalOut<S>& o) {
-  // (1) mode
-  const S vds0 = pp * (V[0] - V[2]);
-  const bool fwd = sval(vds0) >= 0.0;
-  const S VD = fwd ? V[0] : V[2];
-  const S VS = fwd ? V[2] : V[0];
-  const S vgs = pp * (V[1] - VS);
-  const S vds = pp * (VD - VS);
-  const S vbs = pp * (V[3] - VS);
-
-  // (2) body effect: phis = (u + R1)/2, R1 = sqrt(u^2 + 4 D1^2), u = PHI - vbs
-  //     d phis / d u = phis / R1, d sqs / d vbs = -sqs / (2 R1)
+// Terms that depend on vbs alone: body effect (2) and bulk-charge factor (4).
+// phis = (u + R1)/2, R1 = sqrt(u^2 + 4 D1^2), u = PHI - vbs; d phis/du = phis/R1,
+// d sqs/dvbs = -sqs/(2 R1). Vthb is the threshold without the DIBL term.
+template <class S>
+__device__ __forceinline__ void body_terms(const CardK& c, const S& vbs, S& sqs, S& Vthb,
+                                           S& dVth_dvbs, S& Ab, S& dAb_dvbs) {
   const S u = c.PHI - vbs;
   const S R1sq = u * u + c.fourD1sq;
   const S inv_R1 = rsqrt_(R1sq);
@@ -102,32 +101,54 @@ __device__ __forceinline__ void ees_l1(const CardK& c, double pp, const PrmS<S>&
   if (sval(u) >= 0.0) phis = 0.5 * (u + R1);
   else phis = c.twoD1sq * rcp(R1 - u);
   const S inv_sqs = rsqrt_(phis);
-  const S sqs = phis * inv_sqs;
-  const S Vth = c.VTH0 + c.K1 * (sqs - c.sqrtPHI) - c.ETA0 * vds;
+  sqs = phis * inv_sqs;
+  Vthb = c.VTH0 + c.K1 * (sqs - c.sqrtPHI);
   const S hK1R = (0.5 * c.K1) * inv_R1;
-  const S dVth_dvbs = -(hK1R * sqs);            // K1 d sqs / d vbs
-  const S Ab = 1.0 + (0.5 * c.K1) * inv_sqs;     // (4)
-  const S dAb_dvbs = 0.5 * hK1R * inv_sqs;       // K1 / (4 sqs R1)
+  dVth_dvbs = -(hK1R * sqs);
+  Ab = 1.0 + (0.5 * c.K1) * inv_sqs;
+  dAb_dvbs = 0.5 * hK1R * inv_sqs;
+}
+
+// x-independent terms of a device whose source and body are both source-held: in forward mode
+// vbs is constant, and the source junction is constant in either mode.
+struct BodyK {
+  double sqs, Vthb, dVth_dvbs, Ab, dAb_dvbs, Ijs, gjs;
+};
+constexpr int kNBody = 7;
+
+// Mode-frame channel current (steps 3, 5-8) and its gradient g = (gm, gds, gmb) with respect to
+// (vgs, vds, vbs), given the vbs-dependent terms of step (2)/(4). Vg and F1 feed the charges.
+template <class S>
+struct Chan {
+  S Ids, gm, gds, gmb, Vg, F1;
+};
+
+template <class S>
+__device__ __forceinline__ void channel(const CardK& c, const PrmS<S>& P, const S& vgs,
+                                        const S& vds, const S& Vthb, const S& dVth_dvbs,
+                                        const S& Ab, const S& dAb_dvbs, Chan<S>& ch) {
+  const S Vth = Vthb - c.ETA0 * vds;
 
   // (3) Vgsteff = nVt softplus(z), dVgsteff/dz = nVt sigmoid(z)
   const S z = (vgs - Vth) * c.inv_nVt;
   const bool zpos = sval(z) >= 0.0;
   const S e = exp_(zpos ? -z : z);               // exp(-|z|)
-  const S lg = log1p_(e);
-  const S Vg = c.nVt * (zpos ? z + lg : lg);
   const S inv_1pe = rcp(1.0 + e);
+  const S lg = log1p_(e, inv_1pe);
+  const S Vg = c.nVt * (zpos ? z + lg : lg);
   const S sig = zpos ? inv_1pe : e * inv_1pe;
 
   // (5) mobility denominator, (6) velocity saturation
   const S den = 1.0 + Vg * (c.UA + c.UB * Vg);
   const S dden = c.UA + 2.0 * c.UB * Vg;
-  const S inv_den = rcp(den);
+  const S Vgst2 = Vg + c.twoVt;
+  const S inv_pair = rcp(den * Vgst2);           // one reciprocal for 1/den and 1/Vgst2
+  const S inv_den = Vgst2 * inv_pair;
+  const S inv_Vgst2 = den * inv_pair;
   const S beta = P.beta0 * inv_den;
   const S EsatL = P.cE * den;
   const S inv_EsatL = P.inv_cE * inv_den;
   const S EsatL_Vg = P.cE * dden;
-  const S Vgst2 = Vg + c.twoVt;
-  const S inv_Vgst2 = rcp(Vgst2);
   const S Dd = Ab * EsatL + Vgst2;
   const S inv_Dd = rcp(Dd);
   const S r1 = Vgst2 * inv_Dd;
@@ -185,11 +206,50 @@ __device__ __forceinline__ void ees_l1(const CardK& c, double pp, const PrmS<S>&
   const S gm = Ids_Vg * sig;
   const S gds = gm * c.ETA0 + Ids_vds;
   const S gmb = Ids_Ab * dAb_dvbs - gm * dVth_dvbs;
+
+  ch.Ids = Ids;
+  ch.gm = gm;
+  ch.gds = gds;
+  ch.gmb = gmb;
+  ch.Vg = Vg;
+  ch.F1 = F1;
+}
+
+template <class S, bool WANT_Q>
+__device__ __forceinline__ void ees_l1(const CardK& c, unsigned long long psb, const PrmS<S>& P,
+                                       const S V[4], EvalOut<S>& o, bool sb_fixed = false,
+                                       const BodyK* bk = nullptr) {
+  // (1) mode
+  const S vds0 = flip(V[0] - V[2], psb);
+  const bool fwd = sval(vds0) >= 0.0;
+  const S VD = fwd ? V[0] : V[2];
+  const S VS = fwd ? V[2] : V[0];
+  const S vgs = flip(V[1] - VS, psb);
+  const S vds = flip(VD - VS, psb);
+
+  // (2) body effect, (4) bulk charge: precomputed when vbs cannot change
+  S sqs, Vthb, dVth_dvbs, Ab, dAb_dvbs;
+  if (sb_fixed && fwd) {
+    sqs = S(bk->sqs);
+    Vthb = S(bk->Vthb);
+    dVth_dvbs = S(bk->dVth_dvbs);
+    Ab = S(bk->Ab);
+    dAb_dvbs = S(bk->dAb_dvbs);
+  } else {
+    body_terms<S>(c, flip(V[3] - VS, psb), sqs, Vthb, dVth_dvbs, Ab, dAb_dvbs);
+  }
+  Chan<S> ch;
+  channel<S>(c, P, vgs, vds, Vthb, dVth_dvbs, Ab, dAb_dvbs, ch);
+  const S& Ids = ch.Ids;
+  const S& gm = ch.gm;
+  const S& gds = ch.gds;
+  const S& gmb = ch.gmb;
+  const S& Vg = ch.Vg;
+  const S& F1 = ch.F1;
   const S gsum = gm + gds + gmb;
 
   // (9) channel current into physical d (into s is the negative), and its Jacobian row
-  const double m = fwd ? 1.0 : -1.0;
-  const S Ichd = (pp * m) * Ids;
+  const S Ichd = flip(Ids, fwd ? psb : (psb ^ kSignBit));
   const S cdd = fwd ? gds : gsum;
   const S cdg = fwd ? gm : -gm;
   const S cds = fwd ? -gsum : -gds;
@@ -197,13 +257,18 @@ __device__ __forceinline__ void ees_l1(const CardK& c, double pp, const PrmS<S>&
 
   // (10) junctions on the physical terminals
   S Ijd, gjd, Ijs, gjs;
-  junction<S>(c, P.Isat, pp * (V[3] - V[0]), Ijd, gjd);
-  junction<S>(c, P.Isat, pp * (V[3] - V[2]), Ijs, gjs);
+  junction<S>(c, P.Isat, flip(V[3] - V[0], psb), Ijd, gjd);
+  if (sb_fixed) {
+    Ijs = S(bk->Ijs);
+    gjs = S(bk->gjs);
+  } else {
+    junction<S>(c, P.Isat, flip(V[3] - V[2], psb), Ijs, gjs);
+  }
 
-  o.I[0] = Ichd - pp * Ijd;
+  o.I[0] = Ichd - flip(Ijd, psb);
   o.I[1] = S(0.0);
-  o.I[2] = -Ichd - pp * Ijs;
-  o.I[3] = pp * (Ijd + Ijs);
+  o.I[2] = -Ichd - flip(Ijs, psb);
+  o.I[3] = flip(Ijd + Ijs, psb);
   o.G[0][0] = cdd + gjd;  o.G[0][1] = cdg;   o.G[0][2] = cds;        o.G[0][3] = cdb - gjd;
   o.G[1][0] = -cdd;       o.G[1][1] = -cdg;  o.G[1][2] = gjs - cds;  o.G[1][3] = -cdb - gjs;
   o.G[2][0] = -gjd;       o.G[2][1] = S(0.0); o.G[2][2] = -gjs;      o.G[2][3] = gjd + gjs;
@@ -215,12 +280,12 @@ __device__ __forceinline__ void ees_l1(const CardK& c, double pp, const PrmS<S>&
     const S Qg0 = -(Qb + Qinv);
     const S QD = c.XPART * Qinv;
     const S QS = (1.0 - c.XPART) * Qinv;
-    const S Qovs = P.CovS * (pp * (V[1] - V[2]));
-    const S Qovd = P.CovD * (pp * (V[1] - V[0]));
-    o.Q[1] = pp * (Qg0 + Qovs + Qovd);
-    o.Q[0] = pp * ((fwd ? QD : QS) - Qovd);
-    o.Q[2] = pp * ((fwd ? QS : QD) - Qovs);
-    o.Q[3] = pp * Qb;
+    const S Qovs = P.CovS * flip(V[1] - V[2], psb);
+    const S Qovd = P.CovD * flip(V[1] - V[0], psb);
+    o.Q[1] = flip(Qg0 + Qovs + Qovd, psb);
+    o.Q[0] = flip((fwd ? QD : QS) - Qovd, psb);
+    o.Q[2] = flip((fwd ? QS : QD) - Qovs, psb);
+    o.Q[3] = flip(Qb, psb);
   }
 }
 

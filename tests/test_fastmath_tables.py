@@ -1,0 +1,51 @@
+"""CPU checks of the tables behind the library's table-driven exp / expm1 / log1p: every entry of
+eec_tables.h against 200-bit mpmath values (double-double pairs to about 2^-100 relative), and the
+Cody-Waite split of ln2/64."""
+import os
+import re
+
+import mpmath
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+TABLES = os.path.join(ROOT, "paper_2604_03079_gb300", "csrc", "eec_tables.h")
+mpmath.mp.prec = 200
+
+
+def _parse():
+    text = open(TABLES).read()
+    arrays = {}
+    for name, body in re.findall(r"(\w+)\[\d+\] = \{(.*?)\};", text, flags=re.S):
+        arrays[name] = [float.fromhex(v) for v in re.findall(r"-?0x[0-9a-fp.+\-]+", body)]
+    consts = {k: float.fromhex(v) for k, v in
+              re.findall(r"constexpr double (\w+) = (-?0x[0-9a-fp.+\-]+);", text)}
+    return arrays, consts
+
+
+def test_exp_table_is_two_to_the_j_over_64():
+    a, _ = _parse()
+    assert len(a["kExp2Hi"]) == len(a["kExp2Lo"]) == 64
+    for j in range(64):
+        exact = mpmath.power(2, mpmath.mpf(j) / 64)
+        assert float(exact) == a["kExp2Hi"][j]
+        err = abs(mpmath.mpf(a["kExp2Hi"][j]) + mpmath.mpf(a["kExp2Lo"][j]) - exact) / exact
+        assert err < mpmath.mpf(2) ** -100
+
+
+def test_log_tables():
+    a, _ = _parse()
+    for j in range(129):
+        F = 1 + mpmath.mpf(j) / 128
+        assert a["kF"][j] == float(F)
+        assert a["kInvF"][j] == float(1 / F)
+        err = abs(mpmath.mpf(a["kLogFHi"][j]) + mpmath.mpf(a["kLogFLo"][j]) - mpmath.log(F))
+        assert err < mpmath.mpf(2) ** -100
+
+
+def test_reduction_constants():
+    _, c = _parse()
+    ln2o64 = mpmath.log(2) / 64
+    assert c["kLn2o64Hi"] == float(ln2o64)
+    assert abs(mpmath.mpf(c["kLn2o64Hi"]) + mpmath.mpf(c["kLn2o64Lo"]) - ln2o64) < mpmath.mpf(2) ** -110
+    assert c["kInvLn2x64"] == float(64 / mpmath.log(2))

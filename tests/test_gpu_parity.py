@@ -343,6 +343,23 @@ def test_graph_capture_and_autotune(eec):
         assert rel_err(host(b), r["b"], r["b_scale"]).max() <= TOL
 
 
+def test_grid_barrier_timeout_is_reported_and_the_context_recovers(eec):
+    # One block never arrives: the other blocks give up after their bounded wait (about 1 s),
+    # record EEC_ETIMEOUT in the status word and return; nothing hangs or faults.
+    import time
+    net = netgen.inverter_chain(64)
+    o = oracle.Oracle(net, CARDS)
+    circ = eec.Circuit(net, CARDS, color=True)
+    x = netgen.random_x(net)
+    A, b, _ = circ.new_outputs(want_q=False)
+    t0 = time.time()
+    eec.eec_test_barrier_timeout(circ.ctx, dev(x), A, b)
+    assert circ.status() == eec.EEC_ETIMEOUT
+    assert time.time() - t0 < 30
+    assert circ.status() == 0                     # cleared by the read
+    check_against_oracle(eec, circ, o, x, 1)      # the persistent schedule still works
+
+
 def test_debug_checks_flag_non_finite_inputs(eec):
     net = netgen.inverter_chain(8)
     circ = eec.Circuit(net, CARDS, debug_checks=True)
