@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--quick", action="store_true",
                     help="timed steps only (no autotune, e2e, extras, probes, baseline): for ncu")
+    ap.add_argument("--bwd-steps", type=int, default=0,
+                    help="with --quick: also run the backward this many times (for ncu)")
     return ap.parse_args()
 
 
@@ -261,6 +263,7 @@ def run_ours(args):
            "config": {"workload": wname, "n_dev": net.n_dev, "n_unknowns": circ.n,
                       "nnz": circ.nnz, "colors": circ.n_colors,
                       "variant": eec.VARIANT_NAMES[variant],
+                      "block": eec.eec_get_tuning(circ.ctx)[1],
                       "l2": "flushed (256 MiB write) before every timed step",
                       "parallelism": f"replica x{world}" if world > 1 else "single GPU"},
            "gpu_launches": launches,
@@ -269,6 +272,14 @@ def run_ours(args):
         out["clocks"] = clk
 
     if rank == 0 and args.quick:
+        if args.bwd_steps:
+            rng = netgen.Rng(netgen.DEFAULT_SEED, 12)
+            gA = torch.as_tensor(rng.normal(circ.nnz), device=dev)
+            gb = torch.as_tensor(rng.normal(circ.n), device=dev)
+            for _ in range(args.bwd_steps):
+                circ.bwd(xt, gA, gb)
+            torch.cuda.synchronize()
+            assert circ.status() == 0
         print(json.dumps(out))
     elif rank == 0:
         # roofline of the dominant kernel (the evaluate kernel; FP64-pipe bound)

@@ -154,6 +154,9 @@ EEC_API int eec_get_color_offsets(const eec_ctx* ctx, int32_t* off);
  */
 EEC_API int eec_update_params(eec_ctx* ctx, const double* W_dev, const double* L_dev, void* cuda_stream);
 
+/* The schedule and block size eec_eval_stamp will use (after autotuning, if any). */
+EEC_API int eec_get_tuning(const eec_ctx* ctx, int32_t* variant, int32_t* block);
+
 /* Select the schedule (EEC_VARIANT_*) used by eec_eval_stamp. */
 EEC_API int eec_set_variant(eec_ctx* ctx, int32_t variant);
 EEC_API int eec_get_variant(const eec_ctx* ctx, int32_t* variant);
@@ -172,6 +175,25 @@ EEC_API int eec_get_variant(const eec_ctx* ctx, int32_t* variant);
  */
 EEC_API int eec_eval_stamp(eec_ctx* ctx, const double* x_dev, double* A_values_dev, double* b_dev,
                    double* q_dev, void* cuda_stream);
+
+/*
+ * Transient companion stamp of one Newton iterate of a time step (the transient loop of Sec. II,
+ * Fig. 1, re-forms A x = b at every Newton iteration of every step). The terminal charges q_t
+ * are integrated by a one-step rule: the capacitive current into the device is
+ *   ic_t = alpha (q_t(x) - q_prev_t) - beta i_prev_t
+ * (backward Euler: alpha = 1/h, beta = 0; trapezoidal: alpha = 2/h, beta = 1), and
+ *   A = A_lin + sum_dev (G + alpha C),  b = b_lin + sum_dev (-I - ic + (G + alpha C) V)
+ * with C_tu = dq_t/dV_u, over all four terminal rows (the gate row now carries current).
+ *  q_prev_dev  [4*n_dev] charges at the previous time point (terminal-major, original order),
+ *  i_prev_dev  [4*n_dev] capacitive currents there, nullable (zero);
+ *  q_dev       [4*n_dev] out: charges at x;  i_dev [4*n_dev] out, nullable: ic at x.
+ * Schedule: the per-colour store-add when the variant is EEC_VARIANT_COLOR_FUSED (the colouring
+ * must count gate rows: not EEC_CONFLICT_WRITE_ROWS), otherwise FP64 atomics.
+ */
+EEC_API int eec_eval_stamp_tran(eec_ctx* ctx, const double* x_dev, const double* q_prev_dev,
+                                const double* i_prev_dev, double alpha, double beta,
+                                double* A_values_dev, double* b_dev, double* q_dev, double* i_dev,
+                                void* cuda_stream);
 
 /*
  * Gradient of s = sum_e gA[e] A[e] + sum_i gb[i] b[i], with A, b formed at x, with respect to
@@ -219,10 +241,12 @@ EEC_API int eec_graph_capture(eec_ctx* ctx, const double* x_dev, double* A_value
 EEC_API int eec_graph_launch(eec_ctx* ctx, void* cuda_stream);
 
 /*
- * Time every variant on these buffers (CUDA events, `reps` launches each after one warm-up) and
- * select the fastest for eec_eval_stamp; ms_out [EEC_N_VARIANTS] (nullable) receives the mean
- * time per call, negative for a variant that does not apply (e.g. colour schedules when the
- * context is not coloured). Synchronous.
+ * Autotuner: time every schedule on these buffers (CUDA events, `reps` calls each after one
+ * warm-up), at block sizes 0 (library choice), 32, 64 and 128 unless opt.block fixes it, and
+ * select the fastest (schedule, block) pair for eec_eval_stamp when the variant is
+ * EEC_VARIANT_AUTO. ms_out [EEC_N_VARIANTS] (nullable) receives each schedule's best mean time
+ * per call, negative for a schedule that does not apply (colour schedules without colours).
+ * Synchronous.
  */
 EEC_API int eec_autotune(eec_ctx* ctx, const double* x_dev, double* A_values_dev, double* b_dev,
                  double* q_dev, int32_t reps, void* cuda_stream, float* ms_out);

@@ -60,6 +60,9 @@ def _load():
             lib.ora_eval_stamp_grad.argtypes = [P, P, P, P, P, P, P]
             lib.ora_device_eval.argtypes = [P, i32, f64, f64, P, P, P, P]
             lib.ora_card_len.restype = i32
+            lib.ora_eval_stamp_tran.argtypes = [P, P, P, P, f64, f64, P, P, P, P, P, P]
+            lib.ora_device_charge.argtypes = [P, i32, f64, f64, P, P, P]
+            lib.ora_tran_solve.argtypes = [P, P, f64, i32, i32, P, P]
             _lib = lib
     return _lib
 
@@ -162,6 +165,35 @@ class Oracle:
             raise ValueError("adjoint solve failed")
         return lam
 
+    def eval_stamp_tran(self, x, qprev, iprev, alpha, beta, want_scale=False):
+        """Transient companion stamp at x; returns A, b, q (charges at x), i (capacitive
+        currents at x) and, on request, the |contribution| scales."""
+        x = _c(x, np.float64)
+        qp = _c(qprev, np.float64).reshape(-1)
+        ip = None if iprev is None else _c(iprev, np.float64).reshape(-1)
+        A = np.zeros(self.nnz)
+        b = np.zeros(self.n)
+        q = np.zeros(4 * self.n_dev)
+        i = np.zeros(4 * self.n_dev)
+        As = np.zeros(self.nnz) if want_scale else None
+        bs = np.zeros(self.n) if want_scale else None
+        self.lib.ora_eval_stamp_tran(self.h, _p(x), _p(qp), _p(ip), float(alpha), float(beta),
+                                     _p(A), _p(b), _p(q), _p(i), _p(As), _p(bs))
+        out = dict(A=A, b=b, q=q.reshape(4, self.n_dev), i=i.reshape(4, self.n_dev))
+        if want_scale:
+            out["A_scale"], out["b_scale"] = As, bs
+        return out
+
+    def tran_solve(self, x0, h, n_steps, method=0, i0=None):
+        x = _c(x0, np.float64).copy()
+        traj = np.zeros((n_steps + 1) * self.n)
+        ip = None if i0 is None else _c(i0, np.float64).reshape(-1)
+        rc = self.lib.ora_tran_solve(self.h, _p(x), float(h), int(n_steps), int(method), _p(ip),
+                                     _p(traj))
+        if rc != 0:
+            raise RuntimeError("oracle transient step did not converge")
+        return traj.reshape(n_steps + 1, self.n)
+
     def eval_stamp_grad(self, x, gA, gb):
         gx = np.zeros(self.n)
         gW = np.zeros(self.n_dev)
@@ -169,6 +201,19 @@ class Oracle:
         self.lib.ora_eval_stamp_grad(self.h, _p(_c(x, np.float64)), _p(_c(gA, np.float64)),
                                      _p(_c(gb, np.float64)), _p(gx), _p(gW), _p(gL))
         return gx, gW, gL
+
+
+def device_charge(card, p, W, L, V):
+    """Single device: returns (Q[4], C[4,4] = dQ/dV)."""
+    lib = _load()
+    card = _c(card, np.float64)
+    V = _c(V, np.float64)
+    Q = np.zeros(4)
+    C = np.zeros(16)
+    rc = lib.ora_device_charge(_p(card), int(p), float(W), float(L), _p(V), _p(Q), _p(C))
+    if rc != 0:
+        raise ValueError("bad device arguments")
+    return Q, C.reshape(4, 4)
 
 
 def device_eval(card, p, W, L, V):

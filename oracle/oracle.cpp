@@ -122,6 +122,67 @@ Dual<T, N> sqrt(const Dual<T, N>& a) {
   return r;
 }
 
+// Magnitude forward mode: value plus, per direction, the sum over chain-rule paths of the
+// absolute values of the products along each path. It bounds |derivative| and measures how much
+// a derivative cancels; the transient error metric uses it as the size of a Jacobian entry.
+template <int N>
+struct Mag {
+  double v;
+  double m[N];
+  Mag() : v(0.0) { for (int i = 0; i < N; ++i) m[i] = 0.0; }
+  Mag(double c) : v(c) { for (int i = 0; i < N; ++i) m[i] = 0.0; }  // NOLINT: constants
+};
+template <int N> double val(const Mag<N>& x) { return x.v; }
+template <int N> Mag<N> operator+(const Mag<N>& a, const Mag<N>& b) {
+  Mag<N> r; r.v = a.v + b.v;
+  for (int i = 0; i < N; ++i) r.m[i] = a.m[i] + b.m[i];
+  return r;
+}
+template <int N> Mag<N> operator-(const Mag<N>& a, const Mag<N>& b) {
+  Mag<N> r; r.v = a.v - b.v;
+  for (int i = 0; i < N; ++i) r.m[i] = a.m[i] + b.m[i];
+  return r;
+}
+template <int N> Mag<N> operator-(const Mag<N>& a) { Mag<N> r = a; r.v = -a.v; return r; }
+template <int N> Mag<N> operator*(const Mag<N>& a, const Mag<N>& b) {
+  Mag<N> r; r.v = a.v * b.v;
+  for (int i = 0; i < N; ++i) r.m[i] = a.m[i] * std::fabs(b.v) + std::fabs(a.v) * b.m[i];
+  return r;
+}
+template <int N> Mag<N> operator/(const Mag<N>& a, const Mag<N>& b) {
+  Mag<N> r; r.v = a.v / b.v;
+  for (int i = 0; i < N; ++i) r.m[i] = (a.m[i] + std::fabs(r.v) * b.m[i]) / std::fabs(b.v);
+  return r;
+}
+template <int N> Mag<N> operator+(const Mag<N>& a, double b) { return a + Mag<N>(b); }
+template <int N> Mag<N> operator+(double a, const Mag<N>& b) { return Mag<N>(a) + b; }
+template <int N> Mag<N> operator-(const Mag<N>& a, double b) { return a - Mag<N>(b); }
+template <int N> Mag<N> operator-(double a, const Mag<N>& b) { return Mag<N>(a) - b; }
+template <int N> Mag<N> operator*(const Mag<N>& a, double b) { return a * Mag<N>(b); }
+template <int N> Mag<N> operator*(double a, const Mag<N>& b) { return Mag<N>(a) * b; }
+template <int N> Mag<N> operator/(const Mag<N>& a, double b) { return a / Mag<N>(b); }
+template <int N> Mag<N> operator/(double a, const Mag<N>& b) { return Mag<N>(a) / b; }
+template <int N> Mag<N> exp(const Mag<N>& a) {
+  Mag<N> r; r.v = std::exp(a.v);
+  for (int i = 0; i < N; ++i) r.m[i] = r.v * a.m[i];
+  return r;
+}
+template <int N> Mag<N> expm1(const Mag<N>& a) {
+  Mag<N> r; r.v = std::expm1(a.v);
+  for (int i = 0; i < N; ++i) r.m[i] = std::exp(a.v) * a.m[i];
+  return r;
+}
+template <int N> Mag<N> log1p(const Mag<N>& a) {
+  Mag<N> r; r.v = std::log1p(a.v);
+  for (int i = 0; i < N; ++i) r.m[i] = a.m[i] / std::fabs(1.0 + a.v);
+  return r;
+}
+template <int N> Mag<N> sqrt(const Mag<N>& a) {
+  Mag<N> r; r.v = std::sqrt(a.v);
+  for (int i = 0; i < N; ++i) r.m[i] = a.m[i] / (2.0 * r.v);
+  return r;
+}
+
 // ---------------------------------------------------------------------------------------------
 // EES-L1 model card (field order fixed by the card layout of the interface).
 struct Card {
@@ -228,13 +289,16 @@ void ees_l1(const Card& c, int p, const S& W, const S& L, const S V[4], S I[4], 
   I[2] = Ichs - pp * Ijs;
   I[3] = pp * (Ijd + Ijs);
 
-  // (11) Charges: depletion, inversion (partitioned XPART to the mode drain), gate, overlaps.
+  // (11) Charges: depletion, inversion (partitioned to the mode drain by fD, which moves from
+  //      1/2 at vds = 0 to XPART in saturation, so the charges are continuous across the
+  //      source/drain swap), gate, overlaps.
   const S Coxt = Cox * W * L;
   const S Qb = -(Coxt * c.K1 * sqs);
   const S Qinv = -(Coxt * Vgsteff * F1);
   const S Qg0 = -(Qb + Qinv);
-  const S QD = c.XPART * Qinv;
-  const S QS = (1.0 - c.XPART) * Qinv;
+  const S fD = 0.5 - (0.5 - c.XPART) * (Vdseff / Vdsat);
+  const S QD = fD * Qinv;
+  const S QS = (1.0 - fD) * Qinv;
   const S Qovs = c.CGSO * W * (pp * (V[1] - V[2]));
   const S Qovd = c.CGDO * W * (pp * (V[1] - V[0]));
   const S Qd_int = (mode > 0) ? QD : QS;
@@ -351,9 +415,9 @@ void stamp_linear(const Circuit& c, double* A, double* b, double* As, double* bs
 
 using D4 = Dual<double, 4>;
 
-// Evaluate device k with its Jacobian: I[t], G[t][u] = dI_t/dV_u, Q[t].
+// Evaluate device k with its Jacobians: I[t], G[t][u] = dI_t/dV_u, Q[t], Cq[t][u] = dQ_t/dV_u.
 void device_iv(const Circuit& c, int k, const double Vn[4], double I[4], double G[4][4],
-               double Q[4]) {
+               double Q[4], double Cq[4][4] = nullptr) {
   D4 V[4], Id[4], Qd[4];
   for (int t = 0; t < 4; ++t) { V[t] = D4(Vn[t]); V[t].d[t] = 1.0; }
   ees_l1<D4>(c.cards[c.mid[k]], c.type[k], D4(c.W[k]), D4(c.L[k]), V, Id, Qd);
@@ -361,6 +425,69 @@ void device_iv(const Circuit& c, int k, const double Vn[4], double I[4], double 
     I[t] = Id[t].v;
     Q[t] = Qd[t].v;
     for (int u = 0; u < 4; ++u) G[t][u] = Id[t].d[u];
+    if (Cq)
+      for (int u = 0; u < 4; ++u) Cq[t][u] = Qd[t].d[u];
+  }
+}
+
+// Transient companion stamp of one Newton iterate x of a time step (Sec. II, Fig. 1: the
+// transient loop re-forms A x = b at every Newton iteration of every time step). The charge of
+// terminal t is integrated by a one-step rule: the capacitive current into the device is
+// ic_t = alpha (Q_t(x) - qprev_t) - beta iprev_t (backward Euler: alpha = 1/h, beta = 0;
+// trapezoidal: alpha = 2/h, beta = 1). Linearising I_t + ic_t at x gives
+//   A[t][u] += G_tu + alpha C_tu,  b[t] += -I_t - ic_t + sum_u (G_tu + alpha C_tu) x_u
+// over all four terminal rows (the gate row now carries capacitive current).
+void stamp_tran(const Circuit& c, const double* x, const double* qprev, const double* iprev,
+                double alpha, double beta, double* A, double* b, double* q, double* icap,
+                double* As, double* bs) {
+  const long nnz = static_cast<long>(c.col.size());
+  std::fill(A, A + nnz, 0.0);
+  std::fill(b, b + c.n, 0.0);
+  if (As) std::fill(As, As + nnz, 0.0);
+  if (bs) std::fill(bs, bs + c.n, 0.0);
+  stamp_linear(c, A, b, As, bs);
+  for (int k = 0; k < c.n_dev; ++k) {
+    double Vn[4], I[4], G[4][4], Q[4], Cq[4][4];
+    int u_of[4];
+    for (int t = 0; t < 4; ++t) {
+      int node = c.dn[4 * k + t];
+      u_of[t] = c.unk[node];
+      Vn[t] = node_voltage(c, x, node);
+    }
+    device_iv(c, k, Vn, I, G, Q, Cq);
+    double Gm[4][4], Cm[4][4];   // sizes of the Jacobian entries (magnitude forward mode)
+    if (As || bs) {
+      Mag<4> V[4], Im[4], Qm[4];
+      for (int t = 0; t < 4; ++t) { V[t] = Mag<4>(Vn[t]); V[t].m[t] = 1.0; }
+      ees_l1<Mag<4>>(c.cards[c.mid[k]], c.type[k], Mag<4>(c.W[k]), Mag<4>(c.L[k]), V, Im, Qm);
+      for (int t = 0; t < 4; ++t)
+        for (int u = 0; u < 4; ++u) {
+          Gm[t][u] = Im[t].m[u];
+          Cm[t][u] = Qm[t].m[u];
+        }
+    }
+    for (int t = 0; t < 4; ++t) {
+      const long at = static_cast<long>(t) * c.n_dev + k;
+      const double ic = alpha * (Q[t] - qprev[at]) - (iprev ? beta * iprev[at] : 0.0);
+      if (q) q[at] = Q[t];
+      if (icap) icap[at] = ic;
+      if (u_of[t] < 0) continue;
+      double rhs = -I[t] - ic;
+      double scale = std::fabs(I[t]) + alpha * (std::fabs(Q[t]) + std::fabs(qprev[at])) +
+                     (iprev ? std::fabs(beta * iprev[at]) : 0.0);
+      for (int u = 0; u < 4; ++u) {
+        if (u_of[u] < 0) continue;
+        const double a = G[t][u] + alpha * Cq[t][u];
+        long p = c.where.at({u_of[t], u_of[u]});
+        A[p] += a;
+        const double am = (As || bs) ? Gm[t][u] + alpha * Cm[t][u] : 0.0;
+        if (As) As[p] += am;
+        rhs += a * Vn[u];
+        scale += am * std::fabs(Vn[u]);
+      }
+      b[u_of[t]] += rhs;
+      if (bs) bs[u_of[t]] += scale;
+    }
   }
 }
 
@@ -736,5 +863,79 @@ int ora_device_eval(const double* card, int32_t p, double W, double L, const dou
 }
 
 int32_t ora_card_len(void) { return kCardLen; }
+
+// Transient companion stamp at x (see stamp_tran). qprev, iprev (nullable = zero): [4 x n_dev]
+// terminal-major; q_out, i_out (nullable): charges and capacitive currents at x.
+int ora_eval_stamp_tran(void* h, const double* x, const double* qprev, const double* iprev,
+                        double alpha, double beta, double* A, double* b, double* q_out,
+                        double* i_out, double* A_scale, double* b_scale) {
+  Circuit& c = *static_cast<Circuit*>(h);
+  std::vector<double> zero;
+  if (!qprev) {
+    zero.assign(4L * c.n_dev, 0.0);
+    qprev = zero.data();
+  }
+  stamp_tran(c, x, qprev, iprev, alpha, beta, A, b, q_out, i_out, A_scale, b_scale);
+  return kOk;
+}
+
+// Charges and their Jacobian for one device: Q[4], C[16] row-major dQ_t/dV_u.
+int ora_device_charge(const double* card, int32_t p, double W, double L, const double* V,
+                      double* Q, double* C) {
+  if (p != 1 && p != -1) return kEinval;
+  Card cd = read_card(card);
+  D4 Vd[4], Id[4], Qd[4];
+  for (int t = 0; t < 4; ++t) { Vd[t] = D4(V[t]); Vd[t].d[t] = 1.0; }
+  ees_l1<D4>(cd, p, D4(W), D4(L), Vd, Id, Qd);
+  for (int t = 0; t < 4; ++t) {
+    Q[t] = Qd[t].v;
+    for (int u = 0; u < 4; ++u) C[4 * t + u] = Qd[t].d[u];
+  }
+  return kOk;
+}
+
+// Transient analysis by a one-step rule (method 0 backward Euler, 1 trapezoidal) with fixed
+// step h: from x_io (state at t = 0, charges there, capacitive currents i0 or zero) take n_steps
+// steps, each solved by Newton with the companion stamp and every node's update clipped to
+// 0.2 V, converged when |dx| <= 1e-12 + 1e-9 |x|. traj [(n_steps + 1) x n]
+// receives the states. Returns 0, or -6 when a step's Newton fails.
+int ora_tran_solve(void* h, double* x_io, double step, int32_t n_steps, int32_t method,
+                   const double* i0, double* traj) {
+  Circuit& c = *static_cast<Circuit*>(h);
+  if (!(step > 0.0) || n_steps < 0 || method < 0 || method > 1) return kEinval;
+  const double alpha = method == 0 ? 1.0 / step : 2.0 / step;
+  const double beta = method == 0 ? 0.0 : 1.0;
+  const long nq = 4L * c.n_dev;
+  const long nnz = static_cast<long>(c.col.size());
+  std::vector<double> x(x_io, x_io + c.n), qprev(nq), iprev(nq, 0.0), qn(nq), in(nq);
+  std::vector<double> A(nnz), b(c.n), F(c.n);
+  if (i0) iprev.assign(i0, i0 + nq);
+  stamp_tran(c, x.data(), qprev.data(), nullptr, 0.0, 0.0, A.data(), b.data(), qprev.data(),
+             nullptr, nullptr, nullptr);  // charges at t = 0
+  std::copy(x.begin(), x.end(), traj);
+  for (int s = 1; s <= n_steps; ++s) {
+    bool conv = false;
+    for (int it = 0; it < 200 && !conv; ++it) {
+      stamp_tran(c, x.data(), qprev.data(), iprev.data(), alpha, beta, A.data(), b.data(),
+                 qn.data(), in.data(), nullptr, nullptr);
+      std::vector<double> M = to_dense(c, A, false);
+      std::vector<double> y = b;
+      if (!dense_solve(M, y, c.n)) return kEnoconv;
+      // per-node step limiting to 0.2 V (uniform scaling can lock into a 2-cycle here)
+      std::vector<double> dx(c.n);
+      for (int i = 0; i < c.n; ++i) dx[i] = std::max(-0.2, std::min(0.2, y[i] - x[i]));
+      for (int i = 0; i < c.n; ++i) x[i] += dx[i];
+      conv = inf_norm(dx) <= 1e-12 + 1e-9 * inf_norm(x);
+    }
+    if (!conv) return kEnoconv;
+    stamp_tran(c, x.data(), qprev.data(), iprev.data(), alpha, beta, A.data(), b.data(),
+               qn.data(), in.data(), nullptr, nullptr);
+    qprev = qn;
+    iprev = in;
+    std::copy(x.begin(), x.end(), traj + static_cast<long>(s) * c.n);
+  }
+  std::copy(x.begin(), x.end(), x_io);
+  return kOk;
+}
 
 }  // extern "C"

@@ -66,8 +66,10 @@ _SIG = {
     "eec_update_params": (ctypes.c_int, [_P, _P, _P, _P]),
     "eec_set_variant": (ctypes.c_int, [_P, _I32]),
     "eec_get_variant": (ctypes.c_int, [_P, ctypes.POINTER(_I32)]),
+    "eec_get_tuning": (ctypes.c_int, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "eec_eval_stamp": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "eec_eval_stamp_bwd": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "eec_eval_stamp_tran": (ctypes.c_int, [_P, _P, _P, _P, _F64, _F64, _P, _P, _P, _P, _P]),
     "eec_eval_stamp_bwd_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "eec_graph_capture": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "eec_graph_launch": (ctypes.c_int, [_P, _P]),
@@ -279,9 +281,23 @@ def eec_get_variant(ctx) -> int:
     return int(v.value)
 
 
+def eec_get_tuning(ctx):
+    """-> (variant, block) that eec_eval_stamp uses."""
+    v, blk = _I32(0), _I32(0)
+    _check(ctx, _load().eec_get_tuning(ctx, ctypes.byref(v), ctypes.byref(blk)))
+    return int(v.value), int(blk.value)
+
+
 def eec_eval_stamp(ctx, x, A, b, q=None, stream=None):
     _check(ctx, _load().eec_eval_stamp(ctx, _d(x, name="x"), _d(A, name="A"), _d(b, name="b"),
                                    _d(q, name="q"), _stream(stream)))
+
+
+def eec_eval_stamp_tran(ctx, x, q_prev, i_prev, alpha, beta, A, b, q, i=None, stream=None):
+    _check(ctx, _load().eec_eval_stamp_tran(
+        ctx, _d(x, name="x"), _d(q_prev, name="q_prev"), _d(i_prev, name="i_prev"),
+        float(alpha), float(beta), _d(A, name="A"), _d(b, name="b"), _d(q, name="q"),
+        _d(i, name="i"), _stream(stream)))
 
 
 def eec_eval_stamp_bwd(ctx, x, gA, gb, gx, gW, gL, stream=None):

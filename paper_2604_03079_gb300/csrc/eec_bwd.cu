@@ -259,13 +259,40 @@ __global__ void __launch_bounds__(kBwdBlock) k_bwd_device(DevTopo T, const doubl
   gL[od] = dL;
 }
 
-__global__ void k_bwd_gather(DevTopo T, double* __restrict__ gx) {
-  const int u = blockIdx.x * blockDim.x + threadIdx.x;
-  if (u >= T.n) return;
-  double s = 0.0;
+// gx[u] = sum of the terminal gradients at unknown u: one thread per light unknown (summed in
+// original-device order), one warp per heavy unknown (lane-strided, fixed butterfly reduction).
+constexpr int kGatherBlock = 256;
+
+__global__ void __launch_bounds__(kGatherBlock) k_bwd_gather(DevTopo T, double* __restrict__ gx,
+                                                             int nbl) {
+  if ((int)blockIdx.x < nbl) {
+    const int i = blockIdx.x * kGatherBlock + threadIdx.x;
+    if (i >= T.n_inc_light) return;
+    const int u = __ldg(T.inc_light + i);
+    double s = 0.0;
+    const int p1 = __ldg(T.inc_ptr + u + 1);
+    for (int p = __ldg(T.inc_ptr + u); p < p1; ++p) s += __ldg(T.gv + __ldg(T.inc_src + p));
+    gx[u] = s;
+    return;
+  }
+  const int w = (blockIdx.x - nbl) * (kGatherBlock / 32) + (threadIdx.x >> 5);
+  if (w >= T.n_inc_heavy) return;
+  const int lane = threadIdx.x & 31;
+  const int u = __ldg(T.inc_heavy + w);
   const int p1 = __ldg(T.inc_ptr + u + 1);
-  for (int p = __ldg(T.inc_ptr + u); p < p1; ++p) s += __ldg(T.gv + __ldg(T.inc_src + p));
-  gx[u] = s;
+  double s = 0.0;
+  for (int p = __ldg(T.inc_ptr + u) + lane; p < p1; p += 32) s += __ldg(T.gv + __ldg(T.inc_src + p));
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (lane == 0) gx[u] = s;
+}
+
+cudaError_t launch_bwd_gather(const DevTopo& T, double* gx, cudaStream_t s) {
+  const int nbl = (T.n_inc_light + kGatherBlock - 1) / kGatherBlock;
+  const int nbh = (T.n_inc_heavy + kGatherBlock / 32 - 1) / (kGatherBlock / 32);
+  if (nbl + nbh == 0) return cudaSuccess;
+  k_bwd_gather<<<nbl + nbh, kGatherBlock, 0, s>>>(T, gx, nbl);
+  return cudaGetLastError();
 }
 
 // Device address of g_noalloc_gv on the current device, looked up once per device (set-up on the
@@ -304,8 +331,7 @@ cudaError_t launch_bwd_noalloc(const DevTopo& T, const double* x, const double* 
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  if (Ts.n > 0) k_bwd_gather<<<(Ts.n + 255) / 256, 256, 0, s>>>(Ts, gx);
-  return cudaGetLastError();
+  return launch_bwd_gather(Ts, gx, s);
 }
 
 cudaError_t launch_bwd(const DevTopo& T, const double* x, const double* gA, const double* gb,
@@ -316,8 +342,7 @@ cudaError_t launch_bwd(const DevTopo& T, const double* x, const double* gA, cons
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  if (T.n > 0) k_bwd_gather<<<(T.n + 255) / 256, 256, 0, s>>>(T, gx);
-  return cudaGetLastError();
+  return launch_bwd_gather(T, gx, s);
 }
 
 }  // namespace eec

@@ -62,6 +62,8 @@ struct eec_ctx {
   int auto_variant = -100;
   cudaGraphExec_t user_exec = nullptr;
   int tuned_variant = EEC_VARIANT_SEGREDUCE;
+  int tuned_block = 0;         // block size picked by eec_autotune (used when opt.block == 0)
+  int auto_block = -1;         // block size baked into the cached graph
   int sms = 0;
   int persist_grid = 0;
   // phase timing and launch counting
@@ -275,7 +277,7 @@ int run_variant(eec_ctx* c, int v, const double* x, double* A, double* b, double
                 cudaStream_t s, long long* nk) {
   const DevTopo& T = c->d;
   const int dbg = c->opt.debug_checks ? 1 : 0;
-  const int blk = c->opt.block;
+  const int blk = c->opt.block ? c->opt.block : c->tuned_block;
   *nk = 0;
   if (variant_needs_colors(v) && !c->colored)
     return fail(c, EEC_ESTATE, "colour schedules need eec_color before eec_build_scatter");
@@ -379,7 +381,8 @@ int eval_with(eec_ctx* c, int v, const double* x, double* A, double* b, double* 
               cudaStream_t s) {
   if (!c->prof && (v == EEC_VARIANT_COLOR_FUSED || v == EEC_VARIANT_COLOR_BUFFERED)) {
     const void* key[4] = {x, A, b, q};
-    bool hit = c->auto_exec && c->auto_variant == v;
+    const int blk = c->opt.block ? c->opt.block : c->tuned_block;
+    bool hit = c->auto_exec && c->auto_variant == v && c->auto_block == blk;
     for (int i = 0; i < 4 && hit; ++i) hit = key[i] == c->auto_key[i];
     if (!hit) {
       if (c->auto_exec) cudaGraphExecDestroy(c->auto_exec);
@@ -388,6 +391,7 @@ int eval_with(eec_ctx* c, int v, const double* x, double* A, double* b, double* 
       int rc = capture(c, v, x, A, b, q, &c->auto_exec, &c->auto_kernels);
       if (rc) return rc;
       c->auto_variant = v;
+      c->auto_block = blk;
       for (int i = 0; i < 4; ++i) c->auto_key[i] = key[i];
     }
     CUDA_TRY(c, cudaGraphLaunch(c->auto_exec, s));
@@ -740,7 +744,7 @@ int eec_build_scatter(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_out) {
   for (int i = 0; i < C; ++i) c->color_off[i + 1] += c->color_off[i];
   // per-position arrays
   std::vector<int4> tidx(N);
-  std::vector<int> meta(N), slot((size_t)kNSlot * N, -1);
+  std::vector<int> meta(N), slot((size_t)kNSlot * N, -1), slot_g((size_t)4 * N, -1);
   std::vector<double> Wp(N), Lp(N);
   const int rows_t[3] = {0, 2, 3};
   for (int p = 0; p < N; ++p) {
@@ -760,6 +764,9 @@ int eec_build_scatter(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_out) {
       for (int u = 0; u < 4; ++u)
         if (ti[u] >= 0) slot[(size_t)(4 * r + u) * N + p] = find(ti[rows_t[r]], ti[u]);
     }
+    if (ti[1] >= 0)
+      for (int u = 0; u < 4; ++u)
+        if (ti[u] >= 0) slot_g[(size_t)u * N + p] = find(ti[1], ti[u]);
   }
   // linear part, summed in the natural element order: gshunt, resistors, current sources
   std::vector<double> Alin(c->nnz, 0.0), blin(n, 0.0);
@@ -820,6 +827,11 @@ int eec_build_scatter(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_out) {
       }
     }
   }
+  std::vector<int> glight, gheavy;
+  for (long long e = 0; e < E; ++e) {
+    if (gptr[e + 1] - gptr[e] >= kHeavy) gheavy.push_back((int)e);
+    else glight.push_back((int)e);
+  }
   // backward incidence: unknown -> (terminal, position) in original device order
   std::vector<int> iptr(n + 1, 0);
   for (int k = 0; k < N; ++k)
@@ -836,6 +848,11 @@ int eec_build_scatter(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_out) {
         const int a = c->unk[c->dn[4 * k + t]];
         if (a >= 0) isrc[fill[a]++] = t * N + pos_of[k];
       }
+  }
+  std::vector<int> ilight, iheavy;
+  for (int u = 0; u < n; ++u) {
+    if (iptr[u + 1] - iptr[u] >= kHeavy) iheavy.push_back(u);
+    else ilight.push_back(u);
   }
   if ((long long)N * kNContrib > 0x7fffffffLL) return fail(c, EEC_EINVAL, "too many devices");
   // batch offsets
@@ -869,15 +886,22 @@ int eec_build_scatter(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_out) {
   d.N = N;
   d.n = n;
   d.nnz = c->nnz;
+  d.n_light = (int)glight.size();
+  d.n_heavy = (int)gheavy.size();
+  d.n_inc_light = (int)ilight.size();
+  d.n_inc_heavy = (int)iheavy.size();
   std::vector<int> orig(c->perm.begin(), c->perm.end());
   if ((rc = dupload(c, &d.tidx, tidx)) || (rc = dupload(c, &d.meta, meta)) ||
       (rc = dupload(c, &d.orig, orig)) || (rc = dupload(c, &d.slot, slot)) ||
+      (rc = dupload(c, &d.slot_g, slot_g)) ||
       (rc = dupload(c, &d.W, Wp)) || (rc = dupload(c, &d.L, Lp)) ||
       (rc = dalloc(c, &d.prm, (size_t)kNPrm * N)) || (rc = dalloc(c, &d.bodyk, (size_t)7 * N)) ||
       (rc = dupload(c, &d.vfix, vtab)) ||
       (rc = dupload(c, &d.cards, c->cardk)) || (rc = dupload(c, &d.Alin, Alin)) ||
       (rc = dupload(c, &d.blin, blin)) || (rc = dupload(c, &d.gat_ptr, gptr)) ||
-      (rc = dupload(c, &d.gat_src, gsrc)) || (rc = dupload(c, &d.inc_ptr, iptr)) ||
+      (rc = dupload(c, &d.gat_src, gsrc)) || (rc = dupload(c, &d.gat_light, glight)) ||
+      (rc = dupload(c, &d.gat_heavy, gheavy)) || (rc = dupload(c, &d.inc_ptr, iptr)) ||
+      (rc = dupload(c, &d.inc_light, ilight)) || (rc = dupload(c, &d.inc_heavy, iheavy)) ||
       (rc = dupload(c, &d.inc_src, isrc)) || (rc = dupload(c, &c->d_coff, c->color_off))) {
     free_topology(c);
     return rc;
@@ -963,6 +987,37 @@ int eec_eval_stamp(eec_ctx* c, const double* x, double* A, double* b, double* q,
   if (rc) return rc;
   if (!x || !A || !b) return fail(c, EEC_EINVAL, "NULL x, A or b");
   return eval_with(c, effective_variant(c), x, A, b, q, static_cast<cudaStream_t>(stream));
+}
+
+int eec_eval_stamp_tran(eec_ctx* c, const double* x, const double* q_prev, const double* i_prev,
+                        double alpha, double beta, double* A, double* b, double* q, double* icap,
+                        void* stream) {
+  int rc = check_built(c);
+  if (rc) return rc;
+  if (!x || !q_prev || !A || !b || !q) return fail(c, EEC_EINVAL, "NULL x, q_prev, A, b or q");
+  if (!std::isfinite(alpha) || !std::isfinite(beta) || alpha < 0.0)
+    return fail(c, EEC_EINVAL, "alpha must be finite and >= 0, beta finite");
+  int v = effective_variant(c);
+  if (v != EEC_VARIANT_COLOR_FUSED) v = EEC_VARIANT_ATOMIC;
+  if (v == EEC_VARIANT_COLOR_FUSED && (!c->colored || c->opt.conflict_rule == EEC_CONFLICT_WRITE_ROWS))
+    return fail(c, EEC_ESTATE, "transient colour stamping needs a colouring that counts gate rows");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  TranArgs ta{q_prev, i_prev, alpha, beta, q, icap};
+  const int blk = c->opt.block ? c->opt.block : c->tuned_block;
+  CUDA_TRY(c, cudaMemcpyAsync(A, c->d.Alin, sizeof(double) * c->nnz, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(c, cudaMemcpyAsync(b, c->d.blin, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, s));
+  if (v == EEC_VARIANT_ATOMIC) {
+    CUDA_TRY(c, launch_eval_tran(c->d, MODE_ATOMIC, 0, c->n_dev, x, A, b, ta, blk, s));
+    c->n_kernels += c->n_dev > 0;
+  } else {
+    for (int k = 0; k < c->C; ++k) {
+      if (c->color_off[k + 1] <= c->color_off[k]) continue;
+      CUDA_TRY(c, launch_eval_tran(c->d, MODE_RMW, c->color_off[k], c->color_off[k + 1], x, A, b,
+                                   ta, blk, s));
+      ++c->n_kernels;
+    }
+  }
+  return EEC_OK;
 }
 
 int eec_eval_stamp_bwd(eec_ctx* c, const double* x, const double* gA, const double* gb,
@@ -1052,38 +1107,55 @@ int eec_autotune(eec_ctx* c, const double* x, double* A, double* b, double* q, i
   cudaEvent_t e0, e1;
   CUDA_TRY(c, cudaEventCreate(&e0));
   CUDA_TRY(c, cudaEventCreate(&e1));
+  // Blocks tried when the caller left the choice to the library (opt.block == 0).
+  const int cand_auto[4] = {0, 32, 64, 128};
+  const int n_cand = c->opt.block ? 1 : 4;
+  const int saved_tuned = c->tuned_block;
   float best = 1e30f;
-  int best_v = EEC_VARIANT_SEGREDUCE;
+  int best_v = EEC_VARIANT_SEGREDUCE, best_b = 0;
   for (int v = 0; v < EEC_N_VARIANTS; ++v) {
-    float ms = -1.0f;
+    float best_ms_v = -1.0f;
     if (!variant_needs_colors(v) || c->colored) {
-      rc = eval_with(c, v, x, A, b, q, s);
-      if (rc == EEC_OK) {
-        cudaEventRecord(e0, s);
-        for (int r = 0; r < reps && rc == EEC_OK; ++r) rc = eval_with(c, v, x, A, b, q, s);
-        cudaEventRecord(e1, s);
-        if (cudaEventSynchronize(e1) == cudaSuccess && rc == EEC_OK) {
-          cudaEventElapsedTime(&ms, e0, e1);
-          ms /= reps;
-        } else {
-          ms = -1.0f;
+      for (int ib = 0; ib < n_cand; ++ib) {
+        c->tuned_block = c->opt.block ? saved_tuned : cand_auto[ib];
+        float ms = -1.0f;
+        rc = eval_with(c, v, x, A, b, q, s);
+        if (rc == EEC_OK) {
+          cudaEventRecord(e0, s);
+          for (int r = 0; r < reps && rc == EEC_OK; ++r) rc = eval_with(c, v, x, A, b, q, s);
+          cudaEventRecord(e1, s);
+          if (cudaEventSynchronize(e1) == cudaSuccess && rc == EEC_OK) {
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= reps;
+          }
+        }
+        if (rc != EEC_OK) {
+          c->tuned_block = saved_tuned;
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          return rc;
+        }
+        if (ms >= 0.0f && (best_ms_v < 0.0f || ms < best_ms_v)) best_ms_v = ms;
+        if (ms >= 0.0f && ms < best) {
+          best = ms;
+          best_v = v;
+          best_b = c->tuned_block;
         }
       }
-      if (rc != EEC_OK) {
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        return rc;
-      }
     }
-    if (ms_out) ms_out[v] = ms;
-    if (ms >= 0.0f && ms < best) {
-      best = ms;
-      best_v = v;
-    }
+    if (ms_out) ms_out[v] = best_ms_v;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   c->tuned_variant = best_v;
+  c->tuned_block = c->opt.block ? saved_tuned : best_b;
+  return EEC_OK;
+}
+
+int eec_get_tuning(const eec_ctx* c, int32_t* variant, int32_t* block) {
+  if (!c) return EEC_EINVAL;
+  if (variant) *variant = effective_variant(c);
+  if (block) *block = c->opt.block ? c->opt.block : c->tuned_block;
   return EEC_OK;
 }
 

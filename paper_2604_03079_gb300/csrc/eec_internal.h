@@ -40,6 +40,7 @@ struct DevTopo {
   int* meta;        // [N] (card << 2) | (source and body source-held) << 1 | (type < 0)
   int* orig;        // [N] original device index of each position
   int* slot;        // [kNSlot][N] CSR value index or -1
+  int* slot_g;      // [4][N] gate-row slots (transient stamping) or -1
   double* W;        // [N]
   double* L;        // [N]
   double* prm;      // [kNPrm][N]
@@ -52,14 +53,22 @@ struct DevTopo {
   // gat_src[gat_ptr[e] .. gat_ptr[e+1]) in original-device order
   long long* gat_ptr;  // [nnz + n + 1]
   int* gat_src;        // [total contributions], flat index j * N + k into buf
+  int* gat_light;      // entries with fewer than kHeavy contributions (one thread each)
+  int* gat_heavy;      // the others (one warp each)
+  int n_light, n_heavy;
   double* buf;         // [kNContrib][N] (allocated on first use)
   // backward: unknown u gathers gv[src] over inc_src[inc_ptr[u] .. inc_ptr[u+1])
   int* inc_ptr;     // [n + 1]
   int* inc_src;     // flat index t * N + k into gv
+  int* inc_light;   // unknowns with fewer than kHeavy terminals (one thread each)
+  int* inc_heavy;   // the others (one warp each)
+  int n_inc_light, n_inc_heavy;
   double* gv;       // [4][N] (allocated on first use)
   int* status;      // device status word: bit 0 timeout, bit 1 non-finite
   unsigned* bar;    // grid barrier: [0] arrival count, [1] generation
 };
+
+constexpr int kHeavy = 32;  // contributions from which an entry gets a whole warp in the gather
 
 constexpr int kStatusTimeout = 1;
 constexpr int kStatusNumeric = 2;
@@ -80,6 +89,16 @@ cudaError_t launch_persistent(const DevTopo& T, const int* color_off_dev, int n_
                               int grid, int dbg, cudaStream_t s, int absent_block = -1);
 int persistent_max_blocks_per_sm(int block, bool want_q);
 cudaError_t launch_gather(const DevTopo& T, double* A, double* b, cudaStream_t s);
+// Transient companion stamp (mode MODE_RMW over one colour range, or MODE_ATOMIC over all).
+struct TranArgs {
+  const double* qprev;  // [4][N_orig] charges of the previous time point
+  const double* iprev;  // [4][N_orig] capacitive currents of the previous time point, nullable
+  double alpha, beta;   // ic = alpha (q - qprev) - beta iprev
+  double* q;            // [4][N_orig] out: charges at x
+  double* icap;         // [4][N_orig] out: capacitive currents at x, nullable
+};
+cudaError_t launch_eval_tran(const DevTopo& T, int mode, int begin, int end, const double* x,
+                             double* A, double* b, const TranArgs& ta, int block, cudaStream_t s);
 cudaError_t launch_stamp_buffer(const DevTopo& T, int begin, int end, double* A, double* b,
                                 int block, cudaStream_t s);
 cudaError_t launch_bwd(const DevTopo& T, const double* x, const double* gA, const double* gb,

@@ -165,7 +165,72 @@ __device__ __forceinline__ void eval_one(const DevTopo& T, int k, const double* 
   }
 }
 
+// Transient: evaluate with charges and their Jacobian, then stamp all four terminal rows
+// (A += G + alpha C, b += -I - ic + (G + alpha C) V) by store-add (one colour) or atomics.
+template <int MODE>
+__device__ __forceinline__ void eval_one_tran(const DevTopo& T, int k, const double* __restrict__ x,
+                                              double* A, double* b, const TranArgs& ta) {
+  const long long N = T.N;
+  const int4 ti = __ldg(T.tidx + k);
+  const int idx[4] = {ti.x, ti.y, ti.z, ti.w};
+  double V[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t)
+    V[t] = idx[t] >= 0 ? __ldg(x + idx[t]) : __ldg(T.vfix + ~idx[t]);
+  const int meta = __ldg(T.meta + k);
+  const CardK& c = T.cards[meta >> 2];
+  const unsigned long long psb = (meta & 1) ? kSignBit : 0ull;
+  const bool sbf = (meta >> 1) & 1;
+  const PrmS<double> P = load_prm(T, k);
+  BodyK bk;
+  if (sbf) {
+    const double* q0 = T.bodyk + k;
+    bk.sqs = __ldg(q0);
+    bk.Vthb = __ldg(q0 + N);
+    bk.dVth_dvbs = __ldg(q0 + 2 * N);
+    bk.Ab = __ldg(q0 + 3 * N);
+    bk.dAb_dvbs = __ldg(q0 + 4 * N);
+    bk.Ijs = __ldg(q0 + 5 * N);
+    bk.gjs = __ldg(q0 + 6 * N);
+  }
+  EvalOut<double> o;
+  ees_l1<double, true, true>(c, psb, P, V, o, sbf, &bk);
+  const int od = __ldg(T.orig + k);
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const long long at = t * N + od;
+    const double ic = ta.alpha * (o.Q[t] - __ldg(ta.qprev + at)) -
+                      (ta.iprev ? ta.beta * __ldg(ta.iprev + at) : 0.0);
+    ta.q[at] = o.Q[t];
+    if (ta.icap) ta.icap[at] = ic;
+    const int row = idx[t];
+    if (row < 0) continue;
+    const int r = t == 0 ? 0 : (t == 2 ? 1 : 2);   // row of G (gate row of G is zero)
+    double rhs = -(t == 1 ? 0.0 : o.I[t]) - ic;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (idx[u] < 0) continue;
+      const double a = fma(ta.alpha, o.C[t][u], t == 1 ? 0.0 : o.G[r][u]);
+      const int s = t == 1 ? __ldg(T.slot_g + u * N + k) : __ldg(T.slot + (4 * r + u) * N + k);
+      if (MODE == MODE_ATOMIC) atomicAdd(A + s, a);
+      else A[s] += a;
+      rhs = fma(a, V[u], rhs);
+    }
+    if (MODE == MODE_ATOMIC) atomicAdd(b + row, rhs);
+    else b[row] += rhs;
+  }
+}
+
 constexpr int kEvalBlock = 128;
+
+template <int MODE>
+__global__ void __launch_bounds__(kEvalBlock) k_eval_tran(DevTopo T, int begin, int end,
+                                                          const double* __restrict__ x,
+                                                          double* A, double* b, TranArgs ta) {
+  for (int k = begin + blockIdx.x * blockDim.x + threadIdx.x; k < end;
+       k += gridDim.x * blockDim.x)
+    eval_one_tran<MODE>(T, k, x, A, b, ta);
+}
 
 template <int MODE, bool WANT_Q>
 __global__ void __launch_bounds__(kEvalBlock) k_eval(DevTopo T, int begin, int end,
@@ -237,17 +302,38 @@ __global__ void k_params(DevTopo T, const double* __restrict__ Wo, const double*
   T.prm[P_COVD * N + k] = P.CovD;
 }
 
-// Segmented reduction: entry e of [A ; b] = linear part + contributions in original-device
-// order (deterministic, no colours needed).
-__global__ void k_gather(DevTopo T, double* A, double* b) {
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long total = T.nnz + T.n;
-  if (e >= total) return;
-  double s = e < T.nnz ? __ldg(T.Alin + e) : __ldg(T.blin + (e - T.nnz));
+// Segmented reduction: entry e of [A ; b] = linear part + its contributions (deterministic, no
+// colours needed). Light entries (< kHeavy contributions, nearly all) take one thread each and
+// sum in original-device order; heavy entries (diagonals of word and bit lines) take one warp
+// each: lane-strided partial sums, then a fixed butterfly reduction. Blocks [0, nbl) do light
+// entries, the rest heavy ones, in one launch.
+constexpr int kGatherBlock = 256;
+
+__global__ void __launch_bounds__(kGatherBlock) k_gather(DevTopo T, double* A, double* b, int nbl) {
+  if ((int)blockIdx.x < nbl) {
+    const int i = blockIdx.x * kGatherBlock + threadIdx.x;
+    if (i >= T.n_light) return;
+    const long long e = __ldg(T.gat_light + i);
+    double s = e < T.nnz ? __ldg(T.Alin + e) : __ldg(T.blin + (e - T.nnz));
+    const long long p0 = __ldg(T.gat_ptr + e), p1 = __ldg(T.gat_ptr + e + 1);
+    for (long long p = p0; p < p1; ++p) s += __ldg(T.buf + __ldg(T.gat_src + p));
+    if (e < T.nnz) A[e] = s;
+    else b[e - T.nnz] = s;
+    return;
+  }
+  const int w = (blockIdx.x - nbl) * (kGatherBlock / 32) + (threadIdx.x >> 5);
+  if (w >= T.n_heavy) return;   // whole warp leaves together
+  const int lane = threadIdx.x & 31;
+  const long long e = __ldg(T.gat_heavy + w);
   const long long p0 = __ldg(T.gat_ptr + e), p1 = __ldg(T.gat_ptr + e + 1);
-  for (long long p = p0; p < p1; ++p) s += __ldg(T.buf + __ldg(T.gat_src + p));
-  if (e < T.nnz) A[e] = s;
-  else b[e - T.nnz] = s;
+  double s = 0.0;
+  for (long long p = p0 + lane; p < p1; p += 32) s += __ldg(T.buf + __ldg(T.gat_src + p));
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (lane == 0) {
+    if (e < T.nnz) A[e] = __ldg(T.Alin + e) + s;
+    else b[e - T.nnz] = __ldg(T.blin + (e - T.nnz)) + s;
+  }
 }
 
 // One colour's stamp from the buffer (positions begin..end-1 share no row).
@@ -350,6 +436,16 @@ cudaError_t launch_eval(const DevTopo& T, int mode, int begin, int end, const do
   return cudaGetLastError();
 }
 
+cudaError_t launch_eval_tran(const DevTopo& T, int mode, int begin, int end, const double* x,
+                             double* A, double* b, const TranArgs& ta, int block, cudaStream_t s) {
+  if (end <= begin) return cudaSuccess;
+  const int B = eval_block(end - begin, block);
+  const int g = grid_for(end - begin, B);
+  if (mode == MODE_ATOMIC) k_eval_tran<MODE_ATOMIC><<<g, B, 0, s>>>(T, begin, end, x, A, b, ta);
+  else k_eval_tran<MODE_RMW><<<g, B, 0, s>>>(T, begin, end, x, A, b, ta);
+  return cudaGetLastError();
+}
+
 int persistent_max_blocks_per_sm(int block, bool want_q) {
   (void)block;
   int nb = 0;
@@ -385,9 +481,10 @@ cudaError_t launch_persistent(const DevTopo& T, const int* color_off_dev, int n_
 }
 
 cudaError_t launch_gather(const DevTopo& T, double* A, double* b, cudaStream_t s) {
-  const long long total = T.nnz + T.n;
-  if (total == 0) return cudaSuccess;
-  k_gather<<<grid_for(total, 256), 256, 0, s>>>(T, A, b);
+  const int nbl = (T.n_light + kGatherBlock - 1) / kGatherBlock;
+  const int nbh = (T.n_heavy + kGatherBlock / 32 - 1) / (kGatherBlock / 32);
+  if (nbl + nbh == 0) return cudaSuccess;
+  k_gather<<<nbl + nbh, kGatherBlock, 0, s>>>(T, A, b, nbl);
   return cudaGetLastError();
 }
 

@@ -68,6 +68,7 @@ struct EvalOut {
   S I[4];      // current from node t into the device, t = d, g, s, b (I[1] == 0)
   S G[3][4];   // rows d, s, b of dI_t / dV_u, u = d, g, s, b (gate row is zero in DC)
   S Q[4];      // terminal charges (only when requested)
+  S C[4][4];   // dQ_t / dV_u, rows d, g, s, b (transient only)
 };
 
 template <class S>
@@ -121,6 +122,9 @@ constexpr int kNBody = 7;
 template <class S>
 struct Chan {
   S Ids, gm, gds, gmb, Vg, F1;
+  S Vdsat, Vdseff;                      // for the charge partition
+  S sig, F1_Vg, F1_Ab, F1_vds;          // for the charge Jacobian
+  S Vdsat_Vg, Vdsat_Ab, Vde_Vg, Vde_Ab, Vde_vds;
 };
 
 template <class S>
@@ -213,9 +217,20 @@ __device__ __forceinline__ void channel(const CardK& c, const PrmS<S>& P, const 
   ch.gmb = gmb;
   ch.Vg = Vg;
   ch.F1 = F1;
+  ch.Vdsat = Vdsat;
+  ch.Vdseff = Vdseff;
+  ch.sig = sig;
+  ch.F1_Vg = F1_Vg;
+  ch.F1_Ab = F1_Ab;
+  ch.F1_vds = F1_vds;
+  ch.Vdsat_Vg = Vdsat_Vg;
+  ch.Vdsat_Ab = Vdsat_Ab;
+  ch.Vde_Vg = Vde_Vg;
+  ch.Vde_Ab = Vde_Ab;
+  ch.Vde_vds = Vde_vds;
 }
 
-template <class S, bool WANT_Q>
+template <class S, bool WANT_Q, bool WANT_C = false>
 __device__ __forceinline__ void ees_l1(const CardK& c, unsigned long long psb, const PrmS<S>& P,
                                        const S V[4], EvalOut<S>& o, bool sb_fixed = false,
                                        const BodyK* bk = nullptr) {
@@ -274,18 +289,80 @@ __device__ __forceinline__ void ees_l1(const CardK& c, unsigned long long psb, c
   o.G[2][0] = -gjd;       o.G[2][1] = S(0.0); o.G[2][2] = -gjs;      o.G[2][3] = gjd + gjs;
 
   if (WANT_Q) {
-    // (11) charges: depletion, inversion partitioned XPART to the mode drain, overlaps
+    // (11) charges: depletion, inversion partitioned to the mode drain by
+    //      fD = 1/2 - (1/2 - XPART) Vdseff / Vdsat (continuous across the source/drain swap),
+    //      overlaps
     const S Qb = -(P.Coxt * c.K1 * sqs);
     const S Qinv = -(P.Coxt * Vg * F1);
     const S Qg0 = -(Qb + Qinv);
-    const S QD = c.XPART * Qinv;
-    const S QS = (1.0 - c.XPART) * Qinv;
+    const S inv_Vdsat = rcp(ch.Vdsat);
+    const S sr = ch.Vdseff * inv_Vdsat;
+    const S fD = 0.5 - (0.5 - c.XPART) * sr;
+    const S QD = fD * Qinv;
+    const S QS = Qinv - QD;
     const S Qovs = P.CovS * flip(V[1] - V[2], psb);
     const S Qovd = P.CovD * flip(V[1] - V[0], psb);
     o.Q[1] = flip(Qg0 + Qovs + Qovd, psb);
     o.Q[0] = flip((fwd ? QD : QS) - Qovd, psb);
     o.Q[2] = flip((fwd ? QS : QD) - Qovs, psb);
     o.Q[3] = flip(Qb, psb);
+    if (WANT_C) {
+      // (11') charge Jacobian. Mode-frame derivatives of Qinv = -Coxt Vg F1 and Qb, with
+      // dVg/d(vgs, vds, vbs) = sig (1, ETA0, -dVth/dvbs) and the total derivatives of F1; mapped
+      // to the physical terminals as for G (the polarity factors cancel). Columns sum to zero.
+      const S Vg_vds = ch.sig * c.ETA0;
+      const S Vg_vbs = -(ch.sig * dVth_dvbs);
+      const S F1_vgs = ch.F1_Vg * ch.sig;
+      const S F1_vdsT = ch.F1_Vg * Vg_vds + ch.F1_vds;
+      const S F1_vbsT = ch.F1_Vg * Vg_vbs + ch.F1_Ab * dAb_dvbs;
+      const S mC = -P.Coxt;
+      const S Qi_vgs = mC * (ch.sig * F1 + Vg * F1_vgs);
+      const S Qi_vds = mC * (Vg_vds * F1 + Vg * F1_vdsT);
+      const S Qi_vbs = mC * (Vg_vbs * F1 + Vg * F1_vbsT);
+      const S Qb_vbs = mC * dVth_dvbs;
+      // partition fraction: sr = Vdseff / Vdsat with Vdsat(Vg, Ab), Vdseff(Vdsat, vds)
+      const S sr_Vg = (ch.Vde_Vg - sr * ch.Vdsat_Vg) * inv_Vdsat;
+      const S sr_Ab = (ch.Vde_Ab - sr * ch.Vdsat_Ab) * inv_Vdsat;
+      const S sr_vds = ch.Vde_vds * inv_Vdsat;
+      const double mx = -(0.5 - c.XPART);          // dfD / dsr
+      const S fD_vgs = mx * (sr_Vg * ch.sig);
+      const S fD_vds = mx * (sr_Vg * Vg_vds + sr_vds);
+      const S fD_vbs = mx * (sr_Vg * Vg_vbs + sr_Ab * dAb_dvbs);
+      const S QD_vgs = fD * Qi_vgs + Qinv * fD_vgs;
+      const S QD_vds = fD * Qi_vds + Qinv * fD_vds;
+      const S QD_vbs = fD * Qi_vbs + Qinv * fD_vbs;
+      const int iD = fwd ? 0 : 2, iS = fwd ? 2 : 0;
+      S MQi[4], MQb[4], MQD[4];
+      MQi[1] = Qi_vgs;
+      MQi[iD] = Qi_vds;
+      MQi[3] = Qi_vbs;
+      MQi[iS] = -(Qi_vgs + Qi_vds + Qi_vbs);
+      MQD[1] = QD_vgs;
+      MQD[iD] = QD_vds;
+      MQD[3] = QD_vbs;
+      MQD[iS] = -(QD_vgs + QD_vds + QD_vbs);
+      MQb[1] = S(0.0);
+      MQb[iD] = S(0.0);
+      MQb[3] = Qb_vbs;
+      MQb[iS] = -Qb_vbs;
+      // physical d carries QD in forward mode, QS = Qinv - QD in reverse mode
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const S MQS = MQi[u] - MQD[u];
+        o.C[1][u] = -(MQb[u] + MQi[u]);
+        o.C[0][u] = fwd ? MQD[u] : MQS;
+        o.C[2][u] = fwd ? MQS : MQD[u];
+        o.C[3][u] = MQb[u];
+      }
+      // overlaps: q_g += CovS (Vg - Vs) + CovD (Vg - Vd), q_s -= CovS (Vg - Vs), q_d -= CovD (Vg - Vd)
+      o.C[1][1] = o.C[1][1] + (P.CovS + P.CovD);
+      o.C[1][0] = o.C[1][0] - P.CovD;
+      o.C[1][2] = o.C[1][2] - P.CovS;
+      o.C[0][0] = o.C[0][0] + P.CovD;
+      o.C[0][1] = o.C[0][1] - P.CovD;
+      o.C[2][2] = o.C[2][2] + P.CovS;
+      o.C[2][1] = o.C[2][1] - P.CovS;
+    }
   }
 }
 
