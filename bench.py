@@ -406,6 +406,40 @@ def extras(eec, circ, net, x, xt, A, b, q, args, dev):
     eec.eec_set_variant(circ.ctx, v0)
     res["phases_ungraphed"] = phases
 
+    # transient companion stamp (trapezoidal rule) on the same workload
+    qprev = torch.empty_like(q)
+    circ.eval_stamp(xt, A, b, qprev)
+    ic = torch.empty_like(q)
+    ip = torch.zeros_like(q)
+    v0t = eec.eec_get_variant(circ.ctx)
+    tran = {}
+    for v in (eec.EEC_VARIANT_ATOMIC, eec.EEC_VARIANT_COLOR_FUSED):
+        eec.eec_set_variant(circ.ctx, v)
+        ms_t = _time(lambda: eec.eec_eval_stamp_tran(circ.ctx, xt, qprev, ip, 2e11, 1.0, A, b, q, ic),
+                     20 if v == eec.EEC_VARIANT_ATOMIC else 3, stream)
+        tran[eec.VARIANT_NAMES[v]] = {"ms": ms_t, "devices_per_s": net.n_dev / (ms_t * 1e-3)}
+    eec.eec_set_variant(circ.ctx, v0t)
+    res["transient_tr_stamp"] = tran
+
+    # Table II analogue: 64-bit ripple-carry adder (28T mirror full adders), with 14 series
+    # resistors per bit and with every transistor-to-transistor connection split, coloured by the
+    # free-node rule (0) and the literal any-non-ground rule (1, VDD counted)
+    cards0 = netgen.default_cards()
+    base = netgen.ripple_adder(64)
+    study = {}
+    for name, n in (("base", base), ("R14", netgen.insert_series_resistors(base, per_group=14)),
+                    ("R_all", netgen.insert_series_resistors(base))):
+        for rule in (0, 1):
+            c = eec.Circuit(n, cards0, color=True, conflict_rule=rule)
+            xa = torch.as_tensor(netgen.random_x(n), device=dev)
+            A2, b2, q2 = c.new_outputs()
+            msv = eec.eec_autotune(c.ctx, xa, A2, b2, q2, reps=5)
+            study[f"{name}_rule{rule}"] = {
+                "transistors": n.n_dev, "resistors": int(len(n.res_G)), "colors": c.n_colors,
+                "ms": {eec.VARIANT_NAMES[i]: m for i, m in enumerate(msv)}}
+            del c
+    res["adder64_table2_study"] = study
+
     # batched (config 4): one context for 4096 circuits vs 4096 plain per-circuit calls
     nets = netgen.batch_circuits(4096)
     cards = netgen.default_cards()

@@ -258,7 +258,7 @@ EEC_API int eec_autotune(eec_ctx* ctx, const double* x_dev, double* A_values_dev
 EEC_API int eec_status(eec_ctx* ctx, void* cuda_stream);
 
 /*
- * Phase timing, the t_calc / t_stamp split of the paper's Fig. 4. While enabled, every
+ * Phase timing, the t_calc / t_stamp split of the paper's Fig. 5. While enabled, every
  * eec_eval_stamp records CUDA events on the caller's stream around its three phases (copy of the
  * linear part into A/b, evaluate — which includes the store-add in the fused schedules — and the
  * separate stamp pass of the buffered schedules) and launches without CUDA graphs.

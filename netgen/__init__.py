@@ -390,6 +390,93 @@ def random_logic(n_gates: int = 200_000, seed: int = DEFAULT_SEED, n_pi: int = 6
                                                                   nor2=counts[2])))
 
 
+def _mirror_adder(b: _Builder, vdd: int, a: int, bb: int, cin: int):
+    """Textbook 28-transistor mirror full adder (14 PMOS, 14 NMOS); returns (cout, sum) nodes.
+    Carry: Coutb = NOT(maj(A, B, Cin)) by the mirror network; sum: Sb = NOT(sum) from Coutb;
+    two output inverters. NMOS bodies at GND, PMOS bodies at VDD."""
+    x1, x2, x3, x4, x5, y1, y2, y3, y4, y5, coutb, sb, cout, sm = (int(v) for v in b.nodes(14))
+    P, N = (lambda d, g, s_: b.fet(-1, d, g, s_, vdd)), (lambda d, g, s_: b.fet(+1, d, g, s_, 0))
+    # carry mirror
+    P(x1, a, vdd); P(x1, bb, vdd); P(coutb, cin, x1); P(x2, a, vdd); P(coutb, bb, x2)
+    N(y1, a, 0); N(y1, bb, 0); N(coutb, cin, y1); N(y2, a, 0); N(coutb, bb, y2)
+    # sum mirror
+    P(x3, a, vdd); P(x3, bb, vdd); P(x3, cin, vdd); P(sb, coutb, x3)
+    P(x4, a, vdd); P(x5, bb, x4); P(sb, cin, x5)
+    N(y3, a, 0); N(y3, bb, 0); N(y3, cin, 0); N(sb, coutb, y3)
+    N(y4, a, 0); N(y5, bb, y4); N(sb, cin, y5)
+    # output inverters
+    P(cout, coutb, vdd); N(cout, coutb, 0)
+    P(sm, sb, vdd); N(sm, sb, 0)
+    return cout, sm
+
+
+def ripple_adder(n_bits: int = 64, seed: int = DEFAULT_SEED, vdd: float = 1.0) -> Netlist:
+    """n-bit ripple-carry adder of 28T mirror full adders (28 n MOSFETs). Operand bits A_k, B_k
+    and the carry-in are fixed sources with seeded random 0/1 levels; bit k's carry-in is bit
+    k-1's carry-out. Devices bit-major, in the order of _mirror_adder."""
+    rng = Rng(seed, 9)
+    b = _Builder(f"ripple_adder_{n_bits}")
+    nvdd = b.node(True, vdd)
+    lv = (rng.uniform(2 * n_bits + 1) < 0.5) * vdd
+    ins = [b.node(True, float(v)) for v in lv]
+    cin = ins[-1]
+    sums = []
+    for k in range(n_bits):
+        cin, sm = _mirror_adder(b, nvdd, ins[2 * k], ins[2 * k + 1], cin)
+        sums.append(sm)
+    W, L = _draw_wl(Rng(seed, 10), len(b.dev))
+    return b.build(W, L, dict(n_bits=n_bits, cout=cin, sums=sums))
+
+
+def transistor_connections(net: Netlist) -> np.ndarray:
+    """(device, terminal) pairs on a free node that at least two devices touch: the
+    transistor-to-transistor connections where a series resistor can split a net."""
+    nodes = net.dev_nodes
+    free = net.node_fixed == 0
+    devs_at = {}
+    for k in range(net.n_dev):
+        for t in range(4):
+            v = int(nodes[k, t])
+            if free[v]:
+                devs_at.setdefault(v, set()).add(k)
+    out = [(k, t) for k in range(net.n_dev) for t in range(4)
+           if free[int(nodes[k, t])] and len(devs_at[int(nodes[k, t])]) >= 2]
+    return np.asarray(out, dtype=np.int64).reshape(-1, 2)
+
+
+def insert_series_resistors(net: Netlist, per_group: Optional[int] = None, group_size: int = 28,
+                            r_ohm: float = 1e-3, seed: int = DEFAULT_SEED) -> Netlist:
+    """Move transistor terminals off shared nets through small series resistors (the paper's
+    R14 / R89 netlists, Sec. II Benchmark 2): each selected (device, terminal) connection gets
+    a new node tied to the original net by r_ohm. per_group None selects every connection;
+    otherwise per_group connections drawn at random within each group of group_size devices
+    (one full adder = 28 devices)."""
+    conns = transistor_connections(net)
+    if per_group is not None:
+        rng = Rng(seed, 11)
+        pick = []
+        grp = conns[:, 0] // group_size
+        for g in np.unique(grp):
+            idx = np.nonzero(grp == g)[0]
+            order = np.argsort(rng.uniform(len(idx)), kind="stable")
+            pick.extend(idx[order[:per_group]].tolist())
+        conns = conns[np.sort(np.asarray(pick, dtype=np.int64))]
+    dev_nodes = net.dev_nodes.copy()
+    n0 = net.n_nodes
+    new = np.arange(n0, n0 + len(conns))
+    res = np.stack([new, dev_nodes[conns[:, 0], conns[:, 1]]], 1)
+    dev_nodes[conns[:, 0], conns[:, 1]] = new
+    out = dataclasses.replace(
+        net, name=f"{net.name}_R{len(conns)}",
+        node_fixed=np.concatenate([net.node_fixed, np.zeros(len(conns), np.uint8)]),
+        node_vfix=np.concatenate([net.node_vfix, np.zeros(len(conns))]),
+        dev_nodes=dev_nodes.astype(np.int32),
+        res_nodes=np.concatenate([net.res_nodes, res.astype(np.int32)]).reshape(-1, 2),
+        res_G=np.concatenate([net.res_G, np.full(len(conns), 1.0 / r_ohm)]),
+        meta=dict(net.meta, inserted=len(conns)))
+    return out
+
+
 def batch_circuits(n_circ: int = 4096, seed: int = DEFAULT_SEED) -> List[Netlist]:
     """Uneven sizing-candidate batch: 55% inverter chains (16..512 stages), 22.5% 11-stage
     rings, 22.5% 5T OTAs. Each circuit draws template sizes (W ~ U[0.5,5] um, L ~ U[0.1,1] um,

@@ -1,7 +1,9 @@
 """GPU parity of the transient companion stamp (eec_eval_stamp_tran) against the oracle, and a
 transient loop whose every Newton iteration is stamped on the GPU against the oracle's own
-transient solver. Tolerances as for the DC stamp: 1e-12 per entry relative to
-max(|oracle|, sum of |contributions|)."""
+transient solver. A and b: 1e-12 per entry relative to max(|oracle|, S_e), where S_e sums, over
+the contributions to the entry, the size of each device's Jacobian entry as the oracle's
+magnitude forward mode measures it (the sum of |chain-rule products|, so that entries whose
+intrinsic-capacitance terms cancel are judged against the size of those terms)."""
 import numpy as np
 import pytest
 
