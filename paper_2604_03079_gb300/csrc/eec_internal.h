@@ -24,7 +24,9 @@ struct CardK {
 };
 
 // Per-device derived parameters, stored structure-of-arrays [kNPrm][N] by layout position.
-enum Prm : int { P_BETA0 = 0, P_CE, P_INV_CE, P_LAML, P_ISAT, P_COXT, P_COVS, P_COVD, kNPrm };
+enum Prm : int {
+  P_BETA0 = 0, P_CE, P_INV_CE, P_LAML, P_ISAT, P_COXT, P_COVS, P_COVD, P_ISATVT, P_ISATVTG, kNPrm
+};
 
 // Contribution slots of one device: rows (d, s, b) x columns (d, g, s, b) -> j = 4 r + u,
 // then the three right-hand-side rows j = 12 + r.

@@ -83,6 +83,8 @@ __device__ __forceinline__ PrmS<double> load_prm(const DevTopo& T, int k) {
   P.Coxt = __ldg(p + P_COXT * N + k);
   P.CovS = __ldg(p + P_COVS * N + k);
   P.CovD = __ldg(p + P_COVD * N + k);
+  P.IsatVt = __ldg(p + P_ISATVT * N + k);
+  P.IsatVtG = __ldg(p + P_ISATVTG * N + k);
   return P;
 }
 
@@ -282,7 +284,7 @@ __global__ void k_params(DevTopo T, const double* __restrict__ Wo, const double*
     const double vbs = flip(T.vfix[~ti.w] - T.vfix[~ti.z], psb);
     double sqs, Vthb, dVth, Ab, dAb, Ijs, gjs;
     body_terms<double>(c, vbs, sqs, Vthb, dVth, Ab, dAb);
-    junction<double>(c, P.Isat, vbs, Ijs, gjs);
+    junction<double>(c, P, vbs, Ijs, gjs);
     double* q0 = T.bodyk + k;
     q0[0] = sqs;
     q0[N] = Vthb;
@@ -300,6 +302,8 @@ __global__ void k_params(DevTopo T, const double* __restrict__ Wo, const double*
   T.prm[P_COXT * N + k] = P.Coxt;
   T.prm[P_COVS * N + k] = P.CovS;
   T.prm[P_COVD * N + k] = P.CovD;
+  T.prm[P_ISATVT * N + k] = P.IsatVt;
+  T.prm[P_ISATVTG * N + k] = P.IsatVtG;
 }
 
 // Segmented reduction: entry e of [A ; b] = linear part + its contributions (deterministic, no

@@ -44,6 +44,8 @@ struct PrmS {
   S Coxt;    // Cox W L
   S CovS;    // CGSO W
   S CovD;    // CGDO W
+  S IsatVt;  // Isat / Vt   (junction conductance slope)
+  S IsatVtG; // Isat / Vt + GMIN
 };
 
 // Per-device parameters from W and L (the forward stores these per position; the backward
@@ -60,6 +62,8 @@ __device__ __forceinline__ PrmS<S> derive_params(const CardK& c, const S& W, con
   P.Coxt = c.Cox * W * L;
   P.CovS = c.CGSO * W;
   P.CovD = c.CGDO * W;
+  P.IsatVt = P.Isat * c.inv_Vt;
+  P.IsatVtG = P.IsatVt + c.GMIN;
   return P;
 }
 
@@ -75,17 +79,23 @@ template <class S>
 __device__ __forceinline__ S sel(bool c, const S& a, const S& b) { return c ? a : b; }
 
 // Junction current and conductance: Ij(v) = Isat (explim(v/Vt) - 1) + GMIN v with
-// explim(z) = exp(z) for z <= 40 and e^40 (1 + z - 40) above.
+// explim(z) = exp(z) for z <= 40 and e^40 (1 + z - 40) above; gj = dIj/dv
+// = (Isat/Vt) explim'(z) + GMIN, written as fma(Isat/Vt, expm1(z), Isat/Vt + GMIN). Deep in
+// reverse bias (expm1 -> -1) the Isat/Vt e^z part of gj keeps an absolute error of about
+// 1e-16 Isat/Vt, negligible beside GMIN (1e-12 S with the default cards).
 template <class S>
-__device__ __forceinline__ void junction(const CardK& c, const S& Isat, const S& v, S& Ij, S& gj) {
+__device__ __forceinline__ void junction(const CardK& c, const PrmS<S>& P, const S& v, S& Ij,
+                                         S& gj) {
   const S z = v * c.inv_Vt;
-  const bool over = sval(z) > 40.0;
-  const S zc = over ? S(40.0) : z;
-  const S em1 = expm1_(zc);
-  const S ez = em1 + 1.0;
-  const S lin = over ? (z - 40.0) : S(0.0);
-  Ij = Isat * (em1 + ez * lin) + c.GMIN * v;
-  gj = Isat * c.inv_Vt * ez + c.GMIN;
+  if (sval(z) <= 40.0) {
+    const S em1 = expm1_(z);
+    Ij = P.Isat * em1 + c.GMIN * v;
+    gj = P.IsatVt * em1 + P.IsatVtG;
+  } else {
+    const S em1 = expm1_(S(40.0));
+    Ij = P.Isat * (em1 + (em1 + 1.0) * (z - 40.0)) + c.GMIN * v;
+    gj = P.IsatVt * em1 + P.IsatVtG;
+  }
 }
 
 // Terms that depend on vbs alone: body effect (2) and bulk-charge factor (4).
@@ -122,15 +132,18 @@ constexpr int kNBody = 7;
 template <class S>
 struct Chan {
   S Ids, gm, gds, gmb, Vg, F1;
-  S Vdsat, Vdseff;                      // for the charge partition
+  S Vdsat, Vdseff, inv_Vdsat_parts[3];  // for the charge partition: Dd, 1/EsatL, 1/Vgst2
   S sig, F1_Vg, F1_Ab, F1_vds;          // for the charge Jacobian
   S Vdsat_Vg, Vdsat_Ab, Vde_Vg, Vde_Ab, Vde_vds;
 };
 
+// want_vbs = false skips the vbs (bulk-charge) derivative chain: gmb and the Ab partials come
+// back zero. Callers pass false only when the S and b columns of the Jacobian are not stamped.
 template <class S>
 __device__ __forceinline__ void channel(const CardK& c, const PrmS<S>& P, const S& vgs,
                                         const S& vds, const S& Vthb, const S& dVth_dvbs,
-                                        const S& Ab, const S& dAb_dvbs, Chan<S>& ch) {
+                                        const S& Ab, const S& dAb_dvbs, Chan<S>& ch,
+                                        bool want_vbs = true) {
   const S Vth = Vthb - c.ETA0 * vds;
 
   // (3) Vgsteff = nVt softplus(z), dVgsteff/dz = nVt sigmoid(z)
@@ -159,7 +172,7 @@ __device__ __forceinline__ void channel(const CardK& c, const PrmS<S>& P, const 
   const S r2 = EsatL * inv_Dd;
   const S Vdsat = EsatL * r1;
   const S Vdsat_Vg = r1 * r1 * EsatL_Vg + Ab * (r2 * r2);   // dVgst2/dVg = 1
-  const S Vdsat_Ab = -(r2 * r2) * Vgst2;
+
 
   // (7) Vdseff = 2 Vdsat vds / (Vdsat + vds + DELTA + R2), R2 = sqrt(t^2 + 4 DELTA Vdsat)
   const S t = Vdsat - vds - c.DELTA;
@@ -187,29 +200,34 @@ __device__ __forceinline__ void channel(const CardK& c, const PrmS<S>& P, const 
 
   // partial derivatives with Vg, Ab and vds as independent variables
   const S Vde_Vg = Vde_Vdsat * Vdsat_Vg;
-  const S Vde_Ab = Vde_Vdsat * Vdsat_Ab;
   const S F1_Vg = -(Ab * h) * (Vde_Vg - Vdseff * inv_Vgst2);
-  const S F1_Ab = -h * (Vdseff + Ab * Vde_Ab);
   const S F1_vds = -(Ab * h) * Vde_vds;
   const S F2_Vg = inv_EsatL * (Vde_Vg - Vdseff * dden * inv_den);
-  const S F2_Ab = inv_EsatL * Vde_Ab;
   const S F2_vds = inv_EsatL * Vde_vds;
   const S F3_Vg = -(P.lamL * Vde_Vg);
-  const S F3_Ab = -(P.lamL * Vde_Ab);
   const S F3_vds = P.lamL * (1.0 - Vde_vds);
   const S Pb_Vg = beta * (1.0 - Vg * dden * inv_den);
   const S dV_Vg = Vde_Vg * F13 + Vdseff * (F1_Vg * F3 + F1 * F3_Vg);
-  const S dV_Ab = Vde_Ab * F13 + Vdseff * (F1_Ab * F3 + F1 * F3_Ab);
   const S dV_vds = Vde_vds * F13 + Vdseff * (F1_vds * F3 + F1 * F3_vds);
   const S Ids_Vg = (Pb_Vg * VF13 + Pb * dV_Vg - Ids * F2_Vg) * inv_F2;
-  const S Ids_Ab = (Pb * dV_Ab - Ids * F2_Ab) * inv_F2;
   const S Ids_vds = (Pb * dV_vds - Ids * F2_vds) * inv_F2;
 
   // chain to the mode-frame voltages: dVg/dvgs = sig, dVg/dvds = sig ETA0,
   // dVg/dvbs = -sig dVth/dvbs
   const S gm = Ids_Vg * sig;
   const S gds = gm * c.ETA0 + Ids_vds;
-  const S gmb = Ids_Ab * dAb_dvbs - gm * dVth_dvbs;
+  // vbs chain through the bulk-charge factor, only when its columns are stamped
+  S gmb = S(0.0), Vdsat_Ab = S(0.0), Vde_Ab = S(0.0), F1_Ab = S(0.0);
+  if (want_vbs) {
+    Vdsat_Ab = -(r2 * r2) * Vgst2;
+    Vde_Ab = Vde_Vdsat * Vdsat_Ab;
+    F1_Ab = -h * (Vdseff + Ab * Vde_Ab);
+    const S F2_Ab = inv_EsatL * Vde_Ab;
+    const S F3_Ab = -(P.lamL * Vde_Ab);
+    const S dV_Ab = Vde_Ab * F13 + Vdseff * (F1_Ab * F3 + F1 * F3_Ab);
+    const S Ids_Ab = (Pb * dV_Ab - Ids * F2_Ab) * inv_F2;
+    gmb = Ids_Ab * dAb_dvbs - gm * dVth_dvbs;
+  }
 
   ch.Ids = Ids;
   ch.gm = gm;
@@ -219,6 +237,9 @@ __device__ __forceinline__ void channel(const CardK& c, const PrmS<S>& P, const 
   ch.F1 = F1;
   ch.Vdsat = Vdsat;
   ch.Vdseff = Vdseff;
+  ch.inv_Vdsat_parts[0] = Dd;
+  ch.inv_Vdsat_parts[1] = inv_EsatL;
+  ch.inv_Vdsat_parts[2] = inv_Vgst2;
   ch.sig = sig;
   ch.F1_Vg = F1_Vg;
   ch.F1_Ab = F1_Ab;
@@ -254,7 +275,7 @@ __device__ __forceinline__ void ees_l1(const CardK& c, unsigned long long psb, c
     body_terms<S>(c, flip(V[3] - VS, psb), sqs, Vthb, dVth_dvbs, Ab, dAb_dvbs);
   }
   Chan<S> ch;
-  channel<S>(c, P, vgs, vds, Vthb, dVth_dvbs, Ab, dAb_dvbs, ch);
+  channel<S>(c, P, vgs, vds, Vthb, dVth_dvbs, Ab, dAb_dvbs, ch, !(sb_fixed && fwd));
   const S& Ids = ch.Ids;
   const S& gm = ch.gm;
   const S& gds = ch.gds;
@@ -272,12 +293,12 @@ __device__ __forceinline__ void ees_l1(const CardK& c, unsigned long long psb, c
 
   // (10) junctions on the physical terminals
   S Ijd, gjd, Ijs, gjs;
-  junction<S>(c, P.Isat, flip(V[3] - V[0], psb), Ijd, gjd);
+  junction<S>(c, P, flip(V[3] - V[0], psb), Ijd, gjd);
   if (sb_fixed) {
     Ijs = S(bk->Ijs);
     gjs = S(bk->gjs);
   } else {
-    junction<S>(c, P.Isat, flip(V[3] - V[2], psb), Ijs, gjs);
+    junction<S>(c, P, flip(V[3] - V[2], psb), Ijs, gjs);
   }
 
   o.I[0] = Ichd - flip(Ijd, psb);
@@ -295,7 +316,8 @@ __device__ __forceinline__ void ees_l1(const CardK& c, unsigned long long psb, c
     const S Qb = -(P.Coxt * c.K1 * sqs);
     const S Qinv = -(P.Coxt * Vg * F1);
     const S Qg0 = -(Qb + Qinv);
-    const S inv_Vdsat = rcp(ch.Vdsat);
+    // 1 / Vdsat = Dd / (EsatL Vgst2): both reciprocals are already at hand
+    const S inv_Vdsat = ch.inv_Vdsat_parts[0] * ch.inv_Vdsat_parts[1] * ch.inv_Vdsat_parts[2];
     const S sr = ch.Vdseff * inv_Vdsat;
     const S fD = 0.5 - (0.5 - c.XPART) * sr;
     const S QD = fD * Qinv;
