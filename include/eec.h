@@ -144,6 +144,14 @@ EEC_API int eec_build_scatter(eec_ctx* ctx, int32_t* n_unknowns, int64_t* nnz);
 EEC_API int eec_get_pattern(const eec_ctx* ctx, int32_t* row_ptr, int32_t* col_idx,
                     int32_t* unk_of_node);
 
+/*
+ * Host-side race check of the colour schedule (Sec. II: same-colour devices must never stamp
+ * the same entry). Verifies that no two devices of one colour write a common row of A or b —
+ * rows d, s, b (DC) plus g when with_gate_rows (transient). Returns EEC_EINVAL naming the two
+ * devices on a conflict. Needs eec_build_scatter (host part) after eec_color.
+ */
+EEC_API int eec_verify_coloring(const eec_ctx* ctx, int32_t with_gate_rows);
+
 /* Colour offsets [C+1] (host) of the device layout; colour c holds positions
  * off[c] .. off[c+1]-1. Fails with EEC_ESTATE when not coloured. */
 EEC_API int eec_get_color_offsets(const eec_ctx* ctx, int32_t* off);

@@ -63,6 +63,7 @@ _SIG = {
     "eec_build_scatter": (ctypes.c_int, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I64)]),
     "eec_get_pattern": (ctypes.c_int, [_P, _P, _P, _P]),
     "eec_get_color_offsets": (ctypes.c_int, [_P, _P]),
+    "eec_verify_coloring": (ctypes.c_int, [_P, _I32]),
     "eec_update_params": (ctypes.c_int, [_P, _P, _P, _P]),
     "eec_set_variant": (ctypes.c_int, [_P, _I32]),
     "eec_get_variant": (ctypes.c_int, [_P, ctypes.POINTER(_I32)]),
@@ -249,6 +250,10 @@ def eec_get_pattern(ctx, n_nodes):
     _check(ctx, _load().eec_get_pattern(ctx, rp.ctypes.data_as(_P), col.ctypes.data_as(_P),
                                     unk.ctypes.data_as(_P)))
     return rp, col, unk
+
+
+def eec_verify_coloring(ctx, with_gate_rows=False):
+    _check(ctx, _load().eec_verify_coloring(ctx, int(bool(with_gate_rows))))
 
 
 def eec_get_color_offsets(ctx):

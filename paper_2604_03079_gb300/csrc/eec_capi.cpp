@@ -2,6 +2,7 @@
 // MNA pattern and scatter-map construction, device uploads, schedule dispatch, CUDA graphs,
 // autotuning and the device status word.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -377,8 +378,15 @@ int capture(eec_ctx* c, int v, const double* x, double* A, double* b, double* q,
 
 // eval_stamp with schedule v; the per-colour schedules replay a cached CUDA graph unless
 // phase timing is on.
+// Host-side NVTX range (tracing): marks the enqueue of one library call in profiler timelines.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
 int eval_with(eec_ctx* c, int v, const double* x, double* A, double* b, double* q,
               cudaStream_t s) {
+  NvtxRange range("eec/eval_stamp");
   if (!c->prof && (v == EEC_VARIANT_COLOR_FUSED || v == EEC_VARIANT_COLOR_BUFFERED)) {
     const void* key[4] = {x, A, b, q};
     const int blk = c->opt.block ? c->opt.block : c->tuned_block;
@@ -917,6 +925,40 @@ int eec_build_scatter(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_out) {
   return EEC_OK;
 }
 
+int eec_verify_coloring(const eec_ctx* cc, int32_t with_gate_rows) {
+  eec_ctx* c = const_cast<eec_ctx*>(cc);
+  int rc = check_pattern(c);
+  if (rc) return rc;
+  if (!c->colored) return fail(c, EEC_ESTATE, "not coloured");
+  // Within a colour, every written A entry and b row must belong to one device: mark each row
+  // with the last (colour, device) that wrote it. A device writes rows of its free terminals
+  // d, s, b (and g when with_gate_rows); every entry it writes lies in one of those rows, so
+  // disjoint row sets imply disjoint entry sets.
+  std::vector<long long> owner(c->n, -1);
+  for (int k = 0; k < c->n_dev; ++k) {
+    const long long tag = (long long)c->color[k] * c->n_dev + k;
+    int seen[4];
+    int m = 0;
+    for (int t = 0; t < 4; ++t) {
+      if (t == 1 && !with_gate_rows) continue;
+      const int row = c->unk[c->dn[4 * k + t]];
+      if (row < 0) continue;
+      bool dup = false;
+      for (int i = 0; i < m; ++i) dup = dup || seen[i] == row;
+      if (dup) continue;
+      seen[m++] = row;
+      const long long prev = owner[row];
+      if (prev >= 0 && prev / c->n_dev == c->color[k])
+        return fail(c, EEC_EINVAL, "devices " + std::to_string(prev % c->n_dev) + " and " +
+                                       std::to_string(k) + " share colour " +
+                                       std::to_string(c->color[k]) + " and write row " +
+                                       std::to_string(row));
+      owner[row] = tag;
+    }
+  }
+  return EEC_OK;
+}
+
 int eec_get_pattern(const eec_ctx* cc, int32_t* row_ptr, int32_t* col_idx, int32_t* unk_of_node) {
   eec_ctx* c = const_cast<eec_ctx*>(cc);
   int rc = check_pattern(c);
@@ -992,6 +1034,7 @@ int eec_eval_stamp(eec_ctx* c, const double* x, double* A, double* b, double* q,
 int eec_eval_stamp_tran(eec_ctx* c, const double* x, const double* q_prev, const double* i_prev,
                         double alpha, double beta, double* A, double* b, double* q, double* icap,
                         void* stream) {
+  NvtxRange range("eec/eval_stamp_tran");
   int rc = check_built(c);
   if (rc) return rc;
   if (!x || !q_prev || !A || !b || !q) return fail(c, EEC_EINVAL, "NULL x, q_prev, A, b or q");
@@ -1022,6 +1065,7 @@ int eec_eval_stamp_tran(eec_ctx* c, const double* x, const double* q_prev, const
 
 int eec_eval_stamp_bwd(eec_ctx* c, const double* x, const double* gA, const double* gb,
                        double* gx, double* gW, double* gL, void* stream) {
+  NvtxRange range("eec/eval_stamp_bwd");
   int rc = check_built(c);
   if (rc) return rc;
   if (!x || !gA || !gb || !gx || !gW || !gL) return fail(c, EEC_EINVAL, "NULL argument");

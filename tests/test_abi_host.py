@@ -148,6 +148,28 @@ def test_host_pattern_equals_oracle_pattern(eec, net):
         eec.eec_destroy(ctx)
 
 
+@pytest.mark.parametrize("rule", [0, 1, 2])
+def test_coloring_verifier(eec, rule):
+    # every rule gives a race-free DC schedule; only rules 0 and 1 also cover gate rows
+    net = netgen.sram(6, 8)
+    ctx = _ctx_with(eec, net, rule)
+    try:
+        eec.eec_color(ctx, n_dev=net.n_dev)
+        try:
+            eec.eec_build_scatter(ctx)
+        except eec.EECError as e:
+            assert e.code == eec.EEC_ECUDA
+        eec.eec_verify_coloring(ctx, with_gate_rows=False)
+        if rule == 2:
+            with pytest.raises(eec.EECError) as e:
+                eec.eec_verify_coloring(ctx, with_gate_rows=True)
+            assert "share colour" in str(e.value)
+        else:
+            eec.eec_verify_coloring(ctx, with_gate_rows=True)
+    finally:
+        eec.eec_destroy(ctx)
+
+
 def test_batch_offsets_host(eec):
     nets = netgen.batch_circuits(12, seed=9)
     merged = netgen.concat(nets)
