@@ -185,6 +185,20 @@ EEC_API int eec_eval_stamp(eec_ctx* ctx, const double* x_dev, double* A_values_d
                    double* q_dev, void* cuda_stream);
 
 /*
+ * eec_eval_stamp with host buffers: x_host [n] in; A_host [nnz], b_host [n], q_host [4*n_dev]
+ * (nullable) out, layouts as in eec_eval_stamp. The library copies x into its own device
+ * buffer, evaluates and stamps into its own device buffers (allocated on the first call), and
+ * copies A and b back. When q_host is page-locked (cudaHostAlloc / cudaHostRegister) the
+ * evaluate kernel writes the charges directly into it over the host link; otherwise they are
+ * staged and copied. Page-locked buffers make all copies asynchronous; pageable ones still
+ * work. Stream-ordered on cuda_stream: the host outputs are valid once the stream has
+ * synchronised. Calls on one context share the staging buffers, so calls that overlap on the
+ * GPU (unordered streams) race on them.
+ */
+EEC_API int eec_eval_stamp_host(eec_ctx* ctx, const double* x_host, double* A_host, double* b_host,
+                                double* q_host, void* cuda_stream);
+
+/*
  * Transient companion stamp of one Newton iterate of a time step (the transient loop of Sec. II,
  * Fig. 1, re-forms A x = b at every Newton iteration of every step). The terminal charges q_t
  * are integrated by a one-step rule: the capacitive current into the device is

@@ -70,6 +70,7 @@ _SIG = {
     "eec_get_tuning": (ctypes.c_int, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "eec_eval_stamp": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "eec_eval_stamp_bwd": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "eec_eval_stamp_host": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "eec_eval_stamp_tran": (ctypes.c_int, [_P, _P, _P, _P, _F64, _F64, _P, _P, _P, _P, _P]),
     "eec_eval_stamp_bwd_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "eec_graph_capture": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
@@ -296,6 +297,25 @@ def eec_get_tuning(ctx):
 def eec_eval_stamp(ctx, x, A, b, q=None, stream=None):
     _check(ctx, _load().eec_eval_stamp(ctx, _d(x, name="x"), _d(A, name="A"), _d(b, name="b"),
                                    _d(q, name="q"), _stream(stream)))
+
+
+def _hp(t, name):
+    """Host buffer pointer of a contiguous float64 CPU tensor or numpy array (None -> NULL)."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        if t.is_cuda or not t.is_contiguous() or str(t.dtype) != "torch.float64":
+            raise TypeError(f"{name} must be a contiguous float64 host tensor")
+        return _P(t.data_ptr())
+    if t.dtype != np.float64 or not t.flags["C_CONTIGUOUS"]:
+        raise TypeError(f"{name} must be a contiguous float64 array")
+    return t.ctypes.data_as(_P)
+
+
+def eec_eval_stamp_host(ctx, x, A, b, q=None, stream=None):
+    """eval_stamp with host buffers (torch CPU tensors, page-locked for async copies, or numpy)."""
+    _check(ctx, _load().eec_eval_stamp_host(ctx, _hp(x, "x"), _hp(A, "A"), _hp(b, "b"),
+                                            _hp(q, "q"), _stream(stream)))
 
 
 def eec_eval_stamp_tran(ctx, x, q_prev, i_prev, alpha, beta, A, b, q, i=None, stream=None):

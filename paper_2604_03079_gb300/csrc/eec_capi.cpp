@@ -75,6 +75,11 @@ struct eec_ctx {
   long long n_kernels = 0;
   long long auto_kernels = 0;  // kernel nodes of the cached graph
   long long user_kernels = 0;  // kernel nodes of the user graph
+  // staging buffers of eec_eval_stamp_host (allocated on its first call)
+  double* h_x = nullptr;
+  double* h_A = nullptr;
+  double* h_b = nullptr;
+  double* h_q = nullptr;
 };
 
 namespace {
@@ -122,6 +127,7 @@ void drop_graphs(eec_ctx* c) {
 
 void free_topology(eec_ctx* c) {
   drop_graphs(c);
+  c->h_x = c->h_A = c->h_b = c->h_q = nullptr;  // freed with the other device arrays
   if (!c->dmem.empty()) cudaDeviceSynchronize();
   for (void* p : c->dmem) cudaFree(p);
   c->dmem.clear();
@@ -1029,6 +1035,43 @@ int eec_eval_stamp(eec_ctx* c, const double* x, double* A, double* b, double* q,
   if (rc) return rc;
   if (!x || !A || !b) return fail(c, EEC_EINVAL, "NULL x, A or b");
   return eval_with(c, effective_variant(c), x, A, b, q, static_cast<cudaStream_t>(stream));
+}
+
+int eec_eval_stamp_host(eec_ctx* c, const double* x_host, double* A_host, double* b_host,
+                        double* q_host, void* stream) {
+  NvtxRange range("eec/eval_stamp_host");
+  int rc = check_built(c);
+  if (rc) return rc;
+  if (!x_host || !A_host || !b_host) return fail(c, EEC_EINVAL, "NULL x, A or b");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!c->h_x) {
+    if ((rc = dalloc(c, &c->h_x, c->n)) || (rc = dalloc(c, &c->h_A, c->nnz)) ||
+        (rc = dalloc(c, &c->h_b, c->n)))
+      return rc;
+  }
+  // Charges: written by the evaluate kernel straight into page-locked host memory when the
+  // caller's buffer is page-locked (the host link is idle while the FP64 pipe is busy),
+  // otherwise staged on the device and copied.
+  double* qk = nullptr;
+  if (q_host) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, q_host) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+        at.devicePointer) {
+      qk = static_cast<double*>(at.devicePointer);
+    } else {
+      cudaGetLastError();
+      if (!c->h_q && (rc = dalloc(c, &c->h_q, (size_t)4 * c->n_dev))) return rc;
+      qk = c->h_q;
+    }
+  }
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_x, x_host, sizeof(double) * c->n, cudaMemcpyHostToDevice, s));
+  if ((rc = eval_with(c, effective_variant(c), c->h_x, c->h_A, c->h_b, qk, s))) return rc;
+  CUDA_TRY(c, cudaMemcpyAsync(A_host, c->h_A, sizeof(double) * c->nnz, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(c, cudaMemcpyAsync(b_host, c->h_b, sizeof(double) * c->n, cudaMemcpyDeviceToHost, s));
+  if (q_host && qk == c->h_q)
+    CUDA_TRY(c, cudaMemcpyAsync(q_host, c->h_q, sizeof(double) * 4 * c->n_dev,
+                                cudaMemcpyDeviceToHost, s));
+  return EEC_OK;
 }
 
 int eec_eval_stamp_tran(eec_ctx* c, const double* x, const double* q_prev, const double* i_prev,

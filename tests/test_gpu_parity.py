@@ -360,6 +360,28 @@ def test_grid_barrier_timeout_is_reported_and_the_context_recovers(eec):
     check_against_oracle(eec, circ, o, x, 1)      # the persistent schedule still works
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_buffer_entry_point(eec, pinned):
+    import torch
+    net = netgen.sram(16, 16)
+    o = oracle.Oracle(net, CARDS)
+    circ = eec.Circuit(net, CARDS)
+    for seed in range(2):
+        x = netgen.random_x(net, seed=seed)
+        mk = (lambda n: torch.empty(n, dtype=torch.float64).pin_memory()) if pinned else \
+             (lambda n: torch.empty(n, dtype=torch.float64))
+        xh, Ah, bh, qh = mk(circ.n), mk(circ.nnz), mk(circ.n), mk(4 * circ.n_dev)
+        xh.copy_(torch.as_tensor(x))
+        eec.eec_eval_stamp_host(circ.ctx, xh, Ah, bh, qh)
+        torch.cuda.synchronize()
+        assert circ.status() == 0
+        r = o.eval_stamp(x, want_q=True, want_scale=True)
+        assert rel_err(Ah.numpy(), r["A"], r["A_scale"]).max() <= TOL
+        assert rel_err(bh.numpy(), r["b"], r["b_scale"]).max() <= TOL
+        qs = np.maximum(np.abs(r["q"]).max(axis=0, keepdims=True), 1e-300)
+        assert (np.abs(qh.numpy().reshape(4, -1) - r["q"]) / qs).max() <= 1e-13
+
+
 def test_debug_checks_flag_non_finite_inputs(eec):
     net = netgen.inverter_chain(8)
     circ = eec.Circuit(net, CARDS, debug_checks=True)
