@@ -78,6 +78,9 @@ typedef struct {
                             or 8, 16, 32, 64, 96, 128 */
   int32_t conflict_rule; /* EEC_CONFLICT_*; default EEC_CONFLICT_FREE_NODE */
   int32_t debug_checks;  /* nonzero: kernels flag non-finite outputs in the status word */
+  int32_t host_chunks;   /* eec_eval_stamp_host: chunks whose charges are copied out while later
+                            chunks are evaluated; 0 = by size (3 from 2^18 devices, 2 from 2^17,
+                            else 1), or 1..64 */
 } eec_options;
 
 /* eec_options with every field at its default. */
@@ -188,12 +191,14 @@ EEC_API int eec_eval_stamp(eec_ctx* ctx, const double* x_dev, double* A_values_d
  * eec_eval_stamp with host buffers: x_host [n] in; A_host [nnz], b_host [n], q_host [4*n_dev]
  * (nullable) out, layouts as in eec_eval_stamp. The library copies x into its own device
  * buffer, evaluates and stamps into its own device buffers (allocated on the first call), and
- * copies A and b back. When q_host is page-locked (cudaHostAlloc / cudaHostRegister) the
- * evaluate kernel writes the charges directly into it over the host link; otherwise they are
- * staged and copied. Page-locked buffers make all copies asynchronous; pageable ones still
- * work. Stream-ordered on cuda_stream: the host outputs are valid once the stream has
- * synchronised. Calls on one context share the staging buffers, so calls that overlap on the
- * GPU (unordered streams) race on them.
+ * copies A, b and q back. Under the order-free schedules (ATOMIC, SEGREDUCE) the devices are
+ * evaluated in opt.host_chunks spans of original index, and each span's charges are copied on a
+ * library stream while the next span is evaluated; the call joins that stream back into
+ * cuda_stream. Page-locked buffers (cudaHostAlloc / cudaHostRegister) make every copy
+ * asynchronous; pageable ones work but the call returns only once their copies are done.
+ * Stream-ordered on cuda_stream: the host outputs are valid once the stream has synchronised.
+ * Calls on one context share the staging buffers, so calls that overlap on the GPU (unordered
+ * streams) race on them.
  */
 EEC_API int eec_eval_stamp_host(eec_ctx* ctx, const double* x_host, double* A_host, double* b_host,
                                 double* q_host, void* cuda_stream);

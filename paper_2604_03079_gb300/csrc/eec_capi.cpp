@@ -80,6 +80,14 @@ struct eec_ctx {
   double* h_A = nullptr;
   double* h_b = nullptr;
   double* h_q = nullptr;
+  // chunk plan of eec_eval_stamp_host: chunk k = original devices hc_lo[k] .. hc_lo[k+1]-1, as
+  // hc_nr[k] library-order ranges at d_hrbeg + hc_rb[k] with prefix sums at d_hroff + hc_ro[k]
+  int host_K = 0;  // 0 = no plan yet
+  std::vector<int> hc_lo, hc_rb, hc_ro, hc_nr, hc_total;
+  int* d_hrbeg = nullptr;
+  int* d_hroff = nullptr;
+  cudaStream_t side = nullptr;   // charge copies of eec_eval_stamp_host
+  std::vector<cudaEvent_t> hev;  // chunk done (K) + side stream done (1)
 };
 
 namespace {
@@ -128,6 +136,8 @@ void drop_graphs(eec_ctx* c) {
 void free_topology(eec_ctx* c) {
   drop_graphs(c);
   c->h_x = c->h_A = c->h_b = c->h_q = nullptr;  // freed with the other device arrays
+  c->host_K = 0;
+  c->d_hrbeg = c->d_hroff = nullptr;
   if (!c->dmem.empty()) cudaDeviceSynchronize();
   for (void* p : c->dmem) cudaFree(p);
   c->dmem.clear();
@@ -351,6 +361,57 @@ int run_variant(eec_ctx* c, int v, const double* x, double* A, double* b, double
   return EEC_OK;
 }
 
+// Chunk plan of eec_eval_stamp_host. The layout is colour-major, then grouped by card and
+// polarity, then in original order, so library positions form maximal runs of increasing
+// original index; within a run, the devices of an original-index span are contiguous. Chunk k
+// (original indices N k / K .. N (k+1) / K - 1) is one range per run. K = opt.host_chunks, or
+// by size: 3 from 2^18 devices, 2 from 2^17, else 1 (each extra launch ends in a partial wave
+// that costs about as much as a third of the charge copy it hides); 1 when the runs are too
+// many (> 4096).
+int host_plan(eec_ctx* c) {
+  if (c->host_K) return EEC_OK;
+  const int N = c->n_dev;
+  int K = c->opt.host_chunks;
+  if (K == 0) K = N >= (1 << 18) ? 3 : N >= (1 << 17) ? 2 : 1;
+  if (K > N) K = N > 0 ? N : 1;
+  std::vector<int> run{0};
+  for (int p = 1; p < N; ++p)
+    if (c->perm[p] < c->perm[p - 1]) run.push_back(p);
+  run.push_back(N);
+  if (run.size() - 1 > 4096) K = 1;
+  c->hc_lo.assign(K + 1, 0);
+  c->hc_rb.assign(K, 0);
+  c->hc_ro.assign(K, 0);
+  c->hc_nr.assign(K, 0);
+  c->hc_total.assign(K, 0);
+  for (int k = 0; k <= K; ++k) c->hc_lo[k] = (int)((long long)N * k / K);
+  std::vector<int> rbeg, roff;
+  const int* P = c->perm.data();
+  for (int k = 0; k < K; ++k) {
+    c->hc_rb[k] = (int)rbeg.size();
+    c->hc_ro[k] = (int)roff.size();
+    roff.push_back(0);
+    int tot = 0;
+    for (size_t r = 0; r + 1 < run.size(); ++r) {
+      const int p0 = (int)(std::lower_bound(P + run[r], P + run[r + 1], c->hc_lo[k]) - P);
+      const int p1 = (int)(std::lower_bound(P + run[r], P + run[r + 1], c->hc_lo[k + 1]) - P);
+      if (p1 > p0) {
+        rbeg.push_back(p0);
+        tot += p1 - p0;
+        roff.push_back(tot);
+      }
+    }
+    c->hc_nr[k] = (int)rbeg.size() - c->hc_rb[k];
+    c->hc_total[k] = tot;
+  }
+  if (K > 1) {
+    int rc;
+    if ((rc = dupload(c, &c->d_hrbeg, rbeg)) || (rc = dupload(c, &c->d_hroff, roff))) return rc;
+  }
+  c->host_K = K;
+  return EEC_OK;
+}
+
 int effective_variant(const eec_ctx* c) {
   return c->opt.variant == EEC_VARIANT_AUTO ? c->tuned_variant : c->opt.variant;
 }
@@ -493,6 +554,7 @@ eec_options eec_default_options(void) {
   o.block = 0;
   o.conflict_rule = EEC_CONFLICT_FREE_NODE;
   o.debug_checks = 0;
+  o.host_chunks = 0;
   return o;
 }
 
@@ -503,7 +565,8 @@ int eec_create(eec_ctx** out, const eec_options* opt) {
   if (!c) return EEC_ENOMEM;
   c->opt = opt ? *opt : eec_default_options();
   if (c->opt.variant < EEC_VARIANT_AUTO || c->opt.variant >= EEC_N_VARIANTS ||
-      c->opt.conflict_rule < 0 || c->opt.conflict_rule > 2 ||
+      c->opt.conflict_rule < 0 || c->opt.conflict_rule > 2 || c->opt.host_chunks < 0 ||
+      c->opt.host_chunks > 64 ||
       !(c->opt.block == 0 || c->opt.block == 8 || c->opt.block == 16 ||
         (c->opt.block % 32 == 0 && c->opt.block <= 128))) {
     delete c;
@@ -518,6 +581,8 @@ void eec_destroy(eec_ctx* c) {
   free_topology(c);
   if (c->d_status) cudaFree(c->d_status);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->side) cudaStreamDestroy(c->side);
+  for (cudaEvent_t e : c->hev) cudaEventDestroy(e);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   delete c;
 }
@@ -1049,28 +1114,68 @@ int eec_eval_stamp_host(eec_ctx* c, const double* x_host, double* A_host, double
         (rc = dalloc(c, &c->h_b, c->n)))
       return rc;
   }
-  // Charges: written by the evaluate kernel straight into page-locked host memory when the
-  // caller's buffer is page-locked (the host link is idle while the FP64 pipe is busy),
-  // otherwise staged on the device and copied.
-  double* qk = nullptr;
-  if (q_host) {
-    cudaPointerAttributes at{};
-    if (cudaPointerGetAttributes(&at, q_host) == cudaSuccess && at.type == cudaMemoryTypeHost &&
-        at.devicePointer) {
-      qk = static_cast<double*>(at.devicePointer);
-    } else {
-      cudaGetLastError();
-      if (!c->h_q && (rc = dalloc(c, &c->h_q, (size_t)4 * c->n_dev))) return rc;
-      qk = c->h_q;
-    }
+  if (q_host && !c->h_q && (rc = dalloc(c, &c->h_q, (size_t)4 * c->n_dev))) return rc;
+  const int v = effective_variant(c);
+  // The charges go out chunk by chunk while later chunks are still evaluated: only the
+  // order-free schedules can take a chunk of original device indices in one launch.
+  int K = 1;
+  if (q_host && !c->prof && (v == EEC_VARIANT_ATOMIC || v == EEC_VARIANT_SEGREDUCE)) {
+    if ((rc = host_plan(c))) return rc;
+    K = c->host_K;
   }
   CUDA_TRY(c, cudaMemcpyAsync(c->h_x, x_host, sizeof(double) * c->n, cudaMemcpyHostToDevice, s));
-  if ((rc = eval_with(c, effective_variant(c), c->h_x, c->h_A, c->h_b, qk, s))) return rc;
+  if (K <= 1) {
+    if ((rc = eval_with(c, v, c->h_x, c->h_A, c->h_b, q_host ? c->h_q : nullptr, s))) return rc;
+    CUDA_TRY(c, cudaMemcpyAsync(A_host, c->h_A, sizeof(double) * c->nnz, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(c, cudaMemcpyAsync(b_host, c->h_b, sizeof(double) * c->n, cudaMemcpyDeviceToHost, s));
+    if (q_host)
+      CUDA_TRY(c, cudaMemcpyAsync(q_host, c->h_q, sizeof(double) * 4 * c->n_dev,
+                                  cudaMemcpyDeviceToHost, s));
+    return EEC_OK;
+  }
+  if (!c->side) CUDA_TRY(c, cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+  while ((int)c->hev.size() < K + 1) {
+    cudaEvent_t e = nullptr;
+    CUDA_TRY(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    c->hev.push_back(e);
+  }
+  const int dbg = c->opt.debug_checks ? 1 : 0;
+  const int blk = c->opt.block ? c->opt.block : c->tuned_block;
+  int mode = MODE_ATOMIC;
+  if (v == EEC_VARIANT_ATOMIC) {
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_A, c->d.Alin, sizeof(double) * c->nnz,
+                                cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_b, c->d.blin, sizeof(double) * c->n,
+                                cudaMemcpyDeviceToDevice, s));
+  } else {
+    if ((rc = ensure_buf(c))) return rc;
+    mode = MODE_BUFFER;
+  }
+  // every launch first, then the copies (a copy to pageable memory returns only when done)
+  for (int k = 0; k < K; ++k) {
+    CUDA_TRY(c, launch_eval_ranges(c->d, mode, c->d_hrbeg + c->hc_rb[k], c->d_hroff + c->hc_ro[k],
+                                   c->hc_nr[k], c->hc_total[k], c->h_x, c->h_A, c->h_b, c->h_q,
+                                   blk, dbg, s));
+    c->n_kernels += c->hc_total[k] > 0;
+    CUDA_TRY(c, cudaEventRecord(c->hev[k], s));
+  }
+  if (mode == MODE_BUFFER) {
+    CUDA_TRY(c, launch_gather(c->d, c->h_A, c->h_b, s));
+    c->n_kernels += (c->nnz + c->n > 0);
+  }
+  const size_t N = (size_t)c->n_dev;
+  for (int k = 0; k < K; ++k) {
+    CUDA_TRY(c, cudaStreamWaitEvent(c->side, c->hev[k], 0));
+    const size_t lo = (size_t)c->hc_lo[k], cnt = (size_t)(c->hc_lo[k + 1] - c->hc_lo[k]);
+    if (!cnt) continue;
+    for (int t = 0; t < 4; ++t)
+      CUDA_TRY(c, cudaMemcpyAsync(q_host + t * N + lo, c->h_q + t * N + lo, sizeof(double) * cnt,
+                                  cudaMemcpyDeviceToHost, c->side));
+  }
   CUDA_TRY(c, cudaMemcpyAsync(A_host, c->h_A, sizeof(double) * c->nnz, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(c, cudaMemcpyAsync(b_host, c->h_b, sizeof(double) * c->n, cudaMemcpyDeviceToHost, s));
-  if (q_host && qk == c->h_q)
-    CUDA_TRY(c, cudaMemcpyAsync(q_host, c->h_q, sizeof(double) * 4 * c->n_dev,
-                                cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(c, cudaEventRecord(c->hev[K], c->side));
+  CUDA_TRY(c, cudaStreamWaitEvent(s, c->hev[K], 0));
   return EEC_OK;
 }
 

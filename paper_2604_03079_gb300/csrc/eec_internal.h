@@ -84,6 +84,12 @@ cudaError_t launch_update_params(const DevTopo& T, const double* W_dev, const do
                                  cudaStream_t s);
 cudaError_t launch_eval(const DevTopo& T, int mode, int begin, int end, const double* x,
                         double* A, double* b, double* q, int block, int dbg, cudaStream_t s);
+// The devices of a list of library-order ranges: range r starts at position rbeg[r] and holds
+// roff[r+1] - roff[r] devices (roff[0] = 0, roff[nr] = total); only for the order-free modes
+// MODE_ATOMIC and MODE_BUFFER.
+cudaError_t launch_eval_ranges(const DevTopo& T, int mode, const int* rbeg, const int* roff,
+                               int nr, int total, const double* x, double* A, double* b,
+                               double* q, int block, int dbg, cudaStream_t s);
 // absent_block >= 0 is a test hook: that block skips every grid barrier, so the other blocks'
 // bounded waits expire and the status word records a timeout.
 cudaError_t launch_persistent(const DevTopo& T, const int* color_off_dev, int n_colors,

@@ -243,6 +243,26 @@ __global__ void __launch_bounds__(kEvalBlock) k_eval(DevTopo T, int begin, int e
     eval_one<MODE, WANT_Q>(T, k, x, A, b, q, dbg);
 }
 
+// Thread j takes the j-th device of a list of library-order ranges (roff: prefix sums of the
+// range lengths). Used where a launch must cover a contiguous span of original device indices,
+// which the colour-major layout splits into one range per run of increasing original index.
+template <int MODE, bool WANT_Q>
+__global__ void __launch_bounds__(kEvalBlock) k_eval_ranges(DevTopo T, const int* __restrict__ rbeg,
+                                                            const int* __restrict__ roff, int nr,
+                                                            int total, const double* __restrict__ x,
+                                                            double* A, double* b, double* q,
+                                                            int dbg) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= total) return;
+  int lo = 0, hi = nr;  // roff[lo] <= j < roff[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(roff + mid) <= j) lo = mid;
+    else hi = mid;
+  }
+  eval_one<MODE, WANT_Q>(T, __ldg(rbeg + lo) + (j - __ldg(roff + lo)), x, A, b, q, dbg);
+}
+
 // One co-resident grid walks the colours; a colour's devices are dealt out in 32-device chunks
 // round-robin over the blocks first (chunk i -> block i mod grid, then the next warp of that
 // block), so a small colour occupies one warp on each of many SMs instead of whole blocks on a
@@ -436,6 +456,25 @@ cudaError_t launch_eval(const DevTopo& T, int mode, int begin, int end, const do
       if (wq) k_eval<MODE_BUFFER, true><<<g, B, 0, s>>>(T, begin, end, x, A, b, q, dbg);
       else k_eval<MODE_BUFFER, false><<<g, B, 0, s>>>(T, begin, end, x, A, b, q, dbg);
       break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eval_ranges(const DevTopo& T, int mode, const int* rbeg, const int* roff,
+                               int nr, int total, const double* x, double* A, double* b,
+                               double* q, int block, int dbg, cudaStream_t s) {
+  if (total <= 0 || nr <= 0) return cudaSuccess;
+  const int B = eval_block(total, block);
+  const int g = grid_for(total, B);
+  const bool wq = q != nullptr;
+  if (mode == MODE_ATOMIC) {
+    if (wq) k_eval_ranges<MODE_ATOMIC, true><<<g, B, 0, s>>>(T, rbeg, roff, nr, total, x, A, b, q, dbg);
+    else k_eval_ranges<MODE_ATOMIC, false><<<g, B, 0, s>>>(T, rbeg, roff, nr, total, x, A, b, q, dbg);
+  } else if (mode == MODE_BUFFER) {
+    if (wq) k_eval_ranges<MODE_BUFFER, true><<<g, B, 0, s>>>(T, rbeg, roff, nr, total, x, A, b, q, dbg);
+    else k_eval_ranges<MODE_BUFFER, false><<<g, B, 0, s>>>(T, rbeg, roff, nr, total, x, A, b, q, dbg);
+  } else {
+    return cudaErrorInvalidValue;   // colour schedules are not order-free
   }
   return cudaGetLastError();
 }
