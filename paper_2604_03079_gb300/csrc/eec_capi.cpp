@@ -244,6 +244,7 @@ CardK derive_card(const double* a) {
   k.DELTA = DELTA; k.twoDELTA = 2.0 * DELTA; k.fourDELTA = 4.0 * DELTA;
   k.fourD1sq = 4.0 * D1 * D1; k.twoD1sq = 2.0 * D1 * D1;
   k.XPART = XPART; k.GMIN = GMIN;
+  k.halfK1 = 0.5 * K1; k.Vthc = VTH0 - K1 * k.sqrtPHI; k.twoUB = 2.0 * UB; k.XPm = XPART - 0.5;
   k.U0Cox = U0 * Cox; k.twoVSAT_U0 = 2.0 * VSAT / U0; k.LAMBDA_LREF = LAMBDA * LREF;
   k.JS_HDIF = JS * HDIF; k.Cox = Cox; k.CGSO = CGSO; k.CGDO = CGDO;
   return k;
@@ -974,7 +975,7 @@ int eec_build_scatter(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_out) {
       (rc = dupload(c, &d.orig, orig)) || (rc = dupload(c, &d.slot, slot)) ||
       (rc = dupload(c, &d.slot_g, slot_g)) ||
       (rc = dupload(c, &d.W, Wp)) || (rc = dupload(c, &d.L, Lp)) ||
-      (rc = dalloc(c, &d.prm, (size_t)kNPrm * N)) || (rc = dalloc(c, &d.bodyk, (size_t)7 * N)) ||
+      (rc = dalloc(c, &d.prm, (size_t)kNPrm * N)) || (rc = dalloc(c, &d.bodyk, (size_t)kNBody * N)) ||
       (rc = dupload(c, &d.vfix, vtab)) ||
       (rc = dupload(c, &d.cards, c->cardk)) || (rc = dupload(c, &d.Alin, Alin)) ||
       (rc = dupload(c, &d.blin, blin)) || (rc = dupload(c, &d.gat_ptr, gptr)) ||

@@ -26,6 +26,37 @@
 
 namespace eec {
 
+// Comparisons on the bit pattern. For every non-NaN argument each one decides exactly as the
+// floating-point comparison in its name, but runs on the integer pipe: a double compare would
+// occupy the FP64 pipe, which bounds the evaluation.
+constexpr long long kBits40 = 0x4044000000000000LL;            // 40.0
+constexpr long long kBits709 = 0x4086280000000000LL;           // 709.0
+constexpr unsigned long long kBits707 = 0x4086180000000000ull;  // 707.0
+constexpr unsigned long long kBitsM38 = 0xC043000000000000ull;  // -38.0
+constexpr unsigned long long kBits2m6 = 0x3F90000000000000ull;  // 2^-6
+constexpr long long kBits2m7 = 0x3F80000000000000LL;           // 2^-7
+
+__device__ __forceinline__ unsigned long long fm_ubits(double x) {
+  return (unsigned long long)__double_as_longlong(x);
+}
+// x >= 0.0 (true at -0.0): the sign bit is clear, or x is -0.0
+__device__ __forceinline__ bool fm_ge0(double x) { return fm_ubits(x) <= 0x8000000000000000ull; }
+// x < c, x <= c for a constant c > 0 (negative x, -0.0 included, are negative as integers)
+__device__ __forceinline__ bool fm_lt_pos(double x, long long cbits) {
+  return __double_as_longlong(x) < cbits;
+}
+__device__ __forceinline__ bool fm_le_pos(double x, long long cbits) {
+  return __double_as_longlong(x) <= cbits;
+}
+// x < c for a constant c < 0 (below c means a larger magnitude with the sign bit set)
+__device__ __forceinline__ bool fm_lt_neg(double x, unsigned long long cbits) {
+  return fm_ubits(x) > cbits;
+}
+// |x| < c for a constant c > 0
+__device__ __forceinline__ bool fm_abs_lt(double x, unsigned long long cbits) {
+  return (fm_ubits(x) & 0x7fffffffffffffffull) < cbits;
+}
+
 // y * 2^m by adding m to the exponent field (y and the result must be normal, y != 0).
 __device__ __forceinline__ double fm_scale2(double y, int m) {
   return __hiloint2double(__double2hiint(y) + (m << 20), __double2loint(y));
@@ -57,7 +88,7 @@ __device__ __forceinline__ double fm_em1_small6(double r) {
 }
 
 __device__ __forceinline__ double fm_exp(double x) {
-  if (!(x > -707.0 && x < 709.0)) return ::exp(x);   // subnormal / overflow range, NaN
+  if (!fm_abs_lt(x, kBits707)) return ::exp(x);   // near the subnormal / overflow range, NaN
   int j, m;
   const double r = fm_reduce(x, j, m);
   const double p = fm_em1_small(r);
@@ -67,14 +98,14 @@ __device__ __forceinline__ double fm_exp(double x) {
 }
 
 __device__ __forceinline__ double fm_expm1(double x) {
-  if (fabs(x) < 0x1p-6) {
+  if (fm_abs_lt(x, kBits2m6)) {
     // x + x^2/2 + ... + x^7/5040 (truncation below 2^-59 relative)
     const double q = fma(x, fma(x, fma(x, fma(x, fma(x, 1.0 / 5040.0, 1.0 / 720.0), 1.0 / 120.0),
                                        1.0 / 24.0), 1.0 / 6.0), 0.5);
     return fma(x * x, q, x);
   }
-  if (x < -38.0) return -1.0;   // e^x < 2^-54: -1 + e^x rounds to -1
-  if (!(x < 709.0)) return ::expm1(x);
+  if (fm_lt_neg(x, kBitsM38)) return -1.0;   // e^x < 2^-54: -1 + e^x rounds to -1
+  if (!fm_lt_pos(x, kBits709)) return ::expm1(x);
   int j, m;
   const double r = fm_reduce(x, j, m);
   const double p = fm_em1_small6(r);
@@ -86,7 +117,7 @@ __device__ __forceinline__ double fm_expm1(double x) {
 
 // log(1 + e) for e in [0, 1]; inv_y must be 1 / (1 + e) rounded (the caller needs it anyway).
 __device__ __forceinline__ double fm_log1p01(double e, double inv_y) {
-  if (e < 0x1p-7) {
+  if (fm_lt_pos(e, kBits2m7)) {
     // e - e^2/2 + ... + e^7/7 (truncation below 2^-52 relative)
     const double q = fma(e, fma(e, fma(e, fma(e, fma(e, 1.0 / 7.0, -1.0 / 6.0), 0.2), -0.25),
                                 1.0 / 3.0), -0.5);

@@ -19,9 +19,15 @@ struct CardK {
   double DELTA, twoDELTA, fourDELTA;
   double fourD1sq, twoD1sq;
   double XPART, GMIN;
+  // constant products: K1/2, VTH0 - K1 sqrt(PHI), 2 UB, XPART - 1/2
+  double halfK1, Vthc, twoUB, XPm;
   // factors of the per-device parameters (eval_params)
   double U0Cox, twoVSAT_U0, LAMBDA_LREF, JS_HDIF, Cox, CGSO, CGDO;
 };
+
+// x-independent terms of devices whose source and body are source-held: sqs, Vthb, dVth/dvbs,
+// Ab, dAb/dvbs, Ijs, gjs, Qb (layout [kNBody][N]).
+constexpr int kNBody = 8;
 
 // Per-device derived parameters, stored structure-of-arrays [kNPrm][N] by layout position.
 enum Prm : int {

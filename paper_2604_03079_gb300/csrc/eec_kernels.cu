@@ -115,41 +115,44 @@ __device__ __forceinline__ void eval_one(const DevTopo& T, int k, const double* 
     bk.dAb_dvbs = __ldg(q0 + 4 * N);
     bk.Ijs = __ldg(q0 + 5 * N);
     bk.gjs = __ldg(q0 + 6 * N);
+    bk.Qb = __ldg(q0 + 7 * N);
   }
   EvalOut<double> o;
   ees_l1<double, WANT_Q>(c, psb, P, V, o, sbf, &bk);
 
+  // b row r: -I_r + sum over the free columns u of G[r][u] V_u (held columns are eliminated)
   const int term[3] = {0, 2, 3};
-  double bc[3];
-#pragma unroll
-  for (int r = 0; r < 3; ++r) {
-    double s = -o.I[term[r]];
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (idx[u] >= 0) s = fma(o.G[r][u], V[u], s);
-    bc[r] = s;
-  }
+  bool bc_ok = true;
   if (MODE == MODE_BUFFER) {
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
+      double s = -o.I[term[r]];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (idx[u] >= 0) s = fma(o.G[r][u], V[u], s);
 #pragma unroll
       for (int u = 0; u < 4; ++u) T.buf[(4 * r + u) * N + k] = o.G[r][u];
-      T.buf[(kNSlot + r) * N + k] = bc[r];
+      T.buf[(kNSlot + r) * N + k] = s;
+      bc_ok = bc_ok && isfinite(s);
     }
   } else {
+    // rows of source-held terminals are not stamped: their b entries are not formed
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
       const int row = idx[term[r]];
       if (row < 0) continue;
+      double s = -o.I[term[r]];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const int s = __ldg(T.slot + (4 * r + u) * N + k);
-        if (s < 0) continue;
-        if (MODE == MODE_ATOMIC) atomicAdd(A + s, o.G[r][u]);
-        else A[s] += o.G[r][u];
+        if (idx[u] < 0) continue;
+        s = fma(o.G[r][u], V[u], s);
+        const int sl = __ldg(T.slot + (4 * r + u) * N + k);
+        if (MODE == MODE_ATOMIC) atomicAdd(A + sl, o.G[r][u]);
+        else A[sl] += o.G[r][u];
       }
-      if (MODE == MODE_ATOMIC) atomicAdd(b + row, bc[r]);
-      else b[row] += bc[r];
+      if (MODE == MODE_ATOMIC) atomicAdd(b + row, s);
+      else b[row] += s;
+      bc_ok = bc_ok && isfinite(s);
     }
   }
   if (WANT_Q) {
@@ -158,7 +161,7 @@ __device__ __forceinline__ void eval_one(const DevTopo& T, int k, const double* 
     for (int t = 0; t < 4; ++t) q[t * N + od] = o.Q[t];
   }
   if (dbg) {
-    bool ok = isfinite(bc[0]) && isfinite(bc[1]) && isfinite(bc[2]);
+    bool ok = bc_ok;
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
@@ -194,6 +197,7 @@ __device__ __forceinline__ void eval_one_tran(const DevTopo& T, int k, const dou
     bk.dAb_dvbs = __ldg(q0 + 4 * N);
     bk.Ijs = __ldg(q0 + 5 * N);
     bk.gjs = __ldg(q0 + 6 * N);
+    bk.Qb = __ldg(q0 + 7 * N);
   }
   EvalOut<double> o;
   ees_l1<double, true, true>(c, psb, P, V, o, sbf, &bk);
@@ -313,6 +317,7 @@ __global__ void k_params(DevTopo T, const double* __restrict__ Wo, const double*
     q0[4 * N] = dAb;
     q0[5 * N] = Ijs;
     q0[6 * N] = gjs;
+    q0[7 * N] = -(P.Coxt * c.K1 * sqs);
   }
   T.prm[P_BETA0 * N + k] = P.beta0;
   T.prm[P_CE * N + k] = P.cE;

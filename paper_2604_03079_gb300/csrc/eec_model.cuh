@@ -87,7 +87,7 @@ template <class S>
 __device__ __forceinline__ void junction(const CardK& c, const PrmS<S>& P, const S& v, S& Ij,
                                          S& gj) {
   const S z = v * c.inv_Vt;
-  if (sval(z) <= 40.0) {
+  if (fm_le_pos(sval(z), kBits40)) {
     const S em1 = expm1_(z);
     Ij = P.Isat * em1 + c.GMIN * v;
     gj = P.IsatVt * em1 + P.IsatVtG;
@@ -109,23 +109,23 @@ __device__ __forceinline__ void body_terms(const CardK& c, const S& vbs, S& sqs,
   const S inv_R1 = rsqrt_(R1sq);
   const S R1 = R1sq * inv_R1;
   S phis;
-  if (sval(u) >= 0.0) phis = 0.5 * (u + R1);
+  if (fm_ge0(sval(u))) phis = 0.5 * (u + R1);
   else phis = c.twoD1sq * rcp(R1 - u);
   const S inv_sqs = rsqrt_(phis);
   sqs = phis * inv_sqs;
-  Vthb = c.VTH0 + c.K1 * (sqs - c.sqrtPHI);
-  const S hK1R = (0.5 * c.K1) * inv_R1;
+  Vthb = c.K1 * sqs + c.Vthc;                     // VTH0 + K1 (sqs - sqrt(PHI))
+  const S hK1R = c.halfK1 * inv_R1;
   dVth_dvbs = -(hK1R * sqs);
-  Ab = 1.0 + (0.5 * c.K1) * inv_sqs;
+  Ab = c.halfK1 * inv_sqs + 1.0;
   dAb_dvbs = 0.5 * hK1R * inv_sqs;
 }
 
 // x-independent terms of a device whose source and body are both source-held: in forward mode
 // vbs is constant, and the source junction is constant in either mode.
+// Layout [kNBody][N] in this order; Qb = -Cox W L K1 sqs is the depletion charge.
 struct BodyK {
-  double sqs, Vthb, dVth_dvbs, Ab, dAb_dvbs, Ijs, gjs;
+  double sqs, Vthb, dVth_dvbs, Ab, dAb_dvbs, Ijs, gjs, Qb;
 };
-constexpr int kNBody = 7;
 
 // Mode-frame channel current (steps 3, 5-8) and its gradient g = (gm, gds, gmb) with respect to
 // (vgs, vds, vbs), given the vbs-dependent terms of step (2)/(4). Vg and F1 feed the charges.
@@ -148,7 +148,7 @@ __device__ __forceinline__ void channel(const CardK& c, const PrmS<S>& P, const 
 
   // (3) Vgsteff = nVt softplus(z), dVgsteff/dz = nVt sigmoid(z)
   const S z = (vgs - Vth) * c.inv_nVt;
-  const bool zpos = sval(z) >= 0.0;
+  const bool zpos = fm_ge0(sval(z));
   const S e = exp_(zpos ? -z : z);               // exp(-|z|)
   const S inv_1pe = rcp(1.0 + e);
   const S lg = log1p_(e, inv_1pe);
@@ -157,17 +157,20 @@ __device__ __forceinline__ void channel(const CardK& c, const PrmS<S>& P, const 
 
   // (5) mobility denominator, (6) velocity saturation
   const S den = 1.0 + Vg * (c.UA + c.UB * Vg);
-  const S dden = c.UA + 2.0 * c.UB * Vg;
+  const S dden = c.twoUB * Vg + c.UA;
   const S Vgst2 = Vg + c.twoVt;
-  const S inv_pair = rcp(den * Vgst2);           // one reciprocal for 1/den and 1/Vgst2
+  const S EsatL = P.cE * den;
+  const S Dd = Ab * EsatL + Vgst2;
+  // one reciprocal for 1/den, 1/Vgst2 and 1/Dd: r = 1/(X Dd) with X = den Vgst2
+  const S X = den * Vgst2;
+  const S rXD = rcp(X * Dd);
+  const S inv_pair = Dd * rXD;                    // 1 / (den Vgst2)
+  const S inv_Dd = X * rXD;
   const S inv_den = Vgst2 * inv_pair;
   const S inv_Vgst2 = den * inv_pair;
   const S beta = P.beta0 * inv_den;
-  const S EsatL = P.cE * den;
   const S inv_EsatL = P.inv_cE * inv_den;
   const S EsatL_Vg = P.cE * dden;
-  const S Dd = Ab * EsatL + Vgst2;
-  const S inv_Dd = rcp(Dd);
   const S r1 = Vgst2 * inv_Dd;
   const S r2 = EsatL * inv_Dd;
   const S Vdsat = EsatL * r1;
@@ -189,7 +192,8 @@ __device__ __forceinline__ void channel(const CardK& c, const PrmS<S>& P, const 
 
   // (8) Ids = beta Vg Vdseff F1 F3 / F2
   const S h = 0.5 * inv_Vgst2;
-  const S F1 = 1.0 - Ab * Vdseff * h;
+  const S Abh = Ab * h;
+  const S F1 = 1.0 - Abh * Vdseff;
   const S F2 = 1.0 + Vdseff * inv_EsatL;
   const S inv_F2 = rcp(F2);
   const S F3 = 1.0 + P.lamL * (vds - Vdseff);
@@ -200,8 +204,8 @@ __device__ __forceinline__ void channel(const CardK& c, const PrmS<S>& P, const 
 
   // partial derivatives with Vg, Ab and vds as independent variables
   const S Vde_Vg = Vde_Vdsat * Vdsat_Vg;
-  const S F1_Vg = -(Ab * h) * (Vde_Vg - Vdseff * inv_Vgst2);
-  const S F1_vds = -(Ab * h) * Vde_vds;
+  const S F1_Vg = -Abh * (Vde_Vg - Vdseff * inv_Vgst2);
+  const S F1_vds = -Abh * Vde_vds;
   const S F2_Vg = inv_EsatL * (Vde_Vg - Vdseff * dden * inv_den);
   const S F2_vds = inv_EsatL * Vde_vds;
   const S F3_Vg = -(P.lamL * Vde_Vg);
@@ -257,7 +261,7 @@ __device__ __forceinline__ void ees_l1(const CardK& c, unsigned long long psb, c
                                        const BodyK* bk = nullptr) {
   // (1) mode
   const S vds0 = flip(V[0] - V[2], psb);
-  const bool fwd = sval(vds0) >= 0.0;
+  const bool fwd = fm_ge0(sval(vds0));
   const S VD = fwd ? V[0] : V[2];
   const S VS = fwd ? V[2] : V[0];
   const S vgs = flip(V[1] - VS, psb);
@@ -313,13 +317,13 @@ __device__ __forceinline__ void ees_l1(const CardK& c, unsigned long long psb, c
     // (11) charges: depletion, inversion partitioned to the mode drain by
     //      fD = 1/2 - (1/2 - XPART) Vdseff / Vdsat (continuous across the source/drain swap),
     //      overlaps
-    const S Qb = -(P.Coxt * c.K1 * sqs);
+    const S Qb = (sb_fixed && fwd) ? S(bk->Qb) : -(P.Coxt * c.K1 * sqs);
     const S Qinv = -(P.Coxt * Vg * F1);
     const S Qg0 = -(Qb + Qinv);
     // 1 / Vdsat = Dd / (EsatL Vgst2): both reciprocals are already at hand
     const S inv_Vdsat = ch.inv_Vdsat_parts[0] * ch.inv_Vdsat_parts[1] * ch.inv_Vdsat_parts[2];
     const S sr = ch.Vdseff * inv_Vdsat;
-    const S fD = 0.5 - (0.5 - c.XPART) * sr;
+    const S fD = c.XPm * sr + 0.5;
     const S QD = fD * Qinv;
     const S QS = Qinv - QD;
     const S Qovs = P.CovS * flip(V[1] - V[2], psb);
@@ -346,7 +350,7 @@ __device__ __forceinline__ void ees_l1(const CardK& c, unsigned long long psb, c
       const S sr_Vg = (ch.Vde_Vg - sr * ch.Vdsat_Vg) * inv_Vdsat;
       const S sr_Ab = (ch.Vde_Ab - sr * ch.Vdsat_Ab) * inv_Vdsat;
       const S sr_vds = ch.Vde_vds * inv_Vdsat;
-      const double mx = -(0.5 - c.XPART);          // dfD / dsr
+      const double mx = c.XPm;                     // dfD / dsr
       const S fD_vgs = mx * (sr_Vg * ch.sig);
       const S fD_vds = mx * (sr_Vg * Vg_vds + sr_vds);
       const S fD_vbs = mx * (sr_Vg * Vg_vbs + sr_Ab * dAb_dvbs);

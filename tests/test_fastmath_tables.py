@@ -49,3 +49,16 @@ def test_reduction_constants():
     assert c["kLn2o64Hi"] == float(ln2o64)
     assert abs(mpmath.mpf(c["kLn2o64Hi"]) + mpmath.mpf(c["kLn2o64Lo"]) - ln2o64) < mpmath.mpf(2) ** -110
     assert c["kInvLn2x64"] == float(64 / mpmath.log(2))
+
+
+def test_bit_pattern_constants_match_their_values():
+    # the comparisons on the integer pipe use these IEEE-754 patterns; each carries its value
+    import re
+    import struct
+    src = open(os.path.join(ROOT, "paper_2604_03079_gb300", "csrc", "eec_fastmath.cuh")).read()
+    found = re.findall(r"constexpr (?:unsigned )?long long (kBits\w+) = (0x[0-9A-Fa-f]+)(?:LL|ull);"
+                       r"\s*// (\S+)", src)
+    assert len(found) == 6
+    for name, hexv, val in found:
+        v = 2.0 ** int(val[2:]) if val.startswith("2^") else float(val)
+        assert int(hexv, 16) == struct.unpack("<Q", struct.pack("<d", v))[0], name

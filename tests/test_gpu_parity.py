@@ -220,15 +220,21 @@ def test_config5_backward_full_size_vs_oracle_and_fd(eec, sram_full):
     _grad_close(host(gx), ox)
     _grad_close(host(gW), oW)
     _grad_close(host(gL), oL)
-    # central differences (h = 1e-6 relative) of s = <gA, A> + <gb, b> through the GPU forward
+    # central differences (h = 1e-6 relative) of s = <gA, A> + <gb, b> through the GPU forward.
+    # A and b are differenced first (exactly zero away from the perturbed device), then weighted:
+    # differencing two full million-term sums would add their reduction rounding, which is as
+    # large as the tolerance once divided by 2h.
     gAt, gbt = dev(gA), dev(gb)
 
-    def s_of(xv, W=None, L=None):
+    def ab_of(xv, W=None, L=None):
         if W is not None:
             import paper_2604_03079_gb300 as m
             m.eec_update_params(circ.ctx, dev(W), dev(L))
         A, b, _ = circ.eval_stamp(dev(xv), want_q=False)
-        return float((A * gAt).sum() + (b * gbt).sum())
+        return A.clone(), b.clone()
+
+    def central(p, m, h):
+        return float(((p[0] - m[0]) * gAt).sum() + ((p[1] - m[1]) * gbt).sum()) / (2 * h)
 
     sel = np.random.default_rng(0).choice(circ.n, 6, replace=False)
     for i in sel:
@@ -236,7 +242,7 @@ def test_config5_backward_full_size_vs_oracle_and_fd(eec, sram_full):
         xp, xm = x.copy(), x.copy()
         xp[i] += h
         xm[i] -= h
-        fd = (s_of(xp) - s_of(xm)) / (2 * h)
+        fd = central(ab_of(xp), ab_of(xm), h)
         assert abs(fd - ox[i]) <= 1e-5 * max(abs(ox[i]), 1e-3 * np.abs(ox).max())
     W0, L0 = net.W.copy(), net.L.copy()
     for k in np.random.default_rng(1).choice(net.n_dev, 6, replace=False):
@@ -246,10 +252,10 @@ def test_config5_backward_full_size_vs_oracle_and_fd(eec, sram_full):
             for sg in (1, -1):
                 a = base.copy()
                 a[k] += sg * h
-                vals.append(s_of(x, a, L0) if which == "W" else s_of(x, W0, a))
-            fd = (vals[0] - vals[1]) / (2 * h)
+                vals.append(ab_of(x, a, L0) if which == "W" else ab_of(x, W0, a))
+            fd = central(vals[0], vals[1], h)
             assert abs(fd - ref[k]) <= 1e-5 * max(abs(ref[k]), 1e-3 * np.abs(ref).max()), (which, k)
-    s_of(x, W0, L0)
+    ab_of(x, W0, L0)   # restore the sizes
 
 
 def test_adjoint_dc_sensitivity_of_inverter_chain(eec):
