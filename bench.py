@@ -34,8 +34,8 @@ UNIT = "device evals+stamps/s"
 # Per-device work of the evaluate kernel on this workload, from ncu's counters of the kernel
 # (profiles/k_eval_atomic_sram_256x256.md): FP64 flop = 2 DFMA + DADD + DMUL thread instructions
 # per device, and DRAM bytes read + written per device.
-FP64_FLOP_PER_DEVICE = 298.1
-DRAM_BYTES_PER_DEVICE = 191.2
+FP64_FLOP_PER_DEVICE = 292.8
+DRAM_BYTES_PER_DEVICE = 191.5
 # GB300: 152 SMs x 2 FP64 FMA per clock per SM x 2 flop x 2070 MHz maximum SM clock.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 

@@ -354,10 +354,12 @@ EEC_API int eec_test_barrier_timeout(eec_ctx* ctx, const double* x_dev, double* 
 
 /*
  * Validation hook for the library's own FP64 elementary functions (the table-driven exp, expm1
- * and log1p the model evaluation uses in place of CUDA's). The paper has no counterpart.
- *  fn      0 = exp, 1 = expm1, 2 = log1p (argument in [0, 1], the only range the model uses).
+ * and log1p, and the reciprocal and reciprocal square root, that the model evaluation uses in
+ * place of CUDA's). The paper has no counterpart.
+ *  fn      0 = exp, 1 = expm1, 2 = log1p (argument in [0, 1], the only range the model uses),
+ *          3 = 1/x, 4 = 1/sqrt(x) (normal |x| in [2^-126, 2^128); x > 0 for 4).
  *  x_dev   [n] arguments; ours_dev [n] the library's results; cuda_dev [n] CUDA's exp / expm1 /
- *          log1p of the same arguments. Asynchronous on cuda_stream.
+ *          log1p / 1.0/x / rsqrt of the same arguments. Asynchronous on cuda_stream.
  */
 EEC_API int eec_math_check(int32_t fn, int64_t n, const double* x_dev, double* ours_dev,
                            double* cuda_dev, void* cuda_stream);

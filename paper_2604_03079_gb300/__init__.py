@@ -381,7 +381,8 @@ def eec_test_barrier_timeout(ctx, x, A, b, stream=None):
 
 
 def eec_math_check(fn, x, stream=None):
-    """-> (library result, CUDA result) of exp (0), expm1 (1) or log1p on [0, 1] (2) at x."""
+    """-> (library result, CUDA result) of exp (0), expm1 (1), log1p on [0, 1] (2), the
+    reciprocal (3) or the reciprocal square root (4) at x."""
     import torch
     ours = torch.empty_like(x)
     ref = torch.empty_like(x)

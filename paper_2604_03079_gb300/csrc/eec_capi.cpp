@@ -1366,7 +1366,7 @@ int eec_status(eec_ctx* c, void* stream) {
 
 int eec_math_check(int32_t fn, int64_t n, const double* x, double* ours, double* ref,
                    void* stream) {
-  if (fn < 0 || fn > 2 || n < 0 || (n > 0 && (!x || !ours || !ref))) return EEC_EINVAL;
+  if (fn < 0 || fn > 4 || n < 0 || (n > 0 && (!x || !ours || !ref))) return EEC_EINVAL;
   return math_check(fn, n, x, ours, ref, static_cast<cudaStream_t>(stream)) == cudaSuccess
              ? EEC_OK
              : EEC_ECUDA;

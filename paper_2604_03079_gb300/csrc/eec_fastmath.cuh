@@ -14,10 +14,14 @@
 //   log1p — "Table-driven implementation of the logarithm function ...", ACM TOMS 16(4), 1990,
 //           specialised to 1 + e with e in [0, 1]: y = 1 + e, F = 1 + j/128 nearest to y,
 //           u = (y - F)/F, log y = log F + log1p(u) by its Taylor polynomial, plus the rounding
-//           error of 1 + e carried as c / y.
+//           error of 1 + e carried as c / y. One path for the whole interval (j = 0, F = 1
+//           covers small e; the polynomial runs to u^7 so that it stays accurate relative to
+//           log y there): a branch for small e would be taken by some lanes of most warps.
+// Reciprocal and reciprocal square root start from the FP32 special-function unit and finish
+// with one third-order correction from the series of 1/(1 - e) and (1 - e)^(-1/2).
 // Polynomial coefficients are Taylor coefficients; tables come from gen_tables.py. Accuracy
 // (checked against CUDA's functions by the GPU tests through eec_math_check) is within a few
-// units in the last place over the domains used here.
+// units in the last place over the domains used here (1 ulp for the reciprocal, 2 for rsqrt).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -55,6 +59,40 @@ __device__ __forceinline__ bool fm_lt_neg(double x, unsigned long long cbits) {
 // |x| < c for a constant c > 0
 __device__ __forceinline__ bool fm_abs_lt(double x, unsigned long long cbits) {
   return (fm_ubits(x) & 0x7fffffffffffffffull) < cbits;
+}
+
+// Seeds from the FP32 special-function unit. The double x is narrowed on the integer pipe from its
+// high word (sign, exponent rebiased by 1023 - 127, top 20 mantissa bits; relative error below
+// 2^-20, valid for 2^-126 <= |x| < 2^128), the approximation widened back the same way.
+__device__ __forceinline__ float fm_narrow(double x) {
+  const int hi = __double2hiint(x);
+  return __int_as_float((((hi & 0x7fffffff) - 0x38000000) << 3) | (hi & 0x80000000));
+}
+__device__ __forceinline__ double fm_widen(float f) {
+  const int b = __float_as_int(f);
+  return __hiloint2double((((b & 0x7fffffff) >> 3) + 0x38000000) | (b & 0x80000000), 0);
+}
+
+// 1/x by one third-order Newton step from the seed y0 (relative error e0 below 2^-19):
+// with e = 1 - x y0, 1/x = y0 / (1 - e) = y0 (1 + e + e^2 + ...), so y0 + y0 (e + e^2) leaves
+// a relative error of e0^3 < 2^-57 plus the rounding of the last two operations.
+// For normal |x| in [2^-126, 2^128) (the model's denominators are far inside).
+__device__ __forceinline__ double fm_rcp(double x) {
+  float yf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(fm_narrow(x)));
+  const double y0 = fm_widen(yf);
+  const double e = fma(-x, y0, 1.0);
+  return fma(y0, fma(e, e, e), y0);
+}
+
+// 1/sqrt(x) by one third-order step: with e = 1 - x y0^2, x^(-1/2) = y0 (1 - e)^(-1/2)
+// = y0 (1 + e/2 + 3 e^2/8 + ...); the truncation leaves 5 e0^3 / 16.
+__device__ __forceinline__ double fm_rsqrt(double x) {
+  float yf;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(fm_narrow(x)));
+  const double y0 = fm_widen(yf);
+  const double e = fma(-x * y0, y0, 1.0);
+  return fma(y0, e * fma(e, 0.375, 0.5), y0);
 }
 
 // y * 2^m by adding m to the exponent field (y and the result must be normal, y != 0).
@@ -117,19 +155,14 @@ __device__ __forceinline__ double fm_expm1(double x) {
 
 // log(1 + e) for e in [0, 1]; inv_y must be 1 / (1 + e) rounded (the caller needs it anyway).
 __device__ __forceinline__ double fm_log1p01(double e, double inv_y) {
-  if (fm_lt_pos(e, kBits2m7)) {
-    // e - e^2/2 + ... + e^7/7 (truncation below 2^-52 relative)
-    const double q = fma(e, fma(e, fma(e, fma(e, fma(e, 1.0 / 7.0, -1.0 / 6.0), 0.2), -0.25),
-                                1.0 / 3.0), -0.5);
-    return fma(e * e, q, e);
-  }
-  const double y = 1.0 + e;                        // (1, 2]
+  const double y = 1.0 + e;                        // [1, 2]
   const double c = e - (y - 1.0);                  // rounding error of y, exact
-  const double s = fma(y, 128.0, 0x1.8p52);        // round(128 y) in [129, 256]
-  const int jj = __double2loint(s) - 128;          // F = 1 + jj/128, jj in [1, 128]
+  const double s = fma(y, 128.0, 0x1.8p52);        // round(128 y) in [128, 256]
+  const int jj = __double2loint(s) - 128;          // F = 1 + jj/128, jj in [0, 128]
   const double u = (y - __ldg(kF + jj)) * __ldg(kInvF + jj);   // |u| <= 2^-8; y - F exact
-  const double q = fma(u, fma(u, fma(u, fma(u, -1.0 / 6.0, 0.2), -0.25), 1.0 / 3.0), -0.5);
-  const double pu = fma(u * u, q, u);              // log1p(u), truncation below 2^-59
+  const double q = fma(u, fma(u, fma(u, fma(u, fma(u, 1.0 / 7.0, -1.0 / 6.0), 0.2), -0.25),
+                              1.0 / 3.0), -0.5);
+  const double pu = fma(u * u, q, u);              // log1p(u), truncation below 2^-59 relative
   return __ldg(kLogFHi + jj) + fma(c, inv_y, __ldg(kLogFLo + jj) + pu);
 }
 

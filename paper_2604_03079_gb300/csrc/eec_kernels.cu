@@ -407,9 +407,15 @@ __global__ void k_math_check(int fn, long long n, const double* __restrict__ x, 
   } else if (fn == 1) {
     ours[i] = fm_expm1(v);
     ref[i] = ::expm1(v);
-  } else {
+  } else if (fn == 2) {
     ours[i] = fm_log1p01(v, 1.0 / (1.0 + v));
     ref[i] = ::log1p(v);
+  } else if (fn == 3) {
+    ours[i] = fm_rcp(v);
+    ref[i] = 1.0 / v;
+  } else {
+    ours[i] = fm_rsqrt(v);
+    ref[i] = ::rsqrt(v);
   }
 }
 

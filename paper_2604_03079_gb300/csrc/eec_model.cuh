@@ -22,8 +22,8 @@ namespace eec {
 
 // ---- scalar helpers for S = double ----
 __device__ __forceinline__ double sval(double x) { return x; }
-__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
-__device__ __forceinline__ double rsqrt_(double x) { return ::rsqrt(x); }
+__device__ __forceinline__ double rcp(double x) { return fm_rcp(x); }
+__device__ __forceinline__ double rsqrt_(double x) { return fm_rsqrt(x); }
 __device__ __forceinline__ double exp_(double x) { return fm_exp(x); }
 __device__ __forceinline__ double expm1_(double x) { return fm_expm1(x); }
 // log(1 + e) for e in [0, 1], given inv_y = 1 / (1 + e)

@@ -119,12 +119,17 @@ def test_config2_sram_all_variants_full_size(eec, sram_full):
     outs = {}
     for v in ALL_VARIANTS:
         outs[v] = check_against_oracle(eec, circ, o, x, v, ref=ref)
-    # colour schedules stamp every entry in the same colour order: bitwise identical
+    # the colour schedules add every entry's contributions in the same colour order; each kernel
+    # is compiled on its own, so a multiply-add fused in one may be rounded twice in another:
+    # they agree to rounding, not necessarily bitwise
     for v in (1, 4):
-        assert np.array_equal(outs[v][0], outs[0][0]) and np.array_equal(outs[v][1], outs[0][1])
-    # segmented reduction is deterministic: two runs agree bitwise
-    again = check_against_oracle(eec, circ, o, x, 3, ref=ref)
-    assert np.array_equal(again[0], outs[3][0]) and np.array_equal(again[1], outs[3][1])
+        for k in (0, 1):
+            scale = ref["A_scale"] if k == 0 else ref["b_scale"]
+            assert (np.abs(outs[v][k] - outs[0][k]) / np.maximum(scale, 1e-300)).max() <= 1e-14
+    # every schedule except the atomic one is deterministic: two runs agree bitwise
+    for v in (0, 1, 3, 4):
+        again = check_against_oracle(eec, circ, o, x, v, ref=ref)
+        assert np.array_equal(again[0], outs[v][0]) and np.array_equal(again[1], outs[v][1]), v
 
 
 def test_config3_random_logic_full_size_and_gpu_colouring(eec):
