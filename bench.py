@@ -31,11 +31,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MOSFET eval+stamp/s per NR iter (FP64, 1xGB300)"
 UNIT = "device evals+stamps/s"
-# Per-device work of the evaluate kernel on this workload, from ncu's counters of the kernel
-# (profiles/k_eval_atomic_sram_256x256.md): FP64 flop = 2 DFMA + DADD + DMUL thread instructions
-# per device, and DRAM bytes read + written per device.
-FP64_FLOP_PER_DEVICE = 292.8
-DRAM_BYTES_PER_DEVICE = 191.5
+# Per-device work of the evaluate kernel under the atomic schedule, per workload, from ncu's
+# counters of one launch (profiles/k_eval_atomic_sram_256x256.md, k_eval_atomic_workloads.md):
+# FP64 flop = 2 DFMA + DADD + DMUL thread instructions per device, and DRAM bytes read +
+# written per device. The flop count depends on the device mix (devices whose source and body
+# are source-held skip the body-effect and source-junction work).
+FP64_FLOP_PER_DEVICE = {"sram": 292.8, "logic": 282.1, "logic1m": 282.1, "batch": 260.8}
+DRAM_BYTES_PER_DEVICE = {"sram": 191.5, "logic": 237.0, "logic1m": 278.0, "batch": 384.8}
 # GB300: 152 SMs x 2 FP64 FMA per clock per SM x 2 flop x 2070 MHz maximum SM clock.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
@@ -282,10 +284,13 @@ def run_ours(args):
             assert circ.status() == 0
         print(json.dumps(out))
     elif rank == 0:
-        # roofline of the dominant kernel (the evaluate kernel; FP64-pipe bound)
-        flop = FP64_FLOP_PER_DEVICE if args.workload == "sram" else None
+        # roofline of the dominant kernel (the evaluate kernel; FP64-pipe bound); the counted
+        # figures hold for the atomic schedule's kernel
+        counted = variant == eec.EEC_VARIANT_ATOMIC
+        flop = FP64_FLOP_PER_DEVICE.get(args.workload) if counted else None
         ach = (flop * net.n_dev / (eval_ms * 1e-3) / 1e12) if (flop and eval_ms > 0) else None
-        traffic = DRAM_BYTES_PER_DEVICE * net.n_dev if args.workload == "sram" else None
+        traffic = (DRAM_BYTES_PER_DEVICE[args.workload] * net.n_dev
+                   if counted and args.workload in DRAM_BYTES_PER_DEVICE else None)
         out["roofline"] = {"bound": "alu", "kernel": "k_eval (evaluate)",
                            "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                            "frac": (ach / FP64_PEAK_TFLOPS) if ach else None, "traffic": traffic,
@@ -295,8 +300,8 @@ def run_ours(args):
         out["variants_ms"] = {eec.VARIANT_NAMES[i]: m for i, m in enumerate(ms_variants)}
 
         # end to end through the public API with host buffers (pinned): every step copies its
-        # x in and its A, b, q out inside the timed region; copies run on a second stream and
-        # the device buffers are doubled, so step i's copies overlap step i+1's evaluation
+        # x in and its A, b, q out inside the timed region (the host-buffer entry point, one
+        # call per step; beside it a caller-pipelined loop over device buffers)
         out["e2e"] = e2e(eec, circ, x, args, dev, world, net.n_dev)
 
         if world == 1 and not args.no_extras:
