@@ -36,8 +36,8 @@ UNIT = "device evals+stamps/s"
 # FP64 flop = 2 DFMA + DADD + DMUL thread instructions per device, and DRAM bytes read +
 # written per device. The flop count depends on the device mix (devices whose source and body
 # are source-held skip the body-effect and source-junction work).
-FP64_FLOP_PER_DEVICE = {"sram": 292.8, "logic": 282.1, "logic1m": 282.1, "batch": 260.8}
-DRAM_BYTES_PER_DEVICE = {"sram": 191.5, "logic": 237.0, "logic1m": 278.0, "batch": 384.8}
+FP64_FLOP_PER_DEVICE = {"sram": 284.2}
+DRAM_BYTES_PER_DEVICE = {"sram": 191.3}
 # GB300: 152 SMs x 2 FP64 FMA per clock per SM x 2 flop x 2070 MHz maximum SM clock.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 

@@ -102,7 +102,7 @@ __device__ __forceinline__ Tan<K> operator*(double a, const Tan<K>& b) { return 
 // d(1/a) = -da / a^2
 template <int K>
 __device__ __forceinline__ Tan<K> rcp(const Tan<K>& a) {
-  Tan<K> r; r.v = 1.0 / a.v;
+  Tan<K> r; r.v = fm_rcp(a.v);
   const double m = -r.v * r.v;
 #pragma unroll
   for (int i = 0; i < K; ++i) r.d[i] = m * a.d[i];
@@ -111,7 +111,7 @@ __device__ __forceinline__ Tan<K> rcp(const Tan<K>& a) {
 // d(a^-1/2) = -a^-3/2 da / 2
 template <int K>
 __device__ __forceinline__ Tan<K> rsqrt_(const Tan<K>& a) {
-  Tan<K> r; r.v = ::rsqrt(a.v);
+  Tan<K> r; r.v = fm_rsqrt(a.v);
   const double m = -0.5 * r.v * r.v * r.v;
 #pragma unroll
   for (int i = 0; i < K; ++i) r.d[i] = m * a.d[i];

@@ -61,6 +61,15 @@ __device__ __forceinline__ bool fm_abs_lt(double x, unsigned long long cbits) {
   return (fm_ubits(x) & 0x7fffffffffffffffull) < cbits;
 }
 
+// x * 2^k by adding k to the exponent field (integer pipe). Exact whenever x and the result are
+// normal; x with a zero exponent field (+-0, subnormals below 2.3e-308) or an all-ones one
+// (inf, NaN) is returned unchanged.
+__device__ __forceinline__ double fm_pow2(double x, int k) {
+  const long long b = __double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff);
+  return (e == 0 || e == 0x7ff) ? x : __longlong_as_double(b + ((long long)k << 52));
+}
+
 // Seeds from the FP32 special-function unit. The double x is narrowed on the integer pipe from its
 // high word (sign, exponent rebiased by 1023 - 127, top 20 mantissa bits; relative error below
 // 2^-20, valid for 2^-126 <= |x| < 2^128), the approximation widened back the same way.

@@ -33,6 +33,14 @@ __device__ __forceinline__ double flip(double x, unsigned long long sb) {
   return __longlong_as_double(__double_as_longlong(x) ^ (long long)sb);
 }
 constexpr unsigned long long kSignBit = 0x8000000000000000ull;
+// 2 x and x / 2: for S = double exact exponent-field adds on the integer pipe (fm_pow2), for
+// the tangent types of the backward a multiplication.
+__device__ __forceinline__ double twice(double x) { return fm_pow2(x, 1); }
+__device__ __forceinline__ double half(double x) { return fm_pow2(x, -1); }
+template <class S>
+__device__ __forceinline__ S twice(const S& x) { return 2.0 * x; }
+template <class S>
+__device__ __forceinline__ S half(const S& x) { return 0.5 * x; }
 
 template <class S>
 struct PrmS {
@@ -117,7 +125,7 @@ __device__ __forceinline__ void body_terms(const CardK& c, const S& vbs, S& sqs,
   const S hK1R = c.halfK1 * inv_R1;
   dVth_dvbs = -(hK1R * sqs);
   Ab = c.halfK1 * inv_sqs + 1.0;
-  dAb_dvbs = 0.5 * hK1R * inv_sqs;
+  dAb_dvbs = half(hK1R * inv_sqs);
 }
 
 // x-independent terms of a device whose source and body are both source-held: in forward mode
@@ -132,7 +140,8 @@ struct BodyK {
 template <class S>
 struct Chan {
   S Ids, gm, gds, gmb, Vg, F1;
-  S Vdsat, Vdseff, inv_Vdsat_parts[3];  // for the charge partition: Dd, 1/EsatL, 1/Vgst2
+  S Vdsat, Vdseff, inv_Vdsat_parts[3];  // for the charge Jacobian: Dd, 1/EsatL, 1/Vgst2
+  S sr;                                 // Vdseff / Vdsat = 2 vds / E (charge partition)
   S sig, F1_Vg, F1_Ab, F1_vds;          // for the charge Jacobian
   S Vdsat_Vg, Vdsat_Ab, Vde_Vg, Vde_Ab, Vde_vds;
 };
@@ -184,14 +193,16 @@ __device__ __forceinline__ void channel(const CardK& c, const PrmS<S>& P, const 
   const S R2 = R2sq * inv_R2;
   const S E = Vdsat + vds + c.DELTA + R2;
   const S inv_E = rcp(E);
-  const S Vdseff = 2.0 * Vdsat * vds * inv_E;
+  const S twoVdsat = twice(Vdsat);
+  const S twoVds = twice(vds);
+  const S Vdseff = twoVdsat * vds * inv_E;
   const S dE_dVdsat = 1.0 + (t + c.twoDELTA) * inv_R2;
   const S dE_dvds = 1.0 - t * inv_R2;
-  const S Vde_Vdsat = (2.0 * vds - Vdseff * dE_dVdsat) * inv_E;
-  const S Vde_vds = (2.0 * Vdsat - Vdseff * dE_dvds) * inv_E;
+  const S Vde_Vdsat = (twoVds - Vdseff * dE_dVdsat) * inv_E;
+  const S Vde_vds = (twoVdsat - Vdseff * dE_dvds) * inv_E;
 
   // (8) Ids = beta Vg Vdseff F1 F3 / F2
-  const S h = 0.5 * inv_Vgst2;
+  const S h = half(inv_Vgst2);
   const S Abh = Ab * h;
   const S F1 = 1.0 - Abh * Vdseff;
   const S F2 = 1.0 + Vdseff * inv_EsatL;
@@ -244,6 +255,7 @@ __device__ __forceinline__ void channel(const CardK& c, const PrmS<S>& P, const 
   ch.inv_Vdsat_parts[0] = Dd;
   ch.inv_Vdsat_parts[1] = inv_EsatL;
   ch.inv_Vdsat_parts[2] = inv_Vgst2;
+  ch.sr = twoVds * inv_E;
   ch.sig = sig;
   ch.F1_Vg = F1_Vg;
   ch.F1_Ab = F1_Ab;
@@ -320,9 +332,7 @@ __device__ __forceinline__ void ees_l1(const CardK& c, unsigned long long psb, c
     const S Qb = (sb_fixed && fwd) ? S(bk->Qb) : -(P.Coxt * c.K1 * sqs);
     const S Qinv = -(P.Coxt * Vg * F1);
     const S Qg0 = -(Qb + Qinv);
-    // 1 / Vdsat = Dd / (EsatL Vgst2): both reciprocals are already at hand
-    const S inv_Vdsat = ch.inv_Vdsat_parts[0] * ch.inv_Vdsat_parts[1] * ch.inv_Vdsat_parts[2];
-    const S sr = ch.Vdseff * inv_Vdsat;
+    const S sr = ch.sr;   // Vdseff / Vdsat
     const S fD = c.XPm * sr + 0.5;
     const S QD = fD * Qinv;
     const S QS = Qinv - QD;
@@ -347,6 +357,8 @@ __device__ __forceinline__ void ees_l1(const CardK& c, unsigned long long psb, c
       const S Qi_vbs = mC * (Vg_vbs * F1 + Vg * F1_vbsT);
       const S Qb_vbs = mC * dVth_dvbs;
       // partition fraction: sr = Vdseff / Vdsat with Vdsat(Vg, Ab), Vdseff(Vdsat, vds)
+      // 1 / Vdsat = Dd / (EsatL Vgst2): both reciprocals are already at hand
+      const S inv_Vdsat = ch.inv_Vdsat_parts[0] * ch.inv_Vdsat_parts[1] * ch.inv_Vdsat_parts[2];
       const S sr_Vg = (ch.Vde_Vg - sr * ch.Vdsat_Vg) * inv_Vdsat;
       const S sr_Ab = (ch.Vde_Ab - sr * ch.Vdsat_Ab) * inv_Vdsat;
       const S sr_vds = ch.Vde_vds * inv_Vdsat;
