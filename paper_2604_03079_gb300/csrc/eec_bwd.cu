@@ -167,6 +167,7 @@ __global__ void __launch_bounds__(kBwdBlock) k_bwd_device(DevTopo T, const doubl
   const int meta = __ldg(T.meta + k);
   const CardK& c = T.cards[meta >> 2];
   const double p = (meta & 1) ? -1.0 : 1.0;
+  const bool sbf = (meta >> 1) & 1;   // source and body source-held
   const double W = __ldg(T.W + k), L = __ldg(T.L + k);
 
   // weights: wb by terminal (rows d, s, b), cw[t][u] = gA[slot] + wb_t V_u over free (t, u)
@@ -188,7 +189,7 @@ __global__ void __launch_bounds__(kBwdBlock) k_bwd_device(DevTopo T, const doubl
   }
 
   // (1) mode frame
-  const bool fwd = p * (V[0] - V[2]) >= 0.0;
+  const bool fwd = fm_ge0(p * (V[0] - V[2]));
   const int iD = fwd ? 0 : 2, iS = fwd ? 2 : 0;
   const double m = fwd ? 1.0 : -1.0;
   const double vgs = p * (V[1] - V[iS]), vds = p * (V[iD] - V[iS]), vbs = p * (V[3] - V[iS]);
@@ -199,17 +200,42 @@ __global__ void __launch_bounds__(kBwdBlock) k_bwd_device(DevTopo T, const doubl
   for (int u = 0; u < 4; ++u) wt[u] = cw[0][u] - cw[2][u];
   const double omega = wb[0] - wb[2];
   const double w0 = wt[1] - wt[iS], w1 = wt[iD] - wt[iS], w2 = wt[3] - wt[iS];
-  T2 Lt(L);
-  Lt.d[1] = 1.0;
-  const PrmS<T2> P = derive_params<T2>(c, T2(W), Lt);
+  // the channel's per-device constants with their L tangents: beta0 ~ W/L, cE ~ L,
+  // 1/cE ~ 1/L, lamL ~ 1/L, so d/dL is (+-1/L) times the stored value
+  const double* pr = T.prm + k;
+  const double iL = fm_rcp(L);
+  PrmS<T2> P;
+  const double b0 = __ldg(pr + P_BETA0 * N), cE = __ldg(pr + P_CE * N);
+  const double icE = __ldg(pr + P_INV_CE * N), lamL = __ldg(pr + P_LAML * N);
+  P.beta0 = T2(b0);
+  P.beta0.d[1] = -b0 * iL;
+  P.cE = T2(cE);
+  P.cE.d[1] = cE * iL;
+  P.inv_cE = T2(icE);
+  P.inv_cE.d[1] = -icE * iL;
+  P.lamL = T2(lamL);
+  P.lamL.d[1] = -lamL * iL;
   T2 vgs2(vgs), vds2(vds), vbs2(vbs);
   vgs2.d[0] = w0;
   vds2.d[0] = w1;
   vbs2.d[0] = w2;
+  // In forward mode a device with source and body held has no free column at s or b: w2 = 0,
+  // and the body-effect terms are the constants stored for the forward (no tangent), nor is
+  // the vbs chain of the channel needed.
+  const bool hoist = sbf && fwd;
   T2 sqs, Vthb, dVth, Ab, dAb;
-  body_terms<T2>(c, vbs2, sqs, Vthb, dVth, Ab, dAb);
+  if (hoist) {
+    const double* q0 = T.bodyk + k;
+    sqs = T2(__ldg(q0));
+    Vthb = T2(__ldg(q0 + N));
+    dVth = T2(__ldg(q0 + 2 * N));
+    Ab = T2(__ldg(q0 + 3 * N));
+    dAb = T2(__ldg(q0 + 4 * N));
+  } else {
+    body_terms<T2>(c, vbs2, sqs, Vthb, dVth, Ab, dAb);
+  }
   Chan<T2> ch;
-  channel<T2>(c, P, vgs2, vds2, Vthb, dVth, Ab, dAb, ch);
+  channel<T2>(c, P, vgs2, vds2, Vthb, dVth, Ab, dAb, ch, !hoist);
   const double gm = ch.gm.v, gds = ch.gds.v, gmb = ch.gmb.v, Ids = ch.Ids.v;
   const double pmw = p * m * omega;
   const double s_ch = m * (gm * w0 + gds * w1 + gmb * w2) - pmw * Ids;
@@ -225,11 +251,13 @@ __global__ void __launch_bounds__(kBwdBlock) k_bwd_device(DevTopo T, const doubl
   g[iS] = -p * (dv0 + dv1 + dv2);
 
   // junctions (physical d-b and s-b): s_j = kappa gj - rho Ij
-  const double Isat = P.Isat.v;
-  double IjdI, gjdI, gjd2, IjsI, gjsI, gjs2;
+  const double Isat = __ldg(pr + P_ISAT * N);
+  double IjdI, gjdI, gjd2, IjsI = 0.0, gjsI = 0.0, gjs2 = 0.0;
   const double vbd = p * (V[3] - V[0]), vbsj = p * (V[3] - V[2]);
   junction2(c, Isat, vbd, IjdI, gjdI, gjd2);
-  junction2(c, Isat, vbsj, IjsI, gjsI, gjs2);
+  // with source and body held the source junction carries no weight (rows and columns s, b
+  // are not stamped): its terms below are multiplied by zero
+  if (!sbf) junction2(c, Isat, vbsj, IjsI, gjsI, gjs2);
   const double gjd = gjdI + c.GMIN, gjs = gjsI + c.GMIN;
   const double kd = cw[0][0] - cw[0][3] - cw[3][0] + cw[3][3];
   const double rd = p * (wb[3] - wb[0]);
