@@ -67,6 +67,8 @@ struct eec_ctx {
   int auto_block = -1;         // block size baked into the cached graph
   int sms = 0;
   int persist_grid = 0;
+  int stamp_grid = 0;          // blocks of the one-launch colour stamp
+  int stamp_mode = 0;          // colour-buffered stamp: 0 per-colour launches, 1 grid, 2 cluster
   // phase timing and launch counting
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -348,10 +350,20 @@ int run_variant(eec_ctx* c, int v, const double* x, double* A, double* b, double
       CUDA_TRY(c, launch_eval(c->d, MODE_BUFFER, 0, c->n_dev, x, A, b, q, blk, dbg, s));
       prof_mark(c, s);
       *nk = c->n_dev > 0;
-      for (int k = 0; k < c->C; ++k) {
-        if (c->color_off[k + 1] <= c->color_off[k]) continue;
-        CUDA_TRY(c, launch_stamp_buffer(c->d, c->color_off[k], c->color_off[k + 1], A, b, blk, s));
+      // colour order: one launch per colour for a few colours, else one co-resident launch
+      // that steps through the colours with a grid barrier
+      if (c->stamp_mode == 2) {
+        CUDA_TRY(c, launch_stamp_cluster(c->d, c->d_coff, c->C, A, b, s));
         ++*nk;
+      } else if (c->stamp_mode == 1) {
+        CUDA_TRY(c, launch_stamp_persistent(c->d, c->d_coff, c->C, A, b, c->stamp_grid, s));
+        ++*nk;
+      } else {
+        for (int k = 0; k < c->C; ++k) {
+          if (c->color_off[k + 1] <= c->color_off[k]) continue;
+          CUDA_TRY(c, launch_stamp_buffer(c->d, c->color_off[k], c->color_off[k + 1], A, b, blk, s));
+          ++*nk;
+        }
       }
       break;
     default:
@@ -993,6 +1005,30 @@ int eec_build_scatter(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_out) {
   const int bps = persistent_max_blocks_per_sm(0, false);
   const int bpsq = persistent_max_blocks_per_sm(0, true);
   c->persist_grid = std::max(1, std::min(std::min(bps, bpsq), 4)) * c->sms;
+  // enough 256-thread blocks for the largest colour, within one co-resident wave (fewer blocks
+  // make each barrier cheaper)
+  int maxcol = 0;
+  for (int k = 0; k < c->C; ++k) maxcol = std::max(maxcol, c->color_off[k + 1] - c->color_off[k]);
+  const int sbps = stamp_persistent_max_blocks_per_sm();
+  c->stamp_grid = sbps > 0 ? std::max(1, std::min(sbps * c->sms, (maxcol + 255) / 256)) : 0;
+  // Colour-buffered stamp: pick the cheapest of per-colour launches (about 8 us per colour on
+  // GB300), one grid with a grid barrier (about 7 us per barrier) and one 8-block cluster with
+  // the hardware cluster barrier (about one 2 us round of read-modify-writes per 8,192 devices
+  // of a colour), from the colour sizes.
+  {
+    const double nt = (double)stamp_cluster_threads();
+    double t_launch = 0.0, t_grid = 0.0, t_cluster = 0.0;
+    for (int k = 0; k < c->C; ++k) {
+      const double sz = c->color_off[k + 1] - c->color_off[k];
+      t_launch += 8.0;
+      t_grid += 7.0 + 2.0 * std::ceil(sz / (256.0 * std::max(1, c->stamp_grid)));
+      t_cluster += 0.5 + 2.0 * std::ceil(sz / nt);
+    }
+    c->stamp_mode = 0;
+    double best = t_launch;
+    if (c->stamp_grid > 0 && t_grid < best) { best = t_grid; c->stamp_mode = 1; }
+    if (t_cluster < best) c->stamp_mode = 2;
+  }
   c->built = true;
   return EEC_OK;
 }

@@ -103,6 +103,16 @@ cudaError_t launch_persistent(const DevTopo& T, const int* color_off_dev, int n_
                               int grid, int dbg, cudaStream_t s, int absent_block = -1);
 int persistent_max_blocks_per_sm(int block, bool want_q);
 cudaError_t launch_gather(const DevTopo& T, double* A, double* b, cudaStream_t s);
+// Buffered contributions of every colour, in colour order, in one cooperative launch of `grid`
+// blocks (co-resident: at most stamp_persistent_max_blocks_per_sm() per SM).
+cudaError_t launch_stamp_persistent(const DevTopo& T, const int* color_off_dev, int n_colors,
+                                    double* A, double* b, int grid, cudaStream_t s);
+int stamp_persistent_max_blocks_per_sm();
+// The same by one thread-block cluster with the hardware cluster barrier between colours
+// (stamp_cluster_threads() threads in all).
+cudaError_t launch_stamp_cluster(const DevTopo& T, const int* color_off_dev, int n_colors,
+                                 double* A, double* b, cudaStream_t s);
+int stamp_cluster_threads();
 // Transient companion stamp (mode MODE_RMW over one colour range, or MODE_ATOMIC over all).
 struct TranArgs {
   const double* qprev;  // [4][N_orig] charges of the previous time point

@@ -366,23 +366,87 @@ __global__ void __launch_bounds__(kGatherBlock) k_gather(DevTopo T, double* A, d
 }
 
 // One colour's stamp from the buffer (positions begin..end-1 share no row).
+// Add device k's buffered contributions to A and b (store-add: callers guarantee that no other
+// thread touches the same entries meanwhile — one colour at a time).
+__device__ __forceinline__ void stamp_buffered(const DevTopo& T, int k, double* A, double* b) {
+  const long long N = T.N;
+  const int4 ti = __ldg(T.tidx + k);
+  const int rows[3] = {ti.x, ti.z, ti.w};
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    if (rows[r] < 0) continue;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int s = __ldg(T.slot + (4 * r + u) * N + k);
+      if (s >= 0) A[s] += __ldg(T.buf + (4 * r + u) * N + k);
+    }
+    b[rows[r]] += __ldg(T.buf + (kNSlot + r) * N + k);
+  }
+}
+
 __global__ void __launch_bounds__(kEvalBlock) k_stamp_buffer(DevTopo T, int begin, int end,
                                                              double* A, double* b) {
-  const long long N = T.N;
   for (int k = begin + blockIdx.x * blockDim.x + threadIdx.x; k < end;
-       k += gridDim.x * blockDim.x) {
-    const int4 ti = __ldg(T.tidx + k);
-    const int rows[3] = {ti.x, ti.z, ti.w};
+       k += gridDim.x * blockDim.x)
+    stamp_buffered(T, k, A, b);
+}
+
+// The same through L2 only (ld.cg / st.cg): for kernels whose blocks on other SMs updated the
+// entries in an earlier colour, so that no stale L1 line is read.
+__device__ __forceinline__ void stamp_buffered_l2(const DevTopo& T, int k, double* A, double* b) {
+  const long long N = T.N;
+  const int4 ti = __ldg(T.tidx + k);
+  const int rows[3] = {ti.x, ti.z, ti.w};
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      if (rows[r] < 0) continue;
+  for (int r = 0; r < 3; ++r) {
+    if (rows[r] < 0) continue;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int s = __ldg(T.slot + (4 * r + u) * N + k);
-        if (s >= 0) A[s] += __ldg(T.buf + (4 * r + u) * N + k);
-      }
-      b[rows[r]] += __ldg(T.buf + (kNSlot + r) * N + k);
+    for (int u = 0; u < 4; ++u) {
+      const int s = __ldg(T.slot + (4 * r + u) * N + k);
+      if (s >= 0) __stcg(A + s, __ldcg(A + s) + __ldg(T.buf + (4 * r + u) * N + k));
     }
+    __stcg(b + rows[r], __ldcg(b + rows[r]) + __ldg(T.buf + (kNSlot + r) * N + k));
+  }
+}
+
+// All colours' buffered stamps by one thread-block cluster (kClusterBlocks blocks of 1024
+// threads on as many SMs), colour after colour, with the cluster's hardware barrier between
+// colours (release/acquire at cluster scope; every thread passes it the same number of times,
+// so it cannot wait on an absent thread). For netlists with many small colours: a colour then
+// costs one round of read-modify-writes and a barrier of a few hundred cycles.
+constexpr int kClusterBlocks = 8;
+constexpr int kClusterThreads = 1024;
+__global__ void __launch_bounds__(kClusterThreads) k_stamp_cluster(DevTopo T,
+                                                                  const int* __restrict__ coff,
+                                                                  int C, double* A, double* b) {
+  const int nthreads = gridDim.x * blockDim.x;   // the grid is one cluster
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int c = 0; c < C; ++c) {
+    const int begin = __ldg(coff + c), end = __ldg(coff + c + 1);
+    for (int k = begin + tid; k < end; k += nthreads) stamp_buffered_l2(T, k, A, b);
+    if (c + 1 < C) {
+      __syncwarp();   // the .aligned barrier is executed by whole warps
+      asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+      asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+    }
+  }
+}
+
+// All colours' buffered stamps in one co-resident launch: the grid adds colour c, passes the
+// bounded grid barrier, then adds colour c + 1 — the order of the per-colour launches, without
+// a launch (or graph node) per colour. Stamping a colour is a few read-modify-writes per device,
+// so a colour costs about one barrier.
+constexpr int kStampBlock = 256;
+__global__ void __launch_bounds__(kStampBlock) k_stamp_persistent(DevTopo T,
+                                                                  const int* __restrict__ coff,
+                                                                  int C, double* A, double* b,
+                                                                  int absent_block) {
+  for (int c = 0; c < C; ++c) {
+    const int begin = __ldg(coff + c), end = __ldg(coff + c + 1);
+    for (int k = begin + blockIdx.x * blockDim.x + threadIdx.x; k < end;
+         k += gridDim.x * blockDim.x)
+      stamp_buffered(T, k, A, b);
+    if (c + 1 < C && !grid_sync(T.bar, T.status, absent_block)) return;
   }
 }
 
@@ -540,6 +604,48 @@ cudaError_t launch_gather(const DevTopo& T, double* A, double* b, cudaStream_t s
   if (nbl + nbh == 0) return cudaSuccess;
   k_gather<<<nbl + nbh, kGatherBlock, 0, s>>>(T, A, b, nbl);
   return cudaGetLastError();
+}
+
+cudaError_t launch_stamp_cluster(const DevTopo& T, const int* color_off_dev, int n_colors,
+                                 double* A, double* b, cudaStream_t s) {
+  if (n_colors <= 0) return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kClusterBlocks);
+  cfg.blockDim = dim3(kClusterThreads);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kClusterBlocks;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_stamp_cluster, T, color_off_dev, n_colors, A, b);
+}
+
+int stamp_cluster_threads() { return kClusterBlocks * kClusterThreads; }
+
+int stamp_persistent_max_blocks_per_sm() {
+  int nb = 0;
+  const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stamp_persistent,
+                                                                      kStampBlock, 0);
+  return e == cudaSuccess ? nb : 0;
+}
+
+cudaError_t launch_stamp_persistent(const DevTopo& T, const int* color_off_dev, int n_colors,
+                                    double* A, double* b, int grid, cudaStream_t s) {
+  if (n_colors <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(T.bar, 0, 2 * sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  DevTopo Tc = T;
+  const int* coff = color_off_dev;
+  int C = n_colors;
+  double* AA = A;
+  double* bb = b;
+  int ab = -1;
+  void* args[] = {&Tc, &coff, &C, &AA, &bb, &ab};
+  return cudaLaunchCooperativeKernel((const void*)k_stamp_persistent, dim3(grid),
+                                     dim3(kStampBlock), args, 0, s);
 }
 
 cudaError_t launch_stamp_buffer(const DevTopo& T, int begin, int end, double* A, double* b,
