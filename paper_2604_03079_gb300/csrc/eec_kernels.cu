@@ -391,42 +391,74 @@ __global__ void __launch_bounds__(kEvalBlock) k_stamp_buffer(DevTopo T, int begi
     stamp_buffered(T, k, A, b);
 }
 
-// The same through L2 only (ld.cg / st.cg): for kernels whose blocks on other SMs updated the
-// entries in an earlier colour, so that no stale L1 line is read.
-__device__ __forceinline__ void stamp_buffered_l2(const DevTopo& T, int k, double* A, double* b) {
+// All colours' buffered stamps by one thread-block cluster (kClusterBlocks blocks of
+// kClusterThreads threads on as many SMs), colour after colour, with the cluster's hardware
+// barrier between colours (release on arrive, acquire on wait; every thread passes it the same
+// number of times, so it cannot wait on an absent thread). Between arrive and wait each thread
+// loads the read-only data of its first device of the next colour (indices, slots, buffered
+// contributions), so that after the barrier only the read-modify-writes of A and b remain; A
+// and b go through L2 (ld.cg / st.cg), so no SM reads a stale L1 line.
+constexpr int kClusterBlocks = 8;
+constexpr int kClusterThreads = 512;
+
+struct StampPre {
+  int rows[3];
+  int sl[kNSlot];
+  double v[kNContrib];
+};
+
+__device__ __forceinline__ void stamp_load(const DevTopo& T, int k, StampPre& p) {
   const long long N = T.N;
   const int4 ti = __ldg(T.tidx + k);
-  const int rows[3] = {ti.x, ti.z, ti.w};
+  p.rows[0] = ti.x;
+  p.rows[1] = ti.z;
+  p.rows[2] = ti.w;
+#pragma unroll
+  for (int j = 0; j < kNSlot; ++j) p.sl[j] = __ldg(T.slot + j * N + k);
+#pragma unroll
+  for (int j = 0; j < kNContrib; ++j) p.v[j] = __ldg(T.buf + j * N + k);
+}
+
+__device__ __forceinline__ void stamp_apply(const StampPre& p, double* A, double* b) {
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
-    if (rows[r] < 0) continue;
+    if (p.rows[r] < 0) continue;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const int s = __ldg(T.slot + (4 * r + u) * N + k);
-      if (s >= 0) __stcg(A + s, __ldcg(A + s) + __ldg(T.buf + (4 * r + u) * N + k));
+      const int s = p.sl[4 * r + u];
+      if (s >= 0) __stcg(A + s, __ldcg(A + s) + p.v[4 * r + u]);
     }
-    __stcg(b + rows[r], __ldcg(b + rows[r]) + __ldg(T.buf + (kNSlot + r) * N + k));
+    __stcg(b + p.rows[r], __ldcg(b + p.rows[r]) + p.v[kNSlot + r]);
   }
 }
 
-// All colours' buffered stamps by one thread-block cluster (kClusterBlocks blocks of 1024
-// threads on as many SMs), colour after colour, with the cluster's hardware barrier between
-// colours (release/acquire at cluster scope; every thread passes it the same number of times,
-// so it cannot wait on an absent thread). For netlists with many small colours: a colour then
-// costs one round of read-modify-writes and a barrier of a few hundred cycles.
-constexpr int kClusterBlocks = 8;
-constexpr int kClusterThreads = 1024;
 __global__ void __launch_bounds__(kClusterThreads) k_stamp_cluster(DevTopo T,
                                                                   const int* __restrict__ coff,
                                                                   int C, double* A, double* b) {
   const int nthreads = gridDim.x * blockDim.x;   // the grid is one cluster
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  StampPre cur;
+  bool have = false;
+  if (C > 0) {
+    const int k = __ldg(coff) + tid;
+    have = k < __ldg(coff + 1);
+    if (have) stamp_load(T, k, cur);
+  }
   for (int c = 0; c < C; ++c) {
     const int begin = __ldg(coff + c), end = __ldg(coff + c + 1);
-    for (int k = begin + tid; k < end; k += nthreads) stamp_buffered_l2(T, k, A, b);
+    if (have) stamp_apply(cur, A, b);
+    for (int k = begin + tid + nthreads; k < end; k += nthreads) {
+      StampPre extra;
+      stamp_load(T, k, extra);
+      stamp_apply(extra, A, b);
+    }
     if (c + 1 < C) {
       __syncwarp();   // the .aligned barrier is executed by whole warps
       asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+      const int k = __ldg(coff + c + 1) + tid;
+      have = k < __ldg(coff + c + 2);
+      if (have) stamp_load(T, k, cur);   // read-only data: safe before the acquire
+      __syncwarp();
       asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
     }
   }
