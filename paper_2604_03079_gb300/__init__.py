@@ -113,6 +113,11 @@ def _load():
 def __getattr__(name):
     if name == "lib":
         return _load()
+    if name == "EvalStamp":   # the torch.autograd.Function (built on first use: imports torch)
+        global _EvalStamp
+        if _EvalStamp is None:
+            _EvalStamp = _autograd()
+        return _EvalStamp
     raise AttributeError(name)
 
 

@@ -202,3 +202,9 @@ def test_batch_offsets_host(eec):
             assert no[k] == rp[r0]
     finally:
         eec.eec_destroy(ctx)
+
+
+def test_autograd_function_is_exposed(eec):
+    import torch
+    assert issubclass(eec.EvalStamp, torch.autograd.Function)
+    assert eec.EvalStamp is eec.EvalStamp   # built once
