@@ -386,6 +386,15 @@ def e2e(eec, circ, x, args, dev, world, n_dev):
                        "streams, double-buffered across steps (independent evaluations)"}}
 
 
+def hbm_peak_gbs():
+    """(GB/s, source): the measured copy bandwidth of this GPU pool, else the fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured (MEASURED_PEAKS.json, STREAM-style copy)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback (6.8 TB/s, one earlier GB300 copy measurement)"
+
+
 def _time(fn, reps, stream):
     import torch
     for _ in range(2):
@@ -433,6 +442,23 @@ def extras(eec, circ, net, x, xt, A, b, q, args, dev):
                                         "stamp_ms": p["ms_stamp"] / n}
     eec.eec_set_variant(circ.ctx, v0)
     res["phases_ungraphed"] = phases
+
+    # HBM roofline of the stamp-only kernel (the segmented-reduction gather from the buffer):
+    # per contribution 8 B of buffer + 4 B of source index, per A/b entry 8 B written, 8 B of
+    # its linear part, 4 B of offset and 4 B of list index
+    _, _, unk = circ.pattern()
+    free = unk[net.dev_nodes] >= 0
+    contrib = int((free[:, [0, 2, 3]].sum(axis=1) * (1 + free.sum(axis=1))).sum())
+    entries = circ.nnz + circ.n
+    gbytes = 12 * contrib + 24 * entries
+    st_ms = phases["segreduce"]["stamp_ms"]
+    hbm = hbm_peak_gbs()
+    res["stamp_roofline"] = {
+        "kernel": "k_gather (segmented-reduction stamp)", "bound": "hbm",
+        "achieved": gbytes / (st_ms * 1e-3) / 1e9, "peak": hbm[0], "unit": "GB/s",
+        "frac": gbytes / (st_ms * 1e-3) / 1e9 / hbm[0], "algorithmic_bytes": gbytes,
+        "contributions": contrib, "entries": entries, "peak_source": hbm[1],
+        "note": "inputs L2-resident: the buffer is read right after the evaluate kernel wrote it"}
 
     # transient companion stamp (trapezoidal rule) on the same workload
     qprev = torch.empty_like(q)
