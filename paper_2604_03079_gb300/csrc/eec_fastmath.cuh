@@ -5,18 +5,18 @@
 // effective overdrive, expm1 in each junction) are worth specialising. The methods are P. T. P.
 // Tang's table-driven algorithms:
 //   exp   — "Table-driven implementation of the exponential function in IEEE floating-point
-//           arithmetic", ACM TOMS 15(2), 1989: x = (64 m + j) ln2/64 + r with |r| <= ln2/128
-//           (Cody–Waite reduction with a two-part ln2/64), exp(x) = 2^m 2^(j/64) e^r, e^r - 1 by
-//           its Taylor polynomial;
+//           arithmetic", ACM TOMS 15(2), 1989: x = (256 m + j) ln2/256 + r with |r| <= ln2/512
+//           (Cody–Waite reduction with a two-part ln2/256), exp(x) = 2^m 2^(j/256) e^r, e^r - 1
+//           by its Taylor polynomial (256 entries rather than Tang's 32: one degree less);
 //   expm1 — "Table-driven implementation of the expm1 function ...", ACM TOMS 18(2), 1992: a
-//           Taylor polynomial for small |x|, otherwise the exp reduction with 2^(j/64) held as a
+//           Taylor polynomial for small |x|, otherwise the exp reduction with 2^(j/256) held as a
 //           double-double so that (2^m T - 1) is formed without losing the leading bits;
 //   log1p — "Table-driven implementation of the logarithm function ...", ACM TOMS 16(4), 1990,
-//           specialised to 1 + e with e in [0, 1]: y = 1 + e, F = 1 + j/128 nearest to y,
+//           specialised to 1 + e with e in [0, 1]: y = 1 + e, F = 1 + j/256 nearest to y,
 //           u = (y - F)/F, log y = log F + log1p(u) by its Taylor polynomial, plus the rounding
 //           error of 1 + e carried as c / y. One path for the whole interval (j = 0, F = 1
-//           covers small e; the polynomial runs to u^7 so that it stays accurate relative to
-//           log y there): a branch for small e would be taken by some lanes of most warps.
+//           covers small e, where the polynomial's truncation stays below 2^-54 relative to
+//           log y): a branch for small e would be taken by some lanes of most warps.
 // Reciprocal and reciprocal square root start from the FP32 special-function unit and finish
 // with one third-order correction from the series of 1/(1 - e) and (1 - e)^(-1/2).
 // Polynomial coefficients are Taylor coefficients; tables come from gen_tables.py. Accuracy
@@ -109,28 +109,28 @@ __device__ __forceinline__ double fm_scale2(double y, int m) {
   return __hiloint2double(__double2hiint(y) + (m << 20), __double2loint(y));
 }
 
-// Argument reduction shared by exp and expm1: x = (64 m + j) ln2/64 + r.
+// Argument reduction shared by exp and expm1: x = (256 m + j) ln2/256 + r.
+static_assert(kExpN == 256, "fm_reduce splits n into 8 table bits and the exponent");
 __device__ __forceinline__ double fm_reduce(double x, int& j, int& m) {
-  const double s = fma(x, kInvLn2x64, 0x1.8p52);   // 1.5 * 2^52 shifter: rounds x*64/ln2
+  const double s = fma(x, kInvLn2xN, 0x1.8p52);   // 1.5 * 2^52 shifter: rounds x*256/ln2
   const int n = __double2loint(s);
   const double nf = s - 0x1.8p52;
-  j = n & 63;
-  m = n >> 6;
-  return fma(-nf, kLn2o64Lo, fma(-nf, kLn2o64Hi, x));
+  j = n & (kExpN - 1);
+  m = n >> 8;
+  return fma(-nf, kLn2oNLo, fma(-nf, kLn2oNHi, x));
 }
 
-// e^r - 1 for |r| <= ln2/128: Taylor polynomial through r^5 (truncation 1.7e-17, below 0.3 ulp
+// e^r - 1 for |r| <= ln2/512: Taylor polynomial through r^4 (truncation 3.8e-17, below 0.2 ulp
 // of e^r; enough for exp, whose result is near 1).
 __device__ __forceinline__ double fm_em1_small(double r) {
-  const double q = fma(r, fma(r, fma(r, fma(r, 1.0 / 120.0, 1.0 / 24.0), 1.0 / 6.0), 0.5), 1.0);
+  const double q = fma(r, fma(r, fma(r, 1.0 / 24.0, 1.0 / 6.0), 0.5), 1.0);
   return r * q;
 }
 
-// The same through r^6 (truncation 3e-20): expm1 results can be as small as 2^-6, so the
+// The same through r^5 (truncation 9e-21): expm1 results can be as small as 2^-6, so the
 // polynomial error must stay below their ulp.
-__device__ __forceinline__ double fm_em1_small6(double r) {
-  const double q = fma(r, fma(r, fma(r, fma(r, fma(r, 1.0 / 720.0, 1.0 / 120.0), 1.0 / 24.0),
-                                       1.0 / 6.0), 0.5), 1.0);
+__device__ __forceinline__ double fm_em1_small5(double r) {
+  const double q = fma(r, fma(r, fma(r, fma(r, 1.0 / 120.0, 1.0 / 24.0), 1.0 / 6.0), 0.5), 1.0);
   return r * q;
 }
 
@@ -155,7 +155,7 @@ __device__ __forceinline__ double fm_expm1(double x) {
   if (!fm_lt_pos(x, kBits709)) return ::expm1(x);
   int j, m;
   const double r = fm_reduce(x, j, m);
-  const double p = fm_em1_small6(r);
+  const double p = fm_em1_small5(r);
   const double T = fm_scale2(__ldg(kExp2Hi + j), m);
   const double tl = __ldg(kExp2Lo + j);
   const double Tl = (__double2hiint(tl) == 0 && __double2loint(tl) == 0) ? 0.0 : fm_scale2(tl, m);
@@ -166,12 +166,11 @@ __device__ __forceinline__ double fm_expm1(double x) {
 __device__ __forceinline__ double fm_log1p01(double e, double inv_y) {
   const double y = 1.0 + e;                        // [1, 2]
   const double c = e - (y - 1.0);                  // rounding error of y, exact
-  const double s = fma(y, 128.0, 0x1.8p52);        // round(128 y) in [128, 256]
-  const int jj = __double2loint(s) - 128;          // F = 1 + jj/128, jj in [0, 128]
-  const double u = (y - __ldg(kF + jj)) * __ldg(kInvF + jj);   // |u| <= 2^-8; y - F exact
-  const double q = fma(u, fma(u, fma(u, fma(u, fma(u, 1.0 / 7.0, -1.0 / 6.0), 0.2), -0.25),
-                              1.0 / 3.0), -0.5);
-  const double pu = fma(u * u, q, u);              // log1p(u), truncation below 2^-59 relative
+  const double s = fma(y, (double)kLogN, 0x1.8p52);   // round(256 y) in [256, 512]
+  const int jj = __double2loint(s) - kLogN;        // F = 1 + jj/256, jj in [0, 256]
+  const double u = (y - __ldg(kF + jj)) * __ldg(kInvF + jj);   // |u| <= 2^-9; y - F exact
+  const double q = fma(u, fma(u, fma(u, fma(u, -1.0 / 6.0, 0.2), -0.25), 1.0 / 3.0), -0.5);
+  const double pu = fma(u * u, q, u);              // log1p(u), truncation below 2^-54 relative
   return __ldg(kLogFHi + jj) + fma(c, inv_y, __ldg(kLogFLo + jj) + pu);
 }
 

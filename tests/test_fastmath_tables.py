@@ -1,6 +1,6 @@
 """CPU checks of the tables behind the library's table-driven exp / expm1 / log1p: every entry of
 eec_tables.h against 200-bit mpmath values (double-double pairs to about 2^-100 relative), and the
-Cody-Waite split of ln2/64."""
+Cody-Waite split of ln2/256."""
 import os
 import re
 
@@ -23,11 +23,11 @@ def _parse():
     return arrays, consts
 
 
-def test_exp_table_is_two_to_the_j_over_64():
+def test_exp_table_is_two_to_the_j_over_256():
     a, _ = _parse()
-    assert len(a["kExp2Hi"]) == len(a["kExp2Lo"]) == 64
-    for j in range(64):
-        exact = mpmath.power(2, mpmath.mpf(j) / 64)
+    assert len(a["kExp2Hi"]) == len(a["kExp2Lo"]) == 256
+    for j in range(256):
+        exact = mpmath.power(2, mpmath.mpf(j) / 256)
         assert float(exact) == a["kExp2Hi"][j]
         err = abs(mpmath.mpf(a["kExp2Hi"][j]) + mpmath.mpf(a["kExp2Lo"][j]) - exact) / exact
         assert err < mpmath.mpf(2) ** -100
@@ -35,8 +35,9 @@ def test_exp_table_is_two_to_the_j_over_64():
 
 def test_log_tables():
     a, _ = _parse()
-    for j in range(129):
-        F = 1 + mpmath.mpf(j) / 128
+    assert len(a["kF"]) == len(a["kInvF"]) == len(a["kLogFHi"]) == len(a["kLogFLo"]) == 257
+    for j in range(257):
+        F = 1 + mpmath.mpf(j) / 256
         assert a["kF"][j] == float(F)
         assert a["kInvF"][j] == float(1 / F)
         err = abs(mpmath.mpf(a["kLogFHi"][j]) + mpmath.mpf(a["kLogFLo"][j]) - mpmath.log(F))
@@ -45,10 +46,10 @@ def test_log_tables():
 
 def test_reduction_constants():
     _, c = _parse()
-    ln2o64 = mpmath.log(2) / 64
-    assert c["kLn2o64Hi"] == float(ln2o64)
-    assert abs(mpmath.mpf(c["kLn2o64Hi"]) + mpmath.mpf(c["kLn2o64Lo"]) - ln2o64) < mpmath.mpf(2) ** -110
-    assert c["kInvLn2x64"] == float(64 / mpmath.log(2))
+    ln2oN = mpmath.log(2) / 256
+    assert c["kLn2oNHi"] == float(ln2oN)
+    assert abs(mpmath.mpf(c["kLn2oNHi"]) + mpmath.mpf(c["kLn2oNLo"]) - ln2oN) < mpmath.mpf(2) ** -110
+    assert c["kInvLn2xN"] == float(256 / mpmath.log(2))
 
 
 def test_bit_pattern_constants_match_their_values():

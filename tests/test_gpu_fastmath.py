@@ -35,7 +35,8 @@ CASES = {
                -1e-300]),
     "log1p": (2, np.log1p, [(0.0, 1.0), (0.0, 2 ** -6), (2 ** -8, 2 ** -6), (0.0, 2 ** -9)],
               [0.0, 1.0, 2 ** -7, np.nextafter(2 ** -7, 0), 1e-300, 5e-324, 0.5, 2 ** -8,
-               np.nextafter(2 ** -8, 1), 1 / 256 + 1 / 512]),
+               np.nextafter(2 ** -8, 1), 1 / 256 + 1 / 512, 2 ** -9, np.nextafter(2 ** -9, 0),
+               1 / 512 + 1 / 1024]),
     "rcp": (3, lambda v: 1.0 / v, [(1e-3, 1e6), (1.0, 2.0), (-1e3, -1e-3)],
             [1.0, 2.0, 0.5, 1 + 2 ** -52, 2 - 2 ** -52, 3.0, -1.0, 1e-3, 1e6]),
     "rsqrt": (4, lambda v: 1.0 / np.sqrt(v), [(1e-6, 1e6), (1.0, 4.0), (1e-3, 1e-2)],
