@@ -140,7 +140,7 @@ __device__ __forceinline__ double fm_exp(double x) {
   const double r = fm_reduce(x, j, m);
   const double p = fm_em1_small(r);
   const double th = __ldg(kExp2Hi + j);
-  const double y = fma(th, p, __ldg(kExp2Lo + j)) + th;   // 2^(j/64) e^r in [0.99, 2)
+  const double y = fma(th, p, __ldg(kExp2Lo + j)) + th;   // 2^(j/256) e^r in [0.997, 2)
   return fm_scale2(y, m);
 }
 
