@@ -36,8 +36,8 @@ UNIT = "device evals+stamps/s"
 # FP64 flop = 2 DFMA + DADD + DMUL thread instructions per device, and DRAM bytes read +
 # written per device. The flop count depends on the device mix (devices whose source and body
 # are source-held skip the body-effect and source-junction work).
-FP64_FLOP_PER_DEVICE = {"sram": 277.5}
-DRAM_BYTES_PER_DEVICE = {"sram": 192.0}
+FP64_FLOP_PER_DEVICE = {"sram": 277.5, "logic": 267.2, "logic1m": 267.2, "batch": 246.8}
+DRAM_BYTES_PER_DEVICE = {"sram": 192.0, "logic": 237.8, "logic1m": 278.2, "batch": 384.5}
 # GB300: 152 SMs x 2 FP64 FMA per clock per SM x 2 flop x 2070 MHz maximum SM clock.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 

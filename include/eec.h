@@ -78,6 +78,10 @@ typedef struct {
                             or 8, 16, 32, 64, 96, 128 */
   int32_t conflict_rule; /* EEC_CONFLICT_*; default EEC_CONFLICT_FREE_NODE */
   int32_t debug_checks;  /* nonzero: kernels flag non-finite outputs in the status word */
+  int32_t color_stamp;   /* stamp of EEC_VARIANT_COLOR_BUFFERED, colour after colour: 0 = chosen
+                            from the colour sizes, 1 = one launch per colour, 2 = one co-resident
+                            grid with a grid barrier between colours, 3 = one 8-block thread-block
+                            cluster with the cluster barrier between colours */
   int32_t host_chunks;   /* eec_eval_stamp_host: chunks whose charges are copied out while later
                             chunks are evaluated; 0 = by size (3 from 2^18 devices, 2 from 2^17,
                             else 1), or 1..64 */

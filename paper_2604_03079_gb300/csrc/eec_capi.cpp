@@ -567,6 +567,7 @@ eec_options eec_default_options(void) {
   o.block = 0;
   o.conflict_rule = EEC_CONFLICT_FREE_NODE;
   o.debug_checks = 0;
+  o.color_stamp = 0;
   o.host_chunks = 0;
   return o;
 }
@@ -579,6 +580,7 @@ int eec_create(eec_ctx** out, const eec_options* opt) {
   c->opt = opt ? *opt : eec_default_options();
   if (c->opt.variant < EEC_VARIANT_AUTO || c->opt.variant >= EEC_N_VARIANTS ||
       c->opt.conflict_rule < 0 || c->opt.conflict_rule > 2 || c->opt.host_chunks < 0 ||
+      c->opt.color_stamp < 0 || c->opt.color_stamp > 3 ||
       c->opt.host_chunks > 64 ||
       !(c->opt.block == 0 || c->opt.block == 8 || c->opt.block == 16 ||
         (c->opt.block % 32 == 0 && c->opt.block <= 128))) {
@@ -1028,6 +1030,9 @@ int eec_build_scatter(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_out) {
     double best = t_launch;
     if (c->stamp_grid > 0 && t_grid < best) { best = t_grid; c->stamp_mode = 1; }
     if (t_cluster < best) c->stamp_mode = 2;
+    if (c->opt.color_stamp == 1) c->stamp_mode = 0;
+    if (c->opt.color_stamp == 2 && c->stamp_grid > 0) c->stamp_mode = 1;
+    if (c->opt.color_stamp == 3) c->stamp_mode = 2;
   }
   c->built = true;
   return EEC_OK;

@@ -100,7 +100,8 @@ def test_validation_errors(eec):
             eec.eec_set_variant(ctx, 7)
     finally:
         eec.eec_destroy(ctx)
-    for bad in ({"host_chunks": -1}, {"host_chunks": 65}, {"block": 48}, {"conflict_rule": 3}):
+    for bad in ({"host_chunks": -1}, {"host_chunks": 65}, {"block": 48}, {"conflict_rule": 3},
+                {"color_stamp": 4}, {"color_stamp": -1}):
         with pytest.raises(eec.EECError):
             eec.eec_create(**bad)
     eec.eec_destroy(eec.eec_create(host_chunks=64))

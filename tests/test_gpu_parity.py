@@ -403,6 +403,24 @@ def test_host_buffer_entry_point(eec, pinned, variant, chunks):
             assert np.isnan(qh.numpy()).all()   # q not requested: left alone
 
 
+@pytest.mark.parametrize("make", [lambda: netgen.sram(24, 20), lambda: netgen.random_logic(3000, seed=4),
+                                  lambda: netgen.ripple_adder(8)])
+def test_color_buffered_stamp_implementations_agree_bitwise(eec, make):
+    # per-colour launches, one grid with a grid barrier, one cluster with the cluster barrier:
+    # the same additions in the same colour order, so the same bits; and the oracle's values
+    net = make()
+    o = oracle.Oracle(net, CARDS)
+    x = netgen.random_x(net, seed=5)
+    ref = o.eval_stamp(x, want_q=True, want_scale=True)
+    outs = []
+    for mode in (1, 2, 3):
+        circ = eec.Circuit(net, CARDS, variant=eec.EEC_VARIANT_COLOR_BUFFERED, color_stamp=mode)
+        assert circ.n_colors >= 3
+        outs.append(check_against_oracle(eec, circ, o, x, eec.EEC_VARIANT_COLOR_BUFFERED, ref=ref))
+    for k in (0, 1):
+        assert np.array_equal(outs[1][k], outs[0][k]) and np.array_equal(outs[2][k], outs[0][k])
+
+
 def test_debug_checks_flag_non_finite_inputs(eec):
     net = netgen.inverter_chain(8)
     circ = eec.Circuit(net, CARDS, debug_checks=True)
