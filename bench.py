@@ -56,6 +56,9 @@ def parse():
                     help="timed steps only (no autotune, e2e, extras, probes, baseline): for ncu")
     ap.add_argument("--bwd-steps", type=int, default=0,
                     help="with --quick: also run the backward this many times (for ncu)")
+    ap.add_argument("--tran-steps", type=int, default=0,
+                    help="with --quick: also run the trapezoidal transient stamp this many times "
+                         "(for ncu)")
     return ap.parse_args()
 
 
@@ -280,6 +283,14 @@ def run_ours(args):
             gb = torch.as_tensor(rng.normal(circ.n), device=dev)
             for _ in range(args.bwd_steps):
                 circ.bwd(xt, gA, gb)
+            torch.cuda.synchronize()
+            assert circ.status() == 0
+        if args.tran_steps:
+            qprev = torch.empty_like(q)
+            circ.eval_stamp(xt, A, b, qprev)
+            ic, ip = torch.empty_like(q), torch.zeros_like(q)
+            for _ in range(args.tran_steps):
+                eec.eec_eval_stamp_tran(circ.ctx, xt, qprev, ip, 2e11, 1.0, A, b, q, ic)
             torch.cuda.synchronize()
             assert circ.status() == 0
         print(json.dumps(out))

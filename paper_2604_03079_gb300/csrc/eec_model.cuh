@@ -347,28 +347,33 @@ __device__ __forceinline__ void ees_l1(const CardK& c, unsigned long long psb, c
       // dVg/d(vgs, vds, vbs) = sig (1, ETA0, -dVth/dvbs) and the total derivatives of F1; mapped
       // to the physical terminals as for G (the polarity factors cancel). Columns sum to zero.
       const S Vg_vds = ch.sig * c.ETA0;
-      const S Vg_vbs = -(ch.sig * dVth_dvbs);
       const S F1_vgs = ch.F1_Vg * ch.sig;
       const S F1_vdsT = ch.F1_Vg * Vg_vds + ch.F1_vds;
-      const S F1_vbsT = ch.F1_Vg * Vg_vbs + ch.F1_Ab * dAb_dvbs;
       const S mC = -P.Coxt;
       const S Qi_vgs = mC * (ch.sig * F1 + Vg * F1_vgs);
       const S Qi_vds = mC * (Vg_vds * F1 + Vg * F1_vdsT);
-      const S Qi_vbs = mC * (Vg_vbs * F1 + Vg * F1_vbsT);
-      const S Qb_vbs = mC * dVth_dvbs;
       // partition fraction: sr = Vdseff / Vdsat with Vdsat(Vg, Ab), Vdseff(Vdsat, vds)
       // 1 / Vdsat = Dd / (EsatL Vgst2): both reciprocals are already at hand
       const S inv_Vdsat = ch.inv_Vdsat_parts[0] * ch.inv_Vdsat_parts[1] * ch.inv_Vdsat_parts[2];
       const S sr_Vg = (ch.Vde_Vg - sr * ch.Vdsat_Vg) * inv_Vdsat;
-      const S sr_Ab = (ch.Vde_Ab - sr * ch.Vdsat_Ab) * inv_Vdsat;
       const S sr_vds = ch.Vde_vds * inv_Vdsat;
       const double mx = c.XPm;                     // dfD / dsr
       const S fD_vgs = mx * (sr_Vg * ch.sig);
       const S fD_vds = mx * (sr_Vg * Vg_vds + sr_vds);
-      const S fD_vbs = mx * (sr_Vg * Vg_vbs + sr_Ab * dAb_dvbs);
       const S QD_vgs = fD * Qi_vgs + Qinv * fD_vgs;
       const S QD_vds = fD * Qi_vds + Qinv * fD_vds;
-      const S QD_vbs = fD * Qi_vbs + Qinv * fD_vbs;
+      // vbs column: with source and body held, in forward mode, the body and source columns are
+      // never stamped (both terminals are held), so their entries are left at zero
+      S Qi_vbs = S(0.0), Qb_vbs = S(0.0), QD_vbs = S(0.0);
+      if (!(sb_fixed && fwd)) {
+        const S Vg_vbs = -(ch.sig * dVth_dvbs);
+        const S F1_vbsT = ch.F1_Vg * Vg_vbs + ch.F1_Ab * dAb_dvbs;
+        Qi_vbs = mC * (Vg_vbs * F1 + Vg * F1_vbsT);
+        Qb_vbs = mC * dVth_dvbs;
+        const S sr_Ab = (ch.Vde_Ab - sr * ch.Vdsat_Ab) * inv_Vdsat;
+        const S fD_vbs = mx * (sr_Vg * Vg_vbs + sr_Ab * dAb_dvbs);
+        QD_vbs = fD * Qi_vbs + Qinv * fD_vbs;
+      }
       const int iD = fwd ? 0 : 2, iS = fwd ? 2 : 0;
       S MQi[4], MQb[4], MQD[4];
       MQi[1] = Qi_vgs;
