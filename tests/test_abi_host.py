@@ -209,3 +209,16 @@ def test_autograd_function_is_exposed(eec):
     import torch
     assert issubclass(eec.EvalStamp, torch.autograd.Function)
     assert eec.EvalStamp is eec.EvalStamp   # built once
+
+
+def test_header_is_plain_c_and_a_c_program_links(eec, tmp_path):
+    # the boundary is a C ABI: a C99 program sees only include/eec.h and _libeec.so
+    import subprocess
+    src = os.path.join(ROOT, "tests", "c_abi", "host_calls.c")
+    exe = str(tmp_path / "host_calls")
+    libdir = os.path.dirname(eec.LIB_PATH)
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                    "-I", os.path.join(ROOT, "include"), src, "-o", exe, "-L", libdir,
+                    "-l:_libeec.so", "-Wl,-rpath," + libdir], check=True)
+    out = subprocess.run([exe], capture_output=True, text=True)
+    assert out.returncode == 0 and out.stdout.strip() == "ok", (out.returncode, out.stderr)
