@@ -302,7 +302,7 @@ def run_ours(args):
         ach = (flop * net.n_dev / (eval_ms * 1e-3) / 1e12) if (flop and eval_ms > 0) else None
         traffic = (DRAM_BYTES_PER_DEVICE[args.workload] * net.n_dev
                    if counted and args.workload in DRAM_BYTES_PER_DEVICE else None)
-        out["roofline"] = {"bound": "alu", "kernel": "k_eval (evaluate)",
+        out["roofline"] = {"bound": "alu", "kernel": "k_eval_ranges / k_eval (evaluate)",
                            "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                            "frac": (ach / FP64_PEAK_TFLOPS) if ach else None, "traffic": traffic,
                            "peak_source": "152 SM x 2 DFMA/clk x 2 flop x 2070 MHz (recipe unit "

@@ -89,6 +89,11 @@ struct eec_ctx {
   int* d_hrbeg = nullptr;
   int* d_hroff = nullptr;
   cudaStream_t side = nullptr;   // charge copies of eec_eval_stamp_host
+  // launch order of the order-free evaluations: layout ranges, devices with a free source or
+  // body first (eval_nr = 0: plain layout order)
+  int eval_nr = 0;
+  int* d_erbeg = nullptr;
+  int* d_eroff = nullptr;
   std::vector<cudaEvent_t> hev;  // chunk done (K) + side stream done (1)
 };
 
@@ -140,6 +145,8 @@ void free_topology(eec_ctx* c) {
   c->h_x = c->h_A = c->h_b = c->h_q = nullptr;  // freed with the other device arrays
   c->host_K = 0;
   c->d_hrbeg = c->d_hroff = nullptr;
+  c->eval_nr = 0;
+  c->d_erbeg = c->d_eroff = nullptr;
   if (!c->dmem.empty()) cudaDeviceSynchronize();
   for (void* p : c->dmem) cudaFree(p);
   c->dmem.clear();
@@ -293,6 +300,15 @@ bool variant_needs_colors(int v) {
 
 // Enqueue one evaluate-and-stamp with schedule v on stream s. Returns the number of kernels
 // launched in *nk. With profiling on, four events bracket the phases init | evaluate | stamp.
+// Every device once, in the cost order of eval_nr (order-free modes only).
+cudaError_t launch_eval_all(eec_ctx* c, int mode, const double* x, double* A, double* b,
+                            double* q, int blk, int dbg, cudaStream_t s) {
+  if (c->eval_nr >= 2)
+    return launch_eval_ranges(c->d, mode, c->d_erbeg, c->d_eroff, c->eval_nr, c->n_dev, x, A, b,
+                              q, blk, dbg, s);
+  return launch_eval(c->d, mode, 0, c->n_dev, x, A, b, q, blk, dbg, s);
+}
+
 int run_variant(eec_ctx* c, int v, const double* x, double* A, double* b, double* q,
                 cudaStream_t s, long long* nk) {
   const DevTopo& T = c->d;
@@ -333,13 +349,13 @@ int run_variant(eec_ctx* c, int v, const double* x, double* A, double* b, double
     case EEC_VARIANT_ATOMIC:
       if ((rc = init_Ab())) return rc;
       prof_mark(c, s);
-      CUDA_TRY(c, launch_eval(T, MODE_ATOMIC, 0, c->n_dev, x, A, b, q, blk, dbg, s));
+      CUDA_TRY(c, launch_eval_all(c, MODE_ATOMIC, x, A, b, q, blk, dbg, s));
       *nk = c->n_dev > 0;
       prof_mark(c, s);
       break;
     case EEC_VARIANT_SEGREDUCE:
       prof_mark(c, s);
-      CUDA_TRY(c, launch_eval(c->d, MODE_BUFFER, 0, c->n_dev, x, A, b, q, blk, dbg, s));
+      CUDA_TRY(c, launch_eval_all(c, MODE_BUFFER, x, A, b, q, blk, dbg, s));
       prof_mark(c, s);
       CUDA_TRY(c, launch_gather(c->d, A, b, s));
       *nk = (c->n_dev > 0) + (c->nnz + c->n > 0);
@@ -347,7 +363,7 @@ int run_variant(eec_ctx* c, int v, const double* x, double* A, double* b, double
     case EEC_VARIANT_COLOR_BUFFERED:
       if ((rc = init_Ab())) return rc;
       prof_mark(c, s);
-      CUDA_TRY(c, launch_eval(c->d, MODE_BUFFER, 0, c->n_dev, x, A, b, q, blk, dbg, s));
+      CUDA_TRY(c, launch_eval_all(c, MODE_BUFFER, x, A, b, q, blk, dbg, s));
       prof_mark(c, s);
       *nk = c->n_dev > 0;
       // colour order: one launch per colour for a few colours, else one co-resident launch
@@ -1033,6 +1049,32 @@ int eec_build_scatter(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_out) {
     if (c->opt.color_stamp == 1) c->stamp_mode = 0;
     if (c->opt.color_stamp == 2 && c->stamp_grid > 0) c->stamp_mode = 1;
     if (c->opt.color_stamp == 3) c->stamp_mode = 2;
+  }
+  // Launch order of the order-free evaluations: devices with a free source or body (the body
+  // effect, the source junction and the vbs chain are evaluated per call) before those with both
+  // held, so that the last partial wave of blocks holds the cheaper devices.
+  {
+    std::vector<int> rb, ro{0};
+    for (int want = 0; want < 2; ++want) {
+      for (int p = 0; p < N;) {
+        const int f = (meta[p] >> 1) & 1;
+        int e = p + 1;
+        while (e < N && ((meta[e] >> 1) & 1) == f) ++e;
+        if (f == want) {
+          rb.push_back(p);
+          ro.push_back(ro.back() + (e - p));
+        }
+        p = e;
+      }
+    }
+    c->eval_nr = 0;
+    // already in that order when every free-source run precedes every held one
+    bool sorted = true;
+    for (size_t i = 1; i < rb.size(); ++i) sorted = sorted && rb[i] > rb[i - 1];
+    if (rb.size() >= 2 && rb.size() <= 4096 && !sorted) {
+      if ((rc = dupload(c, &c->d_erbeg, rb)) || (rc = dupload(c, &c->d_eroff, ro))) return rc;
+      c->eval_nr = (int)rb.size();
+    }
   }
   c->built = true;
   return EEC_OK;
