@@ -36,8 +36,13 @@ UNIT = "device evals+stamps/s"
 # FP64 flop = 2 DFMA + DADD + DMUL thread instructions per device, and DRAM bytes read +
 # written per device. The flop count depends on the device mix (devices whose source and body
 # are source-held skip the body-effect and source-junction work).
-FP64_FLOP_PER_DEVICE = {"sram": 277.5, "logic": 267.2, "logic1m": 267.2, "batch": 246.8}
-DRAM_BYTES_PER_DEVICE = {"sram": 192.0, "logic": 237.8, "logic1m": 278.2, "batch": 384.5}
+# Keys: (workload, evaluation launch order) -> k_eval (layout order) or k_eval_ranges (cost order).
+FP64_FLOP_PER_DEVICE = {("sram", 0): 277.5, ("logic", 0): 267.2, ("logic1m", 0): 267.2,
+                        ("batch", 0): 246.8, ("sram", 1): 280.5, ("logic", 1): 270.2,
+                        ("logic1m", 1): 270.2, ("batch", 1): 249.8}
+DRAM_BYTES_PER_DEVICE = {("sram", 0): 192.0, ("logic", 0): 237.8, ("logic1m", 0): 278.2,
+                         ("batch", 0): 384.5, ("sram", 1): 191.8, ("logic", 1): 243.6,
+                         ("logic1m", 1): 291.3, ("batch", 1): 383.3}
 # GB300: 152 SMs x 2 FP64 FMA per clock per SM x 2 flop x 2070 MHz maximum SM clock.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
@@ -269,6 +274,8 @@ def run_ours(args):
                       "nnz": circ.nnz, "colors": circ.n_colors,
                       "variant": eec.VARIANT_NAMES[variant],
                       "block": eec.eec_get_tuning(circ.ctx)[1],
+                      "eval_order": ("free source/body first" if eec.eec_get_tuning(circ.ctx)[2]
+                                     else "layout order"),
                       "l2": "flushed (256 MiB write) before every timed step",
                       "parallelism": f"replica x{world}" if world > 1 else "single GPU"},
            "gpu_launches": launches,
@@ -298,10 +305,11 @@ def run_ours(args):
         # roofline of the dominant kernel (the evaluate kernel; FP64-pipe bound); the counted
         # figures hold for the atomic schedule's kernel
         counted = variant == eec.EEC_VARIANT_ATOMIC
-        flop = FP64_FLOP_PER_DEVICE.get(args.workload) if counted else None
+        key = (args.workload, eec.eec_get_tuning(circ.ctx)[2])
+        flop = FP64_FLOP_PER_DEVICE.get(key) if counted else None
         ach = (flop * net.n_dev / (eval_ms * 1e-3) / 1e12) if (flop and eval_ms > 0) else None
-        traffic = (DRAM_BYTES_PER_DEVICE[args.workload] * net.n_dev
-                   if counted and args.workload in DRAM_BYTES_PER_DEVICE else None)
+        traffic = (DRAM_BYTES_PER_DEVICE[key] * net.n_dev
+                   if counted and key in DRAM_BYTES_PER_DEVICE else None)
         out["roofline"] = {"bound": "alu", "kernel": "k_eval_ranges / k_eval (evaluate)",
                            "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                            "frac": (ach / FP64_PEAK_TFLOPS) if ach else None, "traffic": traffic,

@@ -169,8 +169,11 @@ EEC_API int eec_get_color_offsets(const eec_ctx* ctx, int32_t* off);
  */
 EEC_API int eec_update_params(eec_ctx* ctx, const double* W_dev, const double* L_dev, void* cuda_stream);
 
-/* The schedule and block size eec_eval_stamp will use (after autotuning, if any). */
-EEC_API int eec_get_tuning(const eec_ctx* ctx, int32_t* variant, int32_t* block);
+/* The schedule, block size and evaluation launch order eec_eval_stamp will use (after
+ * autotuning, if any). eval_order (nullable): 1 = devices with a free source or body first (a
+ * list of layout ranges), 0 = layout order (also when the layout already is in that order). */
+EEC_API int eec_get_tuning(const eec_ctx* ctx, int32_t* variant, int32_t* block,
+                           int32_t* eval_order);
 
 /* Select the schedule (EEC_VARIANT_*) used by eec_eval_stamp. */
 EEC_API int eec_set_variant(eec_ctx* ctx, int32_t variant);
@@ -274,8 +277,10 @@ EEC_API int eec_graph_launch(eec_ctx* ctx, void* cuda_stream);
 /*
  * Autotuner: time every schedule on these buffers (CUDA events, `reps` calls each after one
  * warm-up), at block sizes 0 (library choice), 32, 64 and 128 unless opt.block fixes it, and
- * select the fastest (schedule, block) pair for eec_eval_stamp when the variant is
- * EEC_VARIANT_AUTO. ms_out [EEC_N_VARIANTS] (nullable) receives each schedule's best mean time
+ * for the order-free schedules (ATOMIC, SEGREDUCE, COLOR_BUFFERED) in both evaluation launch
+ * orders (devices with a free source or body first, or layout order); select the fastest
+ * combination for eec_eval_stamp when the variant is EEC_VARIANT_AUTO (the launch order applies
+ * whatever the variant). ms_out [EEC_N_VARIANTS] (nullable) receives each schedule's best mean time
  * per call, negative for a schedule that does not apply (colour schedules without colours).
  * Synchronous.
  */

@@ -68,7 +68,8 @@ _SIG = {
     "eec_update_params": (ctypes.c_int, [_P, _P, _P, _P]),
     "eec_set_variant": (ctypes.c_int, [_P, _I32]),
     "eec_get_variant": (ctypes.c_int, [_P, ctypes.POINTER(_I32)]),
-    "eec_get_tuning": (ctypes.c_int, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
+    "eec_get_tuning": (ctypes.c_int, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32),
+                                      ctypes.POINTER(_I32)]),
     "eec_eval_stamp": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "eec_eval_stamp_bwd": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "eec_eval_stamp_host": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
@@ -294,10 +295,10 @@ def eec_get_variant(ctx) -> int:
 
 
 def eec_get_tuning(ctx):
-    """-> (variant, block) that eec_eval_stamp uses."""
-    v, blk = _I32(0), _I32(0)
-    _check(ctx, _load().eec_get_tuning(ctx, ctypes.byref(v), ctypes.byref(blk)))
-    return int(v.value), int(blk.value)
+    """-> (variant, block, eval_order) that eec_eval_stamp uses."""
+    v, blk, od = _I32(0), _I32(0), _I32(0)
+    _check(ctx, _load().eec_get_tuning(ctx, ctypes.byref(v), ctypes.byref(blk), ctypes.byref(od)))
+    return int(v.value), int(blk.value), int(od.value)
 
 
 def eec_eval_stamp(ctx, x, A, b, q=None, stream=None):

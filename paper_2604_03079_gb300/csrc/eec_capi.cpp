@@ -65,6 +65,7 @@ struct eec_ctx {
   int tuned_variant = EEC_VARIANT_SEGREDUCE;
   int tuned_block = 0;         // block size picked by eec_autotune (used when opt.block == 0)
   int auto_block = -1;         // block size baked into the cached graph
+  bool auto_ordered = true;    // evaluation launch order baked into the cached graph
   int sms = 0;
   int persist_grid = 0;
   int stamp_grid = 0;          // blocks of the one-launch colour stamp
@@ -94,6 +95,7 @@ struct eec_ctx {
   int eval_nr = 0;
   int* d_erbeg = nullptr;
   int* d_eroff = nullptr;
+  bool eval_ordered = true;   // use that order (eec_autotune times both)
   std::vector<cudaEvent_t> hev;  // chunk done (K) + side stream done (1)
 };
 
@@ -303,7 +305,7 @@ bool variant_needs_colors(int v) {
 // Every device once, in the cost order of eval_nr (order-free modes only).
 cudaError_t launch_eval_all(eec_ctx* c, int mode, const double* x, double* A, double* b,
                             double* q, int blk, int dbg, cudaStream_t s) {
-  if (c->eval_nr >= 2)
+  if (c->eval_nr >= 2 && c->eval_ordered)
     return launch_eval_ranges(c->d, mode, c->d_erbeg, c->d_eroff, c->eval_nr, c->n_dev, x, A, b,
                               q, blk, dbg, s);
   return launch_eval(c->d, mode, 0, c->n_dev, x, A, b, q, blk, dbg, s);
@@ -486,7 +488,8 @@ int eval_with(eec_ctx* c, int v, const double* x, double* A, double* b, double* 
   if (!c->prof && (v == EEC_VARIANT_COLOR_FUSED || v == EEC_VARIANT_COLOR_BUFFERED)) {
     const void* key[4] = {x, A, b, q};
     const int blk = c->opt.block ? c->opt.block : c->tuned_block;
-    bool hit = c->auto_exec && c->auto_variant == v && c->auto_block == blk;
+    bool hit = c->auto_exec && c->auto_variant == v && c->auto_block == blk &&
+               c->auto_ordered == c->eval_ordered;
     for (int i = 0; i < 4 && hit; ++i) hit = key[i] == c->auto_key[i];
     if (!hit) {
       if (c->auto_exec) cudaGraphExecDestroy(c->auto_exec);
@@ -496,6 +499,7 @@ int eval_with(eec_ctx* c, int v, const double* x, double* A, double* b, double* 
       if (rc) return rc;
       c->auto_variant = v;
       c->auto_block = blk;
+      c->auto_ordered = c->eval_ordered;
       for (int i = 0; i < 4; ++i) c->auto_key[i] = key[i];
     }
     CUDA_TRY(c, cudaGraphLaunch(c->auto_exec, s));
@@ -1389,10 +1393,17 @@ int eec_autotune(eec_ctx* c, const double* x, double* A, double* b, double* q, i
   const int saved_tuned = c->tuned_block;
   float best = 1e30f;
   int best_v = EEC_VARIANT_SEGREDUCE, best_b = 0;
+  bool best_o = c->eval_ordered;
   for (int v = 0; v < EEC_N_VARIANTS; ++v) {
     float best_ms_v = -1.0f;
+    // the order-free schedules are also timed in both launch orders (cost order, layout order)
+    const bool order_free = v == EEC_VARIANT_ATOMIC || v == EEC_VARIANT_SEGREDUCE ||
+                            v == EEC_VARIANT_COLOR_BUFFERED;
+    const int n_ord = (order_free && c->eval_nr >= 2) ? 2 : 1;
     if (!variant_needs_colors(v) || c->colored) {
-      for (int ib = 0; ib < n_cand; ++ib) {
+      for (int io = 0; io < n_cand * n_ord; ++io) {
+        const int ib = io / n_ord;
+        c->eval_ordered = n_ord == 2 ? (io % 2 == 0) : true;
         c->tuned_block = c->opt.block ? saved_tuned : cand_auto[ib];
         float ms = -1.0f;
         rc = eval_with(c, v, x, A, b, q, s);
@@ -1416,6 +1427,7 @@ int eec_autotune(eec_ctx* c, const double* x, double* A, double* b, double* q, i
           best = ms;
           best_v = v;
           best_b = c->tuned_block;
+          best_o = c->eval_ordered;
         }
       }
     }
@@ -1425,13 +1437,15 @@ int eec_autotune(eec_ctx* c, const double* x, double* A, double* b, double* q, i
   cudaEventDestroy(e1);
   c->tuned_variant = best_v;
   c->tuned_block = c->opt.block ? saved_tuned : best_b;
+  c->eval_ordered = best_o;
   return EEC_OK;
 }
 
-int eec_get_tuning(const eec_ctx* c, int32_t* variant, int32_t* block) {
+int eec_get_tuning(const eec_ctx* c, int32_t* variant, int32_t* block, int32_t* eval_order) {
   if (!c) return EEC_EINVAL;
   if (variant) *variant = effective_variant(c);
   if (block) *block = c->opt.block ? c->opt.block : c->tuned_block;
+  if (eval_order) *eval_order = (c->eval_nr >= 2 && c->eval_ordered) ? 1 : 0;
   return EEC_OK;
 }
 
