@@ -23,7 +23,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
-from typing import List, Optional
+from typing import List, Optional, Tuple
 
 import numpy as np
 
@@ -540,6 +540,32 @@ def concat(nets: List[Netlist], name: str = "batch") -> Netlist:
         res_G=np.concatenate(resG), isrc_nodes=np.concatenate(isn).astype(np.int32).reshape(-1, 2),
         isrc_val=np.concatenate(isv), gshunt=nets[0].gshunt if nets else 1e-12,
         meta=dict(node_off=node_off, n_circ=len(nets)))
+
+
+def partition_rows(net: Netlist, k: int) -> List[Tuple[Netlist, np.ndarray]]:
+    """Split the free nodes (in increasing order) into k contiguous blocks; part i keeps every
+    node, so the unknowns keep their numbering, and every device, resistor and current source
+    that touches one of its owned nodes. Each owned row of part i then receives all of its
+    contributions: the rows a rank owning that block would stamp, after a halo exchange of the
+    voltages of the other nodes its devices touch. Returns [(sub-netlist, owned node ids)]."""
+    free = net.free_nodes()
+    bounds = [len(free) * i // k for i in range(k + 1)]
+    parts = []
+    for i in range(k):
+        owned = free[bounds[i]:bounds[i + 1]]
+        mask = np.zeros(net.n_nodes, bool)
+        mask[owned] = True
+        d = mask[net.dev_nodes].any(axis=1)
+        r = mask[net.res_nodes].any(axis=1) if len(net.res_nodes) else np.zeros(0, bool)
+        c = mask[net.isrc_nodes].any(axis=1) if len(net.isrc_nodes) else np.zeros(0, bool)
+        sub = dataclasses.replace(
+            net, name=f"{net.name}_part{i}of{k}", dev_nodes=net.dev_nodes[d],
+            dev_type=net.dev_type[d], W=net.W[d], L=net.L[d], model_id=net.model_id[d],
+            res_nodes=net.res_nodes[r].reshape(-1, 2), res_G=net.res_G[r],
+            isrc_nodes=net.isrc_nodes[c].reshape(-1, 2), isrc_val=net.isrc_val[c],
+            meta=dict(net.meta, owned=owned))
+        parts.append((sub, owned))
+    return parts
 
 
 def random_x(net: Netlist, seed: int = DEFAULT_SEED, lo: float = 0.0, hi: float = 1.0,
