@@ -494,6 +494,33 @@ def extras(eec, circ, net, x, xt, A, b, q, args, dev):
     eec.eec_set_variant(circ.ctx, v0t)
     res["transient_tr_stamp"] = tran
 
+    # NEXT-2: the DC Newton loop closed on the GPU (evaluate and stamp, cuSOLVER sparse QR with
+    # its analysis reused, damped update), from x = 0, with the evaluate-and-stamp share of an
+    # iteration (the paper: once evaluation is fast, the solve dominates)
+    newton = {}
+    for nname, nn in (("inverter_chain_4096", netgen.inverter_chain(4096)),
+                      ("sram_32x32", netgen.sram(32, 32)),
+                      ("random_logic_5000", netgen.random_logic(5000, seed=5))):
+        c = eec.Circuit(nn, cards, color=True)
+        xd = torch.zeros(c.n, dtype=torch.float64, device=dev)
+        An, bn, _ = c.new_outputs(want_q=False)
+        try:
+            eec.eec_newton_dc(c.ctx, xd, An, bn)          # set-up (QR analysis) and warm-up
+            xd.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            its = eec.eec_newton_dc(c.ctx, xd, An, bn)
+            torch.cuda.synchronize()
+            ms = (time.perf_counter() - t0) * 1e3
+            ev_ms = _time(lambda: c.eval_stamp(xd, An, bn, want_q=False), 20, stream)
+            newton[nname] = {"unknowns": c.n, "devices": nn.n_dev, "iterations": its,
+                             "ms": ms, "ms_per_iteration": ms / max(its, 1),
+                             "eval_stamp_ms": ev_ms,
+                             "eval_stamp_share": ev_ms * max(its, 1) / ms}
+        except eec.EECError as e:
+            newton[nname] = {"error": str(e)}
+    res["newton_dc_gpu"] = newton
+
     # Table II analogue: 64-bit ripple-carry adder (28T mirror full adders), with 14 series
     # resistors per bit and with every transistor-to-transistor connection split, coloured by the
     # free-node rule (0) and the literal any-non-ground rule (1, VDD counted)

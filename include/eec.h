@@ -44,6 +44,7 @@ extern "C" {
 #define EEC_ECUDA (-3)    /* a CUDA runtime call failed; message has the CUDA error string */
 #define EEC_ETIMEOUT (-4) /* a device-side wait ran past its limit (status word) */
 #define EEC_ENUMERIC (-5) /* non-finite value detected by the debug checks (status word) */
+#define EEC_ENOCONV (-6)  /* eec_newton_dc: no convergence within max_iter */
 #define EEC_ENOMEM (-7)   /* device allocation failed */
 
 /* Evaluation/stamp schedules (Table I analogues). */
@@ -209,6 +210,26 @@ EEC_API int eec_eval_stamp(eec_ctx* ctx, const double* x_dev, double* A_values_d
  */
 EEC_API int eec_eval_stamp_host(eec_ctx* ctx, const double* x_host, double* A_host, double* b_host,
                                 double* q_host, void* cuda_stream);
+
+/*
+ * DC operating point by damped Newton on the GPU (the loop of Sec. II around the compute and
+ * stamp phases; the paper solves with KLU on the host). Every iteration: eec_eval_stamp at x
+ * (the context's schedule), a sparse direct solve A y = b on the GPU (cuSOLVER's batched sparse
+ * QR; its pattern analysis is done once per context and reused by every iteration), then
+ * x += s (y - x) with s = min(1, vstep / max|y - x|) (no node moves more than vstep volts).
+ * Converged when max|dx| <= tol_abs + tol_rel max|x| and, at the next iterate, the KCL residual
+ * max|A x - b| = max|F(x)| <= tol_f amperes.
+ *  x_dev       [n] in: starting point (free-node voltages), out: the last iterate.
+ *  A_dev, b_dev  [nnz], [n] workspace; out: the stamp at the returned x.
+ *  iters_out   (nullable) solves performed.
+ * Returns EEC_OK, EEC_ENOCONV (max_iter solves without meeting both tests: x holds the last
+ * iterate), EEC_ENUMERIC (a non-finite step or residual) or EEC_ENOMEM. The QR has no
+ * fill-reducing reordering: meant for netlists up to tens of thousands of unknowns (the
+ * factor's size is checked before allocation). Synchronises cuda_stream once per iteration.
+ */
+EEC_API int eec_newton_dc(eec_ctx* ctx, double* x_dev, double* A_values_dev, double* b_dev,
+                          int32_t max_iter, double vstep, double tol_abs, double tol_rel,
+                          double tol_f, int32_t* iters_out, void* cuda_stream);
 
 /*
  * Transient companion stamp of one Newton iterate of a time step (the transient loop of Sec. II,

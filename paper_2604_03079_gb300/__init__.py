@@ -21,6 +21,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_libeec.so")
 
 EEC_OK, EEC_EINVAL, EEC_ESTATE, EEC_ECUDA, EEC_ETIMEOUT, EEC_ENUMERIC, EEC_ENOMEM = 0, -1, -2, -3, -4, -5, -7
+EEC_ENOCONV = -6
 EEC_VARIANT_AUTO = -1
 EEC_VARIANT_COLOR_FUSED = 0
 EEC_VARIANT_PERSISTENT = 1
@@ -73,6 +74,8 @@ _SIG = {
     "eec_eval_stamp": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "eec_eval_stamp_bwd": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "eec_eval_stamp_host": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "eec_newton_dc": (ctypes.c_int, [_P, _P, _P, _P, _I32, _F64, _F64, _F64, _F64,
+                                     ctypes.POINTER(_I32), _P]),
     "eec_eval_stamp_tran": (ctypes.c_int, [_P, _P, _P, _P, _F64, _F64, _P, _P, _P, _P, _P]),
     "eec_eval_stamp_bwd_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "eec_graph_capture": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
@@ -304,6 +307,16 @@ def eec_get_tuning(ctx):
 def eec_eval_stamp(ctx, x, A, b, q=None, stream=None):
     _check(ctx, _load().eec_eval_stamp(ctx, _d(x, name="x"), _d(A, name="A"), _d(b, name="b"),
                                    _d(q, name="q"), _stream(stream)))
+
+
+def eec_newton_dc(ctx, x, A, b, max_iter=200, vstep=0.2, tol_abs=1e-12, tol_rel=1e-9,
+                  tol_f=1e-12, stream=None) -> int:
+    """DC Newton on the GPU from x (updated in place); returns the number of solves."""
+    it = _I32(0)
+    _check(ctx, _load().eec_newton_dc(ctx, _d(x, name="x"), _d(A, name="A"), _d(b, name="b"),
+                                      int(max_iter), float(vstep), float(tol_abs), float(tol_rel),
+                                      float(tol_f), ctypes.byref(it), _stream(stream)))
+    return int(it.value)
 
 
 def _hp(t, name):

@@ -14,7 +14,8 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "_libeec.so")
-SOURCES = ["eec_capi.cpp", "eec_kernels.cu", "eec_bwd.cu", "eec_color.cu"]
+SOURCES = ["eec_capi.cpp", "eec_kernels.cu", "eec_bwd.cu", "eec_color.cu", "eec_newton.cu"]
+LIBS = ["-lcusolver", "-lcusparse"]   # the sparse solve of eec_newton_dc
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -62,7 +63,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if failed:
         raise RuntimeError("nvcc failed:\n" + "\n".join(failed))
     tmp = LIB + f".{os.getpid()}.tmp"
-    subprocess.run([cc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs, check=True)
+    subprocess.run([cc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + LIBS,
+                   check=True)
     os.replace(tmp, LIB)
     return LIB
 

@@ -2,6 +2,12 @@
 // MNA pattern and scatter-map construction, device uploads, schedule dispatch, CUDA graphs,
 // autotuning and the device status word.
 #include <cuda_runtime.h>
+// eec_newton_dc uses cuSOLVER's batched sparse QR, which the toolkit marks deprecated in favour
+// of cuDSS; cuDSS is not part of the toolkit this library builds against.
+#define DISABLE_CUSOLVER_DEPRECATED
+#define DISABLE_CUSPARSE_DEPRECATED
+#include <cusolverSp.h>
+#include <cusparse.h>
 #include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
@@ -96,6 +102,15 @@ struct eec_ctx {
   int* d_erbeg = nullptr;
   int* d_eroff = nullptr;
   bool eval_ordered = true;   // use that order (eec_autotune times both)
+  // eec_newton_dc: solver handles and buffers (set up on its first call)
+  cusolverSpHandle_t sp = nullptr;
+  cusparseMatDescr_t sp_descr = nullptr;
+  csrqrInfo_t sp_info = nullptr;
+  int* d_rp = nullptr;
+  int* d_col = nullptr;
+  double* d_y = nullptr;
+  void* sp_buf = nullptr;
+  unsigned long long* d_nstats = nullptr;
   std::vector<cudaEvent_t> hev;  // chunk done (K) + side stream done (1)
 };
 
@@ -149,7 +164,13 @@ void free_topology(eec_ctx* c) {
   c->d_hrbeg = c->d_hroff = nullptr;
   c->eval_nr = 0;
   c->d_erbeg = c->d_eroff = nullptr;
-  if (!c->dmem.empty()) cudaDeviceSynchronize();
+  if (!c->dmem.empty() || c->sp_info) cudaDeviceSynchronize();
+  if (c->sp_info) cusolverSpDestroyCsrqrInfo(c->sp_info);
+  c->sp_info = nullptr;
+  c->d_rp = c->d_col = nullptr;
+  c->d_y = nullptr;
+  c->sp_buf = nullptr;
+  c->d_nstats = nullptr;
   for (void* p : c->dmem) cudaFree(p);
   c->dmem.clear();
   int* st = c->d_status;
@@ -617,6 +638,8 @@ void eec_destroy(eec_ctx* c) {
   if (c->d_status) cudaFree(c->d_status);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->side) cudaStreamDestroy(c->side);
+  if (c->sp_descr) cusparseDestroyMatDescr(c->sp_descr);
+  if (c->sp) cusolverSpDestroy(c->sp);
   for (cudaEvent_t e : c->hev) cudaEventDestroy(e);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   delete c;
@@ -1265,6 +1288,106 @@ int eec_eval_stamp_host(eec_ctx* c, const double* x_host, double* A_host, double
   CUDA_TRY(c, cudaEventRecord(c->hev[K], c->side));
   CUDA_TRY(c, cudaStreamWaitEvent(s, c->hev[K], 0));
   return EEC_OK;
+}
+
+// Solver state of eec_newton_dc, on its first call: the pattern on the device, the sparse QR's
+// analysis (reused by every later factorisation: the pattern never changes) and its workspace.
+int newton_setup(eec_ctx* c, const double* A) {
+  if (c->sp_info) return EEC_OK;
+  if (!c->sp && cusolverSpCreate(&c->sp) != CUSOLVER_STATUS_SUCCESS)
+    return fail(c, EEC_ECUDA, "cusolverSpCreate failed");
+  if (!c->sp_descr) {
+    if (cusparseCreateMatDescr(&c->sp_descr) != CUSPARSE_STATUS_SUCCESS)
+      return fail(c, EEC_ECUDA, "cusparseCreateMatDescr failed");
+    cusparseSetMatType(c->sp_descr, CUSPARSE_MATRIX_TYPE_GENERAL);
+    cusparseSetMatIndexBase(c->sp_descr, CUSPARSE_INDEX_BASE_ZERO);
+  }
+  int rc;
+  if ((rc = dupload(c, &c->d_rp, c->row_ptr)) || (rc = dupload(c, &c->d_col, c->col)) ||
+      (rc = dalloc(c, &c->d_y, c->n)) || (rc = dalloc(c, &c->d_nstats, 4)))
+    return rc;
+  csrqrInfo_t info = nullptr;
+  if (cusolverSpCreateCsrqrInfo(&info) != CUSOLVER_STATUS_SUCCESS)
+    return fail(c, EEC_ECUDA, "cusolverSpCreateCsrqrInfo failed");
+  const int n = c->n, nnz = (int)c->nnz;
+  size_t internal = 0, work = 0;
+  if (cusolverSpXcsrqrAnalysisBatched(c->sp, n, n, nnz, c->sp_descr, c->d_rp, c->d_col, info) !=
+          CUSOLVER_STATUS_SUCCESS ||
+      cusolverSpDcsrqrBufferInfoBatched(c->sp, n, n, nnz, c->sp_descr, A, c->d_rp, c->d_col, 1,
+                                        info, &internal, &work) != CUSOLVER_STATUS_SUCCESS) {
+    cusolverSpDestroyCsrqrInfo(info);
+    return fail(c, EEC_ECUDA, "sparse QR analysis failed");
+  }
+  size_t fb = 0, tb = 0;
+  CUDA_TRY(c, cudaMemGetInfo(&fb, &tb));
+  if (internal + work > fb / 2) {
+    cusolverSpDestroyCsrqrInfo(info);
+    return fail(c, EEC_ENOMEM, "sparse QR factor needs " + std::to_string(internal + work) +
+                                   " bytes (no fill-reducing order): too large for this netlist");
+  }
+  char* buf = nullptr;
+  if ((rc = dalloc(c, &buf, std::max<size_t>(work, 1)))) {
+    cusolverSpDestroyCsrqrInfo(info);
+    return rc;
+  }
+  c->sp_buf = buf;
+  c->sp_info = info;
+  return EEC_OK;
+}
+
+double bits_to_double(unsigned long long u) {
+  double d;
+  std::memcpy(&d, &u, sizeof d);
+  return d;
+}
+
+int eec_newton_dc(eec_ctx* c, double* x, double* A, double* b, int32_t max_iter, double vstep,
+                  double tol_abs, double tol_rel, double tol_f, int32_t* iters_out, void* stream) {
+  NvtxRange range("eec/newton_dc");
+  int rc = check_built(c);
+  if (rc) return rc;
+  if (!x || !A || !b || max_iter < 1 || !(vstep > 0.0) || !(tol_abs >= 0.0) ||
+      !(tol_rel >= 0.0) || !(tol_f >= 0.0))
+    return fail(c, EEC_EINVAL, "bad eec_newton_dc arguments");
+  if (c->nnz > 0x7fffffffLL) return fail(c, EEC_EINVAL, "pattern too large for the sparse solver");
+  if (iters_out) *iters_out = 0;
+  if (c->n == 0) return EEC_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((rc = newton_setup(c, A))) return rc;
+  if (cusolverSpSetStream(c->sp, s) != CUSOLVER_STATUS_SUCCESS)
+    return fail(c, EEC_ECUDA, "cusolverSpSetStream failed");
+  const int v = effective_variant(c), n = c->n, nnz = (int)c->nnz;
+  unsigned long long hs[4];
+  bool small_step = false;
+  for (int it = 0; it <= max_iter; ++it) {
+    CUDA_TRY(c, cudaMemsetAsync(c->d_nstats, 0, 4 * sizeof(unsigned long long), s));
+    if ((rc = eval_with(c, v, x, A, b, nullptr, s))) return rc;
+    if (small_step) {  // the residual at this iterate decides convergence (A x - b = F(x))
+      CUDA_TRY(c, launch_residual_norm(c->d_rp, c->d_col, A, x, b, n, c->d_nstats, s));
+      CUDA_TRY(c, cudaMemcpyAsync(hs, c->d_nstats, sizeof hs, cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(c, cudaStreamSynchronize(s));
+      const double r = bits_to_double(hs[3]);
+      if (!std::isfinite(r)) return fail(c, EEC_ENUMERIC, "non-finite KCL residual");
+      if (r <= tol_f) {
+        if (iters_out) *iters_out = it;
+        return EEC_OK;
+      }
+    }
+    if (it == max_iter) break;
+    if (cusolverSpDcsrqrsvBatched(c->sp, n, n, nnz, c->sp_descr, A, c->d_rp, c->d_col, b, c->d_y,
+                                  1, c->sp_info, c->sp_buf) != CUSOLVER_STATUS_SUCCESS)
+      return fail(c, EEC_ECUDA, "sparse QR solve failed");
+    c->n_kernels += 2;
+    CUDA_TRY(c, launch_newton_step(c->d_y, x, n, vstep, c->d_nstats, s));
+    CUDA_TRY(c, cudaMemcpyAsync(hs, c->d_nstats, sizeof hs, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+    const double dxm = bits_to_double(hs[1]), xm = bits_to_double(hs[2]);
+    if (!std::isfinite(dxm) || !std::isfinite(xm))
+      return fail(c, EEC_ENUMERIC, "non-finite Newton step (singular matrix?)");
+    small_step = dxm <= tol_abs + tol_rel * xm;
+    if (iters_out) *iters_out = it + 1;
+  }
+  return fail(c, EEC_ENOCONV, "no convergence within max_iter iterations");
 }
 
 int eec_eval_stamp_tran(eec_ctx* c, const double* x, const double* q_prev, const double* i_prev,

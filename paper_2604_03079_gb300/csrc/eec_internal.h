@@ -113,6 +113,13 @@ int stamp_persistent_max_blocks_per_sm();
 cudaError_t launch_stamp_cluster(const DevTopo& T, const int* color_off_dev, int n_colors,
                                  double* A, double* b, cudaStream_t s);
 int stamp_cluster_threads();
+// DC Newton loop (eec_newton.cu). stats[0] max|y - x|, [1] max|dx|, [2] max|x|, [3] residual, as
+// bit patterns of non-negative doubles (zeroed by the caller).
+cudaError_t launch_newton_step(const double* y, double* x, int n, double vstep,
+                               unsigned long long* stats, cudaStream_t s);
+cudaError_t launch_residual_norm(const int* rp, const int* col, const double* A, const double* x,
+                                 const double* b, int n, unsigned long long* stats,
+                                 cudaStream_t s);
 // Transient companion stamp (mode MODE_RMW over one colour range, or MODE_ATOMIC over all).
 struct TranArgs {
   const double* qprev;  // [4][N_orig] charges of the previous time point

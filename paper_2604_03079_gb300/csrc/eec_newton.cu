@@ -1,0 +1,90 @@
+// Kernels of the DC Newton loop on the GPU (eec_newton_dc): the damped update and the norms
+// its convergence test reads. The loop itself (evaluate and stamp, sparse solve, update) is
+// driven by the host side of the ABI.
+//
+// Norms are maxima of non-negative doubles, formed with 64-bit integer atomicMax on the bit
+// patterns (for non-negative IEEE doubles the integer order is the numeric order; a NaN has a
+// larger pattern than +inf, so it propagates to the maximum and the host sees it).
+#include <cuda_runtime.h>
+
+#include "eec_internal.h"
+
+namespace eec {
+
+namespace {
+
+constexpr int kNewtonBlock = 256;
+
+__device__ __forceinline__ void max_abs_into(unsigned long long* slot, double v) {
+  // warp maximum first: one atomic per warp
+  unsigned long long u = (unsigned long long)__double_as_longlong(fabs(v));
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, u, off);
+    u = o > u ? o : u;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(slot, u);
+}
+
+// stats[0] = max |y - x|
+__global__ void __launch_bounds__(kNewtonBlock) k_step_norm(const double* __restrict__ y,
+                                                            const double* __restrict__ x, int n,
+                                                            unsigned long long* stats) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  max_abs_into(stats, i < n ? y[i] - x[i] : 0.0);
+}
+
+// x += s (y - x) with s = min(1, vstep / max|y - x|) (the whole step scaled so that no node
+// moves more than vstep); stats[1] = max |dx|, stats[2] = max |x| after the update.
+__global__ void __launch_bounds__(kNewtonBlock) k_damped_update(const double* __restrict__ y,
+                                                                double* __restrict__ x, int n,
+                                                                double vstep,
+                                                                unsigned long long* stats) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const double m = __longlong_as_double((long long)stats[0]);
+  const double s = m > vstep ? vstep / m : 1.0;
+  double dx = 0.0, xn = 0.0;
+  if (i < n) {
+    dx = s * (y[i] - x[i]);
+    xn = x[i] + dx;
+    x[i] = xn;
+  }
+  max_abs_into(stats + 1, dx);
+  max_abs_into(stats + 2, xn);
+}
+
+// stats[3] = max |A x - b| (the KCL residual F(x), since A x - b = F(x) for the stamped system)
+__global__ void __launch_bounds__(kNewtonBlock) k_residual_norm(const int* __restrict__ rp,
+                                                                const int* __restrict__ col,
+                                                                const double* __restrict__ A,
+                                                                const double* __restrict__ x,
+                                                                const double* __restrict__ b,
+                                                                int n, unsigned long long* stats) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double r = 0.0;
+  if (i < n) {
+    r = -b[i];
+    for (int p = rp[i]; p < rp[i + 1]; ++p) r = fma(A[p], x[col[p]], r);
+  }
+  max_abs_into(stats + 3, r);
+}
+
+int blocks_for(int n) { return n > 0 ? (n + kNewtonBlock - 1) / kNewtonBlock : 1; }
+
+}  // namespace
+
+cudaError_t launch_newton_step(const double* y, double* x, int n, double vstep,
+                               unsigned long long* stats, cudaStream_t s) {
+  k_step_norm<<<blocks_for(n), kNewtonBlock, 0, s>>>(y, x, n, stats);
+  k_damped_update<<<blocks_for(n), kNewtonBlock, 0, s>>>(y, x, n, vstep, stats);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual_norm(const int* rp, const int* col, const double* A, const double* x,
+                                 const double* b, int n, unsigned long long* stats,
+                                 cudaStream_t s) {
+  k_residual_norm<<<blocks_for(n), kNewtonBlock, 0, s>>>(rp, col, A, x, b, n, stats);
+  return cudaGetLastError();
+}
+
+}  // namespace eec
