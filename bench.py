@@ -61,6 +61,8 @@ def parse():
                     help="timed steps only (no autotune, e2e, extras, probes, baseline): for ncu")
     ap.add_argument("--bwd-steps", type=int, default=0,
                     help="with --quick: also run the backward this many times (for ncu)")
+    ap.add_argument("--newton", action="store_true",
+                    help="only run the GPU Newton-loop study (NEXT-2) and print it as JSON")
     ap.add_argument("--tran-steps", type=int, default=0,
                     help="with --quick: also run the trapezoidal transient stamp this many times "
                          "(for ncu)")
@@ -414,6 +416,46 @@ def hbm_peak_gbs():
         return 6800.0, "fallback (6.8 TB/s, one earlier GB300 copy measurement)"
 
 
+def newton_study(eec, dev, stream):
+    """NEXT-2: the DC Newton loop closed on the GPU (evaluate and stamp, cuSOLVER sparse QR with
+    its analysis reused, damped update) from x = 0, per netlist: iterations, time per iteration
+    and the evaluate-and-stamp share of it (the paper: once evaluation is fast, the solve
+    dominates). Banded netlists only: the QR has no fill-reducing order. Bounded: at most 300
+    iterations per netlist and about a minute in all."""
+    import torch
+    import netgen
+    out = {}
+    t_start = time.perf_counter()
+    for nname, nn in (("inverter_chain_4096", netgen.inverter_chain(4096)),
+                      ("ripple_adder_64", netgen.ripple_adder(64))):
+        if time.perf_counter() - t_start > 60:
+            out[nname] = {"skipped": "time budget of the study used up"}
+            continue
+        c = eec.Circuit(nn, netgen.default_cards(), color=True)
+        xd = torch.zeros(c.n, dtype=torch.float64, device=dev)
+        An, bn, _ = c.new_outputs(want_q=False)
+        try:
+            eec.eec_newton_dc(c.ctx, xd, An, bn, max_iter=1, step_rule=1)   # QR analysis
+        except eec.EECError:
+            pass
+        xd.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        try:
+            its = eec.eec_newton_dc(c.ctx, xd, An, bn, max_iter=300, step_rule=1)
+        except eec.EECError as e:
+            out[nname] = {"error": str(e), "s": time.perf_counter() - t0}
+            continue
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3
+        ev_ms = _time(lambda: c.eval_stamp(xd, An, bn, want_q=False), 20, stream)
+        out[nname] = {"unknowns": c.n, "devices": nn.n_dev, "iterations": its,
+                      "step_rule": "per-node clip to 0.2 V", "ms": ms,
+                      "ms_per_iteration": ms / max(its, 1), "eval_stamp_ms": ev_ms,
+                      "eval_stamp_share": ev_ms * max(its, 1) / ms}
+    return out
+
+
 def _time(fn, reps, stream):
     import torch
     for _ in range(2):
@@ -494,32 +536,6 @@ def extras(eec, circ, net, x, xt, A, b, q, args, dev):
     eec.eec_set_variant(circ.ctx, v0t)
     res["transient_tr_stamp"] = tran
 
-    # NEXT-2: the DC Newton loop closed on the GPU (evaluate and stamp, cuSOLVER sparse QR with
-    # its analysis reused, damped update), from x = 0, with the evaluate-and-stamp share of an
-    # iteration (the paper: once evaluation is fast, the solve dominates)
-    newton = {}
-    for nname, nn in (("inverter_chain_4096", netgen.inverter_chain(4096)),
-                      ("sram_32x32", netgen.sram(32, 32)),
-                      ("random_logic_5000", netgen.random_logic(5000, seed=5))):
-        c = eec.Circuit(nn, cards, color=True)
-        xd = torch.zeros(c.n, dtype=torch.float64, device=dev)
-        An, bn, _ = c.new_outputs(want_q=False)
-        try:
-            eec.eec_newton_dc(c.ctx, xd, An, bn)          # set-up (QR analysis) and warm-up
-            xd.zero_()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            its = eec.eec_newton_dc(c.ctx, xd, An, bn)
-            torch.cuda.synchronize()
-            ms = (time.perf_counter() - t0) * 1e3
-            ev_ms = _time(lambda: c.eval_stamp(xd, An, bn, want_q=False), 20, stream)
-            newton[nname] = {"unknowns": c.n, "devices": nn.n_dev, "iterations": its,
-                             "ms": ms, "ms_per_iteration": ms / max(its, 1),
-                             "eval_stamp_ms": ev_ms,
-                             "eval_stamp_share": ev_ms * max(its, 1) / ms}
-        except eec.EECError as e:
-            newton[nname] = {"error": str(e)}
-    res["newton_dc_gpu"] = newton
 
     # Table II analogue: 64-bit ripple-carry adder (28T mirror full adders), with 14 series
     # resistors per bit and with every transistor-to-transistor connection split, coloured by the
@@ -579,6 +595,12 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.newton:
+        import torch
+        import paper_2604_03079_gb300 as eec
+        dev = torch.device("cuda", torch.cuda.current_device())
+        print(json.dumps({"newton_dc_gpu": newton_study(eec, dev, torch.cuda.current_stream())}))
+        return 0
     return run_ours(args)
 
 

@@ -216,7 +216,9 @@ EEC_API int eec_eval_stamp_host(eec_ctx* ctx, const double* x_host, double* A_ho
  * stamp phases; the paper solves with KLU on the host). Every iteration: eec_eval_stamp at x
  * (the context's schedule), a sparse direct solve A y = b on the GPU (cuSOLVER's batched sparse
  * QR; its pattern analysis is done once per context and reused by every iteration), then
- * x += s (y - x) with s = min(1, vstep / max|y - x|) (no node moves more than vstep volts).
+ * a damped step: step_rule 0 scales the whole step, x += s (y - x) with s = min(1, vstep /
+ * max|y - x|); step_rule 1 clips every node's move to [-vstep, vstep] on its own (long chains of
+ * gates converge in far fewer iterations).
  * Converged when max|dx| <= tol_abs + tol_rel max|x| and, at the next iterate, the KCL residual
  * max|A x - b| = max|F(x)| <= tol_f amperes.
  *  x_dev       [n] in: starting point (free-node voltages), out: the last iterate.
@@ -228,8 +230,8 @@ EEC_API int eec_eval_stamp_host(eec_ctx* ctx, const double* x_host, double* A_ho
  * factor's size is checked before allocation). Synchronises cuda_stream once per iteration.
  */
 EEC_API int eec_newton_dc(eec_ctx* ctx, double* x_dev, double* A_values_dev, double* b_dev,
-                          int32_t max_iter, double vstep, double tol_abs, double tol_rel,
-                          double tol_f, int32_t* iters_out, void* cuda_stream);
+                          int32_t max_iter, double vstep, int32_t step_rule, double tol_abs,
+                          double tol_rel, double tol_f, int32_t* iters_out, void* cuda_stream);
 
 /*
  * Transient companion stamp of one Newton iterate of a time step (the transient loop of Sec. II,

@@ -1342,11 +1342,13 @@ double bits_to_double(unsigned long long u) {
 }
 
 int eec_newton_dc(eec_ctx* c, double* x, double* A, double* b, int32_t max_iter, double vstep,
-                  double tol_abs, double tol_rel, double tol_f, int32_t* iters_out, void* stream) {
+                  int32_t step_rule, double tol_abs, double tol_rel, double tol_f,
+                  int32_t* iters_out, void* stream) {
   NvtxRange range("eec/newton_dc");
   int rc = check_built(c);
   if (rc) return rc;
-  if (!x || !A || !b || max_iter < 1 || !(vstep > 0.0) || !(tol_abs >= 0.0) ||
+  if (!x || !A || !b || max_iter < 1 || !(vstep > 0.0) || step_rule < 0 || step_rule > 1 ||
+      !(tol_abs >= 0.0) ||
       !(tol_rel >= 0.0) || !(tol_f >= 0.0))
     return fail(c, EEC_EINVAL, "bad eec_newton_dc arguments");
   if (c->nnz > 0x7fffffffLL) return fail(c, EEC_EINVAL, "pattern too large for the sparse solver");
@@ -1378,7 +1380,7 @@ int eec_newton_dc(eec_ctx* c, double* x, double* A, double* b, int32_t max_iter,
                                   1, c->sp_info, c->sp_buf) != CUSOLVER_STATUS_SUCCESS)
       return fail(c, EEC_ECUDA, "sparse QR solve failed");
     c->n_kernels += 2;
-    CUDA_TRY(c, launch_newton_step(c->d_y, x, n, vstep, c->d_nstats, s));
+    CUDA_TRY(c, launch_newton_step(c->d_y, x, n, vstep, step_rule, c->d_nstats, s));
     CUDA_TRY(c, cudaMemcpyAsync(hs, c->d_nstats, sizeof hs, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(c, cudaStreamSynchronize(s));
     const double dxm = bits_to_double(hs[1]), xm = bits_to_double(hs[2]);

@@ -115,7 +115,7 @@ cudaError_t launch_stamp_cluster(const DevTopo& T, const int* color_off_dev, int
 int stamp_cluster_threads();
 // DC Newton loop (eec_newton.cu). stats[0] max|y - x|, [1] max|dx|, [2] max|x|, [3] residual, as
 // bit patterns of non-negative doubles (zeroed by the caller).
-cudaError_t launch_newton_step(const double* y, double* x, int n, double vstep,
+cudaError_t launch_newton_step(const double* y, double* x, int n, double vstep, int per_node,
                                unsigned long long* stats, cudaStream_t s);
 cudaError_t launch_residual_norm(const int* rp, const int* col, const double* A, const double* x,
                                  const double* b, int n, unsigned long long* stats,

@@ -34,18 +34,21 @@ __global__ void __launch_bounds__(kNewtonBlock) k_step_norm(const double* __rest
   max_abs_into(stats, i < n ? y[i] - x[i] : 0.0);
 }
 
-// x += s (y - x) with s = min(1, vstep / max|y - x|) (the whole step scaled so that no node
-// moves more than vstep); stats[1] = max |dx|, stats[2] = max |x| after the update.
+// The damped step: per_node = 0, x += s (y - x) with s = min(1, vstep / max|y - x|) (the whole
+// step scaled so that no node moves more than vstep); per_node = 1, every node's move clipped to
+// [-vstep, vstep] on its own. stats[1] = max |dx|, stats[2] = max |x| after the update.
 __global__ void __launch_bounds__(kNewtonBlock) k_damped_update(const double* __restrict__ y,
                                                                 double* __restrict__ x, int n,
-                                                                double vstep,
+                                                                double vstep, int per_node,
                                                                 unsigned long long* stats) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const double m = __longlong_as_double((long long)stats[0]);
   const double s = m > vstep ? vstep / m : 1.0;
   double dx = 0.0, xn = 0.0;
   if (i < n) {
-    dx = s * (y[i] - x[i]);
+    const double d = y[i] - x[i];
+    // comparisons, not fmin/fmax: a NaN step stays NaN and the host sees it
+    dx = per_node ? (d > vstep ? vstep : (d < -vstep ? -vstep : d)) : s * d;
     xn = x[i] + dx;
     x[i] = xn;
   }
@@ -73,10 +76,10 @@ int blocks_for(int n) { return n > 0 ? (n + kNewtonBlock - 1) / kNewtonBlock : 1
 
 }  // namespace
 
-cudaError_t launch_newton_step(const double* y, double* x, int n, double vstep,
+cudaError_t launch_newton_step(const double* y, double* x, int n, double vstep, int per_node,
                                unsigned long long* stats, cudaStream_t s) {
   k_step_norm<<<blocks_for(n), kNewtonBlock, 0, s>>>(y, x, n, stats);
-  k_damped_update<<<blocks_for(n), kNewtonBlock, 0, s>>>(y, x, n, vstep, stats);
+  k_damped_update<<<blocks_for(n), kNewtonBlock, 0, s>>>(y, x, n, vstep, per_node, stats);
   return cudaGetLastError();
 }
 
