@@ -426,8 +426,11 @@ def newton_study(eec, dev, stream):
     import netgen
     out = {}
     t_start = time.perf_counter()
-    for nname, nn in (("inverter_chain_4096", netgen.inverter_chain(4096)),
-                      ("ripple_adder_64", netgen.ripple_adder(64))):
+    for nname, nn, solver in (("ripple_adder_64", netgen.ripple_adder(64), 0),
+                              ("ripple_adder_64", netgen.ripple_adder(64), 1),
+                              ("inverter_chain_1024", netgen.inverter_chain(1024), 1),
+                              ("inverter_chain_4096", netgen.inverter_chain(4096), 1)):
+        nname = f"{nname}_solver{solver}"
         if time.perf_counter() - t_start > 60:
             out[nname] = {"skipped": "time budget of the study used up"}
             continue
@@ -435,14 +438,15 @@ def newton_study(eec, dev, stream):
         xd = torch.zeros(c.n, dtype=torch.float64, device=dev)
         An, bn, _ = c.new_outputs(want_q=False)
         try:
-            eec.eec_newton_dc(c.ctx, xd, An, bn, max_iter=1, step_rule=1)   # QR analysis
+            eec.eec_newton_dc(c.ctx, xd, An, bn, max_iter=1, step_rule=1, solver=solver)
         except eec.EECError:
             pass
         xd.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         try:
-            its = eec.eec_newton_dc(c.ctx, xd, An, bn, max_iter=300, step_rule=1)
+            its = eec.eec_newton_dc(c.ctx, xd, An, bn, max_iter=300, step_rule=1,
+                                    solver=solver)
         except eec.EECError as e:
             out[nname] = {"error": str(e), "s": time.perf_counter() - t0}
             continue
@@ -450,7 +454,9 @@ def newton_study(eec, dev, stream):
         ms = (time.perf_counter() - t0) * 1e3
         ev_ms = _time(lambda: c.eval_stamp(xd, An, bn, want_q=False), 20, stream)
         out[nname] = {"unknowns": c.n, "devices": nn.n_dev, "iterations": its,
-                      "step_rule": "per-node clip to 0.2 V", "ms": ms,
+                      "step_rule": "per-node clip to 0.2 V",
+                      "solver": ("batched sparse QR, analysis reused" if solver == 0 else
+                                 "sparse QR after symmetric AMD ordering"), "ms": ms,
                       "ms_per_iteration": ms / max(its, 1), "eval_stamp_ms": ev_ms,
                       "eval_stamp_share": ev_ms * max(its, 1) / ms}
     return out

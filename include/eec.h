@@ -214,8 +214,10 @@ EEC_API int eec_eval_stamp_host(eec_ctx* ctx, const double* x_host, double* A_ho
 /*
  * DC operating point by damped Newton on the GPU (the loop of Sec. II around the compute and
  * stamp phases; the paper solves with KLU on the host). Every iteration: eec_eval_stamp at x
- * (the context's schedule), a sparse direct solve A y = b on the GPU (cuSOLVER's batched sparse
- * QR; its pattern analysis is done once per context and reused by every iteration), then
+ * (the context's schedule), a sparse direct solve A y = b on the GPU with cuSOLVER — solver 0:
+ * batched sparse QR, its pattern analysis done once per context and reused by every iteration,
+ * no fill-reducing order; solver 1: sparse QR after a symmetric approximate-minimum-degree
+ * ordering, analysed on every call (less fill on irregular netlists) — then
  * a damped step: step_rule 0 scales the whole step, x += s (y - x) with s = min(1, vstep /
  * max|y - x|); step_rule 1 clips every node's move to [-vstep, vstep] on its own (long chains of
  * gates converge in far fewer iterations).
@@ -225,13 +227,14 @@ EEC_API int eec_eval_stamp_host(eec_ctx* ctx, const double* x_host, double* A_ho
  *  A_dev, b_dev  [nnz], [n] workspace; out: the stamp at the returned x.
  *  iters_out   (nullable) solves performed.
  * Returns EEC_OK, EEC_ENOCONV (max_iter solves without meeting both tests: x holds the last
- * iterate), EEC_ENUMERIC (a non-finite step or residual) or EEC_ENOMEM. The QR has no
- * fill-reducing reordering: meant for netlists up to tens of thousands of unknowns (the
- * factor's size is checked before allocation). Synchronises cuda_stream once per iteration.
+ * iterate), EEC_ENUMERIC (a non-finite step or residual, or a singular matrix) or
+ * EEC_ENOMEM. Meant for netlists up to tens of thousands of unknowns (solver 0 checks its
+ * factor's size before allocating). Synchronises cuda_stream once per iteration.
  */
 EEC_API int eec_newton_dc(eec_ctx* ctx, double* x_dev, double* A_values_dev, double* b_dev,
-                          int32_t max_iter, double vstep, int32_t step_rule, double tol_abs,
-                          double tol_rel, double tol_f, int32_t* iters_out, void* cuda_stream);
+                          int32_t max_iter, double vstep, int32_t step_rule, int32_t solver,
+                          double tol_abs, double tol_rel, double tol_f, int32_t* iters_out,
+                          void* cuda_stream);
 
 /*
  * Transient companion stamp of one Newton iterate of a time step (the transient loop of Sec. II,

@@ -74,7 +74,7 @@ _SIG = {
     "eec_eval_stamp": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "eec_eval_stamp_bwd": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "eec_eval_stamp_host": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
-    "eec_newton_dc": (ctypes.c_int, [_P, _P, _P, _P, _I32, _F64, _I32, _F64, _F64, _F64,
+    "eec_newton_dc": (ctypes.c_int, [_P, _P, _P, _P, _I32, _F64, _I32, _I32, _F64, _F64, _F64,
                                      ctypes.POINTER(_I32), _P]),
     "eec_eval_stamp_tran": (ctypes.c_int, [_P, _P, _P, _P, _F64, _F64, _P, _P, _P, _P, _P]),
     "eec_eval_stamp_bwd_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
@@ -309,13 +309,14 @@ def eec_eval_stamp(ctx, x, A, b, q=None, stream=None):
                                    _d(q, name="q"), _stream(stream)))
 
 
-def eec_newton_dc(ctx, x, A, b, max_iter=200, vstep=0.2, step_rule=0, tol_abs=1e-12,
+def eec_newton_dc(ctx, x, A, b, max_iter=200, vstep=0.2, step_rule=0, solver=0, tol_abs=1e-12,
                   tol_rel=1e-9, tol_f=1e-12, stream=None) -> int:
     """DC Newton on the GPU from x (updated in place); returns the number of solves.
-    step_rule 0: the whole step scaled to vstep; 1: every node's move clipped to vstep."""
+    step_rule 0: the whole step scaled to vstep; 1: every node's move clipped to vstep.
+    solver 0: batched sparse QR, analysis reused; 1: sparse QR after an AMD ordering."""
     it = _I32(0)
     _check(ctx, _load().eec_newton_dc(ctx, _d(x, name="x"), _d(A, name="A"), _d(b, name="b"),
-                                      int(max_iter), float(vstep), int(step_rule),
+                                      int(max_iter), float(vstep), int(step_rule), int(solver),
                                       float(tol_abs), float(tol_rel), float(tol_f),
                                       ctypes.byref(it), _stream(stream)))
     return int(it.value)

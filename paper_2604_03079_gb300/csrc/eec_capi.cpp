@@ -1342,12 +1342,13 @@ double bits_to_double(unsigned long long u) {
 }
 
 int eec_newton_dc(eec_ctx* c, double* x, double* A, double* b, int32_t max_iter, double vstep,
-                  int32_t step_rule, double tol_abs, double tol_rel, double tol_f,
-                  int32_t* iters_out, void* stream) {
+                  int32_t step_rule, int32_t solver, double tol_abs, double tol_rel,
+                  double tol_f, int32_t* iters_out, void* stream) {
   NvtxRange range("eec/newton_dc");
   int rc = check_built(c);
   if (rc) return rc;
   if (!x || !A || !b || max_iter < 1 || !(vstep > 0.0) || step_rule < 0 || step_rule > 1 ||
+      solver < 0 || solver > 1 ||
       !(tol_abs >= 0.0) ||
       !(tol_rel >= 0.0) || !(tol_f >= 0.0))
     return fail(c, EEC_EINVAL, "bad eec_newton_dc arguments");
@@ -1376,9 +1377,18 @@ int eec_newton_dc(eec_ctx* c, double* x, double* A, double* b, int32_t max_iter,
       }
     }
     if (it == max_iter) break;
-    if (cusolverSpDcsrqrsvBatched(c->sp, n, n, nnz, c->sp_descr, A, c->d_rp, c->d_col, b, c->d_y,
-                                  1, c->sp_info, c->sp_buf) != CUSOLVER_STATUS_SUCCESS)
-      return fail(c, EEC_ECUDA, "sparse QR solve failed");
+    if (solver == 0) {
+      if (cusolverSpDcsrqrsvBatched(c->sp, n, n, nnz, c->sp_descr, A, c->d_rp, c->d_col, b,
+                                    c->d_y, 1, c->sp_info, c->sp_buf) != CUSOLVER_STATUS_SUCCESS)
+        return fail(c, EEC_ECUDA, "sparse QR solve failed");
+    } else {
+      int singular = -1;
+      if (cusolverSpDcsrlsvqr(c->sp, n, nnz, c->sp_descr, A, c->d_rp, c->d_col, b, 0.0, 2,
+                              c->d_y, &singular) != CUSOLVER_STATUS_SUCCESS)
+        return fail(c, EEC_ECUDA, "sparse QR solve failed");
+      if (singular >= 0)
+        return fail(c, EEC_ENUMERIC, "singular matrix (row " + std::to_string(singular) + ")");
+    }
     c->n_kernels += 2;
     CUDA_TRY(c, launch_newton_step(c->d_y, x, n, vstep, step_rule, c->d_nstats, s));
     CUDA_TRY(c, cudaMemcpyAsync(hs, c->d_nstats, sizeof hs, cudaMemcpyDeviceToHost, s));

@@ -26,15 +26,15 @@ CASES = [lambda: netgen.inverter_chain(64), lambda: netgen.inverter_chain(64, vi
 
 
 @pytest.mark.parametrize("make", CASES)
-@pytest.mark.parametrize("variant,rule", [(2, 0), (0, 0), (2, 1)])
-def test_gpu_newton_reaches_the_oracle_operating_point(eec, make, variant, rule):
+@pytest.mark.parametrize("variant,rule,solver", [(2, 0, 0), (0, 0, 0), (2, 1, 0), (2, 0, 1)])
+def test_gpu_newton_reaches_the_oracle_operating_point(eec, make, variant, rule, solver):
     import torch
     net = make()
     ref, _ = oracle.Oracle(net, CARDS).dc_solve()
     circ = eec.Circuit(net, CARDS, variant=variant)
     x = torch.zeros(circ.n, dtype=torch.float64, device="cuda")
     A, b, _ = circ.new_outputs(want_q=False)
-    it = eec.eec_newton_dc(circ.ctx, x, A, b, step_rule=rule)
+    it = eec.eec_newton_dc(circ.ctx, x, A, b, step_rule=rule, solver=solver)
     assert 1 <= it <= 200
     assert circ.status() == 0
     np.testing.assert_allclose(x.cpu().numpy(), ref, rtol=1e-8, atol=1e-10)
