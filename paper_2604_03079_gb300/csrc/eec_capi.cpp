@@ -1056,10 +1056,10 @@ int eec_build_scatter(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_out) {
   for (int k = 0; k < c->C; ++k) maxcol = std::max(maxcol, c->color_off[k + 1] - c->color_off[k]);
   const int sbps = stamp_persistent_max_blocks_per_sm();
   c->stamp_grid = sbps > 0 ? std::max(1, std::min(sbps * c->sms, (maxcol + 255) / 256)) : 0;
-  // Colour-buffered stamp: pick the cheapest of per-colour launches (about 8 us per colour on
-  // GB300), one grid with a grid barrier (about 7 us per barrier) and one 8-block cluster with
-  // the hardware cluster barrier (about one 2 us round of read-modify-writes per 8,192 devices
-  // of a colour), from the colour sizes.
+  // Colour-buffered stamp: pick the cheapest of per-colour launches (about 4-8 us per colour on
+  // GB300), one grid with a grid barrier (3-9 us per colour) and one 8-block cluster with the
+  // hardware cluster barrier (1-2 us per colour, plus a round per 4,096 devices of a colour),
+  // from the colour sizes; the constants below are conservative for the cluster.
   {
     const double nt = (double)stamp_cluster_threads();
     double t_launch = 0.0, t_grid = 0.0, t_cluster = 0.0;

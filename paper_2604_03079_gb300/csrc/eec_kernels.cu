@@ -366,8 +366,10 @@ __global__ void __launch_bounds__(kGatherBlock) k_gather(DevTopo T, double* A, d
 }
 
 // One colour's stamp from the buffer (positions begin..end-1 share no row).
-// Add device k's buffered contributions to A and b (store-add: callers guarantee that no other
-// thread touches the same entries meanwhile — one colour at a time).
+// Add device k's buffered contributions to A and b. Callers stamp one colour at a time, so no
+// other thread adds to the same entries meanwhile; the additions are fire-and-forget atomics
+// performed in L2 (no load of A into the SM), which give the same sums in the same order as a
+// read-modify-write.
 __device__ __forceinline__ void stamp_buffered(const DevTopo& T, int k, double* A, double* b) {
   const long long N = T.N;
   const int4 ti = __ldg(T.tidx + k);
@@ -378,9 +380,9 @@ __device__ __forceinline__ void stamp_buffered(const DevTopo& T, int k, double* 
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int s = __ldg(T.slot + (4 * r + u) * N + k);
-      if (s >= 0) A[s] += __ldg(T.buf + (4 * r + u) * N + k);
+      if (s >= 0) atomicAdd(A + s, __ldg(T.buf + (4 * r + u) * N + k));
     }
-    b[rows[r]] += __ldg(T.buf + (kNSlot + r) * N + k);
+    atomicAdd(b + rows[r], __ldg(T.buf + (kNSlot + r) * N + k));
   }
 }
 
@@ -396,8 +398,7 @@ __global__ void __launch_bounds__(kEvalBlock) k_stamp_buffer(DevTopo T, int begi
 // barrier between colours (release on arrive, acquire on wait; every thread passes it the same
 // number of times, so it cannot wait on an absent thread). Between arrive and wait each thread
 // loads the read-only data of its first device of the next colour (indices, slots, buffered
-// contributions), so that after the barrier only the read-modify-writes of A and b remain; A
-// and b go through L2 (ld.cg / st.cg), so no SM reads a stale L1 line.
+// contributions), so that after the barrier only the additions into A and b remain.
 constexpr int kClusterBlocks = 8;
 constexpr int kClusterThreads = 512;
 
@@ -419,6 +420,9 @@ __device__ __forceinline__ void stamp_load(const DevTopo& T, int k, StampPre& p)
   for (int j = 0; j < kNContrib; ++j) p.v[j] = __ldg(T.buf + j * N + k);
 }
 
+// The additions are fire-and-forget atomics performed in L2: no load of A on the critical path,
+// and the same sum as a read-modify-write (each entry receives one addition per colour, the
+// barrier orders the colours, so every entry still adds its contributions in colour order).
 __device__ __forceinline__ void stamp_apply(const StampPre& p, double* A, double* b) {
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
@@ -426,9 +430,9 @@ __device__ __forceinline__ void stamp_apply(const StampPre& p, double* A, double
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int s = p.sl[4 * r + u];
-      if (s >= 0) __stcg(A + s, __ldcg(A + s) + p.v[4 * r + u]);
+      if (s >= 0) atomicAdd(A + s, p.v[4 * r + u]);
     }
-    __stcg(b + p.rows[r], __ldcg(b + p.rows[r]) + p.v[kNSlot + r]);
+    atomicAdd(b + p.rows[r], p.v[kNSlot + r]);
   }
 }
 
