@@ -534,10 +534,10 @@ def extras(eec, circ, net, x, xt, A, b, q, args, dev):
     ip = torch.zeros_like(q)
     v0t = eec.eec_get_variant(circ.ctx)
     tran = {}
-    for v in (eec.EEC_VARIANT_ATOMIC, eec.EEC_VARIANT_COLOR_FUSED):
+    for v in (eec.EEC_VARIANT_ATOMIC, eec.EEC_VARIANT_COLOR_FUSED, eec.EEC_VARIANT_COLOR_BUFFERED):
         eec.eec_set_variant(circ.ctx, v)
         ms_t = _time(lambda: eec.eec_eval_stamp_tran(circ.ctx, xt, qprev, ip, 2e11, 1.0, A, b, q, ic),
-                     20 if v == eec.EEC_VARIANT_ATOMIC else 3, stream)
+                     3 if v == eec.EEC_VARIANT_COLOR_FUSED else 20, stream)
         tran[eec.VARIANT_NAMES[v]] = {"ms": ms_t, "devices_per_s": net.n_dev / (ms_t * 1e-3)}
     eec.eec_set_variant(circ.ctx, v0t)
     res["transient_tr_stamp"] = tran

@@ -247,8 +247,10 @@ EEC_API int eec_newton_dc(eec_ctx* ctx, double* x_dev, double* A_values_dev, dou
  *  q_prev_dev  [4*n_dev] charges at the previous time point (terminal-major, original order),
  *  i_prev_dev  [4*n_dev] capacitive currents there, nullable (zero);
  *  q_dev       [4*n_dev] out: charges at x;  i_dev [4*n_dev] out, nullable: ic at x.
- * Schedule: the per-colour store-add when the variant is EEC_VARIANT_COLOR_FUSED (the colouring
- * must count gate rows: not EEC_CONFLICT_WRITE_ROWS), otherwise FP64 atomics.
+ * Schedule: the per-colour store-add when the variant is EEC_VARIANT_COLOR_FUSED; every device
+ * into a buffer, then a colour-ordered stamp by one thread-block cluster, when it is
+ * EEC_VARIANT_COLOR_BUFFERED (both need a colouring that counts gate rows: not
+ * EEC_CONFLICT_WRITE_ROWS); otherwise FP64 atomics.
  */
 EEC_API int eec_eval_stamp_tran(eec_ctx* ctx, const double* x_dev, const double* q_prev_dev,
                                 const double* i_prev_dev, double alpha, double beta,

@@ -1412,9 +1412,12 @@ int eec_eval_stamp_tran(eec_ctx* c, const double* x, const double* q_prev, const
   if (!std::isfinite(alpha) || !std::isfinite(beta) || alpha < 0.0)
     return fail(c, EEC_EINVAL, "alpha must be finite and >= 0, beta finite");
   int v = effective_variant(c);
-  if (v != EEC_VARIANT_COLOR_FUSED) v = EEC_VARIANT_ATOMIC;
-  if (v == EEC_VARIANT_COLOR_FUSED && (!c->colored || c->opt.conflict_rule == EEC_CONFLICT_WRITE_ROWS))
+  if (v != EEC_VARIANT_COLOR_FUSED && v != EEC_VARIANT_COLOR_BUFFERED) v = EEC_VARIANT_ATOMIC;
+  if (v != EEC_VARIANT_ATOMIC && (!c->colored || c->opt.conflict_rule == EEC_CONFLICT_WRITE_ROWS))
     return fail(c, EEC_ESTATE, "transient colour stamping needs a colouring that counts gate rows");
+  if (v == EEC_VARIANT_COLOR_BUFFERED && !c->d.buf_tran &&
+      (rc = dalloc(c, &c->d.buf_tran, (size_t)kNContribTran * c->n_dev)))
+    return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   TranArgs ta{q_prev, i_prev, alpha, beta, q, icap};
   const int blk = c->opt.block ? c->opt.block : c->tuned_block;
@@ -1423,6 +1426,11 @@ int eec_eval_stamp_tran(eec_ctx* c, const double* x, const double* q_prev, const
   if (v == EEC_VARIANT_ATOMIC) {
     CUDA_TRY(c, launch_eval_tran(c->d, MODE_ATOMIC, 0, c->n_dev, x, A, b, ta, blk, s));
     c->n_kernels += c->n_dev > 0;
+  } else if (v == EEC_VARIANT_COLOR_BUFFERED) {
+    // every device into the buffer in one launch, then the colour-ordered stamp by one cluster
+    CUDA_TRY(c, launch_eval_tran(c->d, MODE_BUFFER, 0, c->n_dev, x, A, b, ta, blk, s));
+    CUDA_TRY(c, launch_stamp_cluster_tran(c->d, c->d_coff, c->C, A, b, s));
+    c->n_kernels += 1 + (c->n_dev > 0);
   } else {
     for (int k = 0; k < c->C; ++k) {
       if (c->color_off[k + 1] <= c->color_off[k]) continue;

@@ -38,6 +38,9 @@ enum Prm : int {
 // then the three right-hand-side rows j = 12 + r.
 constexpr int kNSlot = 12;
 constexpr int kNContrib = 15;
+// Transient buffer of one device: A values of rows d, g, s, b x columns d, g, s, b at j = 4 t + u,
+// then the four right-hand-side rows at j = 16 + t.
+constexpr int kNContribTran = 20;
 
 // Device-side topology and parameters, indexed by layout position k (colour-major when coloured).
 struct DevTopo {
@@ -65,6 +68,7 @@ struct DevTopo {
   int* gat_heavy;      // the others (one warp each)
   int n_light, n_heavy;
   double* buf;         // [kNContrib][N] (allocated on first use)
+  double* buf_tran;    // [kNContribTran][N]: transient values G + alpha C (4 x 4) and 4 rhs
   // backward: unknown u gathers gv[src] over inc_src[inc_ptr[u] .. inc_ptr[u+1])
   int* inc_ptr;     // [n + 1]
   int* inc_src;     // flat index t * N + k into gv
@@ -113,6 +117,9 @@ int stamp_persistent_max_blocks_per_sm();
 cudaError_t launch_stamp_cluster(const DevTopo& T, const int* color_off_dev, int n_colors,
                                  double* A, double* b, cudaStream_t s);
 int stamp_cluster_threads();
+// The transient analogue from buf_tran (four rows per device, the gate row's slots in slot_g).
+cudaError_t launch_stamp_cluster_tran(const DevTopo& T, const int* color_off_dev, int n_colors,
+                                      double* A, double* b, cudaStream_t s);
 // DC Newton loop (eec_newton.cu). stats[0] max|y - x|, [1] max|dx|, [2] max|x|, [3] residual, as
 // bit patterns of non-negative doubles (zeroed by the caller).
 cudaError_t launch_newton_step(const double* y, double* x, int n, double vstep, int per_node,
@@ -120,7 +127,8 @@ cudaError_t launch_newton_step(const double* y, double* x, int n, double vstep, 
 cudaError_t launch_residual_norm(const int* rp, const int* col, const double* A, const double* x,
                                  const double* b, int n, unsigned long long* stats,
                                  cudaStream_t s);
-// Transient companion stamp (mode MODE_RMW over one colour range, or MODE_ATOMIC over all).
+// Transient companion stamp (mode MODE_RMW over one colour range, MODE_ATOMIC over all, or
+// MODE_BUFFER over all into buf_tran).
 struct TranArgs {
   const double* qprev;  // [4][N_orig] charges of the previous time point
   const double* iprev;  // [4][N_orig] capacitive currents of the previous time point, nullable

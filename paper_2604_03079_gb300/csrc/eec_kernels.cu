@@ -217,12 +217,17 @@ __device__ __forceinline__ void eval_one_tran(const DevTopo& T, int k, const dou
     for (int u = 0; u < 4; ++u) {
       if (idx[u] < 0) continue;
       const double a = fma(ta.alpha, o.C[t][u], t == 1 ? 0.0 : o.G[r][u]);
-      const int s = t == 1 ? __ldg(T.slot_g + u * N + k) : __ldg(T.slot + (4 * r + u) * N + k);
-      if (MODE == MODE_ATOMIC) atomicAdd(A + s, a);
-      else A[s] += a;
+      if (MODE == MODE_BUFFER) {
+        T.buf_tran[(4 * t + u) * N + k] = a;
+      } else {
+        const int s = t == 1 ? __ldg(T.slot_g + u * N + k) : __ldg(T.slot + (4 * r + u) * N + k);
+        if (MODE == MODE_ATOMIC) atomicAdd(A + s, a);
+        else A[s] += a;
+      }
       rhs = fma(a, V[u], rhs);
     }
-    if (MODE == MODE_ATOMIC) atomicAdd(b + row, rhs);
+    if (MODE == MODE_BUFFER) T.buf_tran[(16 + t) * N + k] = rhs;
+    else if (MODE == MODE_ATOMIC) atomicAdd(b + row, rhs);
     else b[row] += rhs;
   }
 }
@@ -468,6 +473,79 @@ __global__ void __launch_bounds__(kClusterThreads) k_stamp_cluster(DevTopo T,
   }
 }
 
+// The transient buffer, colour after colour, by one cluster as k_stamp_cluster: four rows per
+// device (d, g, s, b; the gate row's slots in slot_g), 16 values and 4 right-hand sides.
+constexpr int kClusterThreadsTran = 256;
+
+struct StampPreTran {
+  int rows[4];
+  int sl[16];
+  double v[kNContribTran];
+};
+
+__device__ __forceinline__ void stamp_load_tran(const DevTopo& T, int k, StampPreTran& p) {
+  const long long N = T.N;
+  const int4 ti = __ldg(T.tidx + k);
+  p.rows[0] = ti.x;
+  p.rows[1] = ti.y;
+  p.rows[2] = ti.z;
+  p.rows[3] = ti.w;
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const int r = t == 0 ? 0 : (t == 2 ? 1 : 2);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      p.sl[4 * t + u] = t == 1 ? __ldg(T.slot_g + u * N + k) : __ldg(T.slot + (4 * r + u) * N + k);
+  }
+#pragma unroll
+  for (int j = 0; j < kNContribTran; ++j)
+    p.v[j] = (p.rows[j < 16 ? j >> 2 : j - 16] >= 0) ? __ldg(T.buf_tran + j * N + k) : 0.0;
+}
+
+__device__ __forceinline__ void stamp_apply_tran(const StampPreTran& p, double* A, double* b) {
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    if (p.rows[t] < 0) continue;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int s = p.sl[4 * t + u];
+      if (s >= 0) atomicAdd(A + s, p.v[4 * t + u]);
+    }
+    atomicAdd(b + p.rows[t], p.v[16 + t]);
+  }
+}
+
+__global__ void __launch_bounds__(kClusterThreadsTran) k_stamp_cluster_tran(
+    DevTopo T, const int* __restrict__ coff, int C, double* A, double* b) {
+  const int nthreads = gridDim.x * blockDim.x;   // the grid is one cluster
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  StampPreTran cur;
+  bool have = false;
+  if (C > 0) {
+    const int k = __ldg(coff) + tid;
+    have = k < __ldg(coff + 1);
+    if (have) stamp_load_tran(T, k, cur);
+  }
+  for (int c = 0; c < C; ++c) {
+    const int begin = __ldg(coff + c), end = __ldg(coff + c + 1);
+    if (have) stamp_apply_tran(cur, A, b);
+    for (int k = begin + tid + nthreads; k < end; k += nthreads) {
+      StampPreTran extra;
+      stamp_load_tran(T, k, extra);
+      stamp_apply_tran(extra, A, b);
+    }
+    if (c + 1 < C) {
+      __syncwarp();   // the .aligned barrier is executed by whole warps
+      asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+      const int k = __ldg(coff + c + 1) + tid;
+      have = k < __ldg(coff + c + 2);
+      if (have) stamp_load_tran(T, k, cur);   // read-only data: safe before the acquire
+      __syncwarp();
+      asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+    }
+  }
+}
+
 // All colours' buffered stamps in one co-resident launch: the grid adds colour c, passes the
 // bounded grid barrier, then adds colour c + 1 — the order of the per-colour launches, without
 // a launch (or graph node) per colour. Stamping a colour is a few read-modify-writes per device,
@@ -596,6 +674,7 @@ cudaError_t launch_eval_tran(const DevTopo& T, int mode, int begin, int end, con
   const int B = eval_block(end - begin, block);
   const int g = grid_for(end - begin, B);
   if (mode == MODE_ATOMIC) k_eval_tran<MODE_ATOMIC><<<g, B, 0, s>>>(T, begin, end, x, A, b, ta);
+  else if (mode == MODE_BUFFER) k_eval_tran<MODE_BUFFER><<<g, B, 0, s>>>(T, begin, end, x, A, b, ta);
   else k_eval_tran<MODE_RMW><<<g, B, 0, s>>>(T, begin, end, x, A, b, ta);
   return cudaGetLastError();
 }
@@ -660,6 +739,23 @@ cudaError_t launch_stamp_cluster(const DevTopo& T, const int* color_off_dev, int
 }
 
 int stamp_cluster_threads() { return kClusterBlocks * kClusterThreads; }
+
+cudaError_t launch_stamp_cluster_tran(const DevTopo& T, const int* color_off_dev, int n_colors,
+                                      double* A, double* b, cudaStream_t s) {
+  if (n_colors <= 0) return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kClusterBlocks);
+  cfg.blockDim = dim3(kClusterThreadsTran);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kClusterBlocks;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_stamp_cluster_tran, T, color_off_dev, n_colors, A, b);
+}
 
 int stamp_persistent_max_blocks_per_sm() {
   int nb = 0;
