@@ -1049,7 +1049,7 @@ int eec_build_scatter(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_out) {
   CUDA_TRY(c, cudaDeviceSynchronize());
   const int bps = persistent_max_blocks_per_sm(0, false);
   const int bpsq = persistent_max_blocks_per_sm(0, true);
-  c->persist_grid = std::max(1, std::min(std::min(bps, bpsq), 4)) * c->sms;
+  c->persist_grid = std::max(1, std::min(std::min(bps, bpsq), 1)) * c->sms;   // one block per SM
   // enough 256-thread blocks for the largest colour, within one co-resident wave (fewer blocks
   // make each barrier cheaper)
   int maxcol = 0;

@@ -62,7 +62,7 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, int* status, int absent
           fail = 1;
           break;
         }
-        __nanosleep(100);
+        __nanosleep(32);
       }
     }
     __threadfence();
@@ -275,9 +275,12 @@ __global__ void __launch_bounds__(kEvalBlock) k_eval_ranges(DevTopo T, const int
 // One co-resident grid walks the colours; a colour's devices are dealt out in 32-device chunks
 // round-robin over the blocks first (chunk i -> block i mod grid, then the next warp of that
 // block), so a small colour occupies one warp on each of many SMs instead of whole blocks on a
-// few. The FP64 pipe of an SM is narrow; spreading the warps is what shortens a colour.
+// few. The FP64 pipe of an SM is narrow; spreading the warps is what shortens a colour. One
+// 512-thread block per SM: the same 16 warps per SM as four 128-thread blocks, and a quarter of
+// the arrivals at every grid barrier.
+constexpr int kPersistBlock = 512;
 template <bool WANT_Q>
-__global__ void __launch_bounds__(kEvalBlock) k_persistent(DevTopo T, const int* __restrict__ coff,
+__global__ void __launch_bounds__(kPersistBlock) k_persistent(DevTopo T, const int* __restrict__ coff,
                                                            int C, const double* __restrict__ x,
                                                            double* A, double* b, double* q,
                                                            int dbg, int absent_block) {
@@ -684,9 +687,9 @@ int persistent_max_blocks_per_sm(int block, bool want_q) {
   int nb = 0;
   cudaError_t e;
   if (want_q)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent<true>, kEvalBlock, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent<true>, kPersistBlock, 0);
   else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent<false>, kEvalBlock, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent<false>, kPersistBlock, 0);
   return e == cudaSuccess ? nb : 0;
 }
 
@@ -708,9 +711,9 @@ cudaError_t launch_persistent(const DevTopo& T, const int* color_off_dev, int n_
   void* args[] = {&Tc, &coff, &C, &xx, &AA, &bb, &qq, &d, &ab};
   if (q)
     return cudaLaunchCooperativeKernel((const void*)k_persistent<true>, dim3(grid),
-                                       dim3(kEvalBlock), args, 0, s);
+                                       dim3(kPersistBlock), args, 0, s);
   return cudaLaunchCooperativeKernel((const void*)k_persistent<false>, dim3(grid),
-                                     dim3(kEvalBlock), args, 0, s);
+                                     dim3(kPersistBlock), args, 0, s);
 }
 
 cudaError_t launch_gather(const DevTopo& T, double* A, double* b, cudaStream_t s) {
