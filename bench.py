@@ -159,7 +159,8 @@ def cpu_baseline(net, x, budget_s=10.0):
         el = time.perf_counter() - t0
         if el >= budget_s or (reps >= 1 and el * (reps + 1) / reps > 3 * budget_s):
             break
-    return {"value": net.n_dev * reps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": net.n_dev * reps / el, "unit": UNIT, "cores": 1,
+            "host_cores_available": len(os.sched_getaffinity(0)), "kind": "oracle",
             "sample": f"whole workload ({net.n_dev} devices) x {reps} eval_stamp calls, "
                       f"{el:.1f} s, 1 thread"}
 
@@ -269,7 +270,8 @@ def run_ours(args):
     init_ms = prof["ms_init"] / max(prof["calls"], 1)
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+           "warmup": args.warmup, "ms_per_step": ms_per_step,
+           "ms_per_step_median": statistics.median(step_ms), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic (seeded netlist generators, random-init node voltages)",
            "config": {"workload": wname, "n_dev": net.n_dev, "n_unknowns": circ.n,
