@@ -341,8 +341,7 @@ int run_variant(eec_ctx* c, int v, const double* x, double* A, double* b, double
   if (variant_needs_colors(v) && !c->colored)
     return fail(c, EEC_ESTATE, "colour schedules need eec_color before eec_build_scatter");
   auto init_Ab = [&]() -> int {
-    CUDA_TRY(c, cudaMemcpyAsync(A, T.Alin, sizeof(double) * c->nnz, cudaMemcpyDeviceToDevice, s));
-    CUDA_TRY(c, cudaMemcpyAsync(b, T.blin, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(c, launch_init_lin(T, A, b, s));
     return EEC_OK;
   };
   int rc;
@@ -1254,10 +1253,7 @@ int eec_eval_stamp_host(eec_ctx* c, const double* x_host, double* A_host, double
   const int blk = c->opt.block ? c->opt.block : c->tuned_block;
   int mode = MODE_ATOMIC;
   if (v == EEC_VARIANT_ATOMIC) {
-    CUDA_TRY(c, cudaMemcpyAsync(c->h_A, c->d.Alin, sizeof(double) * c->nnz,
-                                cudaMemcpyDeviceToDevice, s));
-    CUDA_TRY(c, cudaMemcpyAsync(c->h_b, c->d.blin, sizeof(double) * c->n,
-                                cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(c, launch_init_lin(c->d, c->h_A, c->h_b, s));
   } else {
     if ((rc = ensure_buf(c))) return rc;
     mode = MODE_BUFFER;
@@ -1421,8 +1417,7 @@ int eec_eval_stamp_tran(eec_ctx* c, const double* x, const double* q_prev, const
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   TranArgs ta{q_prev, i_prev, alpha, beta, q, icap};
   const int blk = c->opt.block ? c->opt.block : c->tuned_block;
-  CUDA_TRY(c, cudaMemcpyAsync(A, c->d.Alin, sizeof(double) * c->nnz, cudaMemcpyDeviceToDevice, s));
-  CUDA_TRY(c, cudaMemcpyAsync(b, c->d.blin, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(c, launch_init_lin(c->d, A, b, s));
   if (v == EEC_VARIANT_ATOMIC) {
     CUDA_TRY(c, launch_eval_tran(c->d, MODE_ATOMIC, 0, c->n_dev, x, A, b, ta, blk, s));
     c->n_kernels += c->n_dev > 0;
@@ -1618,8 +1613,7 @@ int eec_test_barrier_timeout(eec_ctx* c, const double* x, double* A, double* b, 
   if (!c->colored || c->C < 2) return fail(c, EEC_ESTATE, "needs a coloured context with >= 2 colours");
   if (!x || !A || !b) return fail(c, EEC_EINVAL, "NULL x, A or b");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  CUDA_TRY(c, cudaMemcpyAsync(A, c->d.Alin, sizeof(double) * c->nnz, cudaMemcpyDeviceToDevice, s));
-  CUDA_TRY(c, cudaMemcpyAsync(b, c->d.blin, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(c, launch_init_lin(c->d, A, b, s));
   CUDA_TRY(c, launch_persistent(c->d, c->d_coff, c->C, x, A, b, nullptr, 0, c->persist_grid, 0, s,
                                 /*absent_block=*/0));
   return EEC_OK;

@@ -107,6 +107,8 @@ cudaError_t launch_persistent(const DevTopo& T, const int* color_off_dev, int n_
                               int grid, int dbg, cudaStream_t s, int absent_block = -1);
 int persistent_max_blocks_per_sm(int block, bool want_q);
 cudaError_t launch_gather(const DevTopo& T, double* A, double* b, cudaStream_t s);
+// A <- A_lin, b <- b_lin (the linear part), one kernel.
+cudaError_t launch_init_lin(const DevTopo& T, double* A, double* b, cudaStream_t s);
 // Buffered contributions of every colour, in colour order, in one cooperative launch of `grid`
 // blocks (co-resident: at most stamp_persistent_max_blocks_per_sm() per SM).
 cudaError_t launch_stamp_persistent(const DevTopo& T, const int* color_off_dev, int n_colors,
