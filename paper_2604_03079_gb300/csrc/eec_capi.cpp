@@ -325,11 +325,11 @@ bool variant_needs_colors(int v) {
 // launched in *nk. With profiling on, four events bracket the phases init | evaluate | stamp.
 // Every device once, in the cost order of eval_nr (order-free modes only).
 cudaError_t launch_eval_all(eec_ctx* c, int mode, const double* x, double* A, double* b,
-                            double* q, int blk, int dbg, cudaStream_t s) {
+                            double* q, int blk, int dbg, cudaStream_t s, bool pdl = false) {
   if (c->eval_nr >= 2 && c->eval_ordered)
     return launch_eval_ranges(c->d, mode, c->d_erbeg, c->d_eroff, c->eval_nr, c->n_dev, x, A, b,
-                              q, blk, dbg, s);
-  return launch_eval(c->d, mode, 0, c->n_dev, x, A, b, q, blk, dbg, s);
+                              q, blk, dbg, s, pdl);
+  return launch_eval(c->d, mode, 0, c->n_dev, x, A, b, q, blk, dbg, s, pdl);
 }
 
 int run_variant(eec_ctx* c, int v, const double* x, double* A, double* b, double* q,
@@ -342,6 +342,7 @@ int run_variant(eec_ctx* c, int v, const double* x, double* A, double* b, double
     return fail(c, EEC_ESTATE, "colour schedules need eec_color before eec_build_scatter");
   auto init_Ab = [&]() -> int {
     CUDA_TRY(c, launch_init_lin(T, A, b, s));
+    ++*nk;
     return EEC_OK;
   };
   int rc;
@@ -365,14 +366,15 @@ int run_variant(eec_ctx* c, int v, const double* x, double* A, double* b, double
       if ((rc = init_Ab())) return rc;
       prof_mark(c, s);
       CUDA_TRY(c, launch_persistent(T, c->d_coff, c->C, x, A, b, q, blk, c->persist_grid, dbg, s));
-      *nk = 1;
+      ++*nk;
       prof_mark(c, s);
       break;
     case EEC_VARIANT_ATOMIC:
       if ((rc = init_Ab())) return rc;
       prof_mark(c, s);
-      CUDA_TRY(c, launch_eval_all(c, MODE_ATOMIC, x, A, b, q, blk, dbg, s));
-      *nk = c->n_dev > 0;
+      // overlaps the initialisation unless a profiling event sits between the two launches
+      CUDA_TRY(c, launch_eval_all(c, MODE_ATOMIC, x, A, b, q, blk, dbg, s, !c->prof));
+      *nk += c->n_dev > 0;
       prof_mark(c, s);
       break;
     case EEC_VARIANT_SEGREDUCE:
@@ -380,14 +382,14 @@ int run_variant(eec_ctx* c, int v, const double* x, double* A, double* b, double
       CUDA_TRY(c, launch_eval_all(c, MODE_BUFFER, x, A, b, q, blk, dbg, s));
       prof_mark(c, s);
       CUDA_TRY(c, launch_gather(c->d, A, b, s));
-      *nk = (c->n_dev > 0) + (c->nnz + c->n > 0);
+      *nk += (c->n_dev > 0) + (c->nnz + c->n > 0);
       break;
     case EEC_VARIANT_COLOR_BUFFERED:
       if ((rc = init_Ab())) return rc;
       prof_mark(c, s);
       CUDA_TRY(c, launch_eval_all(c, MODE_BUFFER, x, A, b, q, blk, dbg, s));
       prof_mark(c, s);
-      *nk = c->n_dev > 0;
+      *nk += c->n_dev > 0;
       // colour order: one launch per colour for a few colours, else one co-resident launch
       // that steps through the colours with a grid barrier
       if (c->stamp_mode == 2) {
@@ -1254,6 +1256,7 @@ int eec_eval_stamp_host(eec_ctx* c, const double* x_host, double* A_host, double
   int mode = MODE_ATOMIC;
   if (v == EEC_VARIANT_ATOMIC) {
     CUDA_TRY(c, launch_init_lin(c->d, c->h_A, c->h_b, s));
+    ++c->n_kernels;
   } else {
     if ((rc = ensure_buf(c))) return rc;
     mode = MODE_BUFFER;
@@ -1262,7 +1265,7 @@ int eec_eval_stamp_host(eec_ctx* c, const double* x_host, double* A_host, double
   for (int k = 0; k < K; ++k) {
     CUDA_TRY(c, launch_eval_ranges(c->d, mode, c->d_hrbeg + c->hc_rb[k], c->d_hroff + c->hc_ro[k],
                                    c->hc_nr[k], c->hc_total[k], c->h_x, c->h_A, c->h_b, c->h_q,
-                                   blk, dbg, s));
+                                   blk, dbg, s, /*pdl=*/k == 0 && mode == MODE_ATOMIC));
     c->n_kernels += c->hc_total[k] > 0;
     CUDA_TRY(c, cudaEventRecord(c->hev[k], s));
   }
@@ -1418,6 +1421,7 @@ int eec_eval_stamp_tran(eec_ctx* c, const double* x, const double* q_prev, const
   TranArgs ta{q_prev, i_prev, alpha, beta, q, icap};
   const int blk = c->opt.block ? c->opt.block : c->tuned_block;
   CUDA_TRY(c, launch_init_lin(c->d, A, b, s));
+  ++c->n_kernels;
   if (v == EEC_VARIANT_ATOMIC) {
     CUDA_TRY(c, launch_eval_tran(c->d, MODE_ATOMIC, 0, c->n_dev, x, A, b, ta, blk, s));
     c->n_kernels += c->n_dev > 0;

@@ -92,14 +92,17 @@ cudaError_t launch_params(const DevTopo& T, cudaStream_t s);
 // W_dev, L_dev in original device order -> per-position W, L and derived parameters.
 cudaError_t launch_update_params(const DevTopo& T, const double* W_dev, const double* L_dev,
                                  cudaStream_t s);
+// pdl: launch with programmatic stream serialisation (the atomic evaluation may start while the
+// linear-part initialisation before it runs; it waits for that kernel before its first addition).
 cudaError_t launch_eval(const DevTopo& T, int mode, int begin, int end, const double* x,
-                        double* A, double* b, double* q, int block, int dbg, cudaStream_t s);
+                        double* A, double* b, double* q, int block, int dbg, cudaStream_t s,
+                        bool pdl = false);
 // The devices of a list of library-order ranges: range r starts at position rbeg[r] and holds
 // roff[r+1] - roff[r] devices (roff[0] = 0, roff[nr] = total); only for the order-free modes
 // MODE_ATOMIC and MODE_BUFFER.
 cudaError_t launch_eval_ranges(const DevTopo& T, int mode, const int* rbeg, const int* roff,
                                int nr, int total, const double* x, double* A, double* b,
-                               double* q, int block, int dbg, cudaStream_t s);
+                               double* q, int block, int dbg, cudaStream_t s, bool pdl = false);
 // absent_block >= 0 is a test hook: that block skips every grid barrier, so the other blocks'
 // bounded waits expire and the status word records a timeout.
 cudaError_t launch_persistent(const DevTopo& T, const int* color_off_dev, int n_colors,

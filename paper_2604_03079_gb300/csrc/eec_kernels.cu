@@ -120,6 +120,9 @@ __device__ __forceinline__ void eval_one(const DevTopo& T, int k, const double* 
   EvalOut<double> o;
   ees_l1<double, WANT_Q>(c, psb, P, V, o, sbf, &bk);
 
+  // A and b may still be being initialised by the kernel launched just before this one
+  // (programmatic dependent launch): wait for it before the first addition
+  if (MODE != MODE_BUFFER) asm volatile("griddepcontrol.wait;" ::: "memory");
   // b row r: -I_r + sum over the free columns u of G[r][u] V_u (held columns are eliminated)
   const int term[3] = {0, 2, 3};
   bool bc_ok = true;
@@ -201,6 +204,7 @@ __device__ __forceinline__ void eval_one_tran(const DevTopo& T, int k, const dou
   }
   EvalOut<double> o;
   ees_l1<double, true, true>(c, psb, P, V, o, sbf, &bk);
+  if (MODE != MODE_BUFFER) asm volatile("griddepcontrol.wait;" ::: "memory");   // see eval_one
   const int od = __ldg(T.orig + k);
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
@@ -629,8 +633,30 @@ int eval_block(long long n, int block) {
   return n < 152LL * kEvalBlock ? 32 : kEvalBlock;
 }
 
+// Launch with programmatic stream serialisation when pdl: the kernel may begin while the previous
+// kernel in the stream runs; it must wait (griddepcontrol.wait) before using that kernel's output.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_maybe_pdl(void (*kern)(KArgs...), int g, int B, cudaStream_t s, bool pdl,
+                             Args... args) {
+  if (!pdl) {
+    kern<<<g, B, 0, s>>>(args...);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(g);
+  cfg.blockDim = dim3(B);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 cudaError_t launch_eval(const DevTopo& T, int mode, int begin, int end, const double* x,
-                        double* A, double* b, double* q, int block, int dbg, cudaStream_t s) {
+                        double* A, double* b, double* q, int block, int dbg, cudaStream_t s,
+                        bool pdl) {
   if (end <= begin) return cudaSuccess;
   const int B = eval_block(end - begin, block);
   const int g = grid_for(end - begin, B);
@@ -641,9 +667,8 @@ cudaError_t launch_eval(const DevTopo& T, int mode, int begin, int end, const do
       else k_eval<MODE_RMW, false><<<g, B, 0, s>>>(T, begin, end, x, A, b, q, dbg);
       break;
     case MODE_ATOMIC:
-      if (wq) k_eval<MODE_ATOMIC, true><<<g, B, 0, s>>>(T, begin, end, x, A, b, q, dbg);
-      else k_eval<MODE_ATOMIC, false><<<g, B, 0, s>>>(T, begin, end, x, A, b, q, dbg);
-      break;
+      if (wq) return launch_maybe_pdl(k_eval<MODE_ATOMIC, true>, g, B, s, pdl, T, begin, end, x, A, b, q, dbg);
+      return launch_maybe_pdl(k_eval<MODE_ATOMIC, false>, g, B, s, pdl, T, begin, end, x, A, b, q, dbg);
     default:
       if (wq) k_eval<MODE_BUFFER, true><<<g, B, 0, s>>>(T, begin, end, x, A, b, q, dbg);
       else k_eval<MODE_BUFFER, false><<<g, B, 0, s>>>(T, begin, end, x, A, b, q, dbg);
@@ -654,14 +679,17 @@ cudaError_t launch_eval(const DevTopo& T, int mode, int begin, int end, const do
 
 cudaError_t launch_eval_ranges(const DevTopo& T, int mode, const int* rbeg, const int* roff,
                                int nr, int total, const double* x, double* A, double* b,
-                               double* q, int block, int dbg, cudaStream_t s) {
+                               double* q, int block, int dbg, cudaStream_t s, bool pdl) {
   if (total <= 0 || nr <= 0) return cudaSuccess;
   const int B = eval_block(total, block);
   const int g = grid_for(total, B);
   const bool wq = q != nullptr;
   if (mode == MODE_ATOMIC) {
-    if (wq) k_eval_ranges<MODE_ATOMIC, true><<<g, B, 0, s>>>(T, rbeg, roff, nr, total, x, A, b, q, dbg);
-    else k_eval_ranges<MODE_ATOMIC, false><<<g, B, 0, s>>>(T, rbeg, roff, nr, total, x, A, b, q, dbg);
+    if (wq)
+      return launch_maybe_pdl(k_eval_ranges<MODE_ATOMIC, true>, g, B, s, pdl, T, rbeg, roff, nr,
+                              total, x, A, b, q, dbg);
+    return launch_maybe_pdl(k_eval_ranges<MODE_ATOMIC, false>, g, B, s, pdl, T, rbeg, roff, nr,
+                            total, x, A, b, q, dbg);
   } else if (mode == MODE_BUFFER) {
     if (wq) k_eval_ranges<MODE_BUFFER, true><<<g, B, 0, s>>>(T, rbeg, roff, nr, total, x, A, b, q, dbg);
     else k_eval_ranges<MODE_BUFFER, false><<<g, B, 0, s>>>(T, rbeg, roff, nr, total, x, A, b, q, dbg);
@@ -676,7 +704,8 @@ cudaError_t launch_eval_tran(const DevTopo& T, int mode, int begin, int end, con
   if (end <= begin) return cudaSuccess;
   const int B = eval_block(end - begin, block);
   const int g = grid_for(end - begin, B);
-  if (mode == MODE_ATOMIC) k_eval_tran<MODE_ATOMIC><<<g, B, 0, s>>>(T, begin, end, x, A, b, ta);
+  if (mode == MODE_ATOMIC)
+    return launch_maybe_pdl(k_eval_tran<MODE_ATOMIC>, g, B, s, true, T, begin, end, x, A, b, ta);
   else if (mode == MODE_BUFFER) k_eval_tran<MODE_BUFFER><<<g, B, 0, s>>>(T, begin, end, x, A, b, ta);
   else k_eval_tran<MODE_RMW><<<g, B, 0, s>>>(T, begin, end, x, A, b, ta);
   return cudaGetLastError();
@@ -721,6 +750,8 @@ cudaError_t launch_persistent(const DevTopo& T, const int* color_off_dev, int n_
 __global__ void __launch_bounds__(256) k_init_lin(const double* __restrict__ Alin,
                                                   const double* __restrict__ blin, double* A,
                                                   double* b, long long nnz, long long n) {
+  // the next kernel (the evaluation) may start now; it waits for this grid before touching A, b
+  asm volatile("griddepcontrol.launch_dependents;");
   const long long total = nnz + n;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
