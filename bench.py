@@ -276,7 +276,8 @@ def run_ours(args):
            "config": {"workload": wname, "n_dev": net.n_dev, "n_unknowns": circ.n,
                       "nnz": circ.nnz, "colors": circ.n_colors,
                       "variant": eec.VARIANT_NAMES[variant],
-                      "block": eec.eec_get_tuning(circ.ctx)[1],
+                      "block": (eec.eec_get_tuning(circ.ctx)[1] or
+                                "library choice: 32 for launches under 19,456 devices, else 128"),
                       "eval_order": ("free source/body first" if eec.eec_get_tuning(circ.ctx)[2]
                                      else "layout order"),
                       "l2": "flushed (256 MiB write) before every timed step",
