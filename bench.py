@@ -562,6 +562,20 @@ def extras(eec, circ, net, x, xt, A, b, q, args, dev):
                 "transistors": n.n_dev, "resistors": int(len(n.res_G)), "colors": c.n_colors,
                 "ms": {eec.VARIANT_NAMES[i]: m for i, m in enumerate(msv)}}
             del c
+    # the same netlists in modified nodal analysis (rails and their source currents are
+    # unknowns): the free-node rule then sees the VDD clique, the reading that gives Table II's
+    # 896 colours with real stamping
+    for name, n in (("base", base), ("R14", netgen.insert_series_resistors(base, per_group=14))):
+        c = eec.Circuit(n, cards0, color=True, rail_mode=eec.EEC_RAIL_MNA_BRANCH)
+        xm = np.concatenate([netgen.Rng(7, 8).uniform(n.n_nodes - 1),
+                             1e-4 * netgen.Rng(7, 9).normal(c.n - n.n_nodes + 1)])
+        xa = torch.as_tensor(xm, device=dev)
+        A2, b2, q2 = c.new_outputs()
+        msv = eec.eec_autotune(c.ctx, xa, A2, b2, q2, reps=5)
+        study[f"{name}_mna_rule0"] = {
+            "transistors": n.n_dev, "resistors": int(len(n.res_G)), "colors": c.n_colors,
+            "unknowns": c.n, "ms": {eec.VARIANT_NAMES[i]: m for i, m in enumerate(msv)}}
+        del c
     res["adder64_table2_study"] = study
 
     # batched (config 4): one context for 4096 circuits vs 4096 plain per-circuit calls

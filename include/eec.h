@@ -57,9 +57,16 @@ extern "C" {
 #define EEC_N_VARIANTS 5
 
 /* Conflict rules for the colouring. */
-#define EEC_CONFLICT_FREE_NODE 0   /* share a free node (rails are not unknowns)  [default] */
+#define EEC_CONFLICT_FREE_NODE 0   /* share a free node (rails are free only under MNA_BRANCH) [default] */
 #define EEC_CONFLICT_ANY_NONGROUND 1 /* share any node but ground (the paper's literal rule) */
 #define EEC_CONFLICT_WRITE_ROWS 2  /* share a free node both write as a DC row (d, s or b) */
+
+/* How nodes held by an ideal voltage source (node_fixed) enter the system. */
+#define EEC_RAIL_ELIMINATE 0   /* held nodes are not unknowns; their voltages enter through the
+                                  device evaluation and b  [default] */
+#define EEC_RAIL_MNA_BRANCH 1  /* modified nodal analysis (Sec. I): every non-ground node is an
+                                  unknown and every held node adds the current of its source as
+                                  an unknown (see eec_build_scatter) */
 
 /* Colouring algorithms. */
 #define EEC_COLOR_GREEDY_SEQ 0  /* host greedy in the given order */
@@ -86,6 +93,10 @@ typedef struct {
   int32_t host_chunks;   /* eec_eval_stamp_host: chunks whose charges are copied out while later
                             chunks are evaluated; 0 = by size (3 from 2^18 devices, 2 from 2^17,
                             else 1), or 1..64 */
+  int32_t rail_mode;     /* EEC_RAIL_*; default EEC_RAIL_ELIMINATE. EEC_RAIL_MNA_BRANCH makes the
+                            rails shared free nodes, so under EEC_CONFLICT_FREE_NODE all devices on
+                            one rail conflict (Table II: 896 colours for the 64-bit adder, one per
+                            PMOS). Not available for eec_upload_batch. */
 } eec_options;
 
 /* eec_options with every field at its default. */
@@ -143,12 +154,18 @@ EEC_API int eec_color(eec_ctx* ctx, const int32_t* order, int32_t algo, int32_t*
  * go to fixed entries of A and b). The pattern holds, over free nodes: the diagonal, resistor
  * pairs, and every (t, u) terminal pair of every device, the gate row included (symmetric).
  * Devices are laid out colour-major on the device (natural order when not coloured).
+ * Under EEC_RAIL_MNA_BRANCH the unknowns are the n_nodes - 1 non-ground nodes in node order,
+ * then one source current j_r per held node r (node_fixed, ground excepted) in node order;
+ * j_r flows from node r through its source to ground. Each adds the entries (r, j_r) = 1 (KCL
+ * at r) and (j_r, r) = 1 with b[j_r] = node_vfix[r] (the source equation v_r = node_vfix[r]);
+ * the diagonal (j_r, j_r) is in the pattern with value 0, and gshunt goes on node rows only.
  * Out: *n_unknowns, *nnz. Synchronous.
  */
 EEC_API int eec_build_scatter(eec_ctx* ctx, int32_t* n_unknowns, int64_t* nnz);
 
 /* Copy the pattern to caller arrays: row_ptr [n+1], col_idx [nnz], unk_of_node [n_nodes]
- * (unknown index of each node, -1 when fixed). Any of them may be NULL. */
+ * (unknown index of each node, -1 when fixed; under EEC_RAIL_MNA_BRANCH only ground is -1).
+ * Any of them may be NULL. */
 EEC_API int eec_get_pattern(const eec_ctx* ctx, int32_t* row_ptr, int32_t* col_idx,
                     int32_t* unk_of_node);
 

@@ -44,7 +44,7 @@ def _load():
             i32, i64, f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
             lib.ora_create.restype = P
             lib.ora_create.argtypes = [i32, P, P, i32, P, P, P, P, P, i32, P, P, i32, P, P, f64,
-                                       i32, P]
+                                       i32, P, i32]
             lib.ora_destroy.argtypes = [P]
             lib.ora_n_unknowns.restype = i32
             lib.ora_n_unknowns.argtypes = [P]
@@ -76,9 +76,12 @@ def _c(a, dt):
 
 
 class Oracle:
-    """Oracle context for one netlist (see ``netgen.Netlist``) and a card table."""
+    """Oracle context for one netlist (see ``netgen.Netlist``) and a card table.
 
-    def __init__(self, net, cards):
+    ``rail_mode`` 0 eliminates the held nodes; 1 is modified nodal analysis: every non-ground
+    node is an unknown, followed by one source-current unknown per held node in node order."""
+
+    def __init__(self, net, cards, rail_mode=0):
         lib = _load()
         self._keep = dict(
             fixed=_c(net.node_fixed, np.uint8), vfix=_c(net.node_vfix, np.float64),
@@ -93,7 +96,7 @@ class Oracle:
             int(k["fixed"].shape[0]), _p(k["fixed"]), _p(k["vfix"]), self.n_dev, _p(k["dev"]),
             _p(k["typ"]), _p(k["W"]), _p(k["L"]), _p(k["mid"]), int(k["rG"].shape[0]),
             _p(k["rn"]), _p(k["rG"]), int(k["sI"].shape[0]), _p(k["sn"]), _p(k["sI"]),
-            float(net.gshunt), int(k["cards"].shape[0]), _p(k["cards"]))
+            float(net.gshunt), int(k["cards"].shape[0]), _p(k["cards"]), int(rail_mode))
         if not self.h:
             raise ValueError("oracle rejected the netlist")
         self.lib = lib

@@ -16,6 +16,9 @@
 //    oracle implements the documented BSIM-style level EES-L1 (mode swap, body effect, softplus
 //    effective overdrive, mobility degradation, velocity saturation, smooth Vdseff, channel-length
 //    modulation, junction diodes, charge partition). Equations are restated next to the code.
+//  * Rails (nodes held by an ideal voltage source) are either eliminated (their voltages enter
+//    b) or, in modified nodal analysis (Sec. I builds on MNA), kept as unknowns with one extra
+//    unknown per source: its current, with the KCL entry at the rail and the source equation.
 //  * The DC Newton loop with a dense LU, the adjoint (transpose) solve and the gradient of a
 //    linear functional of (A, b) use no paper equation; they follow textbook definitions.
 //
@@ -315,6 +318,10 @@ struct Circuit {
   int n_nodes = 0;
   std::vector<uint8_t> fixed;
   std::vector<double> vfix;
+  // Modified nodal analysis: every held node but ground is an unknown; rail[r] is the r-th held
+  // node (in node order) and br[r] the unknown of its source current, which flows from the node
+  // through the source to ground.
+  std::vector<int> rail, br;
   int n_dev = 0;
   std::vector<int> dn;         // 4 per device: d, g, s, b
   std::vector<int> type;       // +1 / -1
@@ -343,8 +350,14 @@ void build_pattern(Circuit& c) {
   c.n = 0;
   for (int i = 0; i < c.n_nodes; ++i)
     if (!c.fixed[i]) c.unk[i] = c.n++;
+  c.br.assign(c.rail.size(), -1);
+  for (size_t r = 0; r < c.rail.size(); ++r) c.br[r] = c.n++;
   std::set<std::pair<int, int>> ent;
   for (int i = 0; i < c.n; ++i) ent.insert({i, i});
+  for (size_t r = 0; r < c.rail.size(); ++r) {
+    ent.insert({c.unk[c.rail[r]], c.br[r]});
+    ent.insert({c.br[r], c.unk[c.rail[r]]});
+  }
   for (size_t r = 0; r < c.rG.size(); ++r) {
     int a = c.unk[c.rn[2 * r]], b = c.unk[c.rn[2 * r + 1]];
     if (a >= 0 && b >= 0) { ent.insert({a, b}); ent.insert({b, a}); }
@@ -410,6 +423,16 @@ void stamp_linear(const Circuit& c, double* A, double* b, double* As, double* bs
     double I = c.sI[s];
     if (a >= 0) { b[a] -= I; if (bs) bs[a] += std::fabs(I); }
     if (bb >= 0) { b[bb] += I; if (bs) bs[bb] += std::fabs(I); }
+  }
+  // Voltage source of each rail: its current j joins the KCL sum of the rail node (+j leaves the
+  // node), and its own row states v_rail - 0 = vfix.
+  for (size_t r = 0; r < c.rail.size(); ++r) {
+    const int a = c.unk[c.rail[r]], j = c.br[r];
+    long p = c.where.at({a, j}), q = c.where.at({j, a});
+    A[p] += 1.0; if (As) As[p] += 1.0;
+    A[q] += 1.0; if (As) As[q] += 1.0;
+    b[j] += c.vfix[c.rail[r]];
+    if (bs) bs[j] += std::fabs(c.vfix[c.rail[r]]);
   }
 }
 
@@ -529,7 +552,8 @@ void stamp_all(const Circuit& c, const double* x, double* A, double* b, double* 
   }
 }
 
-// KCL residual F(x): net current leaving every free node (no linearisation).
+// KCL residual F(x): net current leaving every free node (no linearisation); on the row of a
+// source current, the source equation v_rail - vfix.
 void kcl_residual(const Circuit& c, const double* x, double* F) {
   std::fill(F, F + c.n, 0.0);
   for (int i = 0; i < c.n_nodes; ++i)
@@ -553,6 +577,11 @@ void kcl_residual(const Circuit& c, const double* x, double* F) {
       int a = c.unk[c.dn[4 * k + t]];
       if (a >= 0) F[a] += I[t];
     }
+  }
+  for (size_t r = 0; r < c.rail.size(); ++r) {
+    const int a = c.unk[c.rail[r]], j = c.br[r];
+    F[a] += x[j];
+    F[j] = x[a] - c.vfix[c.rail[r]];
   }
 }
 
@@ -647,14 +676,19 @@ void* ora_create(int32_t n_nodes, const uint8_t* node_fixed, const double* node_
                  int32_t n_dev, const int32_t* dev_nodes, const int8_t* dev_type, const double* W,
                  const double* L, const int32_t* model_id, int32_t n_res, const int32_t* res_nodes,
                  const double* res_G, int32_t n_isrc, const int32_t* isrc_nodes,
-                 const double* isrc_val, double gshunt, int32_t n_cards, const double* cards) {
+                 const double* isrc_val, double gshunt, int32_t n_cards, const double* cards,
+                 int32_t rail_mode) {
   if (n_nodes < 1 || n_dev < 0 || n_res < 0 || n_isrc < 0 || n_cards < 1) return nullptr;
+  if (rail_mode != 0 && rail_mode != 1) return nullptr;
   Circuit* c = new Circuit;
   c->n_nodes = n_nodes;
   c->fixed.assign(node_fixed, node_fixed + n_nodes);
   c->vfix.assign(node_vfix, node_vfix + n_nodes);
   c->fixed[0] = 1;
   c->vfix[0] = 0.0;
+  if (rail_mode == 1)
+    for (int i = 1; i < n_nodes; ++i)
+      if (c->fixed[i]) { c->rail.push_back(i); c->fixed[i] = 0; }
   c->n_dev = n_dev;
   c->dn.assign(dev_nodes, dev_nodes + 4L * n_dev);
   c->type.assign(dev_type, dev_type + n_dev);

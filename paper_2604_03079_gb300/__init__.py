@@ -32,6 +32,7 @@ EEC_N_VARIANTS = 5
 VARIANT_NAMES = {0: "color_fused", 1: "persistent", 2: "atomic", 3: "segreduce", 4: "color_buffered"}
 EEC_CONFLICT_FREE_NODE, EEC_CONFLICT_ANY_NONGROUND, EEC_CONFLICT_WRITE_ROWS = 0, 1, 2
 EEC_COLOR_GREEDY_SEQ, EEC_COLOR_JP_INDEX, EEC_COLOR_JP_RANDOM = 0, 1, 2
+EEC_RAIL_ELIMINATE, EEC_RAIL_MNA_BRANCH = 0, 1
 EEC_CARD_LEN = 21
 
 
@@ -39,7 +40,8 @@ EEC_CARD_LEN = 21
 class eec_options(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("block", ctypes.c_int32),
                 ("conflict_rule", ctypes.c_int32), ("debug_checks", ctypes.c_int32),
-                ("color_stamp", ctypes.c_int32), ("host_chunks", ctypes.c_int32)]
+                ("color_stamp", ctypes.c_int32), ("host_chunks", ctypes.c_int32),
+                ("rail_mode", ctypes.c_int32)]
 
 
 class eec_netlist(ctypes.Structure):
@@ -433,11 +435,12 @@ class Circuit:
     def __init__(self, net, cards, color: bool = True, variant: int = EEC_VARIANT_AUTO,
                  conflict_rule: int = EEC_CONFLICT_FREE_NODE, algo: int = EEC_COLOR_GREEDY_SEQ,
                  order=None, debug_checks: bool = False, batch: Optional[Sequence] = None,
-                 host_chunks: int = 0, color_stamp: int = 0):
+                 host_chunks: int = 0, color_stamp: int = 0,
+                 rail_mode: int = EEC_RAIL_ELIMINATE):
         import torch
         self.ctx = eec_create(variant=variant, conflict_rule=conflict_rule,
                               debug_checks=int(debug_checks), host_chunks=host_chunks,
-                              color_stamp=color_stamp)
+                              color_stamp=color_stamp, rail_mode=rail_mode)
         self.batch = batch
         if batch is not None:
             eec_upload_batch(self.ctx, batch, gshunt=batch[0].gshunt if batch else 1e-12)

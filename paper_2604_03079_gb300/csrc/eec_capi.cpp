@@ -31,6 +31,7 @@ struct eec_ctx {
   int n_nodes = 0;
   std::vector<uint8_t> fixed;
   std::vector<double> vfix;
+  std::vector<int> rail;       // EEC_RAIL_MNA_BRANCH: held nodes (now free), in node order
   int n_dev = 0;
   std::vector<int> dn;
   std::vector<int8_t> type;
@@ -578,6 +579,14 @@ int store_netlist(eec_ctx* c, int32_t n_nodes, const uint8_t* node_fixed, const 
   c->vfix.assign(node_vfix, node_vfix + n_nodes);
   c->fixed[0] = 1;
   c->vfix[0] = 0.0;
+  // modified nodal analysis: a held node becomes an unknown and its source current another one
+  c->rail.clear();
+  if (c->opt.rail_mode == EEC_RAIL_MNA_BRANCH)
+    for (int i = 1; i < n_nodes; ++i)
+      if (c->fixed[i]) {
+        c->rail.push_back(i);
+        c->fixed[i] = 0;
+      }
   c->n_dev = n_dev;
   c->dn.assign(dev_nodes, dev_nodes + 4LL * n_dev);
   c->type.assign(dev_type, dev_type + n_dev);
@@ -611,6 +620,7 @@ eec_options eec_default_options(void) {
   o.debug_checks = 0;
   o.color_stamp = 0;
   o.host_chunks = 0;
+  o.rail_mode = EEC_RAIL_ELIMINATE;
   return o;
 }
 
@@ -623,7 +633,7 @@ int eec_create(eec_ctx** out, const eec_options* opt) {
   if (c->opt.variant < EEC_VARIANT_AUTO || c->opt.variant >= EEC_N_VARIANTS ||
       c->opt.conflict_rule < 0 || c->opt.conflict_rule > 2 || c->opt.host_chunks < 0 ||
       c->opt.color_stamp < 0 || c->opt.color_stamp > 3 ||
-      c->opt.host_chunks > 64 ||
+      c->opt.host_chunks > 64 || c->opt.rail_mode < 0 || c->opt.rail_mode > 1 ||
       !(c->opt.block == 0 || c->opt.block == 8 || c->opt.block == 16 ||
         (c->opt.block % 32 == 0 && c->opt.block <= 128))) {
     delete c;
@@ -662,6 +672,8 @@ int eec_upload_netlist(eec_ctx* c, int32_t n_nodes, const uint8_t* node_fixed,
 int eec_upload_batch(eec_ctx* c, int32_t n_circ, const eec_netlist* nets, double gshunt) {
   if (!c) return EEC_EINVAL;
   if (n_circ < 1 || !nets) return fail(c, EEC_EINVAL, "empty batch");
+  if (c->opt.rail_mode != EEC_RAIL_ELIMINATE)
+    return fail(c, EEC_EINVAL, "batched uploads take EEC_RAIL_ELIMINATE only");
   long long nodes = 1, devs = 0, res = 0, src = 0;
   for (int k = 0; k < n_circ; ++k) {
     const eec_netlist& m = nets[k];
@@ -827,6 +839,9 @@ int eec_build_scatter(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_out) {
       c->unk[i] = n++;
     }
   }
+  const int n_node_unk = n;
+  std::vector<int> jr(c->rail.size());   // source-current unknown of each rail
+  for (size_t r = 0; r < c->rail.size(); ++r) jr[r] = n++;
   c->n = n;
   // pattern: sorted unique (row, col) keys
   std::vector<uint64_t> keys;
@@ -846,6 +861,10 @@ int eec_build_scatter(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_out) {
         if (bb >= 0) keys.push_back(key(a, bb));
       }
     }
+  for (size_t r = 0; r < c->rail.size(); ++r) {
+    keys.push_back(key(c->unk[c->rail[r]], jr[r]));
+    keys.push_back(key(jr[r], c->unk[c->rail[r]]));
+  }
   std::sort(keys.begin(), keys.end());
   keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
   c->nnz = (long long)keys.size();
@@ -906,9 +925,10 @@ int eec_build_scatter(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_out) {
       for (int u = 0; u < 4; ++u)
         if (ti[u] >= 0) slot_g[(size_t)u * N + p] = find(ti[1], ti[u]);
   }
-  // linear part, summed in the natural element order: gshunt, resistors, current sources
+  // linear part, summed in the natural element order: gshunt, resistors, current sources, then
+  // the voltage sources of the rails (modified nodal analysis only)
   std::vector<double> Alin(c->nnz, 0.0), blin(n, 0.0);
-  for (int i = 0; i < n; ++i) Alin[find(i, i)] += c->gshunt;
+  for (int i = 0; i < n_node_unk; ++i) Alin[find(i, i)] += c->gshunt;
   for (size_t r = 0; r < c->rG.size(); ++r) {
     const int ni = c->rn[2 * r], nj = c->rn[2 * r + 1];
     const int a = c->unk[ni], bb = c->unk[nj];
@@ -928,6 +948,12 @@ int eec_build_scatter(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_out) {
     const int a = c->unk[c->sn[2 * s]], bb = c->unk[c->sn[2 * s + 1]];
     if (a >= 0) blin[a] -= c->sI[s];
     if (bb >= 0) blin[bb] += c->sI[s];
+  }
+  for (size_t r = 0; r < c->rail.size(); ++r) {
+    const int a = c->unk[c->rail[r]];
+    Alin[find(a, jr[r])] += 1.0;     // KCL at the rail: the source current leaves the node
+    Alin[find(jr[r], a)] += 1.0;     // source equation: v_rail = its voltage
+    blin[jr[r]] += c->vfix[c->rail[r]];
   }
   // segmented-reduction map: contributions per entry in original device order
   const long long E = c->nnz + n;

@@ -43,7 +43,7 @@ int main(void) {
   card(cards + EEC_CARD_LEN, 0);
 
   eec_options opt = eec_default_options();
-  if (opt.variant != EEC_VARIANT_AUTO || opt.block != 0) return 1;
+  if (opt.variant != EEC_VARIANT_AUTO || opt.block != 0 || opt.rail_mode != EEC_RAIL_ELIMINATE) return 1;
   eec_ctx* ctx = NULL;
   if (eec_create(&ctx, &opt) != EEC_OK || !ctx) return 2;
   if (eec_upload_netlist(ctx, n_nodes, fixed, vfix, 6, dn, type, W, L, mid, 0, NULL, NULL, 0,
