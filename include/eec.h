@@ -91,8 +91,9 @@ typedef struct {
                             grid with a grid barrier between colours, 3 = one 8-block thread-block
                             cluster with the cluster barrier between colours */
   int32_t host_chunks;   /* eec_eval_stamp_host: chunks whose charges are copied out while later
-                            chunks are evaluated; 0 = by size (3 from 2^18 devices, 2 from 2^17,
-                            else 1), or 1..64 */
+                            chunks are evaluated, each half the size of the one before; 0 = by
+                            size (4 from 2^18 devices, 3 from 2^17, 2 from 2^16, else 1), or
+                            1..64 */
   int32_t rail_mode;     /* EEC_RAIL_*; default EEC_RAIL_ELIMINATE. EEC_RAIL_MNA_BRANCH makes the
                             rails shared free nodes, so under EEC_CONFLICT_FREE_NODE all devices on
                             one rail conflict (Table II: 896 colours for the 64-bit adder, one per
@@ -217,9 +218,10 @@ EEC_API int eec_eval_stamp(eec_ctx* ctx, const double* x_dev, double* A_values_d
  * (nullable) out, layouts as in eec_eval_stamp. The library copies x into its own device
  * buffer, evaluates and stamps into its own device buffers (allocated on the first call), and
  * copies A, b and q back. Under the order-free schedules (ATOMIC, SEGREDUCE) the devices are
- * evaluated in opt.host_chunks spans of original index, and each span's charges are copied on a
- * library stream while the next span is evaluated; the call joins that stream back into
- * cuda_stream. Page-locked buffers (cudaHostAlloc / cudaHostRegister) make every copy
+ * evaluated in opt.host_chunks spans of original index (each half the size of the one before),
+ * launched alternately on cuda_stream and a library stream so that no launch's tail leaves the
+ * SMs idle, and each span's charges are copied on another library stream while the next span is
+ * evaluated; the call joins those streams back into cuda_stream. Page-locked buffers (cudaHostAlloc / cudaHostRegister) make every copy
  * asynchronous; pageable ones work but the call returns only once their copies are done.
  * Stream-ordered on cuda_stream: the host outputs are valid once the stream has synchronised.
  * Calls on one context share the staging buffers, so calls that overlap on the GPU (unordered

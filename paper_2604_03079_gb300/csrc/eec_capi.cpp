@@ -97,6 +97,7 @@ struct eec_ctx {
   int* d_hrbeg = nullptr;
   int* d_hroff = nullptr;
   cudaStream_t side = nullptr;   // charge copies of eec_eval_stamp_host
+  cudaStream_t side2 = nullptr;  // second evaluation stream of eec_eval_stamp_host
   // launch order of the order-free evaluations: layout ranges, devices with a free source or
   // body first (eval_nr = 0: plain layout order)
   int eval_nr = 0;
@@ -112,7 +113,7 @@ struct eec_ctx {
   double* d_y = nullptr;
   void* sp_buf = nullptr;
   unsigned long long* d_nstats = nullptr;
-  std::vector<cudaEvent_t> hev;  // chunk done (K) + side stream done (1)
+  std::vector<cudaEvent_t> hev;  // chunk done (K) + side stream done (1) + start of the chunks (1)
 };
 
 namespace {
@@ -418,15 +419,17 @@ int run_variant(eec_ctx* c, int v, const double* x, double* A, double* b, double
 // Chunk plan of eec_eval_stamp_host. The layout is colour-major, then grouped by card and
 // polarity, then in original order, so library positions form maximal runs of increasing
 // original index; within a run, the devices of an original-index span are contiguous. Chunk k
-// (original indices N k / K .. N (k+1) / K - 1) is one range per run. K = opt.host_chunks, or
-// by size: 3 from 2^18 devices, 2 from 2^17, else 1 (each extra launch ends in a partial wave
-// that costs about as much as a third of the charge copy it hides); 1 when the runs are too
-// many (> 4096).
+// is a span of original indices, one range per run. Chunk sizes halve from one chunk to the
+// next (weights 2^(K-1-k)): the charges of a chunk (32 B per device at the link's 189 GB/s)
+// copy out in less time than the next chunk, half its size, takes to evaluate (about 0.41 ns
+// per device), and the last chunk, whose charges go out after the evaluation together with A
+// and b, is the smallest. K = opt.host_chunks, or by size: 4 from 2^18 devices, 3 from 2^17,
+// 2 from 2^16, else 1; 1 when the runs are too many (> 4096).
 int host_plan(eec_ctx* c) {
   if (c->host_K) return EEC_OK;
   const int N = c->n_dev;
   int K = c->opt.host_chunks;
-  if (K == 0) K = N >= (1 << 18) ? 3 : N >= (1 << 17) ? 2 : 1;
+  if (K == 0) K = N >= (1 << 18) ? 4 : N >= (1 << 17) ? 3 : N >= (1 << 16) ? 2 : 1;
   if (K > N) K = N > 0 ? N : 1;
   std::vector<int> run{0};
   for (int p = 1; p < N; ++p)
@@ -438,7 +441,11 @@ int host_plan(eec_ctx* c) {
   c->hc_ro.assign(K, 0);
   c->hc_nr.assign(K, 0);
   c->hc_total.assign(K, 0);
-  for (int k = 0; k <= K; ++k) c->hc_lo[k] = (int)((long long)N * k / K);
+  // boundary k at the fraction (1 - 2^-k) / (1 - 2^-K) of the devices
+  for (int k = 0; k < K; ++k)
+    c->hc_lo[k] = (int)std::floor((double)N * (1.0 - std::ldexp(1.0, -k)) /
+                                  (1.0 - std::ldexp(1.0, -K)));
+  c->hc_lo[K] = N;
   std::vector<int> rbeg, roff;
   const int* P = c->perm.data();
   for (int k = 0; k < K; ++k) {
@@ -649,6 +656,7 @@ void eec_destroy(eec_ctx* c) {
   if (c->d_status) cudaFree(c->d_status);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->side) cudaStreamDestroy(c->side);
+  if (c->side2) cudaStreamDestroy(c->side2);
   if (c->sp_descr) cusparseDestroyMatDescr(c->sp_descr);
   if (c->sp) cusolverSpDestroy(c->sp);
   for (cudaEvent_t e : c->hev) cudaEventDestroy(e);
@@ -1272,7 +1280,8 @@ int eec_eval_stamp_host(eec_ctx* c, const double* x_host, double* A_host, double
     return EEC_OK;
   }
   if (!c->side) CUDA_TRY(c, cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
-  while ((int)c->hev.size() < K + 1) {
+  if (!c->side2) CUDA_TRY(c, cudaStreamCreateWithFlags(&c->side2, cudaStreamNonBlocking));
+  while ((int)c->hev.size() < K + 2) {
     cudaEvent_t e = nullptr;
     CUDA_TRY(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     c->hev.push_back(e);
@@ -1287,14 +1296,24 @@ int eec_eval_stamp_host(eec_ctx* c, const double* x_host, double* A_host, double
     if ((rc = ensure_buf(c))) return rc;
     mode = MODE_BUFFER;
   }
-  // every launch first, then the copies (a copy to pageable memory returns only when done)
+  // Every launch first, then the copies (a copy to pageable memory returns only when done).
+  // The chunks alternate between two streams: launched one after the other on one stream, each
+  // would end in a partial wave (the last warps' dependent FP64 chain, several microseconds)
+  // with the SMs idle; on two streams the next chunk's blocks take the SMs the previous chunk
+  // frees. Blocks are dispatched in launch order, so the chunks still finish in order.
+  CUDA_TRY(c, cudaEventRecord(c->hev[K + 1], s));
+  CUDA_TRY(c, cudaStreamWaitEvent(c->side2, c->hev[K + 1], 0));
   for (int k = 0; k < K; ++k) {
+    cudaStream_t sk = (k & 1) ? c->side2 : s;
     CUDA_TRY(c, launch_eval_ranges(c->d, mode, c->d_hrbeg + c->hc_rb[k], c->d_hroff + c->hc_ro[k],
                                    c->hc_nr[k], c->hc_total[k], c->h_x, c->h_A, c->h_b, c->h_q,
-                                   blk, dbg, s, /*pdl=*/k == 0 && mode == MODE_ATOMIC));
+                                   blk, dbg, sk));
     c->n_kernels += c->hc_total[k] > 0;
-    CUDA_TRY(c, cudaEventRecord(c->hev[k], s));
+    CUDA_TRY(c, cudaEventRecord(c->hev[k], sk));
   }
+  // the stream of the call waits for the chunks of the second stream (the last one suffices)
+  const int last_odd = ((K - 1) & 1) ? K - 1 : K - 2;
+  if (last_odd >= 1) CUDA_TRY(c, cudaStreamWaitEvent(s, c->hev[last_odd], 0));
   if (mode == MODE_BUFFER) {
     CUDA_TRY(c, launch_gather(c->d, c->h_A, c->h_b, s));
     c->n_kernels += (c->nnz + c->n > 0);
@@ -1304,9 +1323,9 @@ int eec_eval_stamp_host(eec_ctx* c, const double* x_host, double* A_host, double
     CUDA_TRY(c, cudaStreamWaitEvent(c->side, c->hev[k], 0));
     const size_t lo = (size_t)c->hc_lo[k], cnt = (size_t)(c->hc_lo[k + 1] - c->hc_lo[k]);
     if (!cnt) continue;
-    for (int t = 0; t < 4; ++t)
-      CUDA_TRY(c, cudaMemcpyAsync(q_host + t * N + lo, c->h_q + t * N + lo, sizeof(double) * cnt,
-                                  cudaMemcpyDeviceToHost, c->side));
+    // the chunk's span of each of the four terminal rows, as one strided copy
+    CUDA_TRY(c, cudaMemcpy2DAsync(q_host + lo, sizeof(double) * N, c->h_q + lo, sizeof(double) * N,
+                                  sizeof(double) * cnt, 4, cudaMemcpyDeviceToHost, c->side));
   }
   CUDA_TRY(c, cudaMemcpyAsync(A_host, c->h_A, sizeof(double) * c->nnz, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(c, cudaMemcpyAsync(b_host, c->h_b, sizeof(double) * c->n, cudaMemcpyDeviceToHost, s));
