@@ -386,6 +386,20 @@ typedef struct {
 
 EEC_API int eec_upload_batch(eec_ctx* ctx, int32_t n_circ, const eec_netlist* nets, double gshunt);
 
+/* A batched context in one call: eec_create(opt) then eec_upload_batch of the circuits
+ * *nets[0] .. *nets[n_circ-1] (an array of pointers; each eec_netlist is copied). On failure
+ * *out is NULL and nothing is left allocated. */
+EEC_API int eec_batch_create(eec_ctx** out, int32_t n_circ, const eec_netlist* const* nets,
+                             double gshunt, const eec_options* opt);
+
+/* From this call on, eec_eval_stamp on ctx replays one CUDA graph of the whole step for every
+ * schedule (the colour schedules always do): the graph is captured at the first call with a
+ * given x, A, b, q and re-captured when those pointers, the schedule, the block size or the
+ * launch order change. The batched pipeline of many small circuits is launch-bound, and a
+ * replay issues the step's kernels as one submission. cuda_stream (nullable) is synchronised
+ * first, so that no launch of the context is in flight while the mode changes. */
+EEC_API int eec_batch_capture_graph(eec_ctx* ctx, void* cuda_stream);
+
 /* After eec_build_scatter on a batch: circ_row_off [n_circ+1], circ_nnz_off [n_circ+1],
  * circ_dev_off [n_circ+1] (first device of each circuit in original order). */
 EEC_API int eec_get_batch_offsets(const eec_ctx* ctx, int32_t* circ_row_off, int64_t* circ_nnz_off,

@@ -88,6 +88,10 @@ _SIG = {
                                      ctypes.POINTER(_I64), ctypes.POINTER(_I32)]),
     "eec_upload_batch": (ctypes.c_int, [_P, _I32, ctypes.POINTER(eec_netlist), _F64]),
     "eec_get_batch_offsets": (ctypes.c_int, [_P, _P, _P, _P]),
+    "eec_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), _I32,
+                                        ctypes.POINTER(ctypes.POINTER(eec_netlist)), _F64,
+                                        ctypes.POINTER(eec_options)]),
+    "eec_batch_capture_graph": (ctypes.c_int, [_P, _P]),
     "eec_fp64_peak": (ctypes.c_int, [_I32, _I32, ctypes.POINTER(_F64)]),
     "eec_math_check": (ctypes.c_int, [_I32, _I64, _P, _P, _P, _P]),
     "eec_test_barrier_timeout": (ctypes.c_int, [_P, _P, _P, _P, _P]),
@@ -201,7 +205,9 @@ def eec_upload_netlist(ctx, node_fixed, node_vfix, dev_nodes, dev_type, W, L, mo
                                        rg.size, prn, prg, sv.size, psn, psv, float(gshunt)))
 
 
-def eec_upload_batch(ctx, nets: Sequence, gshunt=1e-12):
+def _netlist_array(nets: Sequence):
+    """ctypes array of eec_netlist over the circuits' arrays (returned with the arrays it
+    points into, which must stay alive for the call)."""
     keep, arr = [], (eec_netlist * len(nets))()
     for i, net in enumerate(nets):
         parts = [_h(net.node_fixed, np.uint8), _h(net.node_vfix, np.float64),
@@ -219,7 +225,32 @@ def eec_upload_batch(ctx, nets: Sequence, gshunt=1e-12):
         m.res_nodes, m.res_G = parts[7][1], parts[8][1]
         m.n_isrc = parts[10][0].size
         m.isrc_nodes, m.isrc_val = parts[9][1], parts[10][1]
+    return arr, keep
+
+
+def eec_upload_batch(ctx, nets: Sequence, gshunt=1e-12):
+    arr, keep = _netlist_array(nets)
     _check(ctx, _load().eec_upload_batch(ctx, len(nets), arr, float(gshunt)))
+
+
+def eec_batch_create(nets: Sequence, gshunt=1e-12, opt: Optional[eec_options] = None, **kw):
+    """Batched context in one call (eec_create + eec_upload_batch); options as eec_create."""
+    o = eec_default_options() if opt is None else opt
+    for k, v in kw.items():
+        setattr(o, k, int(v))
+    arr, keep = _netlist_array(nets)
+    ptrs = (ctypes.POINTER(eec_netlist) * len(nets))(*[ctypes.pointer(arr[i])
+                                                        for i in range(len(nets))])
+    h = _P()
+    rc = _load().eec_batch_create(ctypes.byref(h), len(nets), ptrs, float(gshunt),
+                                  ctypes.byref(o))
+    if rc != EEC_OK:
+        raise EECError(rc, "eec_batch_create failed")
+    return h
+
+
+def eec_batch_capture_graph(ctx, stream=None):
+    _check(ctx, _load().eec_batch_capture_graph(ctx, _stream(stream)))
 
 
 def eec_set_model_cards(ctx, cards):

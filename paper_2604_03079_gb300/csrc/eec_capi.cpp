@@ -79,6 +79,7 @@ struct eec_ctx {
   int stamp_mode = 0;          // colour-buffered stamp: 0 per-colour launches, 1 grid, 2 cluster
   // phase timing and launch counting
   bool prof = false;
+  bool graph_all = false;      // eec_batch_capture_graph: every schedule replays a cached graph
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
   long long prof_calls = 0;
@@ -515,7 +516,8 @@ struct NvtxRange {
 int eval_with(eec_ctx* c, int v, const double* x, double* A, double* b, double* q,
               cudaStream_t s) {
   NvtxRange range("eec/eval_stamp");
-  if (!c->prof && (v == EEC_VARIANT_COLOR_FUSED || v == EEC_VARIANT_COLOR_BUFFERED)) {
+  if (!c->prof &&
+      (c->graph_all || v == EEC_VARIANT_COLOR_FUSED || v == EEC_VARIANT_COLOR_BUFFERED)) {
     const void* key[4] = {x, A, b, q};
     const int blk = c->opt.block ? c->opt.block : c->tuned_block;
     bool hit = c->auto_exec && c->auto_variant == v && c->auto_block == blk &&
@@ -1519,6 +1521,35 @@ int eec_graph_capture(eec_ctx* c, const double* x, double* A, double* b, double*
   // Order the capture after the caller's pending work on `stream` (nothing runs during capture).
   if (stream) CUDA_TRY(c, cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
   return capture(c, effective_variant(c), x, A, b, q, &c->user_exec, &c->user_kernels);
+}
+
+int eec_batch_create(eec_ctx** out, int32_t n_circ, const eec_netlist* const* nets,
+                     double gshunt, const eec_options* opt) {
+  if (!out) return EEC_EINVAL;
+  *out = nullptr;
+  if (n_circ < 1 || !nets) return EEC_EINVAL;
+  std::vector<eec_netlist> flat((size_t)n_circ);
+  for (int k = 0; k < n_circ; ++k) {
+    if (!nets[k]) return EEC_EINVAL;
+    flat[k] = *nets[k];
+  }
+  eec_ctx* c = nullptr;
+  int rc = eec_create(&c, opt);
+  if (rc) return rc;
+  if ((rc = eec_upload_batch(c, n_circ, flat.data(), gshunt))) {
+    eec_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return EEC_OK;
+}
+
+int eec_batch_capture_graph(eec_ctx* c, void* stream) {
+  if (!c) return EEC_EINVAL;
+  // no launch of the context may be in flight on the caller's stream while the mode changes
+  if (stream) CUDA_TRY(c, cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  c->graph_all = true;
+  return EEC_OK;
 }
 
 int eec_graph_launch(eec_ctx* c, void* stream) {

@@ -205,6 +205,37 @@ def test_batch_offsets_host(eec):
         eec.eec_destroy(ctx)
 
 
+def test_batch_create_equals_create_and_upload(eec):
+    nets = netgen.batch_circuits(9, seed=4)
+    merged = netgen.concat(nets)
+    pats = []
+    for make in (lambda: eec.eec_batch_create(nets, gshunt=1e-12),
+                 lambda: _upload_batch(eec, nets)):
+        ctx = make()
+        try:
+            eec.eec_set_model_cards(ctx, netgen.default_cards())
+            eec.eec_color(ctx, n_dev=merged.n_dev)
+            try:
+                eec.eec_build_scatter(ctx)
+            except eec.EECError as e:
+                assert e.code == eec.EEC_ECUDA
+            pats.append(eec.eec_get_pattern(ctx, merged.n_nodes))
+        finally:
+            eec.eec_destroy(ctx)
+    for a, b in zip(*pats):
+        assert np.array_equal(a, b)
+    with pytest.raises(eec.EECError):
+        eec.eec_batch_create([], gshunt=1e-12)
+    with pytest.raises(eec.EECError):     # batched contexts take the eliminated rails only
+        eec.eec_batch_create(nets, rail_mode=eec.EEC_RAIL_MNA_BRANCH)
+
+
+def _upload_batch(eec, nets):
+    ctx = eec.eec_create()
+    eec.eec_upload_batch(ctx, nets)
+    return ctx
+
+
 def test_autograd_function_is_exposed(eec):
     import torch
     assert issubclass(eec.EvalStamp, torch.autograd.Function)

@@ -354,6 +354,38 @@ def test_graph_capture_and_autotune(eec):
         assert rel_err(host(b), r["b"], r["b_scale"]).max() <= TOL
 
 
+def test_batch_capture_graph_replays_every_schedule(eec):
+    # after eec_batch_capture_graph, eec_eval_stamp replays a cached graph for every schedule,
+    # re-captured when the buffers or the schedule change
+    import torch
+    nets = netgen.batch_circuits(64, seed=6)
+    merged = netgen.concat(nets)
+    o = oracle.Oracle(merged, CARDS)
+    ctx = eec.eec_batch_create(nets, gshunt=merged.gshunt)
+    try:
+        eec.eec_set_model_cards(ctx, CARDS)
+        eec.eec_color(ctx, n_dev=merged.n_dev)
+        n, nnz = eec.eec_build_scatter(ctx)
+        eec.eec_batch_capture_graph(ctx, torch.cuda.current_stream())
+        for seed in (1, 2):
+            x = netgen.random_x(merged, seed=seed)
+            r = o.eval_stamp(x, want_scale=True)
+            xt = dev(x)
+            A = torch.empty(nnz, dtype=torch.float64, device="cuda")
+            b = torch.empty(n, dtype=torch.float64, device="cuda")
+            for v in ALL_VARIANTS:
+                eec.eec_set_variant(ctx, v)
+                for _ in range(2):                  # capture, then replay
+                    A.fill_(7.0)
+                    b.fill_(7.0)
+                    eec.eec_eval_stamp(ctx, xt, A, b, None)
+                    assert eec.eec_status(ctx) == 0
+                    assert rel_err(host(A), r["A"], r["A_scale"]).max() <= TOL, v
+                    assert rel_err(host(b), r["b"], r["b_scale"]).max() <= TOL, v
+    finally:
+        eec.eec_destroy(ctx)
+
+
 def test_grid_barrier_timeout_is_reported_and_the_context_recovers(eec):
     # One block never arrives: the other blocks give up after their bounded wait (about 1 s),
     # record EEC_ETIMEOUT in the status word and return; nothing hangs or faults.
