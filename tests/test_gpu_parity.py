@@ -101,6 +101,21 @@ def test_edge_cases(eec, variant):
             check_against_oracle(eec, circ, o, x, variant)
 
 
+@pytest.mark.parametrize("variant", [0, 2, 3])
+@pytest.mark.parametrize("make", [lambda: netgen.sram(16, 16), netgen.ota5t,
+                                  lambda: netgen.random_logic(500, seed=2)])
+def test_wide_bias(eec, variant, make):
+    # node voltages far outside the rails: forward-biased junctions past the exponent limit
+    # (v / Vt > 40, the linear continuation), reverse-mode channels, deep subthreshold and strong
+    # inversion in one launch
+    net = make()
+    o = oracle.Oracle(net, CARDS)
+    circ = eec.Circuit(net, CARDS, color=True)
+    for s in range(3):
+        x = netgen.random_x(net, seed=40 + s, lo=-3.0, hi=4.0)
+        check_against_oracle(eec, circ, o, x, variant)
+
+
 @pytest.fixture(scope="module")
 def sram_full():
     net = netgen.config(2)
@@ -204,6 +219,23 @@ def test_backward_matches_oracle_nested_duals(eec, make):
     circ = eec.Circuit(net, CARDS)
     rng = netgen.Rng(11, 3)
     x = netgen.random_x(net, seed=5)
+    gA = rng.normal(circ.nnz)
+    gb = rng.normal(circ.n)
+    gx, gW, gL = circ.bwd(dev(x), dev(gA), dev(gb))
+    ox, oW, oL = o.eval_stamp_grad(x, gA, gb)
+    _grad_close(host(gx), ox)
+    _grad_close(host(gW), oW)
+    _grad_close(host(gL), oL)
+
+
+@pytest.mark.parametrize("make", [lambda: netgen.sram(8, 8), netgen.ota5t])
+def test_backward_at_wide_bias(eec, make):
+    # the backward through the exponent-limited junction branch and reverse-mode channels
+    net = make()
+    o = oracle.Oracle(net, CARDS)
+    circ = eec.Circuit(net, CARDS)
+    rng = netgen.Rng(21, 3)
+    x = netgen.random_x(net, seed=44, lo=-3.0, hi=4.0)
     gA = rng.normal(circ.nnz)
     gb = rng.normal(circ.n)
     gx, gW, gL = circ.bwd(dev(x), dev(gA), dev(gb))
