@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 METRIC = "MOSFET eval+stamp/s per NR iter (FP64, 1xGB300)"
 UNIT = "device evals+stamps/s"
 # Per-device work of the evaluate kernel under the atomic schedule, per workload, from ncu's
-# counters of one launch (profiles/k_eval_atomic_sram_256x256.md, k_eval_atomic_workloads.md):
+# counters of one launch (profiles/k_eval_atomic_sram_256x256.md, k_eval_atomic_random_logic_1M.md):
 # FP64 flop = 2 DFMA + DADD + DMUL thread instructions per device, and DRAM bytes read +
 # written per device. The flop count depends on the device mix (devices whose source and body
 # are source-held skip the body-effect and source-junction work).

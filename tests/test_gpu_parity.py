@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path through the C ABI against the oracle, element by element.
 
-Tolerance (stated by the task for A and b): per entry |gpu - oracle| / max(|oracle|, S_e) <= 1e-12,
+Tolerance for A and b: per entry |gpu - oracle| / max(|oracle|, S_e) <= 1e-12,
 where S_e is the sum of |contribution| into that entry (the oracle accumulates it), so rows whose
 terms cancel are judged against the size of their terms. Charges: per device relative to the
 largest terminal charge of that device. Colourings: bit-exact. Gradients: 1e-8 relative to
