@@ -41,8 +41,8 @@ FP64_FLOP_PER_DEVICE = {("sram", 0): 277.5, ("logic", 0): 267.2, ("logic1m", 0):
                         ("batch", 0): 246.8, ("sram", 1): 280.5, ("logic", 1): 270.2,
                         ("logic1m", 1): 270.2, ("batch", 1): 249.8}
 DRAM_BYTES_PER_DEVICE = {("sram", 0): 192.0, ("logic", 0): 237.8, ("logic1m", 0): 278.2,
-                         ("batch", 0): 384.5, ("sram", 1): 191.8, ("logic", 1): 243.6,
-                         ("logic1m", 1): 291.3, ("batch", 1): 383.3}
+                         ("batch", 0): 384.5, ("sram", 1): 191.3, ("logic", 1): 243.7,
+                         ("logic1m", 1): 291.0, ("batch", 1): 383.0}
 # GB300: 152 SMs x 2 FP64 FMA per clock per SM x 2 flop x 2070 MHz maximum SM clock.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
