@@ -241,12 +241,15 @@ EEC_API int eec_eval_stamp_host(eec_ctx* ctx, const double* x_host, double* A_ho
  * max|y - x|); step_rule 1 clips every node's move to [-vstep, vstep] on its own (long chains of
  * gates converge in far fewer iterations).
  * Converged when max|dx| <= tol_abs + tol_rel max|x| and, at the next iterate, the KCL residual
- * max|A x - b| = max|F(x)| <= tol_f amperes.
+ * max|A x - b| = max|F(x)| <= tol_f amperes. When max_iter solves do not converge, the loop
+ * restarts from the starting point with gshunt stepping: a shunt conductance g from every node
+ * to ground, g = 1e-3 S, converged, then g / 10 from that solution, down to the netlist's
+ * gshunt, then the circuit itself (each stage with max_iter solves).
  *  x_dev       [n] in: starting point (free-node voltages), out: the last iterate.
  *  A_dev, b_dev  [nnz], [n] workspace; out: the stamp at the returned x.
- *  iters_out   (nullable) solves performed.
- * Returns EEC_OK, EEC_ENOCONV (max_iter solves without meeting both tests: x holds the last
- * iterate), EEC_ENUMERIC (a non-finite step or residual, or a singular matrix) or
+ *  iters_out   (nullable) solves performed, over all stages.
+ * Returns EEC_OK, EEC_ENOCONV (a stage ran max_iter solves without meeting both tests: x holds
+ * its last iterate), EEC_ENUMERIC (a non-finite step or residual, or a singular matrix) or
  * EEC_ENOMEM. Meant for netlists up to tens of thousands of unknowns (solver 0 checks its
  * factor's size before allocating). Synchronises cuda_stream once per iteration.
  */

@@ -344,7 +344,8 @@ def eec_eval_stamp(ctx, x, A, b, q=None, stream=None):
 
 def eec_newton_dc(ctx, x, A, b, max_iter=200, vstep=0.2, step_rule=0, solver=0, tol_abs=1e-12,
                   tol_rel=1e-9, tol_f=1e-12, stream=None) -> int:
-    """DC Newton on the GPU from x (updated in place); returns the number of solves.
+    """DC Newton on the GPU from x (updated in place), with gshunt stepping when it does not
+    converge; returns the number of solves.
     step_rule 0: the whole step scaled to vstep; 1: every node's move clipped to vstep.
     solver 0: batched sparse QR, analysis reused; 1: sparse QR after an AMD ordering."""
     it = _I32(0)

@@ -112,6 +112,8 @@ struct eec_ctx {
   int* d_rp = nullptr;
   int* d_col = nullptr;
   double* d_y = nullptr;
+  double* d_x0 = nullptr;        // starting point, kept for the gshunt-stepping restart
+  int* d_diag = nullptr;         // CSR position of the diagonal of every node row
   void* sp_buf = nullptr;
   unsigned long long* d_nstats = nullptr;
   std::vector<cudaEvent_t> hev;  // chunk done (K) + side stream done (1) + start of the chunks (1)
@@ -172,6 +174,8 @@ void free_topology(eec_ctx* c) {
   c->sp_info = nullptr;
   c->d_rp = c->d_col = nullptr;
   c->d_y = nullptr;
+  c->d_x0 = nullptr;
+  c->d_diag = nullptr;
   c->sp_buf = nullptr;
   c->d_nstats = nullptr;
   for (void* p : c->dmem) cudaFree(p);
@@ -1349,8 +1353,14 @@ int newton_setup(eec_ctx* c, const double* A) {
     cusparseSetMatIndexBase(c->sp_descr, CUSPARSE_INDEX_BASE_ZERO);
   }
   int rc;
+  const int n_node = c->n - (int)c->rail.size();
+  std::vector<int> diag(n_node);
+  for (int i = 0; i < n_node; ++i)
+    diag[i] = (int)(std::lower_bound(c->col.begin() + c->row_ptr[i],
+                                     c->col.begin() + c->row_ptr[i + 1], i) - c->col.begin());
   if ((rc = dupload(c, &c->d_rp, c->row_ptr)) || (rc = dupload(c, &c->d_col, c->col)) ||
-      (rc = dalloc(c, &c->d_y, c->n)) || (rc = dalloc(c, &c->d_nstats, 4)))
+      (rc = dalloc(c, &c->d_y, c->n)) || (rc = dalloc(c, &c->d_x0, c->n)) ||
+      (rc = dupload(c, &c->d_diag, diag)) || (rc = dalloc(c, &c->d_nstats, 4)))
     return rc;
   csrqrInfo_t info = nullptr;
   if (cusolverSpCreateCsrqrInfo(&info) != CUSOLVER_STATUS_SUCCESS)
@@ -1387,40 +1397,32 @@ double bits_to_double(unsigned long long u) {
   return d;
 }
 
-int eec_newton_dc(eec_ctx* c, double* x, double* A, double* b, int32_t max_iter, double vstep,
-                  int32_t step_rule, int32_t solver, double tol_abs, double tol_rel,
-                  double tol_f, int32_t* iters_out, void* stream) {
-  NvtxRange range("eec/newton_dc");
-  int rc = check_built(c);
-  if (rc) return rc;
-  if (!x || !A || !b || max_iter < 1 || !(vstep > 0.0) || step_rule < 0 || step_rule > 1 ||
-      solver < 0 || solver > 1 ||
-      !(tol_abs >= 0.0) ||
-      !(tol_rel >= 0.0) || !(tol_f >= 0.0))
-    return fail(c, EEC_EINVAL, "bad eec_newton_dc arguments");
-  if (c->nnz > 0x7fffffffLL) return fail(c, EEC_EINVAL, "pattern too large for the sparse solver");
-  if (iters_out) *iters_out = 0;
-  if (c->n == 0) return EEC_OK;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if ((rc = newton_setup(c, A))) return rc;
-  if (cusolverSpSetStream(c->sp, s) != CUSOLVER_STATUS_SUCCESS)
-    return fail(c, EEC_ECUDA, "cusolverSpSetStream failed");
+// One damped Newton run from x with g_extra added to the diagonal of every node row after each
+// stamp (0: the circuit itself). Returns EEC_OK, EEC_ENOCONV (x holds the last iterate) or an
+// error; *iters counts its solves.
+int newton_run(eec_ctx* c, double* x, double* A, double* b, int max_iter, double vstep,
+               int step_rule, int solver, double tol_abs, double tol_rel, double tol_f,
+               double g_extra, int* iters, cudaStream_t s) {
   const int v = effective_variant(c), n = c->n, nnz = (int)c->nnz;
+  const int n_node = n - (int)c->rail.size();
+  int rc;
   unsigned long long hs[4];
   bool small_step = false;
+  *iters = 0;
   for (int it = 0; it <= max_iter; ++it) {
     CUDA_TRY(c, cudaMemsetAsync(c->d_nstats, 0, 4 * sizeof(unsigned long long), s));
     if ((rc = eval_with(c, v, x, A, b, nullptr, s))) return rc;
+    if (g_extra > 0.0) {
+      CUDA_TRY(c, launch_add_diag(A, c->d_diag, n_node, g_extra, s));
+      ++c->n_kernels;
+    }
     if (small_step) {  // the residual at this iterate decides convergence (A x - b = F(x))
       CUDA_TRY(c, launch_residual_norm(c->d_rp, c->d_col, A, x, b, n, c->d_nstats, s));
       CUDA_TRY(c, cudaMemcpyAsync(hs, c->d_nstats, sizeof hs, cudaMemcpyDeviceToHost, s));
       CUDA_TRY(c, cudaStreamSynchronize(s));
       const double r = bits_to_double(hs[3]);
       if (!std::isfinite(r)) return fail(c, EEC_ENUMERIC, "non-finite KCL residual");
-      if (r <= tol_f) {
-        if (iters_out) *iters_out = it;
-        return EEC_OK;
-      }
+      if (r <= tol_f) return EEC_OK;
     }
     if (it == max_iter) break;
     if (solver == 0) {
@@ -1443,9 +1445,55 @@ int eec_newton_dc(eec_ctx* c, double* x, double* A, double* b, int32_t max_iter,
     if (!std::isfinite(dxm) || !std::isfinite(xm))
       return fail(c, EEC_ENUMERIC, "non-finite Newton step (singular matrix?)");
     small_step = dxm <= tol_abs + tol_rel * xm;
-    if (iters_out) *iters_out = it + 1;
+    *iters = it + 1;
   }
-  return fail(c, EEC_ENOCONV, "no convergence within max_iter iterations");
+  return EEC_ENOCONV;
+}
+
+int eec_newton_dc(eec_ctx* c, double* x, double* A, double* b, int32_t max_iter, double vstep,
+                  int32_t step_rule, int32_t solver, double tol_abs, double tol_rel,
+                  double tol_f, int32_t* iters_out, void* stream) {
+  NvtxRange range("eec/newton_dc");
+  int rc = check_built(c);
+  if (rc) return rc;
+  if (!x || !A || !b || max_iter < 1 || !(vstep > 0.0) || step_rule < 0 || step_rule > 1 ||
+      solver < 0 || solver > 1 ||
+      !(tol_abs >= 0.0) ||
+      !(tol_rel >= 0.0) || !(tol_f >= 0.0))
+    return fail(c, EEC_EINVAL, "bad eec_newton_dc arguments");
+  if (c->nnz > 0x7fffffffLL) return fail(c, EEC_EINVAL, "pattern too large for the sparse solver");
+  if (iters_out) *iters_out = 0;
+  if (c->n == 0) return EEC_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((rc = newton_setup(c, A))) return rc;
+  if (cusolverSpSetStream(c->sp, s) != CUSOLVER_STATUS_SUCCESS)
+    return fail(c, EEC_ECUDA, "cusolverSpSetStream failed");
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_x0, x, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, s));
+  int its = 0, total = 0;
+  rc = newton_run(c, x, A, b, max_iter, vstep, step_rule, solver, tol_abs, tol_rel, tol_f, 0.0,
+                  &its, s);
+  total += its;
+  if (rc == EEC_ENOCONV) {
+    // gshunt stepping (the oracle's fallback): restart from the starting point with a shunt of
+    // g = 1e-3 S on every node, converge, divide g by 10 and continue from that solution down
+    // to the circuit's own gshunt, then solve the circuit itself from there
+    CUDA_TRY(c, cudaMemcpyAsync(x, c->d_x0, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, s));
+    rc = EEC_OK;
+    for (double g = 1e-3; rc == EEC_OK && g > c->gshunt * 1.0000001; g *= 0.1) {
+      rc = newton_run(c, x, A, b, max_iter, vstep, step_rule, solver, tol_abs, tol_rel, tol_f,
+                      g - c->gshunt, &its, s);
+      total += its;
+    }
+    if (rc == EEC_OK) {
+      rc = newton_run(c, x, A, b, max_iter, vstep, step_rule, solver, tol_abs, tol_rel, tol_f,
+                      0.0, &its, s);
+      total += its;
+    }
+  }
+  if (iters_out) *iters_out = total;
+  if (rc == EEC_ENOCONV)
+    return fail(c, EEC_ENOCONV, "no convergence within max_iter iterations (gshunt stepping included)");
+  return rc;
 }
 
 int eec_eval_stamp_tran(eec_ctx* c, const double* x, const double* q_prev, const double* i_prev,

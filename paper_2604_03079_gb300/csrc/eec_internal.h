@@ -132,6 +132,8 @@ cudaError_t launch_newton_step(const double* y, double* x, int n, double vstep, 
 cudaError_t launch_residual_norm(const int* rp, const int* col, const double* A, const double* x,
                                  const double* b, int n, unsigned long long* stats,
                                  cudaStream_t s);
+// A[diag[i]] += g, i < n (the gshunt-stepping homotopy of eec_newton_dc)
+cudaError_t launch_add_diag(double* A, const int* diag, int n, double g, cudaStream_t s);
 // Transient companion stamp (mode MODE_RMW over one colour range, MODE_ATOMIC over all, or
 // MODE_BUFFER over all into buf_tran).
 struct TranArgs {

@@ -72,6 +72,15 @@ __global__ void __launch_bounds__(kNewtonBlock) k_residual_norm(const int* __res
   max_abs_into(stats + 3, r);
 }
 
+// A[diag[i]] += g for the n node rows: a shunt conductance g from every node to ground (its
+// current g v is linear in v, so b is unchanged)
+__global__ void __launch_bounds__(kNewtonBlock) k_add_diag(double* __restrict__ A,
+                                                           const int* __restrict__ diag, int n,
+                                                           double g) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) A[diag[i]] += g;
+}
+
 int blocks_for(int n) { return n > 0 ? (n + kNewtonBlock - 1) / kNewtonBlock : 1; }
 
 }  // namespace
@@ -87,6 +96,12 @@ cudaError_t launch_residual_norm(const int* rp, const int* col, const double* A,
                                  const double* b, int n, unsigned long long* stats,
                                  cudaStream_t s) {
   k_residual_norm<<<blocks_for(n), kNewtonBlock, 0, s>>>(rp, col, A, x, b, n, stats);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_diag(double* A, const int* diag, int n, double g, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_add_diag<<<blocks_for(n), kNewtonBlock, 0, s>>>(A, diag, n, g);
   return cudaGetLastError();
 }
 

@@ -58,3 +58,26 @@ def test_gpu_newton_reports_non_convergence_without_a_device_error(eec):
     assert circ.status() == 0
     it = eec.eec_newton_dc(circ.ctx, x, A, b)    # continues from the last iterate
     assert it >= 1
+
+
+@pytest.mark.parametrize("make,rail_mode,max_iter", [(lambda: netgen.inverter_chain(64), 0, 150),
+                                                     (lambda: netgen.inverter_chain(64), 1, 200)])
+def test_gshunt_stepping_where_plain_newton_fails(eec, make, rail_mode, max_iter):
+    # plain damped Newton does not converge on these from the start below (the oracle needs its
+    # gshunt-stepping fallback too); the GPU loop falls back the same way and reaches the
+    # oracle's operating point
+    import torch
+    net = make()
+    o = oracle.Oracle(net, CARDS, rail_mode=rail_mode)
+    x0 = np.zeros(o.n)
+    if rail_mode:
+        R = [i for i in range(1, net.n_nodes) if net.node_fixed[i]]
+        x0[np.array(R) - 1] = net.node_vfix[R]
+    ref, _ = o.dc_solve(x0=x0, max_iter=max_iter)
+    circ = eec.Circuit(net, CARDS, variant=2, rail_mode=rail_mode)
+    x = torch.as_tensor(x0, device="cuda")
+    A, b, _ = circ.new_outputs(want_q=False)
+    it = eec.eec_newton_dc(circ.ctx, x, A, b, max_iter=max_iter)
+    assert it > max_iter                # the plain run used its solves, then the stages
+    assert circ.status() == 0
+    np.testing.assert_allclose(x.cpu().numpy(), ref, rtol=1e-8, atol=1e-10)
