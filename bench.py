@@ -317,8 +317,8 @@ def run_ours(args):
         out["roofline"] = {"bound": "alu", "kernel": "k_eval_ranges / k_eval (evaluate)",
                            "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                            "frac": (ach / FP64_PEAK_TFLOPS) if ach else None, "traffic": traffic,
-                           "peak_source": "152 SM x 2 DFMA/clk x 2 flop x 2070 MHz (recipe unit "
-                                          "counts; nominal 1.25 TFLOP/s FP64)"}
+                           "peak_source": "152 SM x 2 DFMA/clk x 2 flop x 2070 MHz (maximum SM "
+                                          "clock; nominal 1.25 TFLOP/s FP64)"}
         out["fp64_probe_tflops"] = eec.eec_fp64_peak(4096, 8) / 1e12
         out["variants_ms"] = {eec.VARIANT_NAMES[i]: m for i, m in enumerate(ms_variants)}
 
