@@ -37,12 +37,12 @@ UNIT = "device evals+stamps/s"
 # written per device. The flop count depends on the device mix (devices whose source and body
 # are source-held skip the body-effect and source-junction work).
 # Keys: (workload, evaluation launch order) -> k_eval (layout order) or k_eval_ranges (cost order).
-FP64_FLOP_PER_DEVICE = {("sram", 0): 277.5, ("logic", 0): 267.2, ("logic1m", 0): 267.2,
-                        ("batch", 0): 246.8, ("sram", 1): 280.5, ("logic", 1): 270.2,
-                        ("logic1m", 1): 270.2, ("batch", 1): 249.8}
-DRAM_BYTES_PER_DEVICE = {("sram", 0): 192.0, ("logic", 0): 237.8, ("logic1m", 0): 278.2,
-                         ("batch", 0): 384.5, ("sram", 1): 191.3, ("logic", 1): 243.7,
-                         ("logic1m", 1): 291.0, ("batch", 1): 383.0}
+FP64_FLOP_PER_DEVICE = {("sram", 0): 274.5, ("logic", 0): 264.2, ("logic1m", 0): 264.2,
+                        ("batch", 0): 243.8, ("sram", 1): 274.5, ("logic", 1): 264.2,
+                        ("logic1m", 1): 264.2, ("batch", 1): 243.8}
+DRAM_BYTES_PER_DEVICE = {("sram", 0): 191.3, ("logic", 0): 237.4, ("logic1m", 0): 278.0,
+                         ("batch", 0): 384.8, ("sram", 1): 191.1, ("logic", 1): 243.4,
+                         ("logic1m", 1): 290.8, ("batch", 1): 383.7}
 # GB300: 152 SMs x 2 FP64 FMA per clock per SM x 2 flop x 2070 MHz maximum SM clock.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--workload", choices=["sram", "logic", "logic1m", "batch", "chain"],
                     default="sram")
     ap.add_argument("--variant", default="auto")
+    ap.add_argument("--eval-order", choices=["auto", "cost", "layout"], default="auto",
+                    help="evaluation launch order of the order-free schedules (auto: the "
+                         "autotuner's choice; with --quick, cost)")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--quick", action="store_true",
                     help="timed steps only (no autotune, e2e, extras, probes, baseline): for ncu")
@@ -219,6 +222,8 @@ def run_ours(args):
     ms_variants = [] if args.quick else eec.eec_autotune(circ.ctx, xt, A, b, q, reps=5)
     if args.variant != "auto":
         eec.eec_set_variant(circ.ctx, int(args.variant))
+    if args.eval_order != "auto":
+        eec.eec_set_eval_order(circ.ctx, 1 if args.eval_order == "cost" else 0)
     variant = eec.eec_get_variant(circ.ctx)
     graphed = variant in (eec.EEC_VARIANT_COLOR_FUSED, eec.EEC_VARIANT_COLOR_BUFFERED)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)

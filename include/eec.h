@@ -196,6 +196,11 @@ EEC_API int eec_get_tuning(const eec_ctx* ctx, int32_t* variant, int32_t* block,
 
 /* Select the schedule (EEC_VARIANT_*) used by eec_eval_stamp. */
 EEC_API int eec_set_variant(eec_ctx* ctx, int32_t variant);
+
+/* Select the evaluation launch order of the order-free schedules (ATOMIC, SEGREDUCE,
+ * COLOR_BUFFERED): 1 = devices with a free source or body first (the default), 0 = layout
+ * order. eec_autotune sets it to the faster of the two. */
+EEC_API int eec_set_eval_order(eec_ctx* ctx, int32_t cost_order);
 EEC_API int eec_get_variant(const eec_ctx* ctx, int32_t* variant);
 
 /*

@@ -71,6 +71,7 @@ _SIG = {
     "eec_update_params": (ctypes.c_int, [_P, _P, _P, _P]),
     "eec_set_variant": (ctypes.c_int, [_P, _I32]),
     "eec_get_variant": (ctypes.c_int, [_P, ctypes.POINTER(_I32)]),
+    "eec_set_eval_order": (ctypes.c_int, [_P, _I32]),
     "eec_get_tuning": (ctypes.c_int, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32),
                                       ctypes.POINTER(_I32)]),
     "eec_eval_stamp": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
@@ -322,6 +323,10 @@ def eec_update_params(ctx, W, L, stream=None):
 
 def eec_set_variant(ctx, variant: int):
     _check(ctx, _load().eec_set_variant(ctx, int(variant)))
+
+
+def eec_set_eval_order(ctx, cost_order: int):
+    _check(ctx, _load().eec_set_eval_order(ctx, int(cost_order)))
 
 
 def eec_get_variant(ctx) -> int:

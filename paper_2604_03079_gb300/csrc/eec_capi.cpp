@@ -1241,6 +1241,13 @@ int eec_set_variant(eec_ctx* c, int32_t v) {
   return EEC_OK;
 }
 
+int eec_set_eval_order(eec_ctx* c, int32_t cost_order) {
+  if (!c) return EEC_EINVAL;
+  if (cost_order != 0 && cost_order != 1) return fail(c, EEC_EINVAL, "cost_order must be 0 or 1");
+  c->eval_ordered = cost_order == 1;
+  return EEC_OK;
+}
+
 int eec_get_variant(const eec_ctx* c, int32_t* v) {
   if (!c || !v) return EEC_EINVAL;
   *v = effective_variant(c);

@@ -155,13 +155,14 @@ __device__ __forceinline__ void channel(const CardK& c, const PrmS<S>& P, const 
                                         bool want_vbs = true) {
   const S Vth = Vthb - c.ETA0 * vds;
 
-  // (3) Vgsteff = nVt softplus(z), dVgsteff/dz = nVt sigmoid(z)
-  const S z = (vgs - Vth) * c.inv_nVt;
+  // (3) Vgsteff = nVt softplus(z), dVgsteff/dz = nVt sigmoid(z), z = (vgs - Vth) / nVt
+  const S ov = vgs - Vth;
+  const S z = ov * c.inv_nVt;
   const bool zpos = fm_ge0(sval(z));
   const S e = exp_(zpos ? -z : z);               // exp(-|z|)
   const S inv_1pe = rcp(1.0 + e);
   const S lg = log1p_(e, inv_1pe);
-  const S Vg = c.nVt * (zpos ? z + lg : lg);
+  const S Vg = c.nVt * lg + (zpos ? ov : S(0.0));  // nVt (z + lg) = ov + nVt lg for z >= 0
   const S sig = zpos ? inv_1pe : e * inv_1pe;
 
   // (5) mobility denominator, (6) velocity saturation
@@ -191,9 +192,9 @@ __device__ __forceinline__ void channel(const CardK& c, const PrmS<S>& P, const 
   const S R2sq = t * t + c.fourDELTA * Vdsat;
   const S inv_R2 = rsqrt_(R2sq);
   const S R2 = R2sq * inv_R2;
-  const S E = Vdsat + vds + c.DELTA + R2;
-  const S inv_E = rcp(E);
   const S twoVdsat = twice(Vdsat);
+  const S E = (twoVdsat - t) + R2;               // Vdsat + vds + DELTA + R2
+  const S inv_E = rcp(E);
   const S twoVds = twice(vds);
   const S Vdseff = twoVdsat * vds * inv_E;
   const S dE_dVdsat = 1.0 + (t + c.twoDELTA) * inv_R2;
@@ -277,7 +278,7 @@ __device__ __forceinline__ void ees_l1(const CardK& c, unsigned long long psb, c
   const S VD = fwd ? V[0] : V[2];
   const S VS = fwd ? V[2] : V[0];
   const S vgs = flip(V[1] - VS, psb);
-  const S vds = flip(VD - VS, psb);
+  const S vds = flip(vds0, fwd ? 0ull : kSignBit);   // VD - VS in the polarity frame
 
   // (2) body effect, (4) bulk charge: precomputed when vbs cannot change
   S sqs, Vthb, dVth_dvbs, Ab, dAb_dvbs;
@@ -331,17 +332,20 @@ __device__ __forceinline__ void ees_l1(const CardK& c, unsigned long long psb, c
     //      overlaps
     const S Qb = (sb_fixed && fwd) ? S(bk->Qb) : -(P.Coxt * c.K1 * sqs);
     const S Qinv = -(P.Coxt * Vg * F1);
-    const S Qg0 = -(Qb + Qinv);
     const S sr = ch.sr;   // Vdseff / Vdsat
     const S fD = c.XPm * sr + 0.5;
     const S QD = fD * Qinv;
     const S QS = Qinv - QD;
-    const S Qovs = P.CovS * flip(V[1] - V[2], psb);
-    const S Qovd = P.CovD * flip(V[1] - V[0], psb);
-    o.Q[1] = flip(Qg0 + Qovs + Qovd, psb);
-    o.Q[0] = flip((fwd ? QD : QS) - Qovd, psb);
-    o.Q[2] = flip((fwd ? QS : QD) - Qovs, psb);
+    // overlaps: V1 - V2 and V1 - V0 are vgs and vgd in some order (polarity frame)
+    const S vgd = flip(V[1] - VD, psb);
+    const S Qovs = P.CovS * (fwd ? vgs : vgd);
+    const S Qovd = P.CovD * (fwd ? vgd : vgs);
+    const S Q0 = (fwd ? QD : QS) - Qovd;
+    const S Q2 = (fwd ? QS : QD) - Qovs;
+    o.Q[0] = flip(Q0, psb);
+    o.Q[2] = flip(Q2, psb);
     o.Q[3] = flip(Qb, psb);
+    o.Q[1] = flip(-(Q0 + Q2 + Qb), psb);              // the charges sum to zero
     if (WANT_C) {
       // (11') charge Jacobian. Mode-frame derivatives of Qinv = -Coxt Vg F1 and Qb, with
       // dVg/d(vgs, vds, vbs) = sig (1, ETA0, -dVth/dvbs) and the total derivatives of F1; mapped
