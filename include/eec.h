@@ -226,7 +226,10 @@ EEC_API int eec_eval_stamp(eec_ctx* ctx, const double* x_dev, double* A_values_d
  * evaluated in opt.host_chunks spans of original index (each half the size of the one before),
  * launched alternately on cuda_stream and a library stream so that no launch's tail leaves the
  * SMs idle, and each span's charges are copied on another library stream while the next span is
- * evaluated; the call joins those streams back into cuda_stream. Page-locked buffers (cudaHostAlloc / cudaHostRegister) make every copy
+ * evaluated; the call joins those streams back into cuda_stream. The two library streams are
+ * created by eec_build_scatter: CUDA spreads streams over the device's hardware queues in
+ * creation order, and library streams created after a large stream pool could share the
+ * caller's queue and lose the overlap. Page-locked buffers (cudaHostAlloc / cudaHostRegister) make every copy
  * asynchronous; pageable ones work but the call returns only once their copies are done.
  * Stream-ordered on cuda_stream: the host outputs are valid once the stream has synchronised.
  * Calls on one context share the staging buffers, so calls that overlap on the GPU (unordered
