@@ -166,7 +166,9 @@ __global__ void __launch_bounds__(kBwdBlock) k_bwd_device(DevTopo T, const doubl
   for (int t = 0; t < 4; ++t) V[t] = idx[t] >= 0 ? __ldg(x + idx[t]) : __ldg(T.vfix + ~idx[t]);
   const int meta = __ldg(T.meta + k);
   const CardK& c = T.cards[meta >> 2];
-  const double p = (meta & 1) ? -1.0 : 1.0;
+  // the polarity (p = +1 NMOS, -1 PMOS) and the mode sign m enter as sign-bit flips on the
+  // integer pipe, not as multiplications on the FP64 pipe
+  const unsigned long long psb = (meta & 1) ? kSignBit : 0ull;
   const bool sbf = (meta >> 1) & 1;   // source and body source-held
   const double W = __ldg(T.W + k), L = __ldg(T.L + k);
 
@@ -189,10 +191,11 @@ __global__ void __launch_bounds__(kBwdBlock) k_bwd_device(DevTopo T, const doubl
   }
 
   // (1) mode frame
-  const bool fwd = fm_ge0(p * (V[0] - V[2]));
+  const bool fwd = fm_ge0(flip(V[0] - V[2], psb));
   const int iD = fwd ? 0 : 2, iS = fwd ? 2 : 0;
-  const double m = fwd ? 1.0 : -1.0;
-  const double vgs = p * (V[1] - V[iS]), vds = p * (V[iD] - V[iS]), vbs = p * (V[3] - V[iS]);
+  const unsigned long long msb = fwd ? 0ull : kSignBit;   // m = +1 forward, -1 reverse
+  const double vgs = flip(V[1] - V[iS], psb), vds = flip(V[iD] - V[iS], psb);
+  const double vbs = flip(V[3] - V[iS], psb);
 
   // channel: s_ch = m (g . w) - p m omega Ids with w in mode-frame coordinates
   double wt[4];
@@ -237,39 +240,41 @@ __global__ void __launch_bounds__(kBwdBlock) k_bwd_device(DevTopo T, const doubl
   Chan<T2> ch;
   channel<T2>(c, P, vgs2, vds2, Vthb, dVth, Ab, dAb, ch, !hoist);
   const double gm = ch.gm.v, gds = ch.gds.v, gmb = ch.gmb.v, Ids = ch.Ids.v;
-  const double pmw = p * m * omega;
-  const double s_ch = m * (gm * w0 + gds * w1 + gmb * w2) - pmw * Ids;
-  const double dv0 = m * ch.gm.d[0] - pmw * gm;    // d s_ch / d vgs (H w is symmetric in w)
-  const double dv1 = m * ch.gds.d[0] - pmw * gds;  // d s_ch / d vds
-  const double dv2 = m * ch.gmb.d[0] - pmw * gmb;  // d s_ch / d vbs
-  double dW = s_ch / W;
-  const double dL = m * (ch.gm.d[1] * w0 + ch.gds.d[1] * w1 + ch.gmb.d[1] * w2) - pmw * ch.Ids.d[1];
+  const double pmw = flip(omega, psb ^ msb);       // p m omega
+  const double s_ch = flip(gm * w0 + gds * w1 + gmb * w2, msb) - pmw * Ids;
+  const double dv0 = flip(ch.gm.d[0], msb) - pmw * gm;    // d s_ch / d vgs (H w is symmetric in w)
+  const double dv1 = flip(ch.gds.d[0], msb) - pmw * gds;  // d s_ch / d vds
+  const double dv2 = flip(ch.gmb.d[0], msb) - pmw * gmb;  // d s_ch / d vbs
+  const double dL =
+      flip(ch.gm.d[1] * w0 + ch.gds.d[1] * w1 + ch.gmb.d[1] * w2, msb) - pmw * ch.Ids.d[1];
   double g[4];
-  g[1] = p * dv0;
-  g[3] = p * dv2;
-  g[iD] = p * dv1;
-  g[iS] = -p * (dv0 + dv1 + dv2);
+  g[1] = flip(dv0, psb);
+  g[3] = flip(dv2, psb);
+  g[iD] = flip(dv1, psb);
+  g[iS] = flip(dv0 + dv1 + dv2, psb ^ kSignBit);
 
   // junctions (physical d-b and s-b): s_j = kappa gj - rho Ij
   const double Isat = __ldg(pr + P_ISAT * N);
   double IjdI, gjdI, gjd2, IjsI = 0.0, gjsI = 0.0, gjs2 = 0.0;
-  const double vbd = p * (V[3] - V[0]), vbsj = p * (V[3] - V[2]);
+  const double vbd = flip(V[3] - V[0], psb), vbsj = flip(V[3] - V[2], psb);
   junction2(c, Isat, vbd, IjdI, gjdI, gjd2);
   // with source and body held the source junction carries no weight (rows and columns s, b
   // are not stamped): its terms below are multiplied by zero
   if (!sbf) junction2(c, Isat, vbsj, IjsI, gjsI, gjs2);
   const double gjd = gjdI + c.GMIN, gjs = gjsI + c.GMIN;
   const double kd = cw[0][0] - cw[0][3] - cw[3][0] + cw[3][3];
-  const double rd = p * (wb[3] - wb[0]);
-  const double ddv = kd * gjd2 - rd * gjd;
-  g[0] -= p * ddv;
-  g[3] += p * ddv;
+  const double rd = flip(wb[3] - wb[0], psb);
+  const double ddv = flip(kd * gjd2 - rd * gjd, psb);   // p (kd gjd2 - rd gjd)
+  g[0] -= ddv;
+  g[3] += ddv;
   const double ks = cw[2][2] - cw[2][3] - cw[3][2] + cw[3][3];
-  const double rs = p * (wb[3] - wb[2]);
-  const double dsv = ks * gjs2 - rs * gjs;
-  g[2] -= p * dsv;
-  g[3] += p * dsv;
-  dW += (kd * gjdI - rd * IjdI + ks * gjsI - rs * IjsI) / W;
+  const double rs = flip(wb[3] - wb[2], psb);
+  const double dsv = flip(ks * gjs2 - rs * gjs, psb);
+  g[2] -= dsv;
+  g[3] += dsv;
+  // at fixed L the channel terms and the junctions' saturation terms are proportional to W (the
+  // GMIN parts, which are not, are left out of the sums above): d s / dW = s / W
+  const double dW = (s_ch + kd * gjdI - rd * IjdI + ks * gjsI - rs * IjsI) * fm_rcp(W);
 
   // direct term d(sum_r wb_r G_ru V_u)/dV_u = sum_r wb_r G_ru
   const double gsum = gm + gds + gmb;
