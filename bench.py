@@ -524,7 +524,8 @@ def extras(eec, circ, net, x, xt, A, b, q, args, dev):
     free = unk[net.dev_nodes] >= 0
     contrib = int((free[:, [0, 2, 3]].sum(axis=1) * (1 + free.sum(axis=1))).sum())
     entries = circ.nnz + circ.n
-    gbytes = 12 * contrib + 24 * entries
+    gbytes = 12 * contrib + 20 * entries   # value + index per contribution; linear part,
+                                            # 32-bit pointer and output per entry
     st_ms = phases["segreduce"]["stamp_ms"]
     hbm = hbm_peak_gbs()
     res["stamp_roofline"] = {

@@ -1005,11 +1005,11 @@ int eec_build_scatter(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_out) {
       }
     }
   }
-  std::vector<int> glight, gheavy;
-  for (long long e = 0; e < E; ++e) {
+  std::vector<int> gheavy;
+  for (long long e = 0; e < E; ++e)
     if (gptr[e + 1] - gptr[e] >= kHeavy) gheavy.push_back((int)e);
-    else glight.push_back((int)e);
-  }
+  if (gptr[E] > 0x7fffffffLL) return fail(c, EEC_EINVAL, "too many contributions");
+  const std::vector<int> gptr32(gptr.begin(), gptr.end());
   // backward incidence: unknown -> (terminal, position) in original device order
   std::vector<int> iptr(n + 1, 0);
   for (int k = 0; k < N; ++k)
@@ -1064,7 +1064,6 @@ int eec_build_scatter(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_out) {
   d.N = N;
   d.n = n;
   d.nnz = c->nnz;
-  d.n_light = (int)glight.size();
   d.n_heavy = (int)gheavy.size();
   d.n_inc_light = (int)ilight.size();
   d.n_inc_heavy = (int)iheavy.size();
@@ -1076,8 +1075,8 @@ int eec_build_scatter(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_out) {
       (rc = dalloc(c, &d.prm, (size_t)kNPrm * N)) || (rc = dalloc(c, &d.bodyk, (size_t)kNBody * N)) ||
       (rc = dupload(c, &d.vfix, vtab)) ||
       (rc = dupload(c, &d.cards, c->cardk)) || (rc = dupload(c, &d.Alin, Alin)) ||
-      (rc = dupload(c, &d.blin, blin)) || (rc = dupload(c, &d.gat_ptr, gptr)) ||
-      (rc = dupload(c, &d.gat_src, gsrc)) || (rc = dupload(c, &d.gat_light, glight)) ||
+      (rc = dupload(c, &d.blin, blin)) || (rc = dupload(c, &d.gat_ptr, gptr32)) ||
+      (rc = dupload(c, &d.gat_src, gsrc)) || 
       (rc = dupload(c, &d.gat_heavy, gheavy)) || (rc = dupload(c, &d.inc_ptr, iptr)) ||
       (rc = dupload(c, &d.inc_light, ilight)) || (rc = dupload(c, &d.inc_heavy, iheavy)) ||
       (rc = dupload(c, &d.inc_src, isrc)) || (rc = dupload(c, &c->d_coff, c->color_off))) {

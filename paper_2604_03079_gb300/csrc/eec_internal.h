@@ -62,11 +62,10 @@ struct DevTopo {
   double* blin;     // [n]
   // segmented reduction: entry e (A entries 0..nnz-1, then b rows) sums buf[src] over
   // gat_src[gat_ptr[e] .. gat_ptr[e+1]) in original-device order
-  long long* gat_ptr;  // [nnz + n + 1]
+  int* gat_ptr;        // [nnz + n + 1] (at most kNContrib N < 2^31 contributions)
   int* gat_src;        // [total contributions], flat index j * N + k into buf
-  int* gat_light;      // entries with fewer than kHeavy contributions (one thread each)
-  int* gat_heavy;      // the others (one warp each)
-  int n_light, n_heavy;
+  int* gat_heavy;      // entries with kHeavy or more contributions (one warp each)
+  int n_heavy;
   double* buf;         // [kNContrib][N] (allocated on first use)
   double* buf_tran;    // [kNContribTran][N]: transient values G + alpha C (4 x 4) and 4 rhs
   // backward: unknown u gathers gv[src] over inc_src[inc_ptr[u] .. inc_ptr[u+1])

@@ -127,14 +127,18 @@ __device__ __forceinline__ void eval_one(const DevTopo& T, int k, const double* 
   const int term[3] = {0, 2, 3};
   bool bc_ok = true;
   if (MODE == MODE_BUFFER) {
+    // only what a stamp reads is buffered: rows of free terminals, and in them the entries of
+    // free columns (the gather and the colour-ordered stamps skip held rows and columns)
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
+      if (idx[term[r]] < 0) continue;
       double s = -o.I[term[r]];
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (idx[u] >= 0) s = fma(o.G[r][u], V[u], s);
-#pragma unroll
-      for (int u = 0; u < 4; ++u) T.buf[(4 * r + u) * N + k] = o.G[r][u];
+      for (int u = 0; u < 4; ++u) {
+        if (idx[u] < 0) continue;
+        s = fma(o.G[r][u], V[u], s);
+        T.buf[(4 * r + u) * N + k] = o.G[r][u];
+      }
       T.buf[(kNSlot + r) * N + k] = s;
       bc_ok = bc_ok && isfinite(s);
     }
@@ -344,20 +348,22 @@ __global__ void k_params(DevTopo T, const double* __restrict__ Wo, const double*
 }
 
 // Segmented reduction: entry e of [A ; b] = linear part + its contributions (deterministic, no
-// colours needed). Light entries (< kHeavy contributions, nearly all) take one thread each and
-// sum in original-device order; heavy entries (diagonals of word and bit lines) take one warp
-// each: lane-strided partial sums, then a fixed butterfly reduction. Blocks [0, nbl) do light
-// entries, the rest heavy ones, in one launch.
+// colours needed). Light entries (< kHeavy contributions, nearly all) take one thread each, in
+// entry order (coalesced pointer, linear-part and output accesses), and sum in original-device
+// order; heavy entries (diagonals of word and bit lines) are skipped there and take one warp
+// each: lane-strided partial sums, then a fixed butterfly reduction. Blocks [0, nbl) cover the
+// entries, the rest the heavy ones, in one launch.
 constexpr int kGatherBlock = 256;
 
 __global__ void __launch_bounds__(kGatherBlock) k_gather(DevTopo T, double* A, double* b, int nbl) {
+  const long long E = T.nnz + T.n;
   if ((int)blockIdx.x < nbl) {
-    const int i = blockIdx.x * kGatherBlock + threadIdx.x;
-    if (i >= T.n_light) return;
-    const long long e = __ldg(T.gat_light + i);
+    const long long e = (long long)blockIdx.x * kGatherBlock + threadIdx.x;
+    if (e >= E) return;
+    const int p0 = __ldg(T.gat_ptr + e), p1 = __ldg(T.gat_ptr + e + 1);
+    if (p1 - p0 >= kHeavy) return;   // a warp of the heavy blocks sums this one
     double s = e < T.nnz ? __ldg(T.Alin + e) : __ldg(T.blin + (e - T.nnz));
-    const long long p0 = __ldg(T.gat_ptr + e), p1 = __ldg(T.gat_ptr + e + 1);
-    for (long long p = p0; p < p1; ++p) s += __ldg(T.buf + __ldg(T.gat_src + p));
+    for (int p = p0; p < p1; ++p) s += __ldg(T.buf + __ldg(T.gat_src + p));
     if (e < T.nnz) A[e] = s;
     else b[e - T.nnz] = s;
     return;
@@ -366,9 +372,9 @@ __global__ void __launch_bounds__(kGatherBlock) k_gather(DevTopo T, double* A, d
   if (w >= T.n_heavy) return;   // whole warp leaves together
   const int lane = threadIdx.x & 31;
   const long long e = __ldg(T.gat_heavy + w);
-  const long long p0 = __ldg(T.gat_ptr + e), p1 = __ldg(T.gat_ptr + e + 1);
+  const int p0 = __ldg(T.gat_ptr + e), p1 = __ldg(T.gat_ptr + e + 1);
   double s = 0.0;
-  for (long long p = p0 + lane; p < p1; p += 32) s += __ldg(T.buf + __ldg(T.gat_src + p));
+  for (int p = p0 + lane; p < p1; p += 32) s += __ldg(T.buf + __ldg(T.gat_src + p));
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
   if (lane == 0) {
@@ -770,7 +776,7 @@ cudaError_t launch_init_lin(const DevTopo& T, double* A, double* b, cudaStream_t
 }
 
 cudaError_t launch_gather(const DevTopo& T, double* A, double* b, cudaStream_t s) {
-  const int nbl = (T.n_light + kGatherBlock - 1) / kGatherBlock;
+  const int nbl = (int)((T.nnz + T.n + kGatherBlock - 1) / kGatherBlock);
   const int nbh = (T.n_heavy + kGatherBlock / 32 - 1) / (kGatherBlock / 32);
   if (nbl + nbh == 0) return cudaSuccess;
   k_gather<<<nbl + nbh, kGatherBlock, 0, s>>>(T, A, b, nbl);
