@@ -83,9 +83,6 @@ struct EvalOut {
   S C[4][4];   // dQ_t / dV_u, rows d, g, s, b (transient only)
 };
 
-template <class S>
-__device__ __forceinline__ S sel(bool c, const S& a, const S& b) { return c ? a : b; }
-
 // Junction current and conductance: Ij(v) = Isat (explim(v/Vt) - 1) + GMIN v with
 // explim(z) = exp(z) for z <= 40 and e^40 (1 + z - 40) above; gj = dIj/dv
 // = (Isat/Vt) explim'(z) + GMIN, written as fma(Isat/Vt, expm1(z), Isat/Vt + GMIN). Deep in
