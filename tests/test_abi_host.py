@@ -98,6 +98,11 @@ def test_validation_errors(eec):
         assert e.value.code == eec.EEC_EINVAL
         with pytest.raises(eec.EECError):
             eec.eec_set_variant(ctx, 7)
+        for bad_order in (-1, 2):
+            with pytest.raises(eec.EECError):
+                eec.eec_set_eval_order(ctx, bad_order)
+        eec.eec_set_eval_order(ctx, 0)
+        eec.eec_set_eval_order(ctx, 1)
     finally:
         eec.eec_destroy(ctx)
     for bad in ({"host_chunks": -1}, {"host_chunks": 65}, {"block": 48}, {"conflict_rule": 3},
