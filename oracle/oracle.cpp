@@ -24,7 +24,9 @@
 //
 // Parity pins (checked by the "not gpu" tests): resistor divider and diode Lambert-W closed forms,
 // KCL residual A x - b = F(x), symmetric pattern, model invariants and limits, Jacobian vs central
-// differences, brute-force colouring on tiny graphs and hand-derived colour counts.
+// differences, brute-force colouring on tiny graphs and hand-derived colour counts; with the rails
+// as unknowns, the divider's source current in closed form and source currents equal to minus the
+// model's terminal currents.
 
 #include <algorithm>
 #include <cmath>
