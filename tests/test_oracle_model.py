@@ -228,3 +228,43 @@ def test_jacobian_matches_central_differences(p):
             Gfd[:, u] = (ev(c, p, Vp)[0] - ev(c, p, Vm)[0]) / (2 * h)
         scale = np.abs(G).max()
         np.testing.assert_allclose(G, Gfd, rtol=1e-5, atol=1e-6 * scale)
+
+
+def _intrinsic_split(V, p=1, **kw):
+    """Drain and source charges with the overlaps switched off (forward mode: the mode drain is
+    the physical drain)."""
+    c = netgen.card(CGSO=0.0, CGDO=0.0, **kw)
+    _, _, Q = ev(c, p, V)
+    return Q[0], Q[2], f(c, "XPART")
+
+
+def test_charge_partition_is_half_at_zero_vds():
+    # fD = 1/2 - (1/2 - XPART) Vdseff / Vdsat with Vdseff = 0 at vds = 0: an even split
+    for vg in (0.3, 0.7, 1.2):
+        qd, qs, _ = _intrinsic_split([0.4, vg, 0.4, 0.0])
+        assert qd != 0.0 and abs(qd - qs) <= 1e-15 * abs(qd)
+
+
+def test_charge_partition_reaches_xpart_in_deep_saturation():
+    # Vdseff -> Vdsat as vds grows, so the drain share of the inversion charge tends to XPART
+    prev = None
+    for vd in (1.0, 4.0, 16.0, 64.0):
+        qd, qs, xpart = _intrinsic_split([vd, 1.0, 0.0, 0.0], JS=0.0)
+        share = qd / (qd + qs)
+        err = abs(share - xpart)
+        if prev is not None:
+            assert err < prev          # monotone approach
+        prev = err
+    assert prev < 1e-3
+
+
+def test_charges_are_continuous_across_the_source_drain_swap():
+    # the mode swap at vds = 0 moves no charge: with the partition above the terminal charges
+    # are continuous in vds (a constant XPART split would jump by (1/2 - XPART) Qinv)
+    c = netgen.default_cards()[0]
+    for vg in (0.4, 0.9):
+        for eps in (1e-6, 1e-8):
+            _, _, qa = ev(c, 1, [0.5 + eps, vg, 0.5, 0.0])
+            _, _, qb = ev(c, 1, [0.5 - eps, vg, 0.5, 0.0])
+            coxt = cox(c) * W0 * L0
+            assert np.abs(qa - qb).max() <= 10.0 * eps * coxt
