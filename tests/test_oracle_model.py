@@ -268,3 +268,15 @@ def test_charges_are_continuous_across_the_source_drain_swap():
             _, _, qb = ev(c, 1, [0.5 - eps, vg, 0.5, 0.0])
             coxt = cox(c) * W0 * L0
             assert np.abs(qa - qb).max() <= 10.0 * eps * coxt
+
+
+def test_junctions_zero_bias_and_reverse_saturation():
+    # d = g = s = ground, body at v: the two body junctions carry the whole current. It is
+    # exactly zero at zero bias and saturates at -2 JS W HDIF in deep reverse bias (GMIN off).
+    c = netgen.card(GMIN=0.0)
+    I0, _, _ = ev(c, 1, [0.0, 0.0, 0.0, 0.0])
+    assert np.all(I0 == 0.0)
+    isat = f(c, "JS") * W0 * f(c, "HDIF")
+    for v in (-2.0, -5.0):
+        I, _, _ = ev(c, 1, [0.0, 0.0, 0.0, v])
+        np.testing.assert_allclose(I[3], -2.0 * isat, rtol=1e-15)
