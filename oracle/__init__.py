@@ -63,6 +63,7 @@ def _load():
             lib.ora_eval_stamp_tran.argtypes = [P, P, P, P, f64, f64, P, P, P, P, P, P]
             lib.ora_device_charge.argtypes = [P, i32, f64, f64, P, P, P]
             lib.ora_tran_solve.argtypes = [P, P, f64, i32, i32, P, P]
+            lib.ora_count_ops.argtypes = [P, i32, f64, f64, P, i32, P]
             _lib = lib
     return _lib
 
@@ -231,3 +232,19 @@ def device_eval(card, p, W, L, V):
     if rc != 0:
         raise ValueError("bad device arguments")
     return I, G.reshape(4, 4), Q
+
+
+OP_CLASSES = ("add", "mul", "div", "exp", "expm1", "log1p", "sqrt")
+
+
+def count_ops(card, p, W, L, V, free_mask=0b1111):
+    """Floating-point operations of one device evaluation (currents and charges, values only)
+    that depend on the free terminals (bit t of free_mask: terminal d, g, s, b on a free node),
+    by class (see OP_CLASSES)."""
+    lib = _load()
+    out = np.zeros(len(OP_CLASSES), np.int64)
+    rc = lib.ora_count_ops(_p(_c(card, np.float64)), int(p), float(W), float(L),
+                           _p(_c(V, np.float64)), int(free_mask), _p(out))
+    if rc != 0:
+        raise ValueError("bad device arguments")
+    return dict(zip(OP_CLASSES, (int(v) for v in out)))

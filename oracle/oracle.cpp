@@ -127,6 +127,48 @@ Dual<T, N> sqrt(const Dual<T, N>& a) {
   return r;
 }
 
+// Operation counting: a scalar that counts the floating-point operations of one model
+// evaluation (values only, no derivatives) that depend on the terminal voltages. A value derived
+// only from the card, W and L is a per-device constant (a GPU computes it once per device or
+// card), and operations among constants are not counted.
+struct OpCount {
+  long long add = 0, mul = 0, div = 0, exp = 0, expm1 = 0, log1p = 0, sqrt = 0;
+};
+OpCount g_ops;   // one counting evaluation at a time
+struct Cnt {
+  double v;
+  bool dep;      // depends on the terminal voltages
+  Cnt() : v(0.0), dep(false) {}
+  Cnt(double c) : v(c), dep(false) {}  // NOLINT: constants
+  Cnt(double c, bool d) : v(c), dep(d) {}
+};
+inline double val(const Cnt& x) { return x.v; }
+inline Cnt cnt2(double v, const Cnt& a, const Cnt& b, long long* k) {
+  if (a.dep || b.dep) ++*k;
+  return Cnt(v, a.dep || b.dep);
+}
+inline Cnt operator+(const Cnt& a, const Cnt& b) { return cnt2(a.v + b.v, a, b, &g_ops.add); }
+inline Cnt operator-(const Cnt& a, const Cnt& b) { return cnt2(a.v - b.v, a, b, &g_ops.add); }
+inline Cnt operator*(const Cnt& a, const Cnt& b) { return cnt2(a.v * b.v, a, b, &g_ops.mul); }
+inline Cnt operator/(const Cnt& a, const Cnt& b) { return cnt2(a.v / b.v, a, b, &g_ops.div); }
+inline Cnt operator-(const Cnt& a) { return Cnt(-a.v, a.dep); }   // a sign flip, not counted
+inline Cnt operator+(const Cnt& a, double b) { return a + Cnt(b); }
+inline Cnt operator+(double a, const Cnt& b) { return Cnt(a) + b; }
+inline Cnt operator-(const Cnt& a, double b) { return a - Cnt(b); }
+inline Cnt operator-(double a, const Cnt& b) { return Cnt(a) - b; }
+inline Cnt operator*(const Cnt& a, double b) { return a * Cnt(b); }
+inline Cnt operator*(double a, const Cnt& b) { return Cnt(a) * b; }
+inline Cnt operator/(const Cnt& a, double b) { return a / Cnt(b); }
+inline Cnt operator/(double a, const Cnt& b) { return Cnt(a) / b; }
+inline Cnt cnt1(double v, const Cnt& a, long long* k) {
+  if (a.dep) ++*k;
+  return Cnt(v, a.dep);
+}
+inline Cnt exp(const Cnt& a) { return cnt1(std::exp(a.v), a, &g_ops.exp); }
+inline Cnt expm1(const Cnt& a) { return cnt1(std::expm1(a.v), a, &g_ops.expm1); }
+inline Cnt log1p(const Cnt& a) { return cnt1(std::log1p(a.v), a, &g_ops.log1p); }
+inline Cnt sqrt(const Cnt& a) { return cnt1(std::sqrt(a.v), a, &g_ops.sqrt); }
+
 // Magnitude forward mode: value plus, per direction, the sum over chain-rule paths of the
 // absolute values of the products along each path. It bounds |derivative| and measures how much
 // a derivative cancels; the transient error metric uses it as the size of a Jacobian entry.
@@ -899,6 +941,24 @@ int ora_device_eval(const double* card, int32_t p, double W, double L, const dou
 }
 
 int32_t ora_card_len(void) { return kCardLen; }
+
+// Algorithmic work of one device evaluation (terminal currents and charges, values only) at V:
+// counts[7] = additions/subtractions, multiplications, divisions, exp, expm1, log1p, sqrt of the
+// operations that depend on the free terminals (bit t of free_mask: terminal t is on a free
+// node; a held terminal's voltage is a constant like the card, W and L).
+int ora_count_ops(const double* card, int32_t p, double W, double L, const double* V,
+                  int32_t free_mask, int64_t* counts) {
+  if (p != 1 && p != -1) return kEinval;
+  Card cd = read_card(card);
+  Cnt Vc[4], Ic[4], Qc[4];
+  for (int t = 0; t < 4; ++t) Vc[t] = Cnt(V[t], ((free_mask >> t) & 1) != 0);
+  g_ops = OpCount{};
+  ees_l1<Cnt>(cd, p, Cnt(W), Cnt(L), Vc, Ic, Qc);
+  const long long k[7] = {g_ops.add, g_ops.mul, g_ops.div, g_ops.exp, g_ops.expm1, g_ops.log1p,
+                          g_ops.sqrt};
+  for (int i = 0; i < 7; ++i) counts[i] = k[i];
+  return kOk;
+}
 
 // Transient companion stamp at x (see stamp_tran). qprev, iprev (nullable = zero): [4 x n_dev]
 // terminal-major; q_out, i_out (nullable): charges and capacitive currents at x.

@@ -280,3 +280,20 @@ def test_junctions_zero_bias_and_reverse_saturation():
     for v in (-2.0, -5.0):
         I, _, _ = ev(c, 1, [0.0, 0.0, 0.0, v])
         np.testing.assert_allclose(I[3], -2.0 * isat, rtol=1e-15)
+
+
+def test_algorithmic_work_per_device():
+    # the model's transcendental structure, counted by evaluating it on an operation-counting
+    # scalar: softplus (one exp, one log1p), two junction expm1, and three square roots (the
+    # body-effect smoothing and its square root, the smooth min of Vdseff); with source and
+    # body held, the body-effect terms and the source junction are per-device constants
+    c = netgen.default_cards()[0]
+    V = np.array([0.8, 0.9, 0.1, 0.0])
+    full = oracle.count_ops(c, 1, W0, L0, V)
+    assert (full["exp"], full["log1p"], full["expm1"], full["sqrt"]) == (1, 1, 2, 3)
+    held = oracle.count_ops(c, 1, W0, L0, V, free_mask=0b0011)
+    assert (held["exp"], held["log1p"], held["expm1"], held["sqrt"]) == (1, 1, 1, 1)
+    for k in ("add", "mul", "div"):
+        assert 0 < held[k] < full[k]
+    # a device with every terminal held does no voltage-dependent work
+    assert sum(oracle.count_ops(c, 1, W0, L0, V, free_mask=0).values()) == 0
