@@ -21,6 +21,8 @@
 //    unknown per source: its current, with the KCL entry at the rail and the source equation.
 //  * The DC Newton loop with a dense LU, the adjoint (transpose) solve and the gradient of a
 //    linear functional of (A, b) use no paper equation; they follow textbook definitions.
+//  * The same model evaluated on an operation-counting scalar gives the algorithmic work of one
+//    device evaluation by operation class (ora_count_ops).
 //
 // Parity pins (checked by the "not gpu" tests): resistor divider and diode Lambert-W closed forms,
 // KCL residual A x - b = F(x), symmetric pattern, model invariants and limits, Jacobian vs central
