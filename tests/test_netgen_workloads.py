@@ -42,3 +42,39 @@ def test_batch_of_4096_circuits():
     assert len(nets) == 4096 and merged.n_dev == 1_204_234
     assert merged.n_dev == sum(m.n_dev for m in nets)
     assert merged.n_free == sum(m.n_free for m in nets)
+
+
+def test_sram_structure():
+    # every word line drives the gates of the 2 access transistors of each cell in its row;
+    # every bit line carries the access transistors of its column (at 256 x 256: 512 gates per
+    # word line, 256 access transistors per bit line)
+    rows, cols = 16, 24
+    net = netgen.sram(rows, cols)
+    assert net.n_dev == 6 * rows * cols
+    wl = np.arange(4, 4 + rows)
+    bl = np.arange(4 + rows, 4 + rows + 2 * cols)
+    gates = np.bincount(net.dev_nodes[:, 1], minlength=net.n_nodes)
+    assert np.all(gates[wl] == 2 * cols)
+    ds = np.bincount(net.dev_nodes[:, 0], minlength=net.n_nodes) + \
+        np.bincount(net.dev_nodes[:, 2], minlength=net.n_nodes)
+    assert np.all(ds[bl] == rows)
+    assert np.count_nonzero(net.dev_type < 0) == 2 * rows * cols
+
+
+def test_random_logic_mix_fanout_and_order():
+    n = 20_000
+    net = netgen.random_logic(n, seed=11)
+    gc = net.meta["gate_counts"]
+    assert gc["inv"] + gc["nand2"] + gc["nor2"] == n
+    for k, share in (("inv", 0.2), ("nand2", 0.4), ("nor2", 0.4)):   # drawn 1:2:2
+        sd = (n * share * (1 - share)) ** 0.5
+        assert abs(gc[k] - n * share) <= 5 * sd, (k, gc[k])
+    assert net.n_dev == 2 * gc["inv"] + 4 * (gc["nand2"] + gc["nor2"])
+    # each gate input is two device gates (the N and P of one input); a driver feeds at most 8
+    free = net.node_fixed == 0
+    gate_uses = np.bincount(net.dev_nodes[:, 1], minlength=net.n_nodes)
+    assert np.all(gate_uses[free] % 2 == 0) and gate_uses[free].max() // 2 <= 8
+    # a DAG: a gate's inputs come from primary inputs or from gates created before it
+    d, g, s = net.dev_nodes[:, 0], net.dev_nodes[:, 1], net.dev_nodes[:, 2]
+    out = np.maximum(d, s)
+    assert np.all(~free[g] | (g < out))
