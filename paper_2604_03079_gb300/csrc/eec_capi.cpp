@@ -1159,11 +1159,14 @@ int eec_verify_coloring(const eec_ctx* cc, int32_t with_gate_rows) {
   if (rc) return rc;
   if (!c->colored) return fail(c, EEC_ESTATE, "not coloured");
   // Within a colour, every written A entry and b row must belong to one device: mark each row
-  // with the last (colour, device) that wrote it. A device writes rows of its free terminals
-  // d, s, b (and g when with_gate_rows); every entry it writes lies in one of those rows, so
-  // disjoint row sets imply disjoint entry sets.
+  // with the last (colour, device) that wrote it, visiting the devices colour by colour (the
+  // layout order), so that two writers of one row in one colour are visited one after the
+  // other. A device writes rows of its free terminals d, s, b (and g when with_gate_rows);
+  // every entry it writes lies in one of those rows, so disjoint row sets imply disjoint entry
+  // sets.
   std::vector<long long> owner(c->n, -1);
-  for (int k = 0; k < c->n_dev; ++k) {
+  for (int p = 0; p < c->n_dev; ++p) {
+    const int k = c->perm[p];
     const long long tag = (long long)c->color[k] * c->n_dev + k;
     int seen[4];
     int m = 0;

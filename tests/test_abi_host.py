@@ -181,6 +181,29 @@ def test_coloring_verifier(eec, rule):
         eec.eec_destroy(ctx)
 
 
+def test_coloring_verifier_sees_conflicts_across_interleaved_colours(eec):
+    # A (colour 0), B (colour 1), C (colour 0) all write row X once gate rows count: A and C
+    # conflict there although B, of another colour, lies between them in device order.
+    # Under the write-rows rule A conflicts with B (node Y) and C with neither.
+    from helpers import tiny_net
+    net = tiny_net("interleave", [1, 1, 0, 0, 0, 0], [0, 1.0, 0, 0, 0, 0],
+                   [(3, 2, 0, 0), (2, 4, 3, 0), (5, 2, 0, 0)], [1, 1, 1])
+    ctx = _ctx_with(eec, net, rule=2)
+    try:
+        col, C = eec.eec_color(ctx, n_dev=3)
+        assert list(col) == [0, 1, 0]
+        try:
+            eec.eec_build_scatter(ctx)
+        except eec.EECError as e:
+            assert e.code == eec.EEC_ECUDA
+        eec.eec_verify_coloring(ctx, with_gate_rows=False)
+        with pytest.raises(eec.EECError) as e:
+            eec.eec_verify_coloring(ctx, with_gate_rows=True)
+        assert "share colour 0" in str(e.value)
+    finally:
+        eec.eec_destroy(ctx)
+
+
 def test_batch_offsets_host(eec):
     nets = netgen.batch_circuits(12, seed=9)
     merged = netgen.concat(nets)
