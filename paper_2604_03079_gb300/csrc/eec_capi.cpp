@@ -190,6 +190,8 @@ void free_topology(eec_ctx* c) {
 // Pull sizes changed by eec_update_params back into the host copy before a rebuild.
 int sync_params_to_host(eec_ctx* c) {
   if (!c->built || !c->params_dirty) return EEC_OK;
+  // eec_update_params may have run on any stream, non-blocking ones included
+  CUDA_TRY(c, cudaDeviceSynchronize());
   std::vector<double> Wp(c->n_dev), Lp(c->n_dev);
   CUDA_TRY(c, cudaMemcpy(Wp.data(), c->d.W, sizeof(double) * c->n_dev, cudaMemcpyDeviceToHost));
   CUDA_TRY(c, cudaMemcpy(Lp.data(), c->d.L, sizeof(double) * c->n_dev, cudaMemcpyDeviceToHost));
