@@ -163,6 +163,31 @@ def _d(t, n=None, name="tensor"):
     return _P(t.data_ptr())
 
 
+def _numel(t):
+    return int(t.numel()) if hasattr(t, "numel") else int(np.asarray(t).size)
+
+
+def _need(t, k, name):
+    """The library reads and writes every buffer by the context's sizes (the C ABI takes bare
+    pointers): a buffer of another length (None passes) is refused here, before the call."""
+    if t is not None and _numel(t) != k:
+        raise ValueError(f"{name} has {_numel(t)} elements, the context needs {k}")
+
+
+def _sizes(ctx):
+    """(devices, unknowns, nonzeros) of a context with its scatter map built."""
+    nd, n, nnz, _ = eec_get_sizes(ctx)
+    return nd, n, nnz
+
+
+def _need_step(ctx, x, A, b, q=None):
+    nd, n, nnz = _sizes(ctx)
+    _need(x, n, "x")
+    _need(A, nnz, "A")
+    _need(b, n, "b")
+    _need(q, 4 * nd, "q")
+
+
 def _stream(stream):
     import torch
     if stream is None:
@@ -318,6 +343,9 @@ def eec_get_batch_offsets(ctx, n_circ):
 
 
 def eec_update_params(ctx, W, L, stream=None):
+    nd = _sizes(ctx)[0]
+    _need(W, nd, "W")
+    _need(L, nd, "L")
     _check(ctx, _load().eec_update_params(ctx, _d(W, name="W"), _d(L, name="L"), _stream(stream)))
 
 
@@ -343,6 +371,7 @@ def eec_get_tuning(ctx):
 
 
 def eec_eval_stamp(ctx, x, A, b, q=None, stream=None):
+    _need_step(ctx, x, A, b, q)
     _check(ctx, _load().eec_eval_stamp(ctx, _d(x, name="x"), _d(A, name="A"), _d(b, name="b"),
                                    _d(q, name="q"), _stream(stream)))
 
@@ -353,6 +382,7 @@ def eec_newton_dc(ctx, x, A, b, max_iter=200, vstep=0.2, step_rule=0, solver=0, 
     converge; returns the number of solves.
     step_rule 0: the whole step scaled to vstep; 1: every node's move clipped to vstep.
     solver 0: batched sparse QR, analysis reused; 1: sparse QR after an AMD ordering."""
+    _need_step(ctx, x, A, b)
     it = _I32(0)
     _check(ctx, _load().eec_newton_dc(ctx, _d(x, name="x"), _d(A, name="A"), _d(b, name="b"),
                                       int(max_iter), float(vstep), int(step_rule), int(solver),
@@ -376,18 +406,32 @@ def _hp(t, name):
 
 def eec_eval_stamp_host(ctx, x, A, b, q=None, stream=None):
     """eval_stamp with host buffers (torch CPU tensors, page-locked for async copies, or numpy)."""
+    _need_step(ctx, x, A, b, q)
     _check(ctx, _load().eec_eval_stamp_host(ctx, _hp(x, "x"), _hp(A, "A"), _hp(b, "b"),
                                             _hp(q, "q"), _stream(stream)))
 
 
 def eec_eval_stamp_tran(ctx, x, q_prev, i_prev, alpha, beta, A, b, q, i=None, stream=None):
+    _need_step(ctx, x, A, b, q)
+    nd = _sizes(ctx)[0]
+    _need(q_prev, 4 * nd, "q_prev")
+    _need(i_prev, 4 * nd, "i_prev")
+    _need(i, 4 * nd, "i")
     _check(ctx, _load().eec_eval_stamp_tran(
         ctx, _d(x, name="x"), _d(q_prev, name="q_prev"), _d(i_prev, name="i_prev"),
         float(alpha), float(beta), _d(A, name="A"), _d(b, name="b"), _d(q, name="q"),
         _d(i, name="i"), _stream(stream)))
 
 
+def _need_bwd(ctx, x, gA, gb, gx, gW, gL):
+    nd, n, nnz = _sizes(ctx)
+    for t, k, name in ((x, n, "x"), (gA, nnz, "gA"), (gb, n, "gb"), (gx, n, "gx"),
+                       (gW, nd, "gW"), (gL, nd, "gL")):
+        _need(t, k, name)
+
+
 def eec_eval_stamp_bwd(ctx, x, gA, gb, gx, gW, gL, stream=None):
+    _need_bwd(ctx, x, gA, gb, gx, gW, gL)
     _check(ctx, _load().eec_eval_stamp_bwd(ctx, _d(x, name="x"), _d(gA, name="gA"), _d(gb, name="gb"),
                                        _d(gx, name="gx"), _d(gW, name="gW"), _d(gL, name="gL"),
                                        _stream(stream)))
@@ -395,6 +439,7 @@ def eec_eval_stamp_bwd(ctx, x, gA, gb, gx, gW, gL, stream=None):
 
 def eec_eval_stamp_bwd_noalloc(ctx, x, gA, gb, gx, gW, gL, stream=None):
     """Backward with the library's fixed scratch array: allocates nothing (see include/eec.h)."""
+    _need_bwd(ctx, x, gA, gb, gx, gW, gL)
     _check(ctx, _load().eec_eval_stamp_bwd_noalloc(
         ctx, _d(x, name="x"), _d(gA, name="gA"), _d(gb, name="gb"), _d(gx, name="gx"),
         _d(gW, name="gW"), _d(gL, name="gL"), _stream(stream)))
@@ -404,6 +449,7 @@ EEC_NOALLOC_MAX_DEV = 524288
 
 
 def eec_graph_capture(ctx, x, A, b, q=None, stream=None):
+    _need_step(ctx, x, A, b, q)
     _check(ctx, _load().eec_graph_capture(ctx, _d(x), _d(A), _d(b), _d(q), _stream(stream)))
 
 
@@ -412,6 +458,7 @@ def eec_graph_launch(ctx, stream=None):
 
 
 def eec_autotune(ctx, x, A, b, q=None, reps=10, stream=None):
+    _need_step(ctx, x, A, b, q)
     ms = (ctypes.c_float * EEC_N_VARIANTS)()
     _check(ctx, _load().eec_autotune(ctx, _d(x), _d(A), _d(b), _d(q), int(reps), _stream(stream), ms))
     return [float(v) for v in ms]
@@ -437,6 +484,7 @@ def eec_profile_read(ctx):
 
 
 def eec_test_barrier_timeout(ctx, x, A, b, stream=None):
+    _need_step(ctx, x, A, b)
     _check(ctx, _load().eec_test_barrier_timeout(ctx, _d(x, name="x"), _d(A, name="A"),
                                                  _d(b, name="b"), _stream(stream)))
 

@@ -281,3 +281,37 @@ def test_header_is_plain_c_and_a_c_program_links(eec, tmp_path):
                     "-l:_libeec.so", "-Wl,-rpath," + libdir], check=True)
     out = subprocess.run([exe], capture_output=True, text=True)
     assert out.returncode == 0 and out.stdout.strip() == "ok", (out.returncode, out.stderr)
+
+
+def test_binding_refuses_buffers_of_the_wrong_length(eec):
+    # the C ABI takes bare pointers, so the binding checks every buffer's length against the
+    # context before the call (a short buffer would be overrun on the device)
+    import torch
+    net = netgen.ota5t()
+    ctx = _ctx_with(eec, net)
+    try:
+        eec.eec_color(ctx, n_dev=net.n_dev)
+        try:
+            eec.eec_build_scatter(ctx)
+        except eec.EECError as e:
+            assert e.code == eec.EEC_ECUDA
+        nd, n, nnz, _ = eec.eec_get_sizes(ctx)
+        z = lambda k: torch.zeros(k, dtype=torch.float64)
+        with pytest.raises(ValueError, match="A has"):
+            eec.eec_eval_stamp(ctx, z(n), z(nnz + 1), z(n))
+        with pytest.raises(ValueError, match="q has"):
+            eec.eec_eval_stamp(ctx, z(n), z(nnz), z(n), z(4 * nd - 1))
+        with pytest.raises(TypeError):          # right lengths: refused only for not being on the GPU
+            eec.eec_eval_stamp(ctx, z(n), z(nnz), z(n), z(4 * nd))
+        with pytest.raises(ValueError, match="x has"):
+            eec.eec_eval_stamp_host(ctx, np.zeros(n + 2), np.zeros(nnz), np.zeros(n))
+        with pytest.raises(ValueError, match="gW has"):
+            eec.eec_eval_stamp_bwd(ctx, z(n), z(nnz), z(n), z(n), z(nd + 1), z(nd))
+        with pytest.raises(ValueError, match="q_prev has"):
+            eec.eec_eval_stamp_tran(ctx, z(n), z(nd), None, 1e9, 0.0, z(nnz), z(n), z(4 * nd))
+        with pytest.raises(ValueError, match="b has"):
+            eec.eec_newton_dc(ctx, z(n), z(nnz), z(n - 1))
+        with pytest.raises(ValueError, match="L has"):
+            eec.eec_update_params(ctx, z(nd), z(nd + 3))
+    finally:
+        eec.eec_destroy(ctx)
