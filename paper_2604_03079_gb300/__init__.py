@@ -370,10 +370,14 @@ def eec_get_tuning(ctx):
     return int(v.value), int(blk.value), int(od.value)
 
 
-def eec_eval_stamp(ctx, x, A, b, q=None, stream=None):
-    _need_step(ctx, x, A, b, q)
+def _eval_stamp(ctx, x, A, b, q, stream):
     _check(ctx, _load().eec_eval_stamp(ctx, _d(x, name="x"), _d(A, name="A"), _d(b, name="b"),
                                    _d(q, name="q"), _stream(stream)))
+
+
+def eec_eval_stamp(ctx, x, A, b, q=None, stream=None):
+    _need_step(ctx, x, A, b, q)
+    _eval_stamp(ctx, x, A, b, q, stream)
 
 
 def eec_newton_dc(ctx, x, A, b, max_iter=200, vstep=0.2, step_rule=0, solver=0, tol_abs=1e-12,
@@ -563,7 +567,11 @@ class Circuit:
     def eval_stamp(self, x, A=None, b=None, q=None, want_q=True, stream=None):
         if A is None:
             A, b, q = self.new_outputs(want_q)
-        eec_eval_stamp(self.ctx, x, A, b, q, stream)
+        # lengths against the sizes this object holds (no query of the context per call)
+        for t, k, name in ((x, self.n, "x"), (A, self.nnz, "A"), (b, self.n, "b"),
+                           (q, 4 * self.n_dev, "q")):
+            _need(t, k, name)
+        _eval_stamp(self.ctx, x, A, b, q, stream)
         return A, b, q
 
     def bwd(self, x, gA, gb, stream=None):
