@@ -311,10 +311,12 @@ EEC_API int eec_eval_stamp_bwd(eec_ctx* ctx, const double* x_dev, const double* 
  * call; the caller passes every input and output as in eec_eval_stamp_bwd.
  *  - Limit: the context may hold at most EEC_NOALLOC_MAX_DEV devices (the array is
  *    4 * EEC_NOALLOC_MAX_DEV doubles = 16 MiB); larger contexts are rejected with EEC_EINVAL.
- *  - The array exists on every GPU on which the library is loaded and stays allocated until the
- *    process exits.
- *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress with
- *    that device current) and caches it; make that first call before any stream capture.
+ *  - The array exists on every GPU on which the library's backward module is loaded and stays
+ *    allocated until the process exits. eec_build_scatter loads that module on the current
+ *    device and looks up the array's device address there (cudaGetSymbolAddress with that device
+ *    current), so a context built on a device has the array ready before this entry point's
+ *    first call. A first call on a device where no context was built does that set-up itself;
+ *    make such a call before any stream capture.
  *  - Every call, from any context, shares the array, and it keeps the last call's contents. Each
  *    call writes every entry it later reads, so nothing needs clearing, but calls whose work
  *    overlaps on the GPU (e.g. on two streams without ordering between them) race on it.

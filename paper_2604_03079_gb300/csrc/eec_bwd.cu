@@ -328,8 +328,9 @@ cudaError_t launch_bwd_gather(const DevTopo& T, double* gx, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// Device address of g_noalloc_gv on the current device, looked up once per device (set-up on the
-// first call there) and cached; no allocation.
+// Device address of g_noalloc_gv on the current device, looked up once per device and cached; no
+// allocation. The lookup loads this file's module on that device (under lazy module loading the
+// module, and with it the array, would otherwise appear at the first backward launch).
 cudaError_t noalloc_scratch(double** out) {
   static std::mutex mu;
   static std::map<int, double*> cache;
@@ -349,6 +350,11 @@ cudaError_t noalloc_scratch(double** out) {
 }
 
 }  // namespace
+
+cudaError_t noalloc_setup() {
+  double* ptr = nullptr;
+  return noalloc_scratch(&ptr);
+}
 
 cudaError_t launch_bwd_noalloc(const DevTopo& T, const double* x, const double* gA,
                                const double* gb, double* gx, double* gW, double* gL,

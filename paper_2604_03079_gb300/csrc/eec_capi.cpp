@@ -62,7 +62,7 @@ struct eec_ctx {
   DevTopo d{};
   int* d_coff = nullptr;
   std::vector<void*> dmem;
-  int* d_status = nullptr;  // [0] status, [1..2] barrier
+  int* d_status = nullptr;  // [0] status, [1..kBarWords] grid barrier (see DevTopo::bar)
   bool params_dirty = false;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t auto_exec = nullptr;
@@ -1059,8 +1059,11 @@ int eec_build_scatter(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_out) {
       cudaError_t e = cudaGetLastError();
       return fail(c, EEC_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
     }
-    CUDA_TRY(c, cudaMalloc(&c->d_status, 4 * sizeof(int)));
-    CUDA_TRY(c, cudaMemset(c->d_status, 0, 4 * sizeof(int)));
+    CUDA_TRY(c, cudaMalloc(&c->d_status, (1 + kBarWords) * sizeof(int)));
+    CUDA_TRY(c, cudaMemset(c->d_status, 0, (1 + kBarWords) * sizeof(int)));
+    // the fixed scratch of eec_eval_stamp_bwd_noalloc: resolved here, at set-up, so that its
+    // module (and the array) is resident on this device before that entry point's first call
+    CUDA_TRY(c, noalloc_setup());
   }
   DevTopo& d = c->d;
   d.N = N;

@@ -76,8 +76,11 @@ struct DevTopo {
   int n_inc_light, n_inc_heavy;
   double* gv;       // [4][N] (allocated on first use)
   int* status;      // device status word: bit 0 timeout, bit 1 non-finite
-  unsigned* bar;    // grid barrier: [0] arrival count, [1] generation
+  unsigned* bar;    // grid barrier: [0] arrival count, [1] generation, [2] abort word of the
+                    // current launch (all kBarWords zeroed before each persistent launch)
 };
+
+constexpr int kBarWords = 3;
 
 constexpr int kHeavy = 32;  // contributions from which an entry gets a whole warp in the gather
 
@@ -151,6 +154,9 @@ cudaError_t launch_bwd(const DevTopo& T, const double* x, const double* gA, cons
 cudaError_t fp64_peak(int iters, int blocks_per_sm, double* flops);
 cudaError_t math_check(int fn, long long n, const double* x, double* ours, double* ref,
                        cudaStream_t s);
+// Resolve (once per device) the device address of the fixed scratch array of
+// launch_bwd_noalloc on the current device; this loads the module that holds the array.
+cudaError_t noalloc_setup();
 // Backward with its terminal-gradient scratch in the library's fixed array (no allocation).
 cudaError_t launch_bwd_noalloc(const DevTopo& T, const double* x, const double* gA,
                                const double* gb, double* gx, double* gW, double* gL,

@@ -37,8 +37,12 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 constexpr unsigned long long kBarrierLimitNs = 1000000000ull;  // 1 s
 
-// Grid-wide barrier for a co-resident (cooperative) grid. Every wait is bounded: after
-// kBarrierLimitNs the waiting block records kStatusTimeout and the whole grid returns false.
+// Grid-wide barrier for a co-resident (cooperative) grid. bar[0] counts arrivals, bar[1] is the
+// generation, bar[2] is this launch's abort word (zeroed with bar[0..1] before every launch).
+// Every wait is bounded: after kBarrierLimitNs the waiting block records kStatusTimeout in the
+// status word (sticky until the host reads it) and sets the abort word, and every block of the
+// grid returns false at its next wait. Waits test only the abort word, so a timeout recorded by
+// an earlier launch does not make a later launch give up.
 __device__ __forceinline__ bool grid_sync(unsigned* bar, int* status, int absent_block) {
   __shared__ int fail;
   __syncthreads();
@@ -56,9 +60,10 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, int* status, int absent
     } else {
       const unsigned long long t0 = global_ns();
       while (ld_acquire_u32(bar + 1) == gen) {
-        if (*((volatile int*)status) & kStatusTimeout) { fail = 1; break; }
+        if (*((volatile unsigned*)(bar + 2))) { fail = 1; break; }
         if (global_ns() - t0 > kBarrierLimitNs) {
           atomicOr(status, kStatusTimeout);
+          atomicExch(bar + 2, 1u);
           fail = 1;
           break;
         }
@@ -744,7 +749,7 @@ cudaError_t launch_persistent(const DevTopo& T, const int* color_off_dev, int n_
                               const double* x, double* A, double* b, double* q, int block,
                               int grid, int dbg, cudaStream_t s, int absent_block) {
   (void)block;
-  cudaError_t e = cudaMemsetAsync(T.bar, 0, 2 * sizeof(unsigned), s);
+  cudaError_t e = cudaMemsetAsync(T.bar, 0, kBarWords * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   DevTopo Tc = T;
   const int* coff = color_off_dev;
@@ -841,7 +846,7 @@ int stamp_persistent_max_blocks_per_sm() {
 cudaError_t launch_stamp_persistent(const DevTopo& T, const int* color_off_dev, int n_colors,
                                     double* A, double* b, int grid, cudaStream_t s) {
   if (n_colors <= 0) return cudaSuccess;
-  cudaError_t e = cudaMemsetAsync(T.bar, 0, 2 * sizeof(unsigned), s);
+  cudaError_t e = cudaMemsetAsync(T.bar, 0, kBarWords * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   DevTopo Tc = T;
   const int* coff = color_off_dev;

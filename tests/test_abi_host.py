@@ -51,6 +51,9 @@ def test_constants_agree(eec):
         if hasattr(eec, k):
             assert getattr(eec, k) == v, k
     assert d["EEC_CARD_LEN"] == netgen.CARD_LEN == oracle._load().ora_card_len()
+    # the no-allocation backward's limit is written twice (header and binding): named here so
+    # that a renamed or dropped copy fails instead of being skipped by the loop above
+    assert d["EEC_NOALLOC_MAX_DEV"] == eec.EEC_NOALLOC_MAX_DEV
 
 
 def _ctx_with(eec, net, rule=0, cards=None):

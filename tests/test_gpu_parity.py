@@ -435,6 +435,29 @@ def test_grid_barrier_timeout_is_reported_and_the_context_recovers(eec):
     check_against_oracle(eec, circ, o, x, 1)      # the persistent schedule still works
 
 
+@pytest.mark.parametrize("variant", [1, 4])
+def test_timeout_left_unread_does_not_abort_later_launches(eec, variant):
+    # A timeout stays recorded in the status word until the host reads it; the next persistent
+    # launches (the grid-barrier evaluation, and the grid-barrier colour stamp of the buffered
+    # schedule) must still pass every barrier and stamp everything.
+    import torch
+    net = netgen.inverter_chain(64)
+    o = oracle.Oracle(net, CARDS)
+    circ = eec.Circuit(net, CARDS, color=True, color_stamp=2)
+    x = netgen.random_x(net)
+    A, b, _ = circ.new_outputs(want_q=False)
+    eec.eec_test_barrier_timeout(circ.ctx, dev(x), A, b)
+    ref = o.eval_stamp(x, want_scale=True)
+    eec.eec_set_variant(circ.ctx, variant)
+    for _ in range(2):
+        A, b, _ = circ.eval_stamp(dev(x), want_q=False)
+        torch.cuda.synchronize()
+        assert rel_err(host(A), ref["A"], ref["A_scale"]).max() <= TOL
+        assert rel_err(host(b), ref["b"], ref["b_scale"]).max() <= TOL
+    assert circ.status() == eec.EEC_ETIMEOUT      # the one timeout, reported once
+    assert circ.status() == 0
+
+
 @pytest.mark.parametrize("variant,chunks", [(2, 0), (2, 1), (2, 5), (3, 3), (0, 4)])
 @pytest.mark.parametrize("pinned", [True, False])
 def test_host_buffer_entry_point(eec, pinned, variant, chunks):

@@ -6,6 +6,8 @@ same gradients as the allocating eec_eval_stamp_bwd, through the C ABI, on conse
 share the library's fixed scratch array, and refuse contexts larger than that array. This file
 is collected last so that a run stopping at the first failure has run every other test first.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -56,10 +58,42 @@ def test_noalloc_backward_matches_allocating_backward_on_consecutive_calls(eec):
                 assert _close(g, r)
 
 
+def test_noalloc_backward_on_a_fresh_context_allocates_nothing(eec):
+    # A fresh context: the no-allocation entry point runs first, so the allocating backward has
+    # never created its own scratch. Device memory is the same before and after a further call.
+    import torch
+    cards = netgen.default_cards()
+    net = netgen.random_logic(4000, seed=5)
+    circ = eec.Circuit(net, cards)
+    rng = netgen.Rng(300, 7)
+    x = torch.as_tensor(netgen.random_x(net, seed=9), device="cuda")
+    gA = torch.as_tensor(rng.normal(circ.nnz), device="cuda")
+    gb = torch.as_tensor(rng.normal(circ.n), device="cuda")
+    outs = [torch.empty(k, dtype=torch.float64, device="cuda") for k in (circ.n, circ.n_dev, circ.n_dev)]
+    eec.eec_eval_stamp_bwd_noalloc(circ.ctx, x, gA, gb, *outs)
+    torch.cuda.synchronize()
+    first = [t.cpu().numpy() for t in outs]
+    free0, _ = torch.cuda.mem_get_info()
+    eec.eec_eval_stamp_bwd_noalloc(circ.ctx, x, gA, gb, *outs)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    second = [t.cpu().numpy() for t in outs]
+    ref = _grads(eec, circ, eec.eec_eval_stamp_bwd, x, gA, gb)
+    for a, b, r in zip(first, second, ref):
+        assert np.array_equal(a, b)
+        assert np.all(np.isfinite(a)) and _close(a, r)
+
+
 def test_noalloc_backward_rejects_contexts_beyond_the_fixed_scratch(eec):
     import torch
+    import re
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                            "include", "eec.h")).read()
+    limit = int(re.search(r"#define\s+EEC_NOALLOC_MAX_DEV\s+(\d+)", hdr).group(1))
+    assert limit == eec.EEC_NOALLOC_MAX_DEV
     net = netgen.random_logic(200_000)
-    assert net.n_dev > eec.EEC_NOALLOC_MAX_DEV
+    assert net.n_dev > limit
     circ = eec.Circuit(net, netgen.default_cards(), color=False)
     x = torch.zeros(circ.n, dtype=torch.float64, device="cuda")
     gA = torch.zeros(circ.nnz, dtype=torch.float64, device="cuda")
