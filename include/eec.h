@@ -54,7 +54,10 @@ extern "C" {
 #define EEC_VARIANT_ATOMIC 2           /* uncoloured, FP64 atomicAdd stamping */
 #define EEC_VARIANT_SEGREDUCE 3        /* evaluate to buffer, then per-entry gather (no colours) */
 #define EEC_VARIANT_COLOR_BUFFERED 4   /* "Color": evaluate to buffer, then one stamp per colour */
-#define EEC_N_VARIANTS 5
+#define EEC_VARIANT_COLOR_PIPELINED 5  /* colour order in one launch: every device evaluated into
+                                          registers, each colour stamped once the colour before it
+                                          has stamped (per-colour completion counters) */
+#define EEC_N_VARIANTS 6
 
 /* Conflict rules for the colouring. */
 #define EEC_CONFLICT_FREE_NODE 0   /* share a free node (rails are free only under MNA_BRANCH) [default] */
@@ -279,7 +282,8 @@ EEC_API int eec_newton_dc(eec_ctx* ctx, double* x_dev, double* A_values_dev, dou
  *  q_dev       [4*n_dev] out: charges at x;  i_dev [4*n_dev] out, nullable: ic at x.
  * Schedule: the per-colour store-add when the variant is EEC_VARIANT_COLOR_FUSED; every device
  * into a buffer, then a colour-ordered stamp by one thread-block cluster, when it is
- * EEC_VARIANT_COLOR_BUFFERED (both need a colouring that counts gate rows: not
+ * EEC_VARIANT_COLOR_BUFFERED; the pipelined colour order in one launch when it is
+ * EEC_VARIANT_COLOR_PIPELINED (the three need a colouring that counts gate rows: not
  * EEC_CONFLICT_WRITE_ROWS); otherwise FP64 atomics.
  */
 EEC_API int eec_eval_stamp_tran(eec_ctx* ctx, const double* x_dev, const double* q_prev_dev,
@@ -426,11 +430,13 @@ EEC_API int eec_get_batch_offsets(const eec_ctx* ctx, int32_t* circ_row_off, int
 EEC_API int eec_fp64_peak(int32_t iters, int32_t blocks_per_sm, double* flops);
 
 /*
- * Test hook for the failure path of the persistent schedule's grid barrier (the paper has no
- * counterpart): launches the persistent kernel on these buffers with one block that never
- * arrives at the barriers, so the other blocks' waits run out after their 1 s limit and the
- * status word records EEC_ETIMEOUT (read it with eec_status). Nothing faults or hangs; A and b
- * are left partially stamped. Needs a coloured context with at least two colours.
+ * Test hook for the failure path of the device-side waits (the paper has no counterpart). When
+ * the context's schedule is EEC_VARIANT_COLOR_PIPELINED it launches the pipelined kernel with the
+ * first work item never reporting its stamps done, so the next colour's waits run out; otherwise
+ * it launches the persistent kernel with one block that never arrives at the grid barriers. The
+ * waits give up after their 1 s limit and the status word records EEC_ETIMEOUT (read it with
+ * eec_status). Nothing faults or hangs; A and b are left partially stamped. Needs a coloured
+ * context with at least two (non-empty) colours.
  */
 EEC_API int eec_test_barrier_timeout(eec_ctx* ctx, const double* x_dev, double* A_values_dev,
                                      double* b_dev, void* cuda_stream);

@@ -171,67 +171,6 @@ inline Cnt expm1(const Cnt& a) { return cnt1(std::expm1(a.v), a, &g_ops.expm1); 
 inline Cnt log1p(const Cnt& a) { return cnt1(std::log1p(a.v), a, &g_ops.log1p); }
 inline Cnt sqrt(const Cnt& a) { return cnt1(std::sqrt(a.v), a, &g_ops.sqrt); }
 
-// Magnitude forward mode: value plus, per direction, the sum over chain-rule paths of the
-// absolute values of the products along each path. It bounds |derivative| and measures how much
-// a derivative cancels; the transient error metric uses it as the size of a Jacobian entry.
-template <int N>
-struct Mag {
-  double v;
-  double m[N];
-  Mag() : v(0.0) { for (int i = 0; i < N; ++i) m[i] = 0.0; }
-  Mag(double c) : v(c) { for (int i = 0; i < N; ++i) m[i] = 0.0; }  // NOLINT: constants
-};
-template <int N> double val(const Mag<N>& x) { return x.v; }
-template <int N> Mag<N> operator+(const Mag<N>& a, const Mag<N>& b) {
-  Mag<N> r; r.v = a.v + b.v;
-  for (int i = 0; i < N; ++i) r.m[i] = a.m[i] + b.m[i];
-  return r;
-}
-template <int N> Mag<N> operator-(const Mag<N>& a, const Mag<N>& b) {
-  Mag<N> r; r.v = a.v - b.v;
-  for (int i = 0; i < N; ++i) r.m[i] = a.m[i] + b.m[i];
-  return r;
-}
-template <int N> Mag<N> operator-(const Mag<N>& a) { Mag<N> r = a; r.v = -a.v; return r; }
-template <int N> Mag<N> operator*(const Mag<N>& a, const Mag<N>& b) {
-  Mag<N> r; r.v = a.v * b.v;
-  for (int i = 0; i < N; ++i) r.m[i] = a.m[i] * std::fabs(b.v) + std::fabs(a.v) * b.m[i];
-  return r;
-}
-template <int N> Mag<N> operator/(const Mag<N>& a, const Mag<N>& b) {
-  Mag<N> r; r.v = a.v / b.v;
-  for (int i = 0; i < N; ++i) r.m[i] = (a.m[i] + std::fabs(r.v) * b.m[i]) / std::fabs(b.v);
-  return r;
-}
-template <int N> Mag<N> operator+(const Mag<N>& a, double b) { return a + Mag<N>(b); }
-template <int N> Mag<N> operator+(double a, const Mag<N>& b) { return Mag<N>(a) + b; }
-template <int N> Mag<N> operator-(const Mag<N>& a, double b) { return a - Mag<N>(b); }
-template <int N> Mag<N> operator-(double a, const Mag<N>& b) { return Mag<N>(a) - b; }
-template <int N> Mag<N> operator*(const Mag<N>& a, double b) { return a * Mag<N>(b); }
-template <int N> Mag<N> operator*(double a, const Mag<N>& b) { return Mag<N>(a) * b; }
-template <int N> Mag<N> operator/(const Mag<N>& a, double b) { return a / Mag<N>(b); }
-template <int N> Mag<N> operator/(double a, const Mag<N>& b) { return Mag<N>(a) / b; }
-template <int N> Mag<N> exp(const Mag<N>& a) {
-  Mag<N> r; r.v = std::exp(a.v);
-  for (int i = 0; i < N; ++i) r.m[i] = r.v * a.m[i];
-  return r;
-}
-template <int N> Mag<N> expm1(const Mag<N>& a) {
-  Mag<N> r; r.v = std::expm1(a.v);
-  for (int i = 0; i < N; ++i) r.m[i] = std::exp(a.v) * a.m[i];
-  return r;
-}
-template <int N> Mag<N> log1p(const Mag<N>& a) {
-  Mag<N> r; r.v = std::log1p(a.v);
-  for (int i = 0; i < N; ++i) r.m[i] = a.m[i] / std::fabs(1.0 + a.v);
-  return r;
-}
-template <int N> Mag<N> sqrt(const Mag<N>& a) {
-  Mag<N> r; r.v = std::sqrt(a.v);
-  for (int i = 0; i < N; ++i) r.m[i] = a.m[i] / (2.0 * r.v);
-  return r;
-}
-
 // ---------------------------------------------------------------------------------------------
 // EES-L1 model card (field order fixed by the card layout of the interface).
 struct Card {
@@ -499,6 +438,22 @@ void device_iv(const Circuit& c, int k, const double Vn[4], double I[4], double 
   }
 }
 
+// Overlap capacitances of one device (step 11 of the model): the gate-source and gate-drain
+// overlap charges CGSO W p (Vg - Vs) and CGDO W p (Vg - Vd) enter q_g with + and q_s, q_d with -,
+// so their derivatives are the constants +-CGSO W, +-CGDO W (p^2 = 1), independent of the bias.
+void overlap_caps(const Card& cd, double W, double Cov[4][4]) {
+  for (int t = 0; t < 4; ++t)
+    for (int u = 0; u < 4; ++u) Cov[t][u] = 0.0;
+  const double cs = cd.CGSO * W, cdr = cd.CGDO * W;
+  Cov[1][1] = cs + cdr;
+  Cov[1][2] = -cs;
+  Cov[1][0] = -cdr;
+  Cov[2][2] = cs;
+  Cov[2][1] = -cs;
+  Cov[0][0] = cdr;
+  Cov[0][1] = -cdr;
+}
+
 // Transient companion stamp of one Newton iterate x of a time step (Sec. II, Fig. 1: the
 // transient loop re-forms A x = b at every Newton iteration of every time step). The charge of
 // terminal t is integrated by a one-step rule: the capacitive current into the device is
@@ -506,6 +461,10 @@ void device_iv(const Circuit& c, int k, const double Vn[4], double I[4], double 
 // trapezoidal: alpha = 2/h, beta = 1). Linearising I_t + ic_t at x gives
 //   A[t][u] += G_tu + alpha C_tu,  b[t] += -I_t - ic_t + sum_u (G_tu + alpha C_tu) x_u
 // over all four terminal rows (the gate row now carries capacitive current).
+// Scales (sum of |contribution| per entry, as the DC stamp): a device adds three stamps to A[t][u]
+// -- the conductance G_tu, the intrinsic charge capacitance alpha C^int_tu and the overlap
+// capacitance alpha C^ov_tu (C = C^int + C^ov) -- each counted by its size; b[t] adds |I_t|,
+// the sizes of the terms of ic_t and each stamp's size times |x_u|.
 void stamp_tran(const Circuit& c, const double* x, const double* qprev, const double* iprev,
                 double alpha, double beta, double* A, double* b, double* q, double* icap,
                 double* As, double* bs) {
@@ -516,7 +475,7 @@ void stamp_tran(const Circuit& c, const double* x, const double* qprev, const do
   if (bs) std::fill(bs, bs + c.n, 0.0);
   stamp_linear(c, A, b, As, bs);
   for (int k = 0; k < c.n_dev; ++k) {
-    double Vn[4], I[4], G[4][4], Q[4], Cq[4][4];
+    double Vn[4], I[4], G[4][4], Q[4], Cq[4][4], Cov[4][4];
     int u_of[4];
     for (int t = 0; t < 4; ++t) {
       int node = c.dn[4 * k + t];
@@ -524,17 +483,7 @@ void stamp_tran(const Circuit& c, const double* x, const double* qprev, const do
       Vn[t] = node_voltage(c, x, node);
     }
     device_iv(c, k, Vn, I, G, Q, Cq);
-    double Gm[4][4], Cm[4][4];   // sizes of the Jacobian entries (magnitude forward mode)
-    if (As || bs) {
-      Mag<4> V[4], Im[4], Qm[4];
-      for (int t = 0; t < 4; ++t) { V[t] = Mag<4>(Vn[t]); V[t].m[t] = 1.0; }
-      ees_l1<Mag<4>>(c.cards[c.mid[k]], c.type[k], Mag<4>(c.W[k]), Mag<4>(c.L[k]), V, Im, Qm);
-      for (int t = 0; t < 4; ++t)
-        for (int u = 0; u < 4; ++u) {
-          Gm[t][u] = Im[t].m[u];
-          Cm[t][u] = Qm[t].m[u];
-        }
-    }
+    overlap_caps(c.cards[c.mid[k]], c.W[k], Cov);
     for (int t = 0; t < 4; ++t) {
       const long at = static_cast<long>(t) * c.n_dev + k;
       const double ic = alpha * (Q[t] - qprev[at]) - (iprev ? beta * iprev[at] : 0.0);
@@ -549,7 +498,8 @@ void stamp_tran(const Circuit& c, const double* x, const double* qprev, const do
         const double a = G[t][u] + alpha * Cq[t][u];
         long p = c.where.at({u_of[t], u_of[u]});
         A[p] += a;
-        const double am = (As || bs) ? Gm[t][u] + alpha * Cm[t][u] : 0.0;
+        const double am = std::fabs(G[t][u]) + alpha * std::fabs(Cq[t][u] - Cov[t][u]) +
+                          alpha * std::fabs(Cov[t][u]);
         if (As) As[p] += am;
         rhs += a * Vn[u];
         scale += am * std::fabs(Vn[u]);

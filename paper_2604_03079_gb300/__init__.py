@@ -28,8 +28,10 @@ EEC_VARIANT_PERSISTENT = 1
 EEC_VARIANT_ATOMIC = 2
 EEC_VARIANT_SEGREDUCE = 3
 EEC_VARIANT_COLOR_BUFFERED = 4
-EEC_N_VARIANTS = 5
-VARIANT_NAMES = {0: "color_fused", 1: "persistent", 2: "atomic", 3: "segreduce", 4: "color_buffered"}
+EEC_VARIANT_COLOR_PIPELINED = 5
+EEC_N_VARIANTS = 6
+VARIANT_NAMES = {0: "color_fused", 1: "persistent", 2: "atomic", 3: "segreduce", 4: "color_buffered",
+                 5: "color_pipelined"}
 EEC_CONFLICT_FREE_NODE, EEC_CONFLICT_ANY_NONGROUND, EEC_CONFLICT_WRITE_ROWS = 0, 1, 2
 EEC_COLOR_GREEDY_SEQ, EEC_COLOR_JP_INDEX, EEC_COLOR_JP_RANDOM = 0, 1, 2
 EEC_RAIL_ELIMINATE, EEC_RAIL_MNA_BRANCH = 0, 1

@@ -77,6 +77,8 @@ struct eec_ctx {
   int persist_grid = 0;
   int stamp_grid = 0;          // blocks of the one-launch colour stamp
   int stamp_mode = 0;          // colour-buffered stamp: 0 per-colour launches, 1 grid, 2 cluster
+  int pipe_grid = 0;           // blocks of the pipelined colour schedule (resident blocks)
+  int pipe_colors = 0;         // non-empty colours (counters of the pipelined schedule)
   // phase timing and launch counting
   bool prof = false;
   bool graph_all = false;      // eec_batch_capture_graph: every schedule replays a cached graph
@@ -327,7 +329,7 @@ void prof_mark(eec_ctx* c, cudaStream_t s) {
 
 bool variant_needs_colors(int v) {
   return v == EEC_VARIANT_COLOR_FUSED || v == EEC_VARIANT_PERSISTENT ||
-         v == EEC_VARIANT_COLOR_BUFFERED;
+         v == EEC_VARIANT_COLOR_BUFFERED || v == EEC_VARIANT_COLOR_PIPELINED;
 }
 
 // Enqueue one evaluate-and-stamp with schedule v on stream s. Returns the number of kernels
@@ -414,6 +416,16 @@ int run_variant(eec_ctx* c, int v, const double* x, double* A, double* b, double
           ++*nk;
         }
       }
+      break;
+    case EEC_VARIANT_COLOR_PIPELINED:
+      // evaluation and colour-ordered stamping in one launch; it overlaps the initialisation
+      // unless a profiling event sits between the two launches (then the phase split is
+      // init | evaluate-and-stamp, and the stamp phase is empty)
+      if ((rc = init_Ab())) return rc;
+      prof_mark(c, s);
+      CUDA_TRY(c, launch_color_pipe(T, c->pipe_colors, x, A, b, q, c->pipe_grid, dbg, s));
+      *nk += c->d.n_pitem > 0;
+      prof_mark(c, s);
       break;
     default:
       return fail(c, EEC_EINVAL, "unknown variant");
@@ -1128,6 +1140,34 @@ int eec_build_scatter(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_out) {
     if (c->opt.color_stamp == 2 && c->stamp_grid > 0) c->stamp_mode = 1;
     if (c->opt.color_stamp == 3) c->stamp_mode = 2;
   }
+  // Work items of the pipelined colour schedule: the non-empty colours in order, each cut into
+  // items of up to kPipeItem positions; every item carries its colour's index among the
+  // non-empty colours and the number of items of the colour before it (what it waits for).
+  if (c->colored) {
+    std::vector<int4> items;
+    int j = -1, prev_items = 0, cur_items = 0;
+    for (int k = 0; k < c->C; ++k) {
+      const int b0 = c->color_off[k], b1 = c->color_off[k + 1];
+      if (b1 <= b0) continue;
+      if (j >= 0) prev_items = cur_items;
+      ++j;
+      cur_items = 0;
+      for (int p = b0; p < b1; p += kPipeItem) {
+        items.push_back(make_int4(p, std::min(p + kPipeItem, b1), j, j > 0 ? prev_items : 0));
+        ++cur_items;
+      }
+    }
+    c->pipe_colors = j + 1;
+    if ((rc = dupload(c, &d.pitem, items)) ||
+        (rc = dalloc(c, &d.pipe, (size_t)kPipeHdr + c->pipe_colors)))
+      return rc;
+    CUDA_TRY(c, cudaMemset(d.pipe, 0, sizeof(unsigned) * (kPipeHdr + c->pipe_colors)));
+    d.n_pitem = (int)items.size();
+    c->pipe_grid = std::max(1, color_pipe_max_blocks_per_sm()) * c->sms;
+  } else {
+    d.n_pitem = 0;
+    c->pipe_colors = 0;
+  }
   // Launch order of the order-free evaluations: devices with a free source or body (the body
   // effect, the source junction and the vbs chain are evaluated per call) before those with both
   // held, so that the last partial wave of blocks holds the cheaper devices.
@@ -1526,7 +1566,9 @@ int eec_eval_stamp_tran(eec_ctx* c, const double* x, const double* q_prev, const
   if (!std::isfinite(alpha) || !std::isfinite(beta) || alpha < 0.0)
     return fail(c, EEC_EINVAL, "alpha must be finite and >= 0, beta finite");
   int v = effective_variant(c);
-  if (v != EEC_VARIANT_COLOR_FUSED && v != EEC_VARIANT_COLOR_BUFFERED) v = EEC_VARIANT_ATOMIC;
+  if (v != EEC_VARIANT_COLOR_FUSED && v != EEC_VARIANT_COLOR_BUFFERED &&
+      v != EEC_VARIANT_COLOR_PIPELINED)
+    v = EEC_VARIANT_ATOMIC;
   if (v != EEC_VARIANT_ATOMIC && (!c->colored || c->opt.conflict_rule == EEC_CONFLICT_WRITE_ROWS))
     return fail(c, EEC_ESTATE, "transient colour stamping needs a colouring that counts gate rows");
   if (v == EEC_VARIANT_COLOR_BUFFERED && !c->d.buf_tran &&
@@ -1540,6 +1582,9 @@ int eec_eval_stamp_tran(eec_ctx* c, const double* x, const double* q_prev, const
   if (v == EEC_VARIANT_ATOMIC) {
     CUDA_TRY(c, launch_eval_tran(c->d, MODE_ATOMIC, 0, c->n_dev, x, A, b, ta, blk, s));
     c->n_kernels += c->n_dev > 0;
+  } else if (v == EEC_VARIANT_COLOR_PIPELINED) {
+    CUDA_TRY(c, launch_color_pipe_tran(c->d, c->pipe_colors, x, A, b, ta, c->pipe_grid, s));
+    c->n_kernels += c->d.n_pitem > 0;
   } else if (v == EEC_VARIANT_COLOR_BUFFERED) {
     // every device into the buffer in one launch, then the colour-ordered stamp by one cluster
     CUDA_TRY(c, launch_eval_tran(c->d, MODE_BUFFER, 0, c->n_dev, x, A, b, ta, blk, s));
@@ -1762,6 +1807,12 @@ int eec_test_barrier_timeout(eec_ctx* c, const double* x, double* A, double* b, 
   if (!x || !A || !b) return fail(c, EEC_EINVAL, "NULL x, A or b");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   CUDA_TRY(c, launch_init_lin(c->d, A, b, s));
+  if (effective_variant(c) == EEC_VARIANT_COLOR_PIPELINED) {
+    if (c->pipe_colors < 2) return fail(c, EEC_ESTATE, "needs >= 2 non-empty colours");
+    CUDA_TRY(c, launch_color_pipe(c->d, c->pipe_colors, x, A, b, nullptr, c->pipe_grid, 0, s,
+                                  /*absent_item=*/0));
+    return EEC_OK;
+  }
   CUDA_TRY(c, launch_persistent(c->d, c->d_coff, c->C, x, A, b, nullptr, 0, c->persist_grid, 0, s,
                                 /*absent_block=*/0));
   return EEC_OK;

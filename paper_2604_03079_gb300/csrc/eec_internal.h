@@ -75,12 +75,21 @@ struct DevTopo {
   int* inc_heavy;   // the others (one warp each)
   int n_inc_light, n_inc_heavy;
   double* gv;       // [4][N] (allocated on first use)
+  // pipelined colour schedule: work items of up to kPipeItem devices of one colour, in colour
+  // order; item i = {first position, end position, colour j (among the non-empty colours),
+  // number of items of colour j - 1 (0 for the first)}
+  int4* pitem;      // [n_pitem]
+  int n_pitem;
+  unsigned* pipe;   // [kPipeHdr + non-empty colours]: ticket, blocks left, abort word, unused,
+                    // then per colour the items whose stamps are done (all zero between launches)
   int* status;      // device status word: bit 0 timeout, bit 1 non-finite
   unsigned* bar;    // grid barrier: [0] arrival count, [1] generation, [2] abort word of the
                     // current launch (all kBarWords zeroed before each persistent launch)
 };
 
 constexpr int kBarWords = 3;
+constexpr int kPipeItem = 128;   // devices per work item of the pipelined colour schedule
+constexpr int kPipeHdr = 4;
 
 constexpr int kHeavy = 32;  // contributions from which an entry gets a whole warp in the gather
 
@@ -149,6 +158,18 @@ cudaError_t launch_eval_tran(const DevTopo& T, int mode, int begin, int end, con
                              double* A, double* b, const TranArgs& ta, int block, cudaStream_t s);
 cudaError_t launch_stamp_buffer(const DevTopo& T, int begin, int end, double* A, double* b,
                                 int block, cudaStream_t s);
+// Pipelined colour schedule: one launch of `grid` blocks (programmatic dependent of the
+// initialisation of A and b) that evaluates every device and stamps colour after colour, each
+// colour's stamps after every stamp of the colour before it (per-colour completion counters,
+// bounded waits). absent_item >= 0 is a test hook: that item never reports its stamps done, so
+// the next colour's waits expire and the status word records a timeout.
+cudaError_t launch_color_pipe(const DevTopo& T, int n_colors_nonempty, const double* x, double* A,
+                              double* b, double* q, int grid, int dbg, cudaStream_t s,
+                              int absent_item = -1);
+cudaError_t launch_color_pipe_tran(const DevTopo& T, int n_colors_nonempty, const double* x,
+                                   double* A, double* b, const TranArgs& ta, int grid,
+                                   cudaStream_t s);
+int color_pipe_max_blocks_per_sm();
 cudaError_t launch_bwd(const DevTopo& T, const double* x, const double* gA, const double* gb,
                        double* gx, double* gW, double* gL, int block, cudaStream_t s);
 cudaError_t fp64_peak(int iters, int blocks_per_sm, double* flops);

@@ -17,6 +17,8 @@
 // parameters are precomputed per device so that no division on W or L is repeated per call.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "eec_model.cuh"
 
 namespace eec {
@@ -93,15 +95,17 @@ __device__ __forceinline__ PrmS<double> load_prm(const DevTopo& T, int k) {
   return P;
 }
 
-// Evaluate device at layout position k and stamp (MODE_RMW / MODE_ATOMIC) or buffer it.
-template <int MODE, bool WANT_Q>
-__device__ __forceinline__ void eval_one(const DevTopo& T, int k, const double* __restrict__ x,
-                                         double* A, double* b, double* __restrict__ q,
-                                         int dbg) {
+// Device k's terminal unknowns and voltages, its per-device constants and the model at that bias
+// (WANT_C: with the charge Jacobian of the transient stamp).
+template <bool WANT_Q, bool WANT_C>
+__device__ __forceinline__ void eval_model(const DevTopo& T, int k, const double* __restrict__ x,
+                                           int idx[4], double V[4], EvalOut<double>& o) {
   const long long N = T.N;
   const int4 ti = __ldg(T.tidx + k);
-  const int idx[4] = {ti.x, ti.y, ti.z, ti.w};
-  double V[4];
+  idx[0] = ti.x;
+  idx[1] = ti.y;
+  idx[2] = ti.z;
+  idx[3] = ti.w;
 #pragma unroll
   for (int t = 0; t < 4; ++t)
     V[t] = idx[t] >= 0 ? __ldg(x + idx[t]) : __ldg(T.vfix + ~idx[t]);
@@ -122,8 +126,19 @@ __device__ __forceinline__ void eval_one(const DevTopo& T, int k, const double* 
     bk.gjs = __ldg(q0 + 6 * N);
     bk.Qb = __ldg(q0 + 7 * N);
   }
+  ees_l1<double, WANT_Q, WANT_C>(c, psb, P, V, o, sbf, &bk);
+}
+
+// Evaluate device at layout position k and stamp (MODE_RMW / MODE_ATOMIC) or buffer it.
+template <int MODE, bool WANT_Q>
+__device__ __forceinline__ void eval_one(const DevTopo& T, int k, const double* __restrict__ x,
+                                         double* A, double* b, double* __restrict__ q,
+                                         int dbg) {
+  const long long N = T.N;
+  int idx[4];
+  double V[4];
   EvalOut<double> o;
-  ees_l1<double, WANT_Q>(c, psb, P, V, o, sbf, &bk);
+  eval_model<WANT_Q, false>(T, k, x, idx, V, o);
 
   // A and b may still be being initialised by the kernel launched just before this one
   // (programmatic dependent launch): wait for it before the first addition
@@ -188,31 +203,10 @@ template <int MODE>
 __device__ __forceinline__ void eval_one_tran(const DevTopo& T, int k, const double* __restrict__ x,
                                               double* A, double* b, const TranArgs& ta) {
   const long long N = T.N;
-  const int4 ti = __ldg(T.tidx + k);
-  const int idx[4] = {ti.x, ti.y, ti.z, ti.w};
+  int idx[4];
   double V[4];
-#pragma unroll
-  for (int t = 0; t < 4; ++t)
-    V[t] = idx[t] >= 0 ? __ldg(x + idx[t]) : __ldg(T.vfix + ~idx[t]);
-  const int meta = __ldg(T.meta + k);
-  const CardK& c = T.cards[meta >> 2];
-  const unsigned long long psb = (meta & 1) ? kSignBit : 0ull;
-  const bool sbf = (meta >> 1) & 1;
-  const PrmS<double> P = load_prm(T, k);
-  BodyK bk;
-  if (sbf) {
-    const double* q0 = T.bodyk + k;
-    bk.sqs = __ldg(q0);
-    bk.Vthb = __ldg(q0 + N);
-    bk.dVth_dvbs = __ldg(q0 + 2 * N);
-    bk.Ab = __ldg(q0 + 3 * N);
-    bk.dAb_dvbs = __ldg(q0 + 4 * N);
-    bk.Ijs = __ldg(q0 + 5 * N);
-    bk.gjs = __ldg(q0 + 6 * N);
-    bk.Qb = __ldg(q0 + 7 * N);
-  }
   EvalOut<double> o;
-  ees_l1<double, true, true>(c, psb, P, V, o, sbf, &bk);
+  eval_model<true, true>(T, k, x, idx, V, o);
   if (MODE != MODE_BUFFER) asm volatile("griddepcontrol.wait;" ::: "memory");   // see eval_one
   const int od = __ldg(T.orig + k);
 #pragma unroll
@@ -594,6 +588,222 @@ __global__ void __launch_bounds__(kStampBlock) k_stamp_persistent(DevTopo T,
   }
 }
 
+// ---- Pipelined colour schedule -------------------------------------------------------------
+// The colour order of Sec. II (devices of one colour stamp lock-free, colours one after another)
+// without a barrier between colours: work items of up to kPipeItem devices of one colour, in
+// colour order, are taken from a ticket counter. A block evaluates its item's devices into
+// registers, then waits until every item of the previous colour has stamped, stamps, and counts
+// its item done for its colour. While colour c stamps, later items are already evaluating, so on
+// a netlist with few colours the stamps hide under the evaluation; with many small colours the
+// chain of per-colour hand-overs (about a microsecond each) sets the time.
+// Deadlock freedom: an item only waits for items of lower ticket, and a ticket is only taken by
+// a block that is running and finishes its item without waiting for a higher one. Waits are
+// bounded (kBarrierLimitNs): a block that gives up records kStatusTimeout and sets the launch's
+// abort word, after which every later wait gives up at once (no stamp is applied after an
+// abort: A and b are then incomplete and the call reports EEC_ETIMEOUT through eec_status).
+// Within a colour no two devices share a row, so every entry receives at most one device's
+// additions per colour; the additions are performed in L2 (no load of A into the SM) and each
+// entry sums its contributions in colour order, so the result is deterministic and equals the
+// per-colour launches' bitwise.
+constexpr int kPipeBlock = kPipeItem;
+
+// The item loop. Work::eval(k) evaluates device k into registers (before any wait);
+// Work::stamp() applies its additions (after the previous colour is complete).
+template <class Work>
+__device__ __forceinline__ void pipe_loop(const DevTopo& T, Work& w, int absent_item) {
+  __shared__ int4 s_it;
+  __shared__ int s_num, s_go;
+  unsigned* st = T.pipe;
+  bool init_seen = false;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int it = (int)atomicAdd(st, 1u);
+      s_num = it;
+      if (it < T.n_pitem) s_it = __ldg(T.pitem + it);
+    }
+    __syncthreads();
+    const int it = s_num;
+    if (it >= T.n_pitem) break;                       // uniform: the tickets are used up
+    const int4 item = s_it;
+    const int k = item.x + (int)threadIdx.x;
+    const bool valid = k < item.y;
+    if (valid) w.eval(k);
+    // A and b are initialised by the kernel launched before this one (programmatic dependent
+    // launch): wait for it before the first addition
+    if (!init_seen) {
+      asm volatile("griddepcontrol.wait;" ::: "memory");
+      init_seen = true;
+    }
+    if (threadIdx.x == 0) {
+      int go = 1;
+      if (item.w > 0) {
+        const unsigned* dp = st + kPipeHdr + item.z - 1;
+        const unsigned need = (unsigned)item.w;
+        if (ld_acquire_u32(dp) < need) {
+          const unsigned long long t0 = global_ns();
+          while (ld_acquire_u32(dp) < need) {
+            if (*((volatile unsigned*)(st + 2))) { go = 0; break; }
+            if (global_ns() - t0 > kBarrierLimitNs) {
+              atomicOr(T.status, kStatusTimeout);
+              atomicExch(st + 2, 1u);
+              go = 0;
+              break;
+            }
+          }
+        }
+      }
+      s_go = go;
+    }
+    __syncthreads();
+    if (s_go && valid) w.stamp();
+    __syncthreads();                                   // every thread's additions issued
+    if (threadIdx.x == 0 && it != absent_item) {
+      __threadfence();                                 // ... and performed before the count
+      atomicAdd(st + kPipeHdr + item.z, 1u);
+    }
+  }
+  // the last block to leave zeroes the counters for the next launch: every other block has
+  // left, and the next launch in the stream starts after this one has completed
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(st + 1, 1u) == gridDim.x - 1) {
+      const int nc = T.n_pitem > 0 ? __ldg(&T.pitem[T.n_pitem - 1].z) + 1 : 0;
+      for (int j = 0; j < nc; ++j) st[kPipeHdr + j] = 0u;
+      st[0] = 0u;
+      st[2] = 0u;
+      __threadfence();
+      st[1] = 0u;
+    }
+  }
+}
+
+// DC work of one device: currents and conductances at x; rows d, s, b stamped.
+template <bool WANT_Q>
+struct PipeDC {
+  const DevTopo& T;
+  const double* __restrict__ x;
+  double* A;
+  double* b;
+  double* __restrict__ q;
+  int dbg;
+  int row[3];
+  int sl[kNSlot];
+  double g[kNSlot];
+  double rhs[3];
+
+  __device__ __forceinline__ void eval(int k) {
+    const long long N = T.N;
+    int idx[4];
+    double V[4];
+    EvalOut<double> o;
+    eval_model<WANT_Q, false>(T, k, x, idx, V, o);
+    const int term[3] = {0, 2, 3};
+    bool ok = true;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      row[r] = idx[term[r]];
+      double s = -o.I[term[r]];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        g[4 * r + u] = o.G[r][u];
+        sl[4 * r + u] = (row[r] >= 0 && idx[u] >= 0) ? __ldg(T.slot + (4 * r + u) * N + k) : -1;
+        if (idx[u] >= 0) s = fma(o.G[r][u], V[u], s);
+        ok = ok && isfinite(o.G[r][u]);
+      }
+      rhs[r] = s;
+      ok = ok && (row[r] < 0 || isfinite(s));
+    }
+    if (WANT_Q) {
+      const int od = __ldg(T.orig + k);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) q[t * N + od] = o.Q[t];
+    }
+    if (dbg && !ok) atomicOr(T.status, kStatusNumeric);
+  }
+
+  __device__ __forceinline__ void stamp() {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      if (row[r] < 0) continue;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (sl[4 * r + u] >= 0) atomicAdd(A + sl[4 * r + u], g[4 * r + u]);
+      atomicAdd(b + row[r], rhs[r]);
+    }
+  }
+};
+
+// Transient work of one device: G + alpha C on all four rows, -I - ic + (G + alpha C) V.
+struct PipeTran {
+  const DevTopo& T;
+  const double* __restrict__ x;
+  double* A;
+  double* b;
+  const TranArgs& ta;
+  int row[4];
+  int sl[16];
+  double a[16];
+  double rhs[4];
+
+  __device__ __forceinline__ void eval(int k) {
+    const long long N = T.N;
+    int idx[4];
+    double V[4];
+    EvalOut<double> o;
+    eval_model<true, true>(T, k, x, idx, V, o);
+    const int od = __ldg(T.orig + k);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const long long at = t * N + od;
+      const double ic = ta.alpha * (o.Q[t] - __ldg(ta.qprev + at)) -
+                        (ta.iprev ? ta.beta * __ldg(ta.iprev + at) : 0.0);
+      ta.q[at] = o.Q[t];
+      if (ta.icap) ta.icap[at] = ic;
+      row[t] = idx[t];
+      const int r = t == 0 ? 0 : (t == 2 ? 1 : 2);   // row of G (gate row of G is zero)
+      double s = -(t == 1 ? 0.0 : o.I[t]) - ic;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const double v = fma(ta.alpha, o.C[t][u], t == 1 ? 0.0 : o.G[r][u]);
+        a[4 * t + u] = v;
+        sl[4 * t + u] = (idx[t] >= 0 && idx[u] >= 0)
+                            ? (t == 1 ? __ldg(T.slot_g + u * N + k)
+                                      : __ldg(T.slot + (4 * r + u) * N + k))
+                            : -1;
+        if (idx[u] >= 0) s = fma(v, V[u], s);
+      }
+      rhs[t] = s;
+    }
+  }
+
+  __device__ __forceinline__ void stamp() {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      if (row[t] < 0) continue;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (sl[4 * t + u] >= 0) atomicAdd(A + sl[4 * t + u], a[4 * t + u]);
+      atomicAdd(b + row[t], rhs[t]);
+    }
+  }
+};
+
+template <bool WANT_Q>
+__global__ void __launch_bounds__(kPipeBlock) k_color_pipe(DevTopo T, const double* __restrict__ x,
+                                                          double* A, double* b, double* q,
+                                                          int dbg, int absent_item) {
+  PipeDC<WANT_Q> w{T, x, A, b, q, dbg};
+  pipe_loop(T, w, absent_item);
+}
+
+__global__ void __launch_bounds__(kPipeBlock) k_color_pipe_tran(DevTopo T,
+                                                               const double* __restrict__ x,
+                                                               double* A, double* b,
+                                                               TranArgs ta) {
+  PipeTran w{T, x, A, b, ta};
+  pipe_loop(T, w, -1);
+}
+
 __global__ void k_dfma(double* out, int iters, double a, double c) {
   double x0 = threadIdx.x * 1e-3, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3;
   double x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6, x7 = x0 + 7;
@@ -865,6 +1075,40 @@ cudaError_t launch_stamp_buffer(const DevTopo& T, int begin, int end, double* A,
   const int B = eval_block(end - begin, block);
   k_stamp_buffer<<<grid_for(end - begin, B), B, 0, s>>>(T, begin, end, A, b);
   return cudaGetLastError();
+}
+
+int color_pipe_max_blocks_per_sm() {
+  int a = 0, b2 = 0, c2 = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_color_pipe<true>, kPipeBlock, 0) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_color_pipe<false>, kPipeBlock, 0) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c2, k_color_pipe_tran, kPipeBlock, 0) !=
+          cudaSuccess)
+    return 0;
+  return std::min(a, std::min(b2, c2));
+}
+
+cudaError_t launch_color_pipe(const DevTopo& T, int n_colors_nonempty, const double* x, double* A,
+                              double* b, double* q, int grid, int dbg, cudaStream_t s,
+                              int absent_item) {
+  (void)n_colors_nonempty;
+  if (T.n_pitem <= 0) return cudaSuccess;
+  const int g = std::max(1, std::min(grid, T.n_pitem));
+  if (q)
+    return launch_maybe_pdl(k_color_pipe<true>, g, kPipeBlock, s, true, T, x, A, b, q, dbg,
+                            absent_item);
+  return launch_maybe_pdl(k_color_pipe<false>, g, kPipeBlock, s, true, T, x, A, b, q, dbg,
+                          absent_item);
+}
+
+cudaError_t launch_color_pipe_tran(const DevTopo& T, int n_colors_nonempty, const double* x,
+                                   double* A, double* b, const TranArgs& ta, int grid,
+                                   cudaStream_t s) {
+  (void)n_colors_nonempty;
+  if (T.n_pitem <= 0) return cudaSuccess;
+  const int g = std::max(1, std::min(grid, T.n_pitem));
+  return launch_maybe_pdl(k_color_pipe_tran, g, kPipeBlock, s, true, T, x, A, b, ta);
 }
 
 cudaError_t math_check(int fn, long long n, const double* x, double* ours, double* ref,

@@ -75,8 +75,36 @@ def chromatic_number(adj):
     return n
 
 
+# Parity records of this test session: per check, the cancellation-aware error, the plain
+# relative error and how much the entries cancel (printed by conftest at the end of the run).
+PARITY_LOG = []
+
+
 def rel_err(got, ref, scale):
-    """Cancellation-aware per-entry error |got - ref| / max(|ref|, scale)."""
+    """Cancellation-aware per-entry error |got - ref| / max(|ref|, scale). Also records, for the
+    session summary, the plain relative error |got - ref| / |ref| (entries with ref != 0) and the
+    ratio scale / |ref| (how far the entry's contributions cancel)."""
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
     den = np.maximum(np.abs(ref), scale)
     den = np.where(den == 0, 1.0, den)
-    return np.abs(got - ref) / den
+    err = np.abs(got - ref) / den
+    _record(got, ref, scale, err)
+    return err
+
+
+def _record(got, ref, scale, err):
+    import os
+    nz = ref != 0
+    rec = {"test": os.environ.get("PYTEST_CURRENT_TEST", "").split(" ")[0], "n": int(ref.size),
+           "max_err": float(err.max()) if err.size else 0.0}
+    if nz.any():
+        plain = np.abs(got[nz] - ref[nz]) / np.abs(ref[nz])
+        ratio = np.asarray(scale, np.float64)[nz] / np.abs(ref[nz]) if np.ndim(scale) else \
+            np.full(int(nz.sum()), float(scale)) / np.abs(ref[nz])
+        well = ratio <= 10.0
+        rec.update(max_plain=float(plain.max()), p99_plain=float(np.quantile(plain, 0.99)),
+                   p99_ratio=float(np.quantile(ratio, 0.99)), max_ratio=float(ratio.max()),
+                   frac_ratio_gt10=float(1.0 - well.mean()),
+                   max_plain_well=float(plain[well].max()) if well.any() else 0.0)
+    PARITY_LOG.append(rec)

@@ -61,11 +61,15 @@ def test_gpu_newton_reports_non_convergence_without_a_device_error(eec):
 
 
 @pytest.mark.parametrize("make,rail_mode,max_iter", [(lambda: netgen.inverter_chain(64), 0, 150),
-                                                     (lambda: netgen.inverter_chain(64), 1, 200)])
+                                                     (lambda: netgen.inverter_chain(64), 1, 300)])
 def test_gshunt_stepping_where_plain_newton_fails(eec, make, rail_mode, max_iter):
     # plain damped Newton does not converge on these from the start below (the oracle needs its
     # gshunt-stepping fallback too); the GPU loop falls back the same way and reaches the
-    # oracle's operating point
+    # oracle's operating point. Solves needed (whole-step scaling, counted with the oracle's
+    # stamps and a sparse LU): rails eliminated, plain Newton 170 and the stages at most 120;
+    # rails as unknowns, plain Newton none within 600 and the 1e-4 S stage 194-207 depending on
+    # the rounding of A and b -- so that case gets 300 solves per stage, not a limit inside that
+    # spread (the atomic schedule's rounding varies from run to run).
     import torch
     net = make()
     o = oracle.Oracle(net, CARDS, rail_mode=rail_mode)

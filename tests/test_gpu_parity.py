@@ -16,7 +16,8 @@ from helpers import rel_err
 pytestmark = pytest.mark.gpu
 TOL = 1e-12
 CARDS = netgen.default_cards()
-ALL_VARIANTS = [0, 1, 2, 3, 4]
+ALL_VARIANTS = [0, 1, 2, 3, 4, 5]
+DETERMINISTIC = [0, 1, 3, 4, 5]   # every schedule but the atomic one
 
 
 @pytest.fixture(scope="module")
@@ -101,7 +102,7 @@ def test_edge_cases(eec, variant):
             check_against_oracle(eec, circ, o, x, variant)
 
 
-@pytest.mark.parametrize("variant", [0, 2, 3])
+@pytest.mark.parametrize("variant", [0, 2, 3, 5])
 @pytest.mark.parametrize("make", [lambda: netgen.sram(16, 16), netgen.ota5t,
                                   lambda: netgen.random_logic(500, seed=2)])
 def test_wide_bias(eec, variant, make):
@@ -137,12 +138,12 @@ def test_config2_sram_all_variants_full_size(eec, sram_full):
     # the colour schedules add every entry's contributions in the same colour order; each kernel
     # is compiled on its own, so a multiply-add fused in one may be rounded twice in another:
     # they agree to rounding, not necessarily bitwise
-    for v in (1, 4):
+    for v in (1, 4, 5):
         for k in (0, 1):
             scale = ref["A_scale"] if k == 0 else ref["b_scale"]
             assert (np.abs(outs[v][k] - outs[0][k]) / np.maximum(scale, 1e-300)).max() <= 1e-14
     # every schedule except the atomic one is deterministic: two runs agree bitwise
-    for v in (0, 1, 3, 4):
+    for v in DETERMINISTIC:
         again = check_against_oracle(eec, circ, o, x, v, ref=ref)
         assert np.array_equal(again[0], outs[v][0]) and np.array_equal(again[1], outs[v][1]), v
 
@@ -155,8 +156,25 @@ def test_config3_random_logic_full_size_and_gpu_colouring(eec):
     ocol, oC = o.color_greedy()
     circ = eec.Circuit(net, CARDS, color=True, algo=eec.EEC_COLOR_JP_INDEX)
     assert circ.n_colors == oC and np.array_equal(circ.colors, ocol)
-    for v in (0, 2, 3):
+    for v in (0, 2, 3, 5):
         check_against_oracle(eec, circ, o, x, v, ref=ref)
+
+
+def test_million_fet_random_logic_full_size(eec):
+    # the ~1.0M-FET netlist of the throughput bar (277,778 gates of the config-3 generator):
+    # the schedules the bench times there, entry by entry against the oracle
+    net = netgen.random_logic(277_778)
+    assert net.n_dev > 990_000
+    o = oracle.Oracle(net, CARDS)
+    x = netgen.random_x(net)
+    ref = o.eval_stamp(x, want_q=True, want_scale=True)
+    circ = eec.Circuit(net, CARDS, color=True)
+    outs = {}
+    for v in ALL_VARIANTS:
+        outs[v] = check_against_oracle(eec, circ, o, x, v, ref=ref)
+    for v in DETERMINISTIC:   # deterministic schedules repeat bitwise
+        again = check_against_oracle(eec, circ, o, x, v, ref=ref, want_q=False)
+        assert np.array_equal(again[0], outs[v][0]) and np.array_equal(again[1], outs[v][1]), v
 
 
 def test_config4_batch_full_size(eec):
@@ -169,7 +187,7 @@ def test_config4_batch_full_size(eec):
     assert circ.n_dev == merged.n_dev
     ocol, oC = o.color_greedy()
     assert circ.n_colors == oC and np.array_equal(circ.colors, ocol)
-    for v in (0, 1, 3):
+    for v in ALL_VARIANTS:
         check_against_oracle(eec, circ, o, x, v, ref=ref)
     ro, no, do = eec.eec_get_batch_offsets(circ.ctx, len(nets))
     assert ro[-1] == circ.n and no[-1] == circ.nnz
@@ -435,6 +453,32 @@ def test_grid_barrier_timeout_is_reported_and_the_context_recovers(eec):
     check_against_oracle(eec, circ, o, x, 1)      # the persistent schedule still works
 
 
+def test_pipelined_wait_timeout_is_reported_and_the_context_recovers(eec):
+    # The first work item never reports its stamps done: the next colour's waits give up after
+    # their bounded wait (about 1 s), record EEC_ETIMEOUT and abort the launch; the following
+    # launches (the timeout left unread) stamp everything again.
+    import time
+    import torch
+    net = netgen.inverter_chain(64)
+    o = oracle.Oracle(net, CARDS)
+    circ = eec.Circuit(net, CARDS, color=True, variant=eec.EEC_VARIANT_COLOR_PIPELINED)
+    x = netgen.random_x(net)
+    A, b, _ = circ.new_outputs(want_q=False)
+    t0 = time.time()
+    eec.eec_test_barrier_timeout(circ.ctx, dev(x), A, b)
+    torch.cuda.synchronize()
+    assert time.time() - t0 < 30
+    ref = o.eval_stamp(x, want_scale=True)
+    for _ in range(2):
+        A, b, _ = circ.eval_stamp(dev(x), want_q=False)
+        torch.cuda.synchronize()
+        assert rel_err(host(A), ref["A"], ref["A_scale"]).max() <= TOL
+        assert rel_err(host(b), ref["b"], ref["b_scale"]).max() <= TOL
+    assert circ.status() == eec.EEC_ETIMEOUT
+    assert circ.status() == 0
+    check_against_oracle(eec, circ, o, x, eec.EEC_VARIANT_COLOR_PIPELINED)
+
+
 @pytest.mark.parametrize("variant", [1, 4])
 def test_timeout_left_unread_does_not_abort_later_launches(eec, variant):
     # A timeout stays recorded in the status word until the host reads it; the next persistent
@@ -506,6 +550,11 @@ def test_color_buffered_stamp_implementations_agree_bitwise(eec, make):
         outs.append(check_against_oracle(eec, circ, o, x, eec.EEC_VARIANT_COLOR_BUFFERED, ref=ref))
     for k in (0, 1):
         assert np.array_equal(outs[1][k], outs[0][k]) and np.array_equal(outs[2][k], outs[0][k])
+    # the pipelined schedule adds in the same colour order (its own kernel: equal to rounding)
+    circ = eec.Circuit(net, CARDS, variant=eec.EEC_VARIANT_COLOR_PIPELINED)
+    pipe = check_against_oracle(eec, circ, o, x, eec.EEC_VARIANT_COLOR_PIPELINED, ref=ref)
+    for k, sc in ((0, "A_scale"), (1, "b_scale")):
+        assert (np.abs(pipe[k] - outs[0][k]) / np.maximum(ref[sc], 1e-300)).max() <= 1e-14
 
 
 def test_debug_checks_flag_non_finite_inputs(eec):

@@ -45,7 +45,7 @@ NETS = [netgen.ota5t, lambda: netgen.sram(8, 8), lambda: netgen.ripple_adder(4, 
 
 
 @pytest.mark.parametrize("make", NETS)
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
 def test_eval_stamp_matches_oracle_under_mna(eec, make, variant):
     net = make()
     o = oracle.Oracle(net, CARDS, rail_mode=MNA)
@@ -132,7 +132,7 @@ def test_gpu_newton_under_mna_reaches_the_oracle_operating_point(eec, make):
     np.testing.assert_allclose(xh[free - 1], xe[ue[free]], rtol=1e-8, atol=1e-10)
 
 
-@pytest.mark.parametrize("variant", [0, 2, 4])
+@pytest.mark.parametrize("variant", [0, 2, 4, 5])
 @pytest.mark.parametrize("make", [netgen.ota5t, lambda: netgen.sram(8, 8)])
 def test_transient_stamp_under_mna(eec, variant, make):
     import torch

@@ -1,9 +1,10 @@
 """GPU parity of the transient companion stamp (eec_eval_stamp_tran) against the oracle, and a
 transient loop whose every Newton iteration is stamped on the GPU against the oracle's own
-transient solver. A and b: 1e-12 per entry relative to max(|oracle|, S_e), where S_e sums, over
-the contributions to the entry, the size of each device's Jacobian entry as the oracle's
-magnitude forward mode measures it (the sum of |chain-rule products|, so that entries whose
-intrinsic-capacitance terms cancel are judged against the size of those terms)."""
+transient solver. A and b: 1e-12 per entry relative to max(|oracle|, S_e), where S_e is the sum
+of the sizes of the contributions to the entry: per device its conductance |G_tu|, its intrinsic
+charge capacitance alpha |C^int_tu| and its overlap capacitance alpha |C^ov_tu| (three stamps),
+and for b also |I_t|, the sizes of the capacitive-current terms and each stamp's size times
+|x_u|; the linear elements as in the DC stamp."""
 import numpy as np
 import pytest
 
@@ -54,7 +55,7 @@ def check(eec, circ, o, x, qprev, iprev, alpha, beta):
     assert (np.abs(i - r["i"]) / np.maximum(iscale, 1e-300)).max() <= 1e-13
 
 
-@pytest.mark.parametrize("variant", [0, 2, 4])
+@pytest.mark.parametrize("variant", [0, 2, 4, 5])
 @pytest.mark.parametrize("make", [lambda: netgen.inverter_chain(64), netgen.ota5t,
                                   lambda: netgen.sram(32, 32), lambda: netgen.random_logic(4000, seed=9)])
 def test_transient_stamp_matches_oracle(eec, variant, make):
@@ -76,7 +77,7 @@ def test_transient_stamp_full_size_sram(eec):
     x = netgen.random_x(net)
     qprev = o.eval_stamp(netgen.random_x(net, seed=77), want_q=True)["q"]
     iprev = np.random.default_rng(2).normal(size=(4, net.n_dev)) * 1e-5
-    for variant in (0, 2, 4):
+    for variant in (0, 2, 4, 5):
         eec.eec_set_variant(circ.ctx, variant)
         check(eec, circ, o, x, qprev, iprev, 4e10, 1.0)
 
@@ -129,7 +130,7 @@ def test_gpu_stamped_transient_rc_matches_oracle(eec, method):
     np.testing.assert_allclose(got, ref, rtol=1e-10, atol=1e-13)
 
 
-@pytest.mark.parametrize("variant", [0, 2, 4])
+@pytest.mark.parametrize("variant", [0, 2, 4, 5])
 def test_gpu_stamped_transient_inverter_chain_matches_oracle(eec, variant):
     net = netgen.inverter_chain(6, vin=1.0)   # input stepped from 0 V to 1 V at t = 0
     o = oracle.Oracle(net, CARDS)
