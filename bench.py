@@ -2,16 +2,19 @@
 """Benchmark of the evaluate-and-stamp hot path (one JSON line on stdout).
 
 A step is one Newton-iteration eval_stamp of the whole workload: every MOSFET evaluated (currents,
-charges, conductances) and stamped into A and b. Default workload: the 256 x 256 6T SRAM array
-(393,216 MOSFETs, 131,840 unknowns), node voltages U[0, 1] V, sizes W ~ U[0.5, 5] um,
-L ~ U[0.1, 1] um, all from the fixed seed. Inputs are resident in HBM; a 256 MiB buffer is
-written between timed steps so every step starts with a cold L2.
+charges, conductances) and stamped into A and b. Default workload: random CMOS logic of 277,778
+INV/NAND2/NOR2 gates (~1.0M MOSFETs, the million-device netlist of the throughput bar), node
+voltages U[0, 1] V, sizes W ~ U[0.5, 5] um, L ~ U[0.1, 1] um, all from the fixed seed. Inputs are
+resident in HBM; a 256 MiB buffer is written between timed steps so every step starts with a
+cold L2. The SRAM (256 x 256 6T), the backward, the transient stamp, the batch of 4,096 circuits
+and the 64-bit adder study are reported under "extras".
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload ...]
 
-N > 1 (under torchrun): every rank evaluates its own replica of the workload (weak scaling, no
-collective on the data path); rank 0 prints the aggregate. ``--impl reference`` times the serial
-CPU oracle on the host cores on the same workload and metric.
+N > 1 (under torchrun): rank r evaluates its own netlist (the same generator, seed + r) -- or,
+with --workload batch, its round-robin share of the 4,096 circuits (circuits r, r + N, ...);
+no collective on the data path (weak scaling); rank 0 prints the aggregate. ``--impl
+reference`` times the serial CPU oracle on the host cores on the same workload and metric.
 """
 from __future__ import annotations
 
@@ -31,20 +34,30 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MOSFET eval+stamp/s per NR iter (FP64, 1xGB300)"
 UNIT = "device evals+stamps/s"
-# Per-device work of the evaluate kernel under the atomic schedule, per workload, from ncu's
-# counters of one launch (profiles/k_eval_atomic_sram_256x256.md, k_eval_atomic_random_logic_1M.md):
-# FP64 flop = 2 DFMA + DADD + DMUL thread instructions per device, and DRAM bytes read +
-# written per device. The flop count depends on the device mix (devices whose source and body
-# are source-held skip the body-effect and source-junction work).
-# Keys: (workload, evaluation launch order) -> k_eval (layout order) or k_eval_ranges (cost order).
-FP64_FLOP_PER_DEVICE = {("sram", 0): 274.5, ("logic", 0): 264.2, ("logic1m", 0): 264.2,
-                        ("batch", 0): 243.8, ("sram", 1): 274.5, ("logic", 1): 264.2,
-                        ("logic1m", 1): 264.2, ("batch", 1): 243.8}
-DRAM_BYTES_PER_DEVICE = {("sram", 0): 191.3, ("logic", 0): 237.4, ("logic1m", 0): 278.0,
-                         ("batch", 0): 384.8, ("sram", 1): 191.1, ("logic", 1): 243.4,
-                         ("logic1m", 1): 290.8, ("batch", 1): 383.7}
+# Per-device work of the dominant kernel, per workload and kernel, from ncu's counters of one
+# launch: FP64 flop = 2 DFMA + DADD + DMUL thread instructions per device, and DRAM bytes read +
+# written per device (summaries and commands in profiles/). Kernels: "eval_cost" = k_eval_ranges
+# (atomic schedule, cost order), "eval_layout" = k_eval (atomic, layout order), "pipe" =
+# k_color_pipe (pipelined colour schedule, evaluation and stamp in one kernel). The counts hold
+# for the kernel sources they were taken on (COUNTED_SOURCES_SHA16, a hash of the files in
+# KERNEL_SOURCES): once those change, the bench flags the figures as stale and reports no
+# traffic until they are counted again.
+KERNEL_SOURCES = ("eec_model.cuh", "eec_fastmath.cuh", "eec_tables.h", "eec_internal.h",
+                  "eec_kernels.cu")
+COUNTED_SOURCES_SHA16 = None
+COUNTS = {}   # (workload, kernel) -> (FP64 flop per device, DRAM bytes per device)
 # GB300: 152 SMs x 2 FP64 FMA per clock per SM x 2 flop x 2070 MHz maximum SM clock.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+
+def kernel_sources_sha16():
+    """Hash of the evaluate kernels' sources (the files the counted figures depend on)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2604_03079_gb300", "csrc", f), "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read())
+    return h.hexdigest()[:16]
 
 
 def parse():
@@ -54,7 +67,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["sram", "logic", "logic1m", "batch", "chain"],
-                    default="sram")
+                    default="logic1m")
     ap.add_argument("--variant", default="auto")
     ap.add_argument("--eval-order", choices=["auto", "cost", "layout"], default="auto",
                     help="evaluation launch order of the order-free schedules (auto: the "
@@ -72,17 +85,24 @@ def parse():
     return ap.parse_args()
 
 
-def workload(name):
+def workload(name, world=1, rank=0):
+    """(netlist or None, circuits or None, description) of a workload; with world > 1 the share
+    of this rank (its own netlist, seed + rank; for the batch its round-robin circuits)."""
     import netgen
-    if name == "sram":
-        return netgen.config(2), "sram_256x256_6T (393216 MOSFETs)"
-    if name == "logic":
-        return netgen.config(3), "random_logic_200k_gates"
-    if name == "logic1m":
-        return netgen.random_logic(277_778), "random_logic_277778_gates (~1M MOSFETs)"
+    seed = netgen.DEFAULT_SEED + rank
     if name == "batch":
-        return netgen.config(4), "batch_4096_circuits_merged"
-    return netgen.config(1), "inverter_chain_64"
+        nets = netgen.batch_circuits(4096)
+        if world > 1:
+            nets = netgen.shard(nets, world, rank)
+        return None, nets, "batch_4096_circuits_merged"
+    if name == "sram":
+        return netgen.sram(256, 256, seed), None, "sram_256x256_6T (393216 MOSFETs)"
+    if name == "logic":
+        return netgen.random_logic(200_000, seed), None, "random_logic_200k_gates"
+    if name == "logic1m":
+        return (netgen.random_logic(277_778, seed), None,
+                "random_logic_277778_gates (~1M MOSFETs)")
+    return netgen.inverter_chain(64, seed), None, "inverter_chain_64"
 
 
 class Clocks:
@@ -144,10 +164,21 @@ def reduce_max(value, device=None):
     return float(t.item())
 
 
-def aggregate_value(world, n_dev_per_rank, ms_per_step):
-    """Whole-job throughput: every rank evaluates its own replica of n_dev_per_rank devices
-    (weak scaling); the step time is the slowest rank's."""
-    return world * n_dev_per_rank / (ms_per_step * 1e-3)
+def aggregate_value(n_dev_all_ranks, ms_per_step):
+    """Whole-job throughput: the devices of every rank per step, over the slowest rank's step
+    time (weak scaling: each rank's share is fixed as the rank count grows)."""
+    return n_dev_all_ranks / (ms_per_step * 1e-3)
+
+
+def sum_over_ranks(value, device=None):
+    """Sum of a per-rank number over the default process group (identity on one rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
 
 
 def cpu_baseline(net, x, budget_s=10.0):
@@ -168,16 +199,22 @@ def cpu_baseline(net, x, budget_s=10.0):
                       f"{el:.1f} s, 1 thread"}
 
 
+def _merged(net, nets):
+    import netgen
+    return net if net is not None else netgen.concat(nets)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     import netgen
     import oracle
-    net, wname = workload(args.workload)
+    net, nets, wname = workload(args.workload)
+    net = _merged(net, nets)
     x = netgen.random_x(net)
     o = oracle.Oracle(net, netgen.default_cards())
-    # bounded steps: the oracle takes about a second per step on this workload
+    # bounded steps: the oracle takes one to two seconds per step on the default workload
     steps = max(1, min(args.steps, 20))
     warm = max(0, min(args.warmup, 2))
     for _ in range(warm):
@@ -198,6 +235,83 @@ def run_reference(args):
     return 0
 
 
+def make_context(eec, net, nets, cards):
+    if nets is not None:
+        return eec.Circuit(None, cards, color=True, batch=nets)
+    return eec.Circuit(net, cards, color=True)
+
+
+def timed_steps(eec, circ, xt, A, b, q, steps, warmup, flush, stream, world):
+    """Warm-up, then `steps` steps bracketed by barrier + synchronize, each after an L2 flush,
+    timed with CUDA events on the launching stream; returns (per-step ms, library kernels)."""
+    import torch
+    import torch.distributed as dist
+    for _ in range(warmup):
+        circ.eval_stamp(xt, A, b, q)
+    torch.cuda.synchronize()
+    assert circ.status() == 0
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    eec.eec_profile_read(circ.ctx)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        circ.eval_stamp(xt, A, b, q)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    prof = eec.eec_profile_read(circ.ctx)
+    return [a.elapsed_time(bb) for a, bb in ev], prof["kernels"]
+
+
+def phase_split(eec, circ, xt, A, b, q, steps, flush):
+    """init / evaluate / stamp per step from CUDA events around the phases (a second pass: an
+    event between the initialisation and the evaluation keeps them from overlapping)."""
+    eec.eec_profile_enable(circ.ctx, True)
+    eec.eec_profile_read(circ.ctx)
+    for _ in range(steps):
+        flush.zero_()
+        circ.eval_stamp(xt, A, b, q)
+    prof = eec.eec_profile_read(circ.ctx)
+    eec.eec_profile_enable(circ.ctx, False)
+    n = max(prof["calls"], 1)
+    return {"init": prof["ms_init"] / n, "eval": prof["ms_eval"] / n, "stamp": prof["ms_stamp"] / n}
+
+
+def dominant_kernel(eec, circ, variant):
+    """(key into COUNTS, kernel name) of the kernel that dominates a step of this schedule."""
+    if variant == eec.EEC_VARIANT_COLOR_PIPELINED:
+        return "pipe", "k_color_pipe (evaluate and stamp)"
+    if variant == eec.EEC_VARIANT_ATOMIC:
+        if eec.eec_get_tuning(circ.ctx)[2]:
+            return "eval_cost", "k_eval_ranges (evaluate, cost order)"
+        return "eval_layout", "k_eval (evaluate, layout order)"
+    return None, f"evaluate kernel of {eec.VARIANT_NAMES[variant]}"
+
+
+def roofline(eec, circ, variant, wkey, n_dev, kernel_ms):
+    key, kname = dominant_kernel(eec, circ, variant)
+    sha = kernel_sources_sha16()
+    fresh = COUNTED_SOURCES_SHA16 is not None and sha == COUNTED_SOURCES_SHA16
+    cnt = COUNTS.get((wkey, key)) if key else None
+    if cnt and not fresh:
+        sys.stderr.write("bench: the counted FP64/DRAM figures were taken on other kernel "
+                         f"sources ({COUNTED_SOURCES_SHA16} != {sha}); recount them with ncu\n")
+    flop = cnt[0] if cnt else None
+    ach = flop * n_dev / (kernel_ms * 1e-3) / 1e12 if (flop and kernel_ms > 0) else None
+    return {"bound": "alu", "kernel": kname, "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s", "frac": (ach / FP64_PEAK_TFLOPS) if ach else None,
+            "traffic": (cnt[1] * n_dev) if (cnt and fresh) else None,
+            "flop_per_device": flop, "counts_fresh": bool(cnt and fresh),
+            "kernel_sources_sha16": sha, "kernel_ms": kernel_ms,
+            "peak_source": "152 SM x 2 DFMA/clk x 2 flop x 2070 MHz (maximum SM clock; nominal "
+                           "1.25 TFLOP/s FP64); the library's DFMA probe is fp64_probe_tflops"}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -213,10 +327,11 @@ def run_ours(args):
     import paper_2604_03079_gb300 as eec
 
     dev = torch.device("cuda", torch.cuda.current_device())
-    net, wname = workload(args.workload)
-    x = netgen.random_x(net)
+    net, nets, wname = workload(args.workload, world, rank)
+    mnet = _merged(net, nets)
+    x = netgen.random_x(mnet)
     cards = netgen.default_cards()
-    circ = eec.Circuit(net, cards, color=True)
+    circ = make_context(eec, net, nets, cards)
     xt = torch.as_tensor(x, device=dev)
     A, b, q = circ.new_outputs(want_q=True)
     ms_variants = [] if args.quick else eec.eec_autotune(circ.ctx, xt, A, b, q, reps=5)
@@ -225,70 +340,43 @@ def run_ours(args):
     if args.eval_order != "auto":
         eec.eec_set_eval_order(circ.ctx, 1 if args.eval_order == "cost" else 0)
     variant = eec.eec_get_variant(circ.ctx)
-    graphed = variant in (eec.EEC_VARIANT_COLOR_FUSED, eec.EEC_VARIANT_COLOR_BUFFERED)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
-
-    for _ in range(args.warmup):
-        circ.eval_stamp(xt, A, b, q)
-    torch.cuda.synchronize()
-    assert circ.status() == 0
 
     clocks = Clocks(torch.cuda.current_device()) if (rank == 0 and not args.quick) else None
     if clocks:
         clocks.start()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    # the timed steps run without phase events (an event between the initialisation and the
-    # evaluation would keep them from overlapping); the phase split comes from a second pass
-    eec.eec_profile_read(circ.ctx)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    for i in range(args.steps):
-        flush.zero_()
-        ev[i][0].record(stream)
-        circ.eval_stamp(xt, A, b, q)
-        ev[i][1].record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    step_ms, launches = timed_steps(eec, circ, xt, A, b, q, args.steps, args.warmup, flush,
+                                    stream, world)
     clk = clocks.stop() if clocks else None
-    prof = eec.eec_profile_read(circ.ctx)
-    step_ms = [a.elapsed_time(bb) for a, bb in ev]
     total_ms = reduce_max(float(sum(step_ms)), dev)
     assert circ.status() == 0
     ms_per_step = total_ms / args.steps
-    value = aggregate_value(world, net.n_dev, ms_per_step)
-    launches = prof["kernels"]
+    n_dev_all = sum_over_ranks(circ.n_dev, dev)
+    value = aggregate_value(n_dev_all, ms_per_step)
+    phases = phase_split(eec, circ, xt, A, b, q, args.steps, flush)
 
-    # phase split (init / evaluate / stamp) from a profiled pass over the same steps
-    eec.eec_profile_enable(circ.ctx, True)
-    for _ in range(args.steps):
-        flush.zero_()
-        circ.eval_stamp(xt, A, b, q)
-    prof = eec.eec_profile_read(circ.ctx)
-    eec.eec_profile_enable(circ.ctx, False)
-    eval_ms = prof["ms_eval"] / max(prof["calls"], 1)
-    stamp_ms = prof["ms_stamp"] / max(prof["calls"], 1)
-    init_ms = prof["ms_init"] / max(prof["calls"], 1)
-
+    if world > 1:
+        sharding = ("round-robin share of the 4,096 circuits per rank (circuits r, r + N, ...)"
+                    if nets is not None else "own netlist per rank (same generator, seed + rank)")
+    else:
+        sharding = "single GPU"
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_per_step,
            "ms_per_step_median": statistics.median(step_ms), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic (seeded netlist generators, random-init node voltages)",
-           "config": {"workload": wname, "n_dev": net.n_dev, "n_unknowns": circ.n,
-                      "nnz": circ.nnz, "colors": circ.n_colors,
+           "config": {"workload": wname, "n_dev": circ.n_dev, "n_dev_all_ranks": int(n_dev_all),
+                      "n_unknowns": circ.n, "nnz": circ.nnz, "colors": circ.n_colors,
                       "variant": eec.VARIANT_NAMES[variant],
                       "block": (eec.eec_get_tuning(circ.ctx)[1] or
                                 "library choice: 32 for launches under 19,456 devices, else 128"),
                       "eval_order": ("free source/body first" if eec.eec_get_tuning(circ.ctx)[2]
                                      else "layout order"),
                       "l2": "flushed (256 MiB write) before every timed step",
-                      "parallelism": f"replica x{world}" if world > 1 else "single GPU"},
+                      "parallelism": f"dp{world}: {sharding}" if world > 1 else sharding},
            "gpu_launches": launches,
-           "phases_ms": {"init": init_ms, "eval": eval_ms, "stamp": stamp_ms}}
+           "phases_ms": phases}
     if clk:
         out["clocks"] = clk
 
@@ -310,40 +398,29 @@ def run_ours(args):
             torch.cuda.synchronize()
             assert circ.status() == 0
         print(json.dumps(out))
-    elif rank == 0:
-        # roofline of the dominant kernel (the evaluate kernel; FP64-pipe bound); the counted
-        # figures hold for the atomic schedule's kernel
-        counted = variant == eec.EEC_VARIANT_ATOMIC
-        key = (args.workload, eec.eec_get_tuning(circ.ctx)[2])
-        flop = FP64_FLOP_PER_DEVICE.get(key) if counted else None
-        ach = (flop * net.n_dev / (eval_ms * 1e-3) / 1e12) if (flop and eval_ms > 0) else None
-        traffic = (DRAM_BYTES_PER_DEVICE[key] * net.n_dev
-                   if counted and key in DRAM_BYTES_PER_DEVICE else None)
-        out["roofline"] = {"bound": "alu", "kernel": "k_eval_ranges / k_eval (evaluate)",
-                           "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                           "frac": (ach / FP64_PEAK_TFLOPS) if ach else None, "traffic": traffic,
-                           "peak_source": "152 SM x 2 DFMA/clk x 2 flop x 2070 MHz (maximum SM "
-                                          "clock; nominal 1.25 TFLOP/s FP64)"}
-        out["fp64_probe_tflops"] = eec.eec_fp64_peak(4096, 8) / 1e12
+    elif not args.quick:
+        # the evaluate phase is the dominant kernel's time (the whole kernel under the
+        # pipelined schedule, whose stamp runs inside it)
+        out["roofline"] = roofline(eec, circ, variant, args.workload, circ.n_dev, phases["eval"])
         out["variants_ms"] = {eec.VARIANT_NAMES[i]: m for i, m in enumerate(ms_variants)}
-
         # end to end through the public API with host buffers (pinned): every step copies its
-        # x in and its A, b, q out inside the timed region (the host-buffer entry point, one
-        # call per step; beside it a caller-pipelined loop over device buffers)
-        out["e2e"] = e2e(eec, circ, x, args, dev, world, net.n_dev)
-
-        if world == 1 and not args.no_extras:
-            out["extras"] = extras(eec, circ, net, x, xt, A, b, q, args, dev)
-        if world == 1:
-            out["cpu_baseline"] = cpu_baseline(net, x)
-            out["gpu_over_oracle"] = value / out["cpu_baseline"]["value"]
-        print(json.dumps(out))
+        # x in and its A, b, q out inside the timed region
+        out["e2e"] = e2e(eec, circ, x, args, dev, world, n_dev_all)
+        if rank == 0:
+            out["fp64_probe_tflops"] = eec.eec_fp64_peak(4096, 8) / 1e12
+            if world == 1 and not args.no_extras:
+                out["extras"] = extras(eec, circ, mnet, x, xt, A, b, q, args, dev)
+            if world == 1:
+                out["cpu_baseline"] = cpu_baseline(mnet, x)
+                out["gpu_over_oracle"] = value / out["cpu_baseline"]["value"]
+            print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
     return 0
 
 
 def e2e(eec, circ, x, args, dev, world, n_dev):
+    """n_dev: the devices of all ranks (the whole job's work per step)."""
     import torch
     cs = torch.cuda.current_stream()
     ts_in, ts_out = torch.cuda.Stream(), torch.cuda.Stream()   # copies in / out overlap
@@ -401,7 +478,9 @@ def e2e(eec, circ, x, args, dev, world, n_dev):
     e1.record(cs)
     torch.cuda.synchronize()
     ms_pipe = e0.elapsed_time(e1) / steps
-    return {"value": world * n_dev / (ms_host * 1e-3), "unit": UNIT,
+    ms_host = reduce_max(ms_host, dev)     # the slowest rank (identity on one rank)
+    ms_pipe = reduce_max(ms_pipe, dev)
+    return {"value": n_dev / (ms_host * 1e-3), "unit": UNIT,
             "h2d_bytes_per_step": 8 * circ.n,
             "d2h_bytes_per_step": 8 * (circ.nnz + circ.n + 4 * circ.n_dev),
             "ms_per_step": ms_host,
@@ -409,7 +488,7 @@ def e2e(eec, circ, x, args, dev, world, n_dev):
                    "in from page-locked memory, A, b and q copied out (q span by span while later "
                    "spans are evaluated)",
             "pipelined_device_buffers": {
-                "value": world * n_dev / (ms_pipe * 1e-3), "ms_per_step": ms_pipe,
+                "value": n_dev / (ms_pipe * 1e-3), "ms_per_step": ms_pipe,
                 "how": "eec_eval_stamp on device buffers, input and output copies on their own "
                        "streams, double-buffered across steps (independent evaluations)"}}
 
@@ -484,23 +563,41 @@ def _time(fn, reps, stream):
 
 
 def extras(eec, circ, net, x, xt, A, b, q, args, dev):
-    """Backward vs plain forward, per-variant phase split (t_calc / t_stamp), batched vs
-    4096 separate calls."""
+    """The SRAM (high-conflict) step, backward vs plain forward (config 5), per-variant phase
+    split (t_calc / t_stamp), the gather's HBM roofline, the transient stamp, the Table II
+    adder study, batched vs 4096 separate calls."""
     import torch
     import netgen
     stream = torch.cuda.current_stream()
     res = {}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    # the 256 x 256 6T SRAM: high conflict (512 access transistors per word line, 516 colours)
+    sram = netgen.sram(256, 256)
+    sc = eec.Circuit(sram, netgen.default_cards(), color=True)
+    xs = torch.as_tensor(netgen.random_x(sram), device=dev)
+    As, bs, qs = sc.new_outputs()
+    ms_s = eec.eec_autotune(sc.ctx, xs, As, bs, qs, reps=5)
+    st_ms, _ = timed_steps(eec, sc, xs, As, bs, qs, 200, 10, flush, stream, 1)
+    ms = sum(st_ms) / len(st_ms)
+    res["sram_256x256"] = {
+        "devices": sc.n_dev, "unknowns": sc.n, "colors": sc.n_colors,
+        "variant": eec.VARIANT_NAMES[eec.eec_get_variant(sc.ctx)], "ms_per_step": ms,
+        "devices_per_s": sc.n_dev / (ms * 1e-3),
+        "l2": "flushed (256 MiB write) before every timed step",
+        "variants_ms": {eec.VARIANT_NAMES[i]: m for i, m in enumerate(ms_s)}}
+    # backward (config 5: the SRAM with gA, gb ~ N(0, 1)) against its plain forward
     rng = netgen.Rng(netgen.DEFAULT_SEED, 12)
-    gA = torch.as_tensor(rng.normal(circ.nnz), device=dev)
-    gb = torch.as_tensor(rng.normal(circ.n), device=dev)
-    gx = torch.empty(circ.n, dtype=torch.float64, device=dev)
-    gW = torch.empty(circ.n_dev, dtype=torch.float64, device=dev)
-    gL = torch.empty(circ.n_dev, dtype=torch.float64, device=dev)
-    fwd_ms = _time(lambda: circ.eval_stamp(xt, A, b, q), 50, stream)
-    bwd_ms = _time(lambda: eec.eec_eval_stamp_bwd(circ.ctx, xt, gA, gb, gx, gW, gL), 20, stream)
-    res["bwd"] = {"devices_per_s": net.n_dev / (bwd_ms * 1e-3), "ms": bwd_ms,
+    gA = torch.as_tensor(rng.normal(sc.nnz), device=dev)
+    gb = torch.as_tensor(rng.normal(sc.n), device=dev)
+    gx = torch.empty(sc.n, dtype=torch.float64, device=dev)
+    gW = torch.empty(sc.n_dev, dtype=torch.float64, device=dev)
+    gL = torch.empty(sc.n_dev, dtype=torch.float64, device=dev)
+    fwd_ms = _time(lambda: sc.eval_stamp(xs, As, bs, qs), 50, stream)
+    bwd_ms = _time(lambda: eec.eec_eval_stamp_bwd(sc.ctx, xs, gA, gb, gx, gW, gL), 20, stream)
+    res["bwd"] = {"devices_per_s": sc.n_dev / (bwd_ms * 1e-3), "ms": bwd_ms,
                   "fwd_ms": fwd_ms, "bwd_over_fwd_time": bwd_ms / fwd_ms,
                   "workload": "config 5: SRAM 256x256, gA, gb ~ N(0, 1)"}
+    del sc
     phases = {}
     v0 = eec.eec_get_variant(circ.ctx)
     for v in range(eec.EEC_N_VARIANTS):
@@ -533,7 +630,9 @@ def extras(eec, circ, net, x, xt, A, b, q, args, dev):
         "achieved": gbytes / (st_ms * 1e-3) / 1e9, "peak": hbm[0], "unit": "GB/s",
         "frac": gbytes / (st_ms * 1e-3) / 1e9 / hbm[0], "algorithmic_bytes": gbytes,
         "contributions": contrib, "entries": entries, "peak_source": hbm[1],
-        "note": "inputs L2-resident: the buffer is read right after the evaluate kernel wrote it"}
+        "workload": "the bench's workload",
+        "note": "the buffer is read right after the evaluate kernel wrote it (15 doubles per "
+                "device: partly L2-resident)"}
 
     # transient companion stamp (trapezoidal rule) on the same workload
     qprev = torch.empty_like(q)
@@ -542,7 +641,8 @@ def extras(eec, circ, net, x, xt, A, b, q, args, dev):
     ip = torch.zeros_like(q)
     v0t = eec.eec_get_variant(circ.ctx)
     tran = {}
-    for v in (eec.EEC_VARIANT_ATOMIC, eec.EEC_VARIANT_COLOR_FUSED, eec.EEC_VARIANT_COLOR_BUFFERED):
+    for v in (eec.EEC_VARIANT_ATOMIC, eec.EEC_VARIANT_COLOR_FUSED, eec.EEC_VARIANT_COLOR_BUFFERED,
+              eec.EEC_VARIANT_COLOR_PIPELINED):
         eec.eec_set_variant(circ.ctx, v)
         ms_t = _time(lambda: eec.eec_eval_stamp_tran(circ.ctx, xt, qprev, ip, 2e11, 1.0, A, b, q, ic),
                      3 if v == eec.EEC_VARIANT_COLOR_FUSED else 20, stream)

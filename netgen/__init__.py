@@ -542,6 +542,15 @@ def concat(nets: List[Netlist], name: str = "batch") -> Netlist:
         meta=dict(node_off=node_off, n_circ=len(nets)))
 
 
+def shard(items, world: int, rank: int) -> list:
+    """The share of rank `rank` among `world` ranks: every world-th item starting at `rank`
+    (round robin, so circuits of uneven size spread evenly). The shares of the ranks partition
+    the items; item i belongs to rank i % world, at position i // world of its share."""
+    if world < 1 or not 0 <= rank < world:
+        raise ValueError("need 0 <= rank < world")
+    return list(items[rank::world])
+
+
 def partition_rows(net: Netlist, k: int) -> List[Tuple[Netlist, np.ndarray]]:
     """Split the free nodes (in increasing order) into k contiguous blocks; part i keeps every
     node, so the unknowns keep their numbering, and every device, resistor and current source

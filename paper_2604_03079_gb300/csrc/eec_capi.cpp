@@ -79,6 +79,7 @@ struct eec_ctx {
   int stamp_mode = 0;          // colour-buffered stamp: 0 per-colour launches, 1 grid, 2 cluster
   int pipe_grid = 0;           // blocks of the pipelined colour schedule (resident blocks)
   int pipe_colors = 0;         // non-empty colours (counters of the pipelined schedule)
+  long long n_contrib = 0;     // contributions of the segmented reduction (cbuf length)
   // phase timing and launch counting
   bool prof = false;
   bool graph_all = false;      // eec_batch_capture_graph: every schedule replays a cached graph
@@ -306,6 +307,12 @@ int ensure_buf(eec_ctx* c) {
   return dalloc(c, &c->d.buf, (size_t)kNContrib * c->n_dev);
 }
 
+// The segmented reduction's contribution buffer, in entry order (gat_ptr's last value long).
+int ensure_cbuf(eec_ctx* c) {
+  if (c->d.cbuf) return EEC_OK;
+  return dalloc(c, &c->d.cbuf, std::max<size_t>((size_t)c->n_contrib, 1));
+}
+
 int ensure_gv(eec_ctx* c) {
   if (c->d.gv) return EEC_OK;
   return dalloc(c, &c->d.gv, (size_t)4 * c->n_dev);
@@ -357,9 +364,8 @@ int run_variant(eec_ctx* c, int v, const double* x, double* A, double* b, double
     return EEC_OK;
   };
   int rc;
-  if (v == EEC_VARIANT_SEGREDUCE || v == EEC_VARIANT_COLOR_BUFFERED) {
-    if ((rc = ensure_buf(c))) return rc;
-  }
+  if (v == EEC_VARIANT_COLOR_BUFFERED && (rc = ensure_buf(c))) return rc;
+  if (v == EEC_VARIANT_SEGREDUCE && (rc = ensure_cbuf(c))) return rc;
   prof_mark(c, s);
   switch (v) {
     case EEC_VARIANT_COLOR_FUSED:
@@ -390,7 +396,7 @@ int run_variant(eec_ctx* c, int v, const double* x, double* A, double* b, double
       break;
     case EEC_VARIANT_SEGREDUCE:
       prof_mark(c, s);
-      CUDA_TRY(c, launch_eval_all(c, MODE_BUFFER, x, A, b, q, blk, dbg, s));
+      CUDA_TRY(c, launch_eval_all(c, MODE_SORTED, x, A, b, q, blk, dbg, s));
       prof_mark(c, s);
       CUDA_TRY(c, launch_gather(c->d, A, b, s));
       *nk += (c->n_dev > 0) + (c->nnz + c->n > 0);
@@ -501,8 +507,12 @@ int capture(eec_ctx* c, int v, const double* x, double* A, double* b, double* q,
   if (!c->cap_stream)
     CUDA_TRY(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
   // Buffers allocated lazily must exist before capture (no allocation inside a capture).
-  if (v == EEC_VARIANT_SEGREDUCE || v == EEC_VARIANT_COLOR_BUFFERED) {
+  if (v == EEC_VARIANT_COLOR_BUFFERED) {
     int rc = ensure_buf(c);
+    if (rc) return rc;
+  }
+  if (v == EEC_VARIANT_SEGREDUCE) {
+    int rc = ensure_cbuf(c);
     if (rc) return rc;
   }
   CUDA_TRY(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -1001,7 +1011,9 @@ int eec_build_scatter(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_out) {
     }
   }
   for (long long e = 0; e < E; ++e) gptr[e + 1] += gptr[e];
-  std::vector<int> gsrc(gptr[E]);
+  // position in entry order of every contribution (j, p): the evaluation writes it there
+  if ((long long)N * kNContrib > 0x7fffffffLL) return fail(c, EEC_EINVAL, "too many devices");
+  std::vector<int> gpos((size_t)kNContrib * N, -1);
   {
     std::vector<long long> fill(gptr.begin(), gptr.end() - 1);
     for (int k = 0; k < N; ++k) {
@@ -1013,9 +1025,9 @@ int eec_build_scatter(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_out) {
         if (row < 0) continue;
         for (int u = 0; u < 4; ++u) {
           const int s = slot[(size_t)(4 * r + u) * N + p];
-          if (s >= 0) gsrc[fill[s]++] = (4 * r + u) * N + p;
+          if (s >= 0) gpos[(size_t)(4 * r + u) * N + p] = (int)fill[s]++;
         }
-        gsrc[fill[c->nnz + row]++] = (kNSlot + r) * N + p;
+        gpos[(size_t)(kNSlot + r) * N + p] = (int)fill[c->nnz + row]++;
       }
     }
   }
@@ -1023,6 +1035,7 @@ int eec_build_scatter(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_out) {
   for (long long e = 0; e < E; ++e)
     if (gptr[e + 1] - gptr[e] >= kHeavy) gheavy.push_back((int)e);
   if (gptr[E] > 0x7fffffffLL) return fail(c, EEC_EINVAL, "too many contributions");
+  c->n_contrib = gptr[E];
   const std::vector<int> gptr32(gptr.begin(), gptr.end());
   // backward incidence: unknown -> (terminal, position) in original device order
   std::vector<int> iptr(n + 1, 0);
@@ -1046,7 +1059,6 @@ int eec_build_scatter(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_out) {
     if (iptr[u + 1] - iptr[u] >= kHeavy) iheavy.push_back(u);
     else ilight.push_back(u);
   }
-  if ((long long)N * kNContrib > 0x7fffffffLL) return fail(c, EEC_EINVAL, "too many devices");
   // batch offsets
   if (c->n_circ > 0) {
     c->circ_row_off.assign(c->n_circ + 1, 0);
@@ -1093,7 +1105,7 @@ int eec_build_scatter(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_out) {
       (rc = dupload(c, &d.vfix, vtab)) ||
       (rc = dupload(c, &d.cards, c->cardk)) || (rc = dupload(c, &d.Alin, Alin)) ||
       (rc = dupload(c, &d.blin, blin)) || (rc = dupload(c, &d.gat_ptr, gptr32)) ||
-      (rc = dupload(c, &d.gat_src, gsrc)) || 
+      (rc = dupload(c, &d.gat_pos, gpos)) ||
       (rc = dupload(c, &d.gat_heavy, gheavy)) || (rc = dupload(c, &d.inc_ptr, iptr)) ||
       (rc = dupload(c, &d.inc_light, ilight)) || (rc = dupload(c, &d.inc_heavy, iheavy)) ||
       (rc = dupload(c, &d.inc_src, isrc)) || (rc = dupload(c, &c->d_coff, c->color_off))) {
@@ -1359,8 +1371,8 @@ int eec_eval_stamp_host(eec_ctx* c, const double* x_host, double* A_host, double
     CUDA_TRY(c, launch_init_lin(c->d, c->h_A, c->h_b, s));
     ++c->n_kernels;
   } else {
-    if ((rc = ensure_buf(c))) return rc;
-    mode = MODE_BUFFER;
+    if ((rc = ensure_cbuf(c))) return rc;
+    mode = MODE_SORTED;
   }
   // Every launch first, then the copies (a copy to pageable memory returns only when done).
   // The chunks alternate between two streams: launched one after the other on one stream, each
@@ -1380,7 +1392,7 @@ int eec_eval_stamp_host(eec_ctx* c, const double* x_host, double* A_host, double
   // the stream of the call waits for the chunks of the second stream (the last one suffices)
   const int last_odd = ((K - 1) & 1) ? K - 1 : K - 2;
   if (last_odd >= 1) CUDA_TRY(c, cudaStreamWaitEvent(s, c->hev[last_odd], 0));
-  if (mode == MODE_BUFFER) {
+  if (mode == MODE_SORTED) {
     CUDA_TRY(c, launch_gather(c->d, c->h_A, c->h_b, s));
     c->n_kernels += (c->nnz + c->n > 0);
   }

@@ -60,12 +60,15 @@ struct DevTopo {
   CardK* cards;     // [n_cards]
   double* Alin;     // [nnz]
   double* blin;     // [n]
-  // segmented reduction: entry e (A entries 0..nnz-1, then b rows) sums buf[src] over
-  // gat_src[gat_ptr[e] .. gat_ptr[e+1]) in original-device order
+  // segmented reduction: the evaluation writes contribution j of the device at position k to
+  // cbuf[gat_pos[j * N + k]] (-1: not formed), so that entry e (A entries 0..nnz-1, then b rows)
+  // is the linear part plus cbuf[gat_ptr[e] .. gat_ptr[e+1]), its contributions in
+  // original-device order, read as one contiguous run
   int* gat_ptr;        // [nnz + n + 1] (at most kNContrib N < 2^31 contributions)
-  int* gat_src;        // [total contributions], flat index j * N + k into buf
+  int* gat_pos;        // [kNContrib][N] position of each contribution in cbuf, or -1
   int* gat_heavy;      // entries with kHeavy or more contributions (one warp each)
   int n_heavy;
+  double* cbuf;        // [gat_ptr[nnz + n]] contributions in entry order (allocated on first use)
   double* buf;         // [kNContrib][N] (allocated on first use)
   double* buf_tran;    // [kNContribTran][N]: transient values G + alpha C (4 x 4) and 4 rhs
   // backward: unknown u gathers gv[src] over inc_src[inc_ptr[u] .. inc_ptr[u+1])
@@ -97,7 +100,9 @@ constexpr int kStatusTimeout = 1;
 constexpr int kStatusNumeric = 2;
 
 // ---- kernels (eec_kernels.cu) ----
-enum StampMode : int { MODE_RMW = 0, MODE_ATOMIC = 1, MODE_BUFFER = 2 };
+// MODE_BUFFER: contributions into buf (layout position-major, read by the colour-ordered stamps);
+// MODE_SORTED: contributions into cbuf in entry order (read by the segmented-reduction gather).
+enum StampMode : int { MODE_RMW = 0, MODE_ATOMIC = 1, MODE_BUFFER = 2, MODE_SORTED = 3 };
 
 cudaError_t launch_params(const DevTopo& T, cudaStream_t s);
 // W_dev, L_dev in original device order -> per-position W, L and derived parameters.

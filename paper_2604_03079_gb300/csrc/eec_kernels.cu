@@ -142,11 +142,27 @@ __device__ __forceinline__ void eval_one(const DevTopo& T, int k, const double* 
 
   // A and b may still be being initialised by the kernel launched just before this one
   // (programmatic dependent launch): wait for it before the first addition
-  if (MODE != MODE_BUFFER) asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (MODE == MODE_RMW || MODE == MODE_ATOMIC) asm volatile("griddepcontrol.wait;" ::: "memory");
   // b row r: -I_r + sum over the free columns u of G[r][u] V_u (held columns are eliminated)
   const int term[3] = {0, 2, 3};
   bool bc_ok = true;
-  if (MODE == MODE_BUFFER) {
+  if (MODE == MODE_SORTED) {
+    // the same contributions as MODE_BUFFER, each written to its place in entry order (the
+    // gather then reads every entry's contributions as one contiguous run)
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      if (idx[term[r]] < 0) continue;
+      double s = -o.I[term[r]];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (idx[u] < 0) continue;
+        s = fma(o.G[r][u], V[u], s);
+        T.cbuf[__ldg(T.gat_pos + (4 * r + u) * N + k)] = o.G[r][u];
+      }
+      T.cbuf[__ldg(T.gat_pos + (kNSlot + r) * N + k)] = s;
+      bc_ok = bc_ok && isfinite(s);
+    }
+  } else if (MODE == MODE_BUFFER) {
     // only what a stamp reads is buffered: rows of free terminals, and in them the entries of
     // free columns (the gather and the colour-ordered stamps skip held rows and columns)
 #pragma unroll
@@ -347,10 +363,12 @@ __global__ void k_params(DevTopo T, const double* __restrict__ Wo, const double*
 }
 
 // Segmented reduction: entry e of [A ; b] = linear part + its contributions (deterministic, no
-// colours needed). Light entries (< kHeavy contributions, nearly all) take one thread each, in
-// entry order (coalesced pointer, linear-part and output accesses), and sum in original-device
-// order; heavy entries (diagonals of word and bit lines) are skipped there and take one warp
-// each: lane-strided partial sums, then a fixed butterfly reduction. Blocks [0, nbl) cover the
+// colours needed). The evaluation has written every entry's contributions contiguously, in
+// original-device order, at cbuf[gat_ptr[e] .. gat_ptr[e+1]), so the gather streams cbuf: light
+// entries (< kHeavy contributions, nearly all) take one thread each, in entry order (the warp's
+// runs are adjacent, so its loads cover a contiguous stretch of cbuf), and sum in order; heavy
+// entries (diagonals of word and bit lines) are skipped there and take one warp each:
+// lane-strided partial sums, then a fixed butterfly reduction. Blocks [0, nbl) cover the
 // entries, the rest the heavy ones, in one launch.
 constexpr int kGatherBlock = 256;
 
@@ -362,19 +380,15 @@ __global__ void __launch_bounds__(kGatherBlock) k_gather(DevTopo T, double* A, d
     const int p0 = __ldg(T.gat_ptr + e), p1 = __ldg(T.gat_ptr + e + 1);
     if (p1 - p0 >= kHeavy) return;   // a warp of the heavy blocks sums this one
     double s = e < T.nnz ? __ldg(T.Alin + e) : __ldg(T.blin + (e - T.nnz));
-    // the first four contributions: all index loads, then all value loads, then the sum in the
-    // same order as the loop (two memory latencies instead of two per contribution)
+    // the first four contributions loaded together, then summed in the loop's order
     const int cnt = p1 - p0;
-    int src[4];
     double v[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) src[j] = j < cnt ? __ldg(T.gat_src + p0 + j) : 0;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) v[j] = j < cnt ? __ldg(T.buf + src[j]) : 0.0;
+    for (int j = 0; j < 4; ++j) v[j] = j < cnt ? __ldcs(T.cbuf + p0 + j) : 0.0;
 #pragma unroll
     for (int j = 0; j < 4; ++j)
       if (j < cnt) s += v[j];
-    for (int p = p0 + 4; p < p1; ++p) s += __ldg(T.buf + __ldg(T.gat_src + p));
+    for (int p = p0 + 4; p < p1; ++p) s += __ldcs(T.cbuf + p);
     if (e < T.nnz) A[e] = s;
     else b[e - T.nnz] = s;
     return;
@@ -385,7 +399,7 @@ __global__ void __launch_bounds__(kGatherBlock) k_gather(DevTopo T, double* A, d
   const long long e = __ldg(T.gat_heavy + w);
   const int p0 = __ldg(T.gat_ptr + e), p1 = __ldg(T.gat_ptr + e + 1);
   double s = 0.0;
-  for (int p = p0 + lane; p < p1; p += 32) s += __ldg(T.buf + __ldg(T.gat_src + p));
+  for (int p = p0 + lane; p < p1; p += 32) s += __ldcs(T.cbuf + p);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
   if (lane == 0) {
@@ -607,33 +621,31 @@ __global__ void __launch_bounds__(kStampBlock) k_stamp_persistent(DevTopo T,
 // per-colour launches' bitwise.
 constexpr int kPipeBlock = kPipeItem;
 
-// The item loop. Work::eval(k) evaluates device k into registers (before any wait);
-// Work::stamp() applies its additions (after the previous colour is complete).
+// One work item per block: the block takes the next ticket, evaluates the item's devices,
+// waits until every item of the previous colour has stamped, stamps, counts its item done for
+// its colour and leaves (the hardware then starts the next block in its place, so a block holds
+// no state across items). Work::eval(k) evaluates device k (before any wait); Work::stamp()
+// applies its additions (after the previous colour is complete).
 template <class Work>
-__device__ __forceinline__ void pipe_loop(const DevTopo& T, Work& w, int absent_item) {
+__device__ __forceinline__ void pipe_item(const DevTopo& T, Work& w, int absent_item) {
   __shared__ int4 s_it;
   __shared__ int s_num, s_go;
   unsigned* st = T.pipe;
-  bool init_seen = false;
-  for (;;) {
-    if (threadIdx.x == 0) {
-      const int it = (int)atomicAdd(st, 1u);
-      s_num = it;
-      if (it < T.n_pitem) s_it = __ldg(T.pitem + it);
-    }
-    __syncthreads();
-    const int it = s_num;
-    if (it >= T.n_pitem) break;                       // uniform: the tickets are used up
+  if (threadIdx.x == 0) {
+    const int it = (int)atomicAdd(st, 1u);
+    s_num = it;
+    if (it < T.n_pitem) s_it = __ldg(T.pitem + it);
+  }
+  __syncthreads();
+  const int it = s_num;
+  if (it < T.n_pitem) {                               // uniform
     const int4 item = s_it;
     const int k = item.x + (int)threadIdx.x;
     const bool valid = k < item.y;
     if (valid) w.eval(k);
     // A and b are initialised by the kernel launched before this one (programmatic dependent
     // launch): wait for it before the first addition
-    if (!init_seen) {
-      asm volatile("griddepcontrol.wait;" ::: "memory");
-      init_seen = true;
-    }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     if (threadIdx.x == 0) {
       int go = 1;
       if (item.w > 0) {
@@ -677,7 +689,11 @@ __device__ __forceinline__ void pipe_loop(const DevTopo& T, Work& w, int absent_
   }
 }
 
-// DC work of one device: currents and conductances at x; rows d, s, b stamped.
+// DC work of one device: currents and conductances at x; rows d, s, b stamped. The item's
+// contributions and their target slots wait in shared memory (structure of arrays over the
+// block's threads), so that no register is held across the wait for the previous colour and the
+// kernel keeps the evaluation kernel's occupancy.
+constexpr int kPipeDCStage = kNContrib;       // 12 conductances, 3 right-hand sides
 template <bool WANT_Q>
 struct PipeDC {
   const DevTopo& T;
@@ -686,13 +702,12 @@ struct PipeDC {
   double* b;
   double* __restrict__ q;
   int dbg;
-  int row[3];
-  int sl[kNSlot];
-  double g[kNSlot];
-  double rhs[3];
+  double* sv;   // [kPipeDCStage][kPipeBlock] shared: values
+  int* si;      // [kPipeDCStage][kPipeBlock] shared: A slot of each value, then b rows (-1: none)
 
   __device__ __forceinline__ void eval(int k) {
     const long long N = T.N;
+    const int tid = threadIdx.x;
     int idx[4];
     double V[4];
     EvalOut<double> o;
@@ -701,17 +716,19 @@ struct PipeDC {
     bool ok = true;
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-      row[r] = idx[term[r]];
+      const int row = idx[term[r]];
       double s = -o.I[term[r]];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        g[4 * r + u] = o.G[r][u];
-        sl[4 * r + u] = (row[r] >= 0 && idx[u] >= 0) ? __ldg(T.slot + (4 * r + u) * N + k) : -1;
+        sv[(4 * r + u) * kPipeBlock + tid] = o.G[r][u];
+        si[(4 * r + u) * kPipeBlock + tid] =
+            (row >= 0 && idx[u] >= 0) ? __ldg(T.slot + (4 * r + u) * N + k) : -1;
         if (idx[u] >= 0) s = fma(o.G[r][u], V[u], s);
         ok = ok && isfinite(o.G[r][u]);
       }
-      rhs[r] = s;
-      ok = ok && (row[r] < 0 || isfinite(s));
+      sv[(kNSlot + r) * kPipeBlock + tid] = s;
+      si[(kNSlot + r) * kPipeBlock + tid] = row;
+      ok = ok && (row < 0 || isfinite(s));
     }
     if (WANT_Q) {
       const int od = __ldg(T.orig + k);
@@ -722,31 +739,36 @@ struct PipeDC {
   }
 
   __device__ __forceinline__ void stamp() {
+    const int tid = threadIdx.x;
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-      if (row[r] < 0) continue;
+      const int row = si[(kNSlot + r) * kPipeBlock + tid];
+      if (row < 0) continue;
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (sl[4 * r + u] >= 0) atomicAdd(A + sl[4 * r + u], g[4 * r + u]);
-      atomicAdd(b + row[r], rhs[r]);
+      for (int u = 0; u < 4; ++u) {
+        const int sl = si[(4 * r + u) * kPipeBlock + tid];
+        if (sl >= 0) atomicAdd(A + sl, sv[(4 * r + u) * kPipeBlock + tid]);
+      }
+      atomicAdd(b + row, sv[(kNSlot + r) * kPipeBlock + tid]);
     }
   }
 };
 
-// Transient work of one device: G + alpha C on all four rows, -I - ic + (G + alpha C) V.
+// Transient work of one device: G + alpha C on all four rows, -I - ic + (G + alpha C) V, staged
+// in shared memory as the DC work.
+constexpr int kPipeTranStage = kNContribTran;   // 16 values, 4 right-hand sides
 struct PipeTran {
   const DevTopo& T;
   const double* __restrict__ x;
   double* A;
   double* b;
   const TranArgs& ta;
-  int row[4];
-  int sl[16];
-  double a[16];
-  double rhs[4];
+  double* sv;   // [kPipeTranStage][kPipeBlock] shared
+  int* si;      // [kPipeTranStage][kPipeBlock] shared
 
   __device__ __forceinline__ void eval(int k) {
     const long long N = T.N;
+    const int tid = threadIdx.x;
     int idx[4];
     double V[4];
     EvalOut<double> o;
@@ -759,49 +781,57 @@ struct PipeTran {
                         (ta.iprev ? ta.beta * __ldg(ta.iprev + at) : 0.0);
       ta.q[at] = o.Q[t];
       if (ta.icap) ta.icap[at] = ic;
-      row[t] = idx[t];
       const int r = t == 0 ? 0 : (t == 2 ? 1 : 2);   // row of G (gate row of G is zero)
       double s = -(t == 1 ? 0.0 : o.I[t]) - ic;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const double v = fma(ta.alpha, o.C[t][u], t == 1 ? 0.0 : o.G[r][u]);
-        a[4 * t + u] = v;
-        sl[4 * t + u] = (idx[t] >= 0 && idx[u] >= 0)
-                            ? (t == 1 ? __ldg(T.slot_g + u * N + k)
-                                      : __ldg(T.slot + (4 * r + u) * N + k))
-                            : -1;
+        sv[(4 * t + u) * kPipeBlock + tid] = v;
+        si[(4 * t + u) * kPipeBlock + tid] =
+            (idx[t] >= 0 && idx[u] >= 0)
+                ? (t == 1 ? __ldg(T.slot_g + u * N + k) : __ldg(T.slot + (4 * r + u) * N + k))
+                : -1;
         if (idx[u] >= 0) s = fma(v, V[u], s);
       }
-      rhs[t] = s;
+      sv[(16 + t) * kPipeBlock + tid] = s;
+      si[(16 + t) * kPipeBlock + tid] = idx[t];
     }
   }
 
   __device__ __forceinline__ void stamp() {
+    const int tid = threadIdx.x;
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-      if (row[t] < 0) continue;
+      const int row = si[(16 + t) * kPipeBlock + tid];
+      if (row < 0) continue;
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (sl[4 * t + u] >= 0) atomicAdd(A + sl[4 * t + u], a[4 * t + u]);
-      atomicAdd(b + row[t], rhs[t]);
+      for (int u = 0; u < 4; ++u) {
+        const int sl = si[(4 * t + u) * kPipeBlock + tid];
+        if (sl >= 0) atomicAdd(A + sl, sv[(4 * t + u) * kPipeBlock + tid]);
+      }
+      atomicAdd(b + row, sv[(16 + t) * kPipeBlock + tid]);
     }
   }
 };
 
 template <bool WANT_Q>
-__global__ void __launch_bounds__(kPipeBlock) k_color_pipe(DevTopo T, const double* __restrict__ x,
-                                                          double* A, double* b, double* q,
-                                                          int dbg, int absent_item) {
-  PipeDC<WANT_Q> w{T, x, A, b, q, dbg};
-  pipe_loop(T, w, absent_item);
+__global__ void __launch_bounds__(kPipeBlock, 5) k_color_pipe(DevTopo T, const double* __restrict__ x,
+                                                             double* A, double* b, double* q,
+                                                             int dbg, int absent_item) {
+  __shared__ double sv[kPipeDCStage * kPipeBlock];
+  __shared__ int si[kPipeDCStage * kPipeBlock];
+  PipeDC<WANT_Q> w{T, x, A, b, q, dbg, sv, si};
+  pipe_item(T, w, absent_item);
 }
 
-__global__ void __launch_bounds__(kPipeBlock) k_color_pipe_tran(DevTopo T,
-                                                               const double* __restrict__ x,
-                                                               double* A, double* b,
-                                                               TranArgs ta) {
-  PipeTran w{T, x, A, b, ta};
-  pipe_loop(T, w, -1);
+__global__ void __launch_bounds__(kPipeBlock, 4) k_color_pipe_tran(DevTopo T,
+                                                                  const double* __restrict__ x,
+                                                                  double* A, double* b,
+                                                                  TranArgs ta) {
+  __shared__ double sv[kPipeTranStage * kPipeBlock];
+  __shared__ int si[kPipeTranStage * kPipeBlock];
+  PipeTran w{T, x, A, b, ta, sv, si};
+  pipe_item(T, w, -1);
 }
 
 __global__ void k_dfma(double* out, int iters, double a, double c) {
@@ -902,6 +932,10 @@ cudaError_t launch_eval(const DevTopo& T, int mode, int begin, int end, const do
     case MODE_ATOMIC:
       if (wq) return launch_maybe_pdl(k_eval<MODE_ATOMIC, true>, g, B, s, pdl, T, begin, end, x, A, b, q, dbg);
       return launch_maybe_pdl(k_eval<MODE_ATOMIC, false>, g, B, s, pdl, T, begin, end, x, A, b, q, dbg);
+    case MODE_SORTED:
+      if (wq) k_eval<MODE_SORTED, true><<<g, B, 0, s>>>(T, begin, end, x, A, b, q, dbg);
+      else k_eval<MODE_SORTED, false><<<g, B, 0, s>>>(T, begin, end, x, A, b, q, dbg);
+      break;
     default:
       if (wq) k_eval<MODE_BUFFER, true><<<g, B, 0, s>>>(T, begin, end, x, A, b, q, dbg);
       else k_eval<MODE_BUFFER, false><<<g, B, 0, s>>>(T, begin, end, x, A, b, q, dbg);
@@ -926,6 +960,9 @@ cudaError_t launch_eval_ranges(const DevTopo& T, int mode, const int* rbeg, cons
   } else if (mode == MODE_BUFFER) {
     if (wq) k_eval_ranges<MODE_BUFFER, true><<<g, B, 0, s>>>(T, rbeg, roff, nr, total, x, A, b, q, dbg);
     else k_eval_ranges<MODE_BUFFER, false><<<g, B, 0, s>>>(T, rbeg, roff, nr, total, x, A, b, q, dbg);
+  } else if (mode == MODE_SORTED) {
+    if (wq) k_eval_ranges<MODE_SORTED, true><<<g, B, 0, s>>>(T, rbeg, roff, nr, total, x, A, b, q, dbg);
+    else k_eval_ranges<MODE_SORTED, false><<<g, B, 0, s>>>(T, rbeg, roff, nr, total, x, A, b, q, dbg);
   } else {
     return cudaErrorInvalidValue;   // colour schedules are not order-free
   }
@@ -1093,8 +1130,9 @@ cudaError_t launch_color_pipe(const DevTopo& T, int n_colors_nonempty, const dou
                               double* b, double* q, int grid, int dbg, cudaStream_t s,
                               int absent_item) {
   (void)n_colors_nonempty;
+  (void)grid;
   if (T.n_pitem <= 0) return cudaSuccess;
-  const int g = std::max(1, std::min(grid, T.n_pitem));
+  const int g = T.n_pitem;   // one block per work item (the items are taken by ticket)
   if (q)
     return launch_maybe_pdl(k_color_pipe<true>, g, kPipeBlock, s, true, T, x, A, b, q, dbg,
                             absent_item);
@@ -1106,8 +1144,9 @@ cudaError_t launch_color_pipe_tran(const DevTopo& T, int n_colors_nonempty, cons
                                    double* A, double* b, const TranArgs& ta, int grid,
                                    cudaStream_t s) {
   (void)n_colors_nonempty;
+  (void)grid;
   if (T.n_pitem <= 0) return cudaSuccess;
-  const int g = std::max(1, std::min(grid, T.n_pitem));
+  const int g = T.n_pitem;
   return launch_maybe_pdl(k_color_pipe_tran, g, kPipeBlock, s, true, T, x, A, b, ta);
 }
 
