@@ -503,21 +503,26 @@ def hbm_peak_gbs():
 
 
 def newton_study(eec, dev, stream):
-    """NEXT-2: the DC Newton loop closed on the GPU (evaluate and stamp, cuSOLVER sparse QR with
-    its analysis reused, damped update) from x = 0, per netlist: iterations, time per iteration
-    and the evaluate-and-stamp share of it (the paper: once evaluation is fast, the solve
-    dominates). Banded netlists only: the QR has no fill-reducing order. Bounded: at most 300
-    iterations per netlist and about a minute in all."""
+    """NEXT-2: the DC Newton loop closed on the GPU (evaluate and stamp, a sparse solve, damped
+    update) from x = 0, per netlist and solver (0: cuSOLVER batched QR, analysis reused; 1:
+    cuSOLVER QR after AMD; 2: the library's sparse LU, host analysis once, GPU refactorisation):
+    iterations, time per iteration and the evaluate-and-stamp share of it (the paper: once
+    evaluation is fast, the solve dominates). Bounded: at most 300 iterations per netlist and
+    about a minute and a half in all."""
     import torch
     import netgen
     out = {}
     t_start = time.perf_counter()
-    for nname, nn, solver in (("ripple_adder_64", netgen.ripple_adder(64), 0),
+    for nname, nn, solver in (("ripple_adder_64", netgen.ripple_adder(64), 2),
+                              ("ripple_adder_64", netgen.ripple_adder(64), 0),
                               ("ripple_adder_64", netgen.ripple_adder(64), 1),
+                              ("sram_32x32", netgen.sram(32, 32), 2),
+                              ("inverter_chain_1024", netgen.inverter_chain(1024), 2),
                               ("inverter_chain_1024", netgen.inverter_chain(1024), 1),
+                              ("inverter_chain_4096", netgen.inverter_chain(4096), 2),
                               ("inverter_chain_4096", netgen.inverter_chain(4096), 1)):
         nname = f"{nname}_solver{solver}"
-        if time.perf_counter() - t_start > 60:
+        if time.perf_counter() - t_start > 90:
             out[nname] = {"skipped": "time budget of the study used up"}
             continue
         c = eec.Circuit(nn, netgen.default_cards(), color=True)
@@ -541,8 +546,10 @@ def newton_study(eec, dev, stream):
         ev_ms = _time(lambda: c.eval_stamp(xd, An, bn, want_q=False), 20, stream)
         out[nname] = {"unknowns": c.n, "devices": nn.n_dev, "iterations": its,
                       "step_rule": "per-node clip to 0.2 V",
-                      "solver": ("batched sparse QR, analysis reused" if solver == 0 else
-                                 "sparse QR after symmetric AMD ordering"), "ms": ms,
+                      "solver": {0: "batched sparse QR, analysis reused",
+                                 1: "sparse QR after symmetric AMD ordering",
+                                 2: "library sparse LU (static pivots, GPU refactorisation)"}[solver],
+                      "lu_stats": eec.eec_lu_stats(c.ctx) if solver == 2 else None, "ms": ms,
                       "ms_per_iteration": ms / max(its, 1), "eval_stamp_ms": ev_ms,
                       "eval_stamp_share": ev_ms * max(its, 1) / ms}
     return out

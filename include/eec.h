@@ -244,30 +244,72 @@ EEC_API int eec_eval_stamp_host(eec_ctx* ctx, const double* x_host, double* A_ho
 /*
  * DC operating point by damped Newton on the GPU (the loop of Sec. II around the compute and
  * stamp phases; the paper solves with KLU on the host). Every iteration: eec_eval_stamp at x
- * (the context's schedule), a sparse direct solve A y = b on the GPU with cuSOLVER — solver 0:
+ * (the context's schedule), a sparse direct solve A y = b on the GPU — solver 0: cuSOLVER's
  * batched sparse QR, its pattern analysis done once per context and reused by every iteration,
- * no fill-reducing order; solver 1: sparse QR after a symmetric approximate-minimum-degree
- * ordering, analysed on every call (less fill on irregular netlists) — then
+ * no fill-reducing order; solver 1: cuSOLVER's sparse QR after a symmetric approximate-minimum-
+ * degree ordering, analysed on every call; solver EEC_SOLVER_LU (2): the library's sparse LU —
+ * on the host, once per context, a minimum-degree column order and one factorisation of the
+ * first iterate's matrix with threshold partial pivoting fix the row pivots and the patterns of
+ * L and U; every iteration then refactors the numbers on that pattern and solves on the GPU
+ * (one single-block kernel, with one step of iterative refinement once the steps are below
+ * 1 mV), and analyses again on the host if a pivot falls below 1e-4 of the
+ * largest entry of its column (eec_lu_stats counts the
+ * analyses) — then
  * a damped step: step_rule 0 scales the whole step, x += s (y - x) with s = min(1, vstep /
  * max|y - x|); step_rule 1 clips every node's move to [-vstep, vstep] on its own (long chains of
  * gates converge in far fewer iterations).
  * Converged when max|dx| <= tol_abs + tol_rel max|x| and, at the next iterate, the KCL residual
- * max|A x - b| = max|F(x)| <= tol_f amperes. When max_iter solves do not converge, the loop
- * restarts from the starting point with gshunt stepping: a shunt conductance g from every node
+ * max|A x - b| = max|F(x)| <= tol_f amperes. When max_iter solves do not converge, or a solve
+ * fails (a singular matrix, a non-finite step), the loop restarts from the starting point with
+ * gshunt stepping: a shunt conductance g from every node
  * to ground, g = 1e-3 S, converged, then g / 10 from that solution, down to the netlist's
  * gshunt, then the circuit itself (each stage with max_iter solves).
  *  x_dev       [n] in: starting point (free-node voltages), out: the last iterate.
  *  A_dev, b_dev  [nnz], [n] workspace; out: the stamp at the returned x.
  *  iters_out   (nullable) solves performed, over all stages.
  * Returns EEC_OK, EEC_ENOCONV (a stage ran max_iter solves without meeting both tests: x holds
- * its last iterate), EEC_ENUMERIC (a non-finite step or residual, or a singular matrix) or
- * EEC_ENOMEM. Meant for netlists up to tens of thousands of unknowns (solver 0 checks its
+ * its last iterate), EEC_ENUMERIC (a non-finite step or residual, or a singular matrix),
+ * EEC_ETIMEOUT (a bounded wait of the sparse LU's kernels ran out) or EEC_ENOMEM. Meant for netlists up to tens of thousands of unknowns (solver 0 checks its
  * factor's size before allocating). Synchronises cuda_stream once per iteration.
  */
+#define EEC_SOLVER_LU 2
 EEC_API int eec_newton_dc(eec_ctx* ctx, double* x_dev, double* A_values_dev, double* b_dev,
                           int32_t max_iter, double vstep, int32_t step_rule, int32_t solver,
                           double tol_abs, double tol_rel, double tol_f, int32_t* iters_out,
                           void* cuda_stream);
+
+/*
+ * x = A^-1 b on the context's pattern with the library's sparse LU (the solver EEC_SOLVER_LU of
+ * eec_newton_dc): the first call analyses A on the host (column order, row pivots, plan; it
+ * synchronises the stream), every call refactors A's numbers and solves with the library's
+ * kernel (with one step of iterative refinement), analysing again if a pivot has fallen below 1e-4 of its column's
+ * largest L entry.
+ *  A_values_dev [nnz], b_dev [n] in (device, unchanged); x_dev [n] out (device).
+ * Returns EEC_ENUMERIC for a singular matrix, EEC_ETIMEOUT if a bounded device wait ran out.
+ * Synchronises the stream once per call (the pivot check).
+ */
+EEC_API int eec_lu_solve(eec_ctx* ctx, const double* A_values_dev, const double* b_dev,
+                         double* x_dev, void* cuda_stream);
+
+/*
+ * The sparse LU of eec_newton_dc's solver EEC_SOLVER_LU: *nnz_lu = entries of L and U of the
+ * current plan (0 before the first solve), *analyses = host analyses so far (1 + the re-analyses
+ * after a degraded pivot). Either pointer may be NULL.
+ */
+EEC_API int eec_lu_stats(const eec_ctx* ctx, int64_t* nnz_lu, int32_t* analyses);
+
+/*
+ * Host check of the sparse LU (no GPU; the paper has no counterpart): for an n x n matrix in CSR
+ * (row_ptr [n+1], col [nnz], a [nnz], host), the minimum-degree order, the host factorisation
+ * with threshold partial pivoting, then the GPU kernel's refactorisation and triangular solves
+ * executed on the host in the GPU's order, for the right-hand side b [n]; x [n] receives the
+ * solution of A x = b. *nnz_lu (nullable) = entries of L and U; *bad_col
+ * (nullable) = the first column whose refactorised pivot fell below 1e-4 of its column's
+ * largest L entry, or -1.
+ * Returns EEC_EINVAL for a malformed matrix, EEC_ENUMERIC for a singular one.
+ */
+EEC_API int eec_lu_check_host(int32_t n, const int32_t* row_ptr, const int32_t* col, const double* a,
+                              const double* b, double* x, int64_t* nnz_lu, int32_t* bad_col);
 
 /*
  * Transient companion stamp of one Newton iterate of a time step (the transient loop of Sec. II,

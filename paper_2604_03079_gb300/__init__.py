@@ -35,6 +35,7 @@ VARIANT_NAMES = {0: "color_fused", 1: "persistent", 2: "atomic", 3: "segreduce",
 EEC_CONFLICT_FREE_NODE, EEC_CONFLICT_ANY_NONGROUND, EEC_CONFLICT_WRITE_ROWS = 0, 1, 2
 EEC_COLOR_GREEDY_SEQ, EEC_COLOR_JP_INDEX, EEC_COLOR_JP_RANDOM = 0, 1, 2
 EEC_RAIL_ELIMINATE, EEC_RAIL_MNA_BRANCH = 0, 1
+EEC_SOLVER_LU = 2
 EEC_CARD_LEN = 21
 
 
@@ -96,6 +97,10 @@ _SIG = {
                                         ctypes.POINTER(eec_options)]),
     "eec_batch_capture_graph": (ctypes.c_int, [_P, _P]),
     "eec_fp64_peak": (ctypes.c_int, [_I32, _I32, ctypes.POINTER(_F64)]),
+    "eec_lu_stats": (ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I32)]),
+    "eec_lu_solve": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "eec_lu_check_host": (ctypes.c_int, [_I32, _P, _P, _P, _P, _P, ctypes.POINTER(_I64),
+                                         ctypes.POINTER(_I32)]),
     "eec_math_check": (ctypes.c_int, [_I32, _I64, _P, _P, _P, _P]),
     "eec_test_barrier_timeout": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "eec_profile_enable": (ctypes.c_int, [_P, _I32]),
@@ -382,12 +387,49 @@ def eec_eval_stamp(ctx, x, A, b, q=None, stream=None):
     _eval_stamp(ctx, x, A, b, q, stream)
 
 
+def eec_lu_solve(ctx, A, b, x, stream=None):
+    """x = A^-1 b (device tensors) with the library's sparse LU on the context's pattern."""
+    _check(ctx, _load().eec_lu_solve(ctx, _d(A, name="A"), _d(b, name="b"), _d(x, name="x"),
+                                     _stream(stream)))
+
+
+def eec_lu_stats(ctx):
+    """-> (entries of L and U of the current sparse-LU plan, host analyses so far)."""
+    nnz = _I64(0)
+    an = _I32(0)
+    _check(ctx, _load().eec_lu_stats(ctx, ctypes.byref(nnz), ctypes.byref(an)))
+    return int(nnz.value), int(an.value)
+
+
+def eec_lu_check_host(row_ptr, col, a, b):
+    """Host check of the sparse LU (no GPU): -> (x solving A x = b, entries of L and U, first
+    column whose refactorised pivot degraded or -1)."""
+    import numpy as np
+    rp = np.ascontiguousarray(row_ptr, np.int32)
+    cl = np.ascontiguousarray(col, np.int32)
+    av = np.ascontiguousarray(a, np.float64)
+    bv = np.ascontiguousarray(b, np.float64)
+    n = rp.size - 1
+    if cl.size != rp[-1] or av.size != rp[-1] or bv.size != n:
+        raise ValueError("eec_lu_check_host: inconsistent sizes")
+    x = np.zeros(n)
+    nnz = _I64(0)
+    bad = _I32(0)
+    rc = _load().eec_lu_check_host(n, rp.ctypes.data, cl.ctypes.data, av.ctypes.data,
+                                   bv.ctypes.data, x.ctypes.data, ctypes.byref(nnz),
+                                   ctypes.byref(bad))
+    if rc != EEC_OK:
+        raise EECError(rc, "eec_lu_check_host failed")
+    return x, int(nnz.value), int(bad.value)
+
+
 def eec_newton_dc(ctx, x, A, b, max_iter=200, vstep=0.2, step_rule=0, solver=0, tol_abs=1e-12,
                   tol_rel=1e-9, tol_f=1e-12, stream=None) -> int:
     """DC Newton on the GPU from x (updated in place), with gshunt stepping when it does not
     converge; returns the number of solves.
     step_rule 0: the whole step scaled to vstep; 1: every node's move clipped to vstep.
-    solver 0: batched sparse QR, analysis reused; 1: sparse QR after an AMD ordering."""
+    solver 0: batched sparse QR, analysis reused; 1: sparse QR after an AMD ordering;
+    2 (EEC_SOLVER_LU): the library's sparse LU, host analysis once, GPU refactorisation."""
     _need_step(ctx, x, A, b)
     it = _I32(0)
     _check(ctx, _load().eec_newton_dc(ctx, _d(x, name="x"), _d(A, name="A"), _d(b, name="b"),

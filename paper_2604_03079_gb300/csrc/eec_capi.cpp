@@ -119,6 +119,18 @@ struct eec_ctx {
   int* d_diag = nullptr;         // CSR position of the diagonal of every node row
   void* sp_buf = nullptr;
   unsigned long long* d_nstats = nullptr;
+  // eec_newton_dc solver 2 (sparse LU): the column order (pattern only), the plan of the last
+  // analysis and its device copy (freed and replaced when a pivot degrades)
+  std::vector<int> lu_order;
+  LuPlan lu;
+  LuDev lud{};
+  bool lu_ready = false;
+  int lu_analyses = 0;
+  int* lu_ibuf = nullptr;       // the plan's index arrays, packed (grown, never shrunk)
+  size_t lu_icap = 0;
+  double* lu_dbuf = nullptr;    // factor values, work vector and inverse diagonal
+  size_t lu_dcap = 0;
+  int* lu_flag = nullptr;
   std::vector<cudaEvent_t> hev;  // chunk done (K) + side stream done (1) + start of the chunks (1)
 };
 
@@ -181,6 +193,17 @@ void free_topology(eec_ctx* c) {
   c->d_diag = nullptr;
   c->sp_buf = nullptr;
   c->d_nstats = nullptr;
+  if (c->lu_ibuf) cudaFree(c->lu_ibuf);
+  if (c->lu_dbuf) cudaFree(c->lu_dbuf);
+  if (c->lu_flag) cudaFree(c->lu_flag);
+  c->lu_ibuf = nullptr;
+  c->lu_dbuf = nullptr;
+  c->lu_flag = nullptr;
+  c->lu_icap = c->lu_dcap = 0;
+  c->lu_order.clear();
+  c->lu = LuPlan{};
+  c->lud = LuDev{};
+  c->lu_ready = false;
   for (void* p : c->dmem) cudaFree(p);
   c->dmem.clear();
   int* st = c->d_status;
@@ -1414,7 +1437,123 @@ int eec_eval_stamp_host(eec_ctx* c, const double* x_host, double* A_host, double
 
 // Solver state of eec_newton_dc, on its first call: the pattern on the device, the sparse QR's
 // analysis (reused by every later factorisation: the pattern never changes) and its workspace.
+}  // extern "C" (C++ helpers of eec_newton_dc's solvers)
+
+namespace {
+
+// Arrays every solver of eec_newton_dc uses: the pattern on the device, the solution y, the
+// starting point, the diagonal positions and the norms.
+int newton_common(eec_ctx* c) {
+  if (c->d_rp) return EEC_OK;
+  const int n_node = c->n - (int)c->rail.size();
+  std::vector<int> diag(n_node);
+  for (int i = 0; i < n_node; ++i)
+    diag[i] = (int)(std::lower_bound(c->col.begin() + c->row_ptr[i],
+                                     c->col.begin() + c->row_ptr[i + 1], i) - c->col.begin());
+  int rc;
+  if ((rc = dupload(c, &c->d_rp, c->row_ptr)) || (rc = dupload(c, &c->d_col, c->col)) ||
+      (rc = dalloc(c, &c->d_y, c->n)) || (rc = dalloc(c, &c->d_x0, c->n)) ||
+      (rc = dupload(c, &c->d_diag, diag)) || (rc = dalloc(c, &c->d_nstats, 4)))
+    return rc;
+  return EEC_OK;
+}
+
+// Solver 2: analyse A (device values of the current iterate) on the host -- the column order
+// once per pattern, the pivots and the plan from one factorisation -- and upload the plan into
+// the context's two LU buffers (one for the index arrays, packed, one for the values; both kept
+// and reused by later analyses, grown only when a plan needs more room).
+int lu_prepare(eec_ctx* c, const double* A, cudaStream_t s) {
+  std::vector<double> a(c->nnz);
+  CUDA_TRY(c, cudaMemcpyAsync(a.data(), A, sizeof(double) * c->nnz, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(c, cudaStreamSynchronize(s));
+  if (c->lu_order.empty()) c->lu_order = lu_min_degree_order(c->n, c->row_ptr, c->col);
+  LuPlan P;
+  std::string err;
+  if (!lu_analyze(c->n, c->row_ptr, c->col, a, c->lu_order, P, err)) return fail(c, EEC_ENUMERIC, err);
+  const std::vector<int>* parts[] = {&P.cptr, &P.cdiag, &P.a2lu, &P.uptr, &P.uk, &P.upos,
+                                     &P.mptr, &P.msrc, &P.mdst, &P.lrptr, &P.lrcol, &P.lrpos,
+                                     &P.urptr, &P.urcol, &P.urpos, &P.prow, &P.pcol};
+  constexpr int kParts = sizeof(parts) / sizeof(parts[0]);
+  std::vector<int> packed;
+  size_t off[kParts];
+  for (int k = 0; k < kParts; ++k) {
+    off[k] = packed.size();
+    packed.insert(packed.end(), parts[k]->begin(), parts[k]->end());
+    packed.resize((packed.size() + 3) & ~(size_t)3);   // 16-byte aligned starts
+  }
+  const size_t nd = (size_t)P.cptr[P.n] + 4 * (size_t)P.n;
+  c->lu_ready = false;
+  if (packed.size() > c->lu_icap) {
+    if (c->lu_ibuf) cudaFree(c->lu_ibuf);
+    c->lu_ibuf = nullptr;
+    c->lu_icap = 0;
+    if (cudaMalloc(&c->lu_ibuf, sizeof(int) * (packed.size() + packed.size() / 2)) != cudaSuccess)
+      return fail(c, EEC_ENOMEM, "sparse LU: out of memory");
+    c->lu_icap = packed.size() + packed.size() / 2;
+  }
+  if (nd > c->lu_dcap) {
+    if (c->lu_dbuf) cudaFree(c->lu_dbuf);
+    c->lu_dbuf = nullptr;
+    c->lu_dcap = 0;
+    if (cudaMalloc(&c->lu_dbuf, sizeof(double) * (nd + nd / 2)) != cudaSuccess)
+      return fail(c, EEC_ENOMEM, "sparse LU: out of memory");
+    c->lu_dcap = nd + nd / 2;
+  }
+  if (!c->lu_flag && cudaMalloc(&c->lu_flag, 3 * sizeof(int)) != cudaSuccess)
+    return fail(c, EEC_ENOMEM, "sparse LU: out of memory");
+  CUDA_TRY(c, cudaMemcpyAsync(c->lu_ibuf, packed.data(), sizeof(int) * packed.size(),
+                              cudaMemcpyHostToDevice, s));
+  CUDA_TRY(c, cudaStreamSynchronize(s));   // the host vector dies with this call
+  LuDev d{};
+  d.n = P.n;
+  d.nnz_lu = P.cptr[P.n];
+  d.nnz_a = (int)P.a2lu.size();
+  const int** dst[] = {&d.cptr, &d.cdiag, &d.a2lu, &d.uptr, &d.uk, &d.upos, &d.mptr, &d.msrc,
+                       &d.mdst, &d.lrptr, &d.lrcol, &d.lrpos, &d.urptr, &d.urcol, &d.urpos,
+                       &d.prow, &d.pcol};
+  for (int k = 0; k < kParts; ++k) *dst[k] = c->lu_ibuf + off[k];
+  d.vals = c->lu_dbuf;
+  d.y = d.vals + d.nnz_lu;
+  d.flag = c->lu_flag;
+  c->lu = std::move(P);
+  c->lud = d;
+  c->lu_ready = true;
+  ++c->lu_analyses;
+  return EEC_OK;
+}
+
+// Solver 2: factor A on the fixed plan and solve A y = b; analyses again
+// (once) when a pivot has fallen below kLuTiny of the largest entry of its column's L part --
+// the static pivots no longer make a stable factorisation of this matrix.
+constexpr double kLuTiny = 1e-4;   // a fresh analysis keeps scaled L entries <= 1e3 (kLuDiagPref)
+int lu_factor_solve(eec_ctx* c, const double* A, const double* b, double* y, int refine,
+                    cudaStream_t s) {
+  int rc;
+  if (!c->lu_ready && (rc = lu_prepare(c, A, s))) return rc;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    CUDA_TRY(c, cudaMemsetAsync(c->lud.flag, 0, 3 * sizeof(int), s));
+    CUDA_TRY(c, launch_lu_factor_solve(c->lud, A, c->d_rp, c->d_col, b, y, kLuTiny, refine, s));
+    c->n_kernels += 1;
+    int fl[3] = {0, 0, 0};
+    CUDA_TRY(c, cudaMemcpyAsync(fl, c->lud.flag, sizeof fl, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+    if (fl[1]) return fail(c, EEC_ETIMEOUT, "sparse LU: a device wait ran past its limit");
+    // growth beyond the bound: the pivots of the plan no longer suit this matrix -- analyse it
+    // and factor again; growth left after a fresh analysis (rounding of a nearly singular
+    // matrix in the GPU's update order) is accepted: the Newton step's own tests judge it
+    if ((!fl[0] || attempt == 1) && !fl[2]) return EEC_OK;
+    if (attempt == 0 && (rc = lu_prepare(c, A, s))) return rc;
+  }
+  return fail(c, EEC_ENUMERIC, "sparse LU: a zero or non-finite pivot (singular or non-finite matrix)");
+}
+
+}  // namespace
+
+extern "C" {
+
 int newton_setup(eec_ctx* c, const double* A) {
+  int rc0 = newton_common(c);
+  if (rc0) return rc0;
   if (c->sp_info) return EEC_OK;
   if (!c->sp && cusolverSpCreate(&c->sp) != CUSOLVER_STATUS_SUCCESS)
     return fail(c, EEC_ECUDA, "cusolverSpCreate failed");
@@ -1425,15 +1564,6 @@ int newton_setup(eec_ctx* c, const double* A) {
     cusparseSetMatIndexBase(c->sp_descr, CUSPARSE_INDEX_BASE_ZERO);
   }
   int rc;
-  const int n_node = c->n - (int)c->rail.size();
-  std::vector<int> diag(n_node);
-  for (int i = 0; i < n_node; ++i)
-    diag[i] = (int)(std::lower_bound(c->col.begin() + c->row_ptr[i],
-                                     c->col.begin() + c->row_ptr[i + 1], i) - c->col.begin());
-  if ((rc = dupload(c, &c->d_rp, c->row_ptr)) || (rc = dupload(c, &c->d_col, c->col)) ||
-      (rc = dalloc(c, &c->d_y, c->n)) || (rc = dalloc(c, &c->d_x0, c->n)) ||
-      (rc = dupload(c, &c->d_diag, diag)) || (rc = dalloc(c, &c->d_nstats, 4)))
-    return rc;
   csrqrInfo_t info = nullptr;
   if (cusolverSpCreateCsrqrInfo(&info) != CUSOLVER_STATUS_SUCCESS)
     return fail(c, EEC_ECUDA, "cusolverSpCreateCsrqrInfo failed");
@@ -1480,6 +1610,7 @@ int newton_run(eec_ctx* c, double* x, double* A, double* b, int max_iter, double
   int rc;
   unsigned long long hs[4];
   bool small_step = false;
+  bool near = false;   // the last step moved no node by more than 1 mV
   *iters = 0;
   for (int it = 0; it <= max_iter; ++it) {
     CUDA_TRY(c, cudaMemsetAsync(c->d_nstats, 0, 4 * sizeof(unsigned long long), s));
@@ -1497,7 +1628,11 @@ int newton_run(eec_ctx* c, double* x, double* A, double* b, int max_iter, double
       if (r <= tol_f) return EEC_OK;
     }
     if (it == max_iter) break;
-    if (solver == 0) {
+    if (solver == EEC_SOLVER_LU) {
+      // refined solves once the steps are small (the converging tail, where the residual test
+      // needs the solve's full accuracy); plain ones before
+      if ((rc = lu_factor_solve(c, A, b, c->d_y, near ? 1 : 0, s))) return rc;
+    } else if (solver == 0) {
       if (cusolverSpDcsrqrsvBatched(c->sp, n, n, nnz, c->sp_descr, A, c->d_rp, c->d_col, b,
                                     c->d_y, 1, c->sp_info, c->sp_buf) != CUSOLVER_STATUS_SUCCESS)
         return fail(c, EEC_ECUDA, "sparse QR solve failed");
@@ -1509,7 +1644,7 @@ int newton_run(eec_ctx* c, double* x, double* A, double* b, int max_iter, double
       if (singular >= 0)
         return fail(c, EEC_ENUMERIC, "singular matrix (row " + std::to_string(singular) + ")");
     }
-    c->n_kernels += 2;
+    if (solver != EEC_SOLVER_LU) c->n_kernels += 2;
     CUDA_TRY(c, launch_newton_step(c->d_y, x, n, vstep, step_rule, c->d_nstats, s));
     CUDA_TRY(c, cudaMemcpyAsync(hs, c->d_nstats, sizeof hs, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(c, cudaStreamSynchronize(s));
@@ -1517,6 +1652,7 @@ int newton_run(eec_ctx* c, double* x, double* A, double* b, int max_iter, double
     if (!std::isfinite(dxm) || !std::isfinite(xm))
       return fail(c, EEC_ENUMERIC, "non-finite Newton step (singular matrix?)");
     small_step = dxm <= tol_abs + tol_rel * xm;
+    near = dxm < 1e-3;
     *iters = it + 1;
   }
   return EEC_ENOCONV;
@@ -1529,7 +1665,7 @@ int eec_newton_dc(eec_ctx* c, double* x, double* A, double* b, int32_t max_iter,
   int rc = check_built(c);
   if (rc) return rc;
   if (!x || !A || !b || max_iter < 1 || !(vstep > 0.0) || step_rule < 0 || step_rule > 1 ||
-      solver < 0 || solver > 1 ||
+      solver < 0 || solver > EEC_SOLVER_LU ||
       !(tol_abs >= 0.0) ||
       !(tol_rel >= 0.0) || !(tol_f >= 0.0))
     return fail(c, EEC_EINVAL, "bad eec_newton_dc arguments");
@@ -1537,16 +1673,22 @@ int eec_newton_dc(eec_ctx* c, double* x, double* A, double* b, int32_t max_iter,
   if (iters_out) *iters_out = 0;
   if (c->n == 0) return EEC_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if ((rc = newton_setup(c, A))) return rc;
-  if (cusolverSpSetStream(c->sp, s) != CUSOLVER_STATUS_SUCCESS)
-    return fail(c, EEC_ECUDA, "cusolverSpSetStream failed");
+  if (solver == EEC_SOLVER_LU) {
+    if ((rc = newton_common(c))) return rc;
+  } else {
+    if ((rc = newton_setup(c, A))) return rc;
+    if (cusolverSpSetStream(c->sp, s) != CUSOLVER_STATUS_SUCCESS)
+      return fail(c, EEC_ECUDA, "cusolverSpSetStream failed");
+  }
   CUDA_TRY(c, cudaMemcpyAsync(c->d_x0, x, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, s));
   int its = 0, total = 0;
   rc = newton_run(c, x, A, b, max_iter, vstep, step_rule, solver, tol_abs, tol_rel, tol_f, 0.0,
                   &its, s);
   total += its;
-  if (rc == EEC_ENOCONV) {
-    // gshunt stepping (the oracle's fallback): restart from the starting point with a shunt of
+  if (rc == EEC_ENOCONV || rc == EEC_ENUMERIC) {
+    // gshunt stepping (the oracle's fallback, taken as there both when plain Newton runs out of
+    // iterations and when a step fails: a singular matrix or a non-finite step): restart from
+    // the starting point with a shunt of
     // g = 1e-3 S on every node, converge, divide g by 10 and continue from that solution down
     // to the circuit's own gshunt, then solve the circuit itself from there
     CUDA_TRY(c, cudaMemcpyAsync(x, c->d_x0, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, s));
@@ -1827,6 +1969,47 @@ int eec_test_barrier_timeout(eec_ctx* c, const double* x, double* A, double* b, 
   }
   CUDA_TRY(c, launch_persistent(c->d, c->d_coff, c->C, x, A, b, nullptr, 0, c->persist_grid, 0, s,
                                 /*absent_block=*/0));
+  return EEC_OK;
+}
+
+int eec_lu_check_host(int32_t n, const int32_t* row_ptr, const int32_t* col, const double* a,
+                      const double* b, double* x, int64_t* nnz_lu, int32_t* bad_col) {
+  if (n < 1 || !row_ptr || !col || !a || !b || !x) return EEC_EINVAL;
+  const std::vector<int> rp(row_ptr, row_ptr + n + 1);
+  if (rp[0] != 0) return EEC_EINVAL;
+  for (int i = 0; i < n; ++i)
+    if (rp[i + 1] < rp[i]) return EEC_EINVAL;
+  const std::vector<int> cl(col, col + rp[n]);
+  for (int v : cl)
+    if (v < 0 || v >= n) return EEC_EINVAL;
+  const std::vector<double> av(a, a + rp[n]), bv(b, b + n);
+  const std::vector<int> q = lu_min_degree_order(n, rp, cl);
+  LuPlan P;
+  std::string err;
+  if (!lu_analyze(n, rp, cl, av, q, P, err)) return EEC_ENUMERIC;
+  std::vector<double> xv;
+  int bad = -1;
+  lu_refactor_solve_host(P, av, bv, kLuTiny, xv, &bad);
+  std::copy(xv.begin(), xv.end(), x);
+  if (nnz_lu) *nnz_lu = P.cptr[n];
+  if (bad_col) *bad_col = bad;
+  return EEC_OK;
+}
+
+int eec_lu_solve(eec_ctx* c, const double* A, const double* b, double* x, void* stream) {
+  NvtxRange range("eec/lu_solve");
+  int rc = check_built(c);
+  if (rc) return rc;
+  if (!A || !b || !x) return fail(c, EEC_EINVAL, "NULL A, b or x");
+  if (c->n == 0) return EEC_OK;
+  if ((rc = newton_common(c))) return rc;
+  return lu_factor_solve(c, A, b, x, 1, static_cast<cudaStream_t>(stream));
+}
+
+int eec_lu_stats(const eec_ctx* c, int64_t* nnz_lu, int32_t* analyses) {
+  if (!c) return EEC_EINVAL;
+  if (nnz_lu) *nnz_lu = c->lu_ready ? c->lu.cptr[c->lu.n] : 0;
+  if (analyses) *analyses = c->lu_analyses;
   return EEC_OK;
 }
 

@@ -160,7 +160,7 @@ __device__ __forceinline__ void eval_one(const DevTopo& T, int k, const double* 
         T.cbuf[__ldg(T.gat_pos + (4 * r + u) * N + k)] = o.G[r][u];
       }
       T.cbuf[__ldg(T.gat_pos + (kNSlot + r) * N + k)] = s;
-      bc_ok = bc_ok && isfinite(s);
+      if (dbg) bc_ok = bc_ok && isfinite(s);   // FP64 compares: debug checks only
     }
   } else if (MODE == MODE_BUFFER) {
     // only what a stamp reads is buffered: rows of free terminals, and in them the entries of
@@ -176,7 +176,7 @@ __device__ __forceinline__ void eval_one(const DevTopo& T, int k, const double* 
         T.buf[(4 * r + u) * N + k] = o.G[r][u];
       }
       T.buf[(kNSlot + r) * N + k] = s;
-      bc_ok = bc_ok && isfinite(s);
+      if (dbg) bc_ok = bc_ok && isfinite(s);   // FP64 compares: debug checks only
     }
   } else {
     // rows of source-held terminals are not stamped: their b entries are not formed
@@ -195,7 +195,7 @@ __device__ __forceinline__ void eval_one(const DevTopo& T, int k, const double* 
       }
       if (MODE == MODE_ATOMIC) atomicAdd(b + row, s);
       else b[row] += s;
-      bc_ok = bc_ok && isfinite(s);
+      if (dbg) bc_ok = bc_ok && isfinite(s);   // FP64 compares: debug checks only
     }
   }
   if (WANT_Q) {
@@ -713,7 +713,6 @@ struct PipeDC {
     EvalOut<double> o;
     eval_model<WANT_Q, false>(T, k, x, idx, V, o);
     const int term[3] = {0, 2, 3};
-    bool ok = true;
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
       const int row = idx[term[r]];
@@ -724,18 +723,25 @@ struct PipeDC {
         si[(4 * r + u) * kPipeBlock + tid] =
             (row >= 0 && idx[u] >= 0) ? __ldg(T.slot + (4 * r + u) * N + k) : -1;
         if (idx[u] >= 0) s = fma(o.G[r][u], V[u], s);
-        ok = ok && isfinite(o.G[r][u]);
       }
       sv[(kNSlot + r) * kPipeBlock + tid] = s;
       si[(kNSlot + r) * kPipeBlock + tid] = row;
-      ok = ok && (row < 0 || isfinite(s));
     }
     if (WANT_Q) {
       const int od = __ldg(T.orig + k);
 #pragma unroll
       for (int t = 0; t < 4; ++t) q[t * N + od] = o.Q[t];
     }
-    if (dbg && !ok) atomicOr(T.status, kStatusNumeric);
+    if (dbg) {   // non-finite values (debug checks only: the tests cost FP64 issue slots)
+      bool ok = true;
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        ok = ok && (idx[term[r]] < 0 || isfinite(sv[(kNSlot + r) * kPipeBlock + tid]));
+#pragma unroll
+        for (int u = 0; u < 4; ++u) ok = ok && isfinite(o.G[r][u]);
+      }
+      if (!ok) atomicOr(T.status, kStatusNumeric);
+    }
   }
 
   __device__ __forceinline__ void stamp() {

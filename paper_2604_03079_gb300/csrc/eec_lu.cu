@@ -1,0 +1,514 @@
+// Sparse LU of the MNA matrix for the GPU Newton loop (eec_newton_dc, solver EEC_SOLVER_LU).
+//
+// Once the evaluate-and-stamp step is fast the linear solve dominates the Newton iteration
+// (Sec. III: matrix solve against device evaluation, Table II); the paper solves with KLU on the
+// host. Here the pattern of A never changes between iterations, so the expensive symbolic work is
+// done once and only the numbers are recomputed on the GPU every iteration:
+//  * host, once per pattern (again only if a pivot degrades): a fill-reducing column order
+//    (approximate minimum degree on the symmetric pattern), then one left-looking sparse LU of
+//    the first iterate's matrix with threshold partial pivoting (Gilbert-Peierls: the pattern of
+//    every column is the set reached in the graph of the L columns before it, so it does not
+//    depend on the values). It fixes the row pivot sequence and the structural patterns of L and
+//    U, and the plan below;
+//  * GPU, every iteration: the numeric refactorisation on that pattern with those pivots, then
+//    the two triangular solves, each in one single-block kernel. Columns (rows for the solves)
+//    are dealt to the block's 32 warps round robin; a warp waits for the columns its column
+//    depends on through a 32-entry progress array in shared memory (column k is final once the
+//    warp that owns it has moved past k), so independent columns proceed in parallel and a chain
+//    of dependent columns costs one warp step per column. All waits are bounded.
+// Storage, column j of the permuted matrix P A Q: its U part (rows k < j, ascending), the
+// diagonal, then its L part (rows > j, ascending), in one value array.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <iterator>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "eec_internal.h"
+
+namespace eec {
+
+// ---- host analysis ----------------------------------------------------------------------------
+
+// Minimum-degree order of the symmetric pattern of A + A^T (diagonal ignored): repeatedly
+// eliminate a node of least current degree (ties: the lowest index) and join its remaining
+// neighbours into a clique, as elimination does. Explicit adjacency; the netlists this serves
+// have small degrees away from the rails, which the rule leaves to the end.
+std::vector<int> lu_min_degree_order(int n, const std::vector<int>& rp, const std::vector<int>& col) {
+  std::vector<std::vector<int>> adj(n);
+  for (int i = 0; i < n; ++i)
+    for (int e = rp[i]; e < rp[i + 1]; ++e) {
+      const int j = col[e];
+      if (j == i) continue;
+      adj[i].push_back(j);
+      adj[j].push_back(i);
+    }
+  for (auto& a : adj) {
+    std::sort(a.begin(), a.end());
+    a.erase(std::unique(a.begin(), a.end()), a.end());
+  }
+  std::set<std::pair<int, int>> by_deg;   // (degree, node) of the nodes not yet eliminated
+  for (int i = 0; i < n; ++i) by_deg.insert({(int)adj[i].size(), i});
+  std::vector<int> order;
+  order.reserve(n);
+  std::vector<int> merged;
+  while (!by_deg.empty()) {
+    const int v = by_deg.begin()->second;
+    by_deg.erase(by_deg.begin());
+    order.push_back(v);
+    const std::vector<int> nb = std::move(adj[v]);
+    adj[v].clear();
+    for (int a : nb) {
+      by_deg.erase({(int)adj[a].size(), a});
+      // adj[a] := (adj[a] without v) joined with the other neighbours of v
+      merged.clear();
+      std::set_union(adj[a].begin(), adj[a].end(), nb.begin(), nb.end(), std::back_inserter(merged));
+      merged.erase(std::remove_if(merged.begin(), merged.end(),
+                                  [&](int u) { return u == v || u == a; }),
+                   merged.end());
+      adj[a].swap(merged);
+      by_deg.insert({(int)adj[a].size(), a});
+    }
+  }
+  return order;
+}
+
+constexpr double kLuDiagPref = 1e-3;
+
+// Left-looking LU with threshold partial pivoting of B = A(:, q) (A in CSR, symmetric pattern
+// not required); plan out. Returns false (with err) for a numerically singular column.
+bool lu_analyze(int n, const std::vector<int>& rp, const std::vector<int>& col,
+                const std::vector<double>& a, const std::vector<int>& q, LuPlan& P,
+                std::string& err) {
+  const int nnz = rp[n];
+  // CSC of A: column c lists (row, CSR position)
+  std::vector<int> cp(n + 1, 0), ci(nnz), cpos(nnz);
+  for (int e = 0; e < nnz; ++e) cp[col[e] + 1]++;
+  for (int c = 0; c < n; ++c) cp[c + 1] += cp[c];
+  {
+    std::vector<int> fill(cp.begin(), cp.end() - 1);
+    for (int i = 0; i < n; ++i)
+      for (int e = rp[i]; e < rp[i + 1]; ++e) {
+        const int f = fill[col[e]]++;
+        ci[f] = i;
+        cpos[f] = e;
+      }
+  }
+  // factor: L columns with original row indices (values already divided by the pivot)
+  std::vector<std::vector<std::pair<int, double>>> Lc(n);
+  std::vector<std::vector<int>> Uk(n);   // U(:, j): pivot steps k < j (pattern only)
+  std::vector<int> pinv(n, -1), prow(n, -1);
+  std::vector<double> x(n, 0.0);
+  std::vector<char> mark(n, 0);
+  std::vector<int> pat, topo, stack, head;
+  for (int j = 0; j < n; ++j) {
+    const int c = q[j];
+    // pattern: rows of B(:, j) plus everything reached through the L columns of pivoted rows;
+    // topo receives the reached pivot steps in reverse post-order (a valid update order)
+    pat.clear();
+    topo.clear();
+    for (int f = cp[c]; f < cp[c + 1]; ++f) {
+      const int i0 = ci[f];
+      if (mark[i0]) continue;
+      mark[i0] = 1;
+      pat.push_back(i0);
+      if (pinv[i0] < 0) continue;
+      // iterative DFS over pivot steps
+      stack.assign(1, pinv[i0]);
+      head.assign(1, 0);
+      while (!stack.empty()) {
+        const int k = stack.back();
+        int& h = head.back();
+        bool pushed = false;
+        while (h < (int)Lc[k].size()) {
+          const int i = Lc[k][h++].first;
+          if (mark[i]) continue;
+          mark[i] = 1;
+          pat.push_back(i);
+          if (pinv[i] >= 0) {
+            stack.push_back(pinv[i]);
+            head.push_back(0);
+            pushed = true;
+            break;
+          }
+        }
+        if (!pushed) {
+          topo.push_back(k);
+          stack.pop_back();
+          head.pop_back();
+        }
+      }
+    }
+    for (int f = cp[c]; f < cp[c + 1]; ++f) x[ci[f]] = a[cpos[f]];
+    // updates in topological order: reverse of the post-order
+    for (int t = (int)topo.size() - 1; t >= 0; --t) {
+      const int k = topo[t];
+      const double xk = x[prow[k]];
+      for (const auto& e : Lc[k]) x[e.first] -= e.second * xk;
+    }
+    // pivot: the largest unpivoted entry, or the diagonal row c when it is within a factor
+    // kLuDiagPref of it (the default threshold of KLU: keeps the diagonal of circuit matrices,
+    // whose off-diagonal transconductances would otherwise shift every pivot of a long chain
+    // of gates one row down and leave one row to underflow)
+    int piv = -1;
+    double best = 0.0;
+    for (int i : pat)
+      if (pinv[i] < 0 && std::fabs(x[i]) > best) {
+        best = std::fabs(x[i]);
+        piv = i;
+      }
+    if (piv < 0 || !(best > 0.0) || !std::isfinite(best)) {
+      err = "sparse LU: matrix singular at column " + std::to_string(j);
+      for (int i : pat) { x[i] = 0.0; mark[i] = 0; }
+      return false;
+    }
+    if (pinv[c] < 0 && mark[c] && std::fabs(x[c]) >= kLuDiagPref * best) piv = c;
+    const double pv = x[piv];
+    pinv[piv] = j;
+    prow[j] = piv;
+    for (int i : pat) {
+      if (pinv[i] >= 0 && pinv[i] < j) Uk[j].push_back(pinv[i]);
+      else if (i != piv) Lc[j].push_back({i, x[i] / pv});
+      x[i] = 0.0;
+      mark[i] = 0;
+    }
+    std::sort(Uk[j].begin(), Uk[j].end());
+  }
+  // plan: column storage of P A Q (rows in pivot-step numbering)
+  P.n = n;
+  P.prow = prow;
+  P.pcol = q;
+  P.cptr.assign(n + 1, 0);
+  for (int j = 0; j < n; ++j) P.cptr[j + 1] = P.cptr[j] + (int)Uk[j].size() + 1 + (int)Lc[j].size();
+  const int nlu = P.cptr[n];
+  P.crow.assign(nlu, 0);
+  P.cdiag.assign(n, 0);
+  std::vector<std::vector<int>> Lrows(n);   // L(:, j) rows in pivot-step numbering, ascending
+  for (int j = 0; j < n; ++j) {
+    int p = P.cptr[j];
+    for (int k : Uk[j]) P.crow[p++] = k;
+    P.cdiag[j] = p;
+    P.crow[p++] = j;
+    for (const auto& e : Lc[j]) Lrows[j].push_back(pinv[e.first]);
+    std::sort(Lrows[j].begin(), Lrows[j].end());
+    for (int r : Lrows[j]) P.crow[p++] = r;
+  }
+  auto find = [&](int r, int j) -> int {   // position of (r, j) in column j, or -1
+    const int* b0 = P.crow.data() + P.cptr[j];
+    const int* d = P.crow.data() + P.cdiag[j];
+    const int* b1 = P.crow.data() + P.cptr[j + 1];
+    if (r < j) {
+      const int* f = std::lower_bound(b0, d, r);
+      return (f != d && *f == r) ? (int)(f - P.crow.data()) : -1;
+    }
+    if (r == j) return P.cdiag[j];
+    const int* f = std::lower_bound(d + 1, b1, r);
+    return (f != b1 && *f == r) ? (int)(f - P.crow.data()) : -1;
+  };
+  std::vector<int> qinv(n);
+  for (int j = 0; j < n; ++j) qinv[q[j]] = j;
+  P.a2lu.assign(nnz, -1);
+  for (int i = 0; i < n; ++i)
+    for (int e = rp[i]; e < rp[i + 1]; ++e) {
+      P.a2lu[e] = find(pinv[i], qinv[col[e]]);
+      if (P.a2lu[e] < 0) {
+        err = "sparse LU: an entry of A outside the factor pattern";
+        return false;
+      }
+    }
+  // updates of column j: for every k of U(:, j) (ascending), the entries of L(:, k) go to the
+  // rows of column j they hit
+  P.uptr.assign(n + 1, 0);
+  P.uk.clear();
+  P.upos.clear();
+  P.mptr.assign(1, 0);
+  P.msrc.clear();
+  P.mdst.clear();
+  for (int j = 0; j < n; ++j) {
+    for (int p = P.cptr[j]; p < P.cdiag[j]; ++p) {
+      const int k = P.crow[p];
+      P.uk.push_back(k);
+      P.upos.push_back(p);
+      for (int s = P.cdiag[k] + 1; s < P.cptr[k + 1]; ++s) {
+        const int d = find(P.crow[s], j);
+        if (d < 0) {
+          err = "sparse LU: an update outside the factor pattern";
+          return false;
+        }
+        P.msrc.push_back(s);
+        P.mdst.push_back(d);
+      }
+      P.mptr.push_back((int)P.msrc.size());
+    }
+    P.uptr[j + 1] = (int)P.uk.size();
+  }
+  // rows of L (strictly lower) and of U (strictly upper) for the two substitutions
+  std::vector<std::vector<std::pair<int, int>>> lr(n), ur(n);
+  for (int j = 0; j < n; ++j)
+    for (int p = P.cptr[j]; p < P.cptr[j + 1]; ++p) {
+      const int r = P.crow[p];
+      if (r > j) lr[r].push_back({j, p});
+      else if (r < j) ur[r].push_back({j, p});
+    }
+  P.lrptr.assign(n + 1, 0);
+  P.urptr.assign(n + 1, 0);
+  P.lrcol.clear();
+  P.lrpos.clear();
+  P.urcol.clear();
+  P.urpos.clear();
+  for (int r = 0; r < n; ++r) {
+    for (const auto& e : lr[r]) { P.lrcol.push_back(e.first); P.lrpos.push_back(e.second); }
+    for (const auto& e : ur[r]) { P.urcol.push_back(e.first); P.urpos.push_back(e.second); }
+    P.lrptr[r + 1] = (int)P.lrcol.size();
+    P.urptr[r + 1] = (int)P.urcol.size();
+  }
+  return true;
+}
+
+// The GPU's refactorisation and substitutions executed on the host in the same order (column by
+// column, updates in ascending k, rows in order, the same pivot test): a check of the plan
+// without a GPU.
+bool lu_refactor_solve_host(const LuPlan& P, const std::vector<double>& a,
+                            const std::vector<double>& b, double tiny, std::vector<double>& x,
+                            int* bad_col) {
+  const int n = P.n;
+  std::vector<double> v(P.cptr[n], 0.0), dinv(n);
+  for (size_t e = 0; e < P.a2lu.size(); ++e) v[P.a2lu[e]] = a[e];
+  for (int j = 0; j < n; ++j) {
+    for (int t = P.uptr[j]; t < P.uptr[j + 1]; ++t) {
+      const double ukj = v[P.upos[t]];
+      for (int m = P.mptr[t]; m < P.mptr[t + 1]; ++m) v[P.mdst[m]] -= v[P.msrc[m]] * ukj;
+    }
+    dinv[j] = 1.0 / v[P.cdiag[j]];
+    for (int p = P.cdiag[j] + 1; p < P.cptr[j + 1]; ++p) v[p] *= dinv[j];
+  }
+  *bad_col = -1;
+  for (int j = 0; j < n && *bad_col < 0; ++j) {
+    bool bad = !std::isfinite(dinv[j]) || dinv[j] == 0.0;
+    for (int p = P.cdiag[j] + 1; p < P.cptr[j + 1] && !bad; ++p) bad = !(std::fabs(v[p]) < 1.0 / tiny);
+    if (bad) *bad_col = j;
+  }
+  std::vector<double> y(n);
+  for (int r = 0; r < n; ++r) {
+    double s = 0.0;
+    for (int p = P.lrptr[r]; p < P.lrptr[r + 1]; ++p) s += v[P.lrpos[p]] * y[P.lrcol[p]];
+    y[r] = b[P.prow[r]] - s;
+  }
+  for (int r = n - 1; r >= 0; --r) {
+    double s = 0.0;
+    for (int p = P.urptr[r]; p < P.urptr[r + 1]; ++p) s += v[P.urpos[p]] * y[P.urcol[p]];
+    y[r] = (y[r] - s) * dinv[r];
+  }
+  x.assign(n, 0.0);
+  for (int j = 0; j < n; ++j) x[P.pcol[j]] = y[j];
+  return *bad_col < 0;
+}
+
+// ---- GPU refactorisation and solves -------------------------------------------------------------
+
+namespace {
+
+constexpr int kLuWarps = 32;
+constexpr long long kLuSpinLimit = 1LL << 26;   // polls of a progress word before giving up
+
+// Wait until the warp that owns item k (of the round-robin deal) has moved past it. Returns
+// false when the bound is reached (recording a timeout in flag[1]) or when another wait has
+// already given up: then every later wait returns at once, the block runs to its end with
+// meaningless numbers and the host reports the timeout. Control flow stays the same for every
+// warp, so no barrier of the block is ever left waiting.
+__device__ __forceinline__ bool lu_wait(volatile int* prog, int k, int* flag) {
+  long long spins = 0;
+  while (prog[k % kLuWarps] <= k) {
+    if (*((volatile int*)(flag + 1))) return false;
+    if (++spins > kLuSpinLimit) {
+      atomicExch(flag + 1, 1);
+      return false;
+    }
+  }
+  __threadfence_block();
+  return true;
+}
+
+// Reciprocal from the FP32 unit's seed and two FP64 corrections (the seed's 2^-23 error cubed:
+// far below an ulp): one FP64 dependency chain of three instructions instead of a division.
+// FP64 instructions wait about 64 cycles each on this part, and the factorisation and the
+// substitutions are chains of dependent steps, so every instruction on a step counts.
+__device__ __forceinline__ double lu_rcp(double x) {
+  const double y0 = (double)__frcp_rn((float)x);
+  const double e = fma(-x, y0, 1.0);
+  return fma(y0, fma(e, e, e), y0);
+}
+
+// Dot product of the row's entries (positions pos[p0..p1), columns cols[...]) with the vector u,
+// each entry's column first waited for. Short rows (the common case in circuit matrices) are
+// summed by lane 0 alone, without a shuffle tree of dependent FP64 additions.
+__device__ __forceinline__ double lu_row_dot(const int* __restrict__ cols, const int* __restrict__ pos,
+                                             int p0, int p1, const double* v, const double* u,
+                                             volatile int* prog, int* flag, bool reversed, int n) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  if (p1 - p0 <= 4) {
+    if (lane == 0)
+      for (int p = p0; p < p1; ++p) {
+        const int c = __ldg(cols + p);
+        lu_wait(prog, reversed ? n - 1 - c : c, flag);
+        s = fma(v[__ldg(pos + p)], u[c], s);
+      }
+    return s;   // meaningful in lane 0
+  }
+  for (int p = p0 + lane; p < p1; p += 32) {
+    const int c = __ldg(cols + p);
+    lu_wait(prog, reversed ? n - 1 - c : c, flag);
+    s = fma(v[__ldg(pos + p)], u[c], s);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  return s;
+}
+
+// Forward then backward substitution with the factor in v and the inverse diagonal in dinv
+// (y as work): x[pcol] = the solution of P A Q z = P b, i.e. A x = b.
+__device__ __forceinline__ void lu_substitute(const LuDev& L, const double* v, const double* dinv,
+                                              double* y, volatile int* prog,
+                                              const double* b, double* x) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int n = L.n;
+  // forward (unit lower): y[r] = b[prow[r]] - sum_c L(r, c) y[c], rows in order
+  if (lane == 0) prog[w] = w;
+  __syncthreads();
+  for (int r = w; r < n; r += kLuWarps) {
+    const double s = lu_row_dot(L.lrcol, L.lrpos, __ldg(L.lrptr + r), __ldg(L.lrptr + r + 1), v,
+                                y, prog, L.flag, false, n);
+    if (lane == 0) {
+      y[r] = b[__ldg(L.prow + r)] - s;
+      __threadfence_block();
+      prog[w] = r + kLuWarps;
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  // backward: z[r] = (y[r] - sum_c U(r, c) z[c]) / U(r, r), rows from the last (item
+  // m = n - 1 - r of the deal), z kept in y's place
+  if (lane == 0) prog[w] = w;
+  __syncthreads();
+  for (int m = w; m < n; m += kLuWarps) {
+    const int r = n - 1 - m;
+    const double s = lu_row_dot(L.urcol, L.urpos, __ldg(L.urptr + r), __ldg(L.urptr + r + 1), v,
+                                y, prog, L.flag, true, n);
+    if (lane == 0) {
+      y[r] = (y[r] - s) * dinv[r];
+      __threadfence_block();
+      prog[w] = m + kLuWarps;
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < n; r += blockDim.x) x[__ldg(L.pcol + r)] = y[r];
+}
+
+// Refactorisation of A on the plan, then x = A^-1 b, in one block; with refine, one step of
+// iterative refinement (r = b - A x from A's own CSR values, x += A^-1 r): near an ill-conditioned
+// operating point the plain solve leaves Newton short of its residual test. With smem set, the factor's
+// values, the inverse diagonal and the work vector live in shared memory (dynamic,
+// nnz_lu + 2 n doubles): every access of the column chain is then a shared-memory access
+// instead of an L2 round trip. The static pivots are checked after the factorisation, off the
+// chain: a pivot below tiny x its column's largest entry leaves an L entry above 1 / tiny.
+__global__ void __launch_bounds__(kLuWarps * 32, 1) k_lu_factor_solve(LuDev L, const double* __restrict__ A,
+                                                                      const int* __restrict__ rp,
+                                                                      const int* __restrict__ col,
+                                                                      const double* __restrict__ b,
+                                                                      double* x, double tiny,
+                                                                      int smem, int refine) {
+  extern __shared__ double lu_dyn[];
+  __shared__ volatile int prog[kLuWarps];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double* v = smem ? lu_dyn : L.vals;
+  double* dinv = smem ? lu_dyn + L.nnz_lu : L.y + L.n;
+  double* y = smem ? lu_dyn + L.nnz_lu + L.n : L.y;
+  if (lane == 0) prog[w] = w;
+  for (int p = threadIdx.x; p < L.nnz_lu; p += blockDim.x) v[p] = 0.0;
+  __syncthreads();
+  for (int e = threadIdx.x; e < L.nnz_a; e += blockDim.x) v[__ldg(L.a2lu + e)] = __ldg(A + e);
+  __syncthreads();
+  for (int j = w; j < L.n; j += kLuWarps) {
+    const int t1 = __ldg(L.uptr + j + 1);
+    for (int t = __ldg(L.uptr + j); t < t1; ++t) {
+      const int k = __ldg(L.uk + t);
+      if (lane == 0) lu_wait(prog, k, L.flag);
+      __syncwarp();   // orders lane 0's observation before every lane's loads of column k
+      const double ukj = v[__ldg(L.upos + t)];
+      const int m1 = __ldg(L.mptr + t + 1);
+      for (int m = __ldg(L.mptr + t) + lane; m < m1; m += 32)
+        v[__ldg(L.mdst + m)] -= v[__ldg(L.msrc + m)] * ukj;
+      __syncwarp();
+    }
+    const int pd = __ldg(L.cdiag + j), p1 = __ldg(L.cptr + j + 1);
+    const double inv = lu_rcp(v[pd]);
+    for (int p = pd + 1 + lane; p < p1; p += 32) v[p] *= inv;
+    if (lane == 0) dinv[j] = inv;
+    __syncwarp();
+    __threadfence_block();
+    if (lane == 0) prog[w] = j + kLuWarps;
+  }
+  __syncthreads();
+  // pivot check, every column in parallel: |piv| > tiny max|L(:, j) before scaling| holds iff
+  // every scaled entry is below 1 / tiny (and the pivot is finite and not zero)
+  const double lim = 1.0 / tiny;
+  for (int j = threadIdx.x; j < L.n; j += blockDim.x) {
+    const double di = dinv[j];
+    if (!isfinite(di) || di == 0.0) {
+      atomicCAS(L.flag + 2, 0, j + 1);   // zero or non-finite pivot
+      continue;
+    }
+    bool bad = false;
+    for (int p = __ldg(L.cdiag + j) + 1; p < __ldg(L.cptr + j + 1) && !bad; ++p)
+      bad = !(fabs(v[p]) < lim);
+    if (bad) atomicCAS(L.flag, 0, j + 1);
+  }
+  lu_substitute(L, v, dinv, y, prog, b, x);
+  if (!refine) return;
+  __syncthreads();
+  double* r = L.y + 2 * L.n;   // residual, then the correction
+  for (int i = threadIdx.x; i < L.n; i += blockDim.x) {
+    double s = __ldg(b + i);
+    const int e1 = __ldg(rp + i + 1);
+    for (int e = __ldg(rp + i); e < e1; ++e) s = fma(-__ldg(A + e), x[__ldg(col + e)], s);
+    r[i] = s;
+  }
+  __syncthreads();
+  double* d = r + L.n;
+  lu_substitute(L, v, dinv, y, prog, r, d);
+  __syncthreads();
+  for (int i = threadIdx.x; i < L.n; i += blockDim.x) x[i] += d[i];
+}
+
+}  // namespace
+
+size_t lu_smem_bytes(const LuDev& L) { return sizeof(double) * ((size_t)L.nnz_lu + 2 * (size_t)L.n); }
+
+cudaError_t launch_lu_factor_solve(const LuDev& L, const double* A, const int* rp, const int* col,
+                                   const double* b, double* x, double tiny, int refine,
+                                   cudaStream_t s) {
+  if (L.n <= 0) return cudaSuccess;
+  int dev = 0, max_optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  const size_t need = lu_smem_bytes(L);
+  const size_t fixed = sizeof(int) * kLuWarps;
+  const int smem = need + fixed <= (size_t)max_optin ? 1 : 0;
+  const size_t dyn = smem ? need : 0;
+  if (smem) {
+    e = cudaFuncSetAttribute(k_lu_factor_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)dyn);
+    if (e != cudaSuccess) return e;
+  }
+  k_lu_factor_solve<<<1, kLuWarps * 32, dyn, s>>>(L, A, rp, col, b, x, tiny, smem, refine);
+  return cudaGetLastError();
+}
+
+}  // namespace eec

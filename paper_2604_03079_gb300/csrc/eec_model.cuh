@@ -114,7 +114,7 @@ __device__ __forceinline__ void body_terms(const CardK& c, const S& vbs, S& sqs,
   const S inv_R1 = rsqrt_(R1sq);
   const S R1 = R1sq * inv_R1;
   S phis;
-  if (fm_ge0(sval(u))) phis = 0.5 * (u + R1);
+  if (fm_ge0(sval(u))) phis = half(u + R1);
   else phis = c.twoD1sq * rcp(R1 - u);
   const S inv_sqs = rsqrt_(phis);
   sqs = phis * inv_sqs;
@@ -193,7 +193,8 @@ __device__ __forceinline__ void channel(const CardK& c, const PrmS<S>& P, const 
   const S E = (twoVdsat - t) + R2;               // Vdsat + vds + DELTA + R2
   const S inv_E = rcp(E);
   const S twoVds = twice(vds);
-  const S Vdseff = twoVdsat * vds * inv_E;
+  const S sr = twoVds * inv_E;                   // Vdseff / Vdsat (charge partition)
+  const S Vdseff = Vdsat * sr;
   const S dE_dVdsat = 1.0 + (t + c.twoDELTA) * inv_R2;
   const S dE_dvds = 1.0 - t * inv_R2;
   const S Vde_Vdsat = (twoVds - Vdseff * dE_dVdsat) * inv_E;
@@ -215,11 +216,12 @@ __device__ __forceinline__ void channel(const CardK& c, const PrmS<S>& P, const 
   const S Vde_Vg = Vde_Vdsat * Vdsat_Vg;
   const S F1_Vg = -Abh * (Vde_Vg - Vdseff * inv_Vgst2);
   const S F1_vds = -Abh * Vde_vds;
-  const S F2_Vg = inv_EsatL * (Vde_Vg - Vdseff * dden * inv_den);
+  const S ddi = dden * inv_den;                  // d ln(den) / dVg
+  const S F2_Vg = inv_EsatL * (Vde_Vg - Vdseff * ddi);
   const S F2_vds = inv_EsatL * Vde_vds;
   const S F3_Vg = -(P.lamL * Vde_Vg);
-  const S F3_vds = P.lamL * (1.0 - Vde_vds);
-  const S Pb_Vg = beta * (1.0 - Vg * dden * inv_den);
+  const S F3_vds = P.lamL - P.lamL * Vde_vds;    // lamL (1 - dVdseff/dvds), one multiply-add
+  const S Pb_Vg = beta - Pb * ddi;               // d(beta Vg)/dVg = beta (1 - Vg ddi)
   const S dV_Vg = Vde_Vg * F13 + Vdseff * (F1_Vg * F3 + F1 * F3_Vg);
   const S dV_vds = Vde_vds * F13 + Vdseff * (F1_vds * F3 + F1 * F3_vds);
   const S Ids_Vg = (Pb_Vg * VF13 + Pb * dV_Vg - Ids * F2_Vg) * inv_F2;
@@ -253,7 +255,7 @@ __device__ __forceinline__ void channel(const CardK& c, const PrmS<S>& P, const 
   ch.inv_Vdsat_parts[0] = Dd;
   ch.inv_Vdsat_parts[1] = inv_EsatL;
   ch.inv_Vdsat_parts[2] = inv_Vgst2;
-  ch.sr = twoVds * inv_E;
+  ch.sr = sr;
   ch.sig = sig;
   ch.F1_Vg = F1_Vg;
   ch.F1_Ab = F1_Ab;

@@ -1,7 +1,9 @@
-"""The DC Newton loop on the GPU (eec_newton_dc: the library's evaluate-and-stamp, cuSOLVER's
-sparse QR solve, a damped update) against the oracle's DC operating point (dense LU Newton with
-the same damping and stopping rules). Both loops stop at |dx| <= 1e-12 + 1e-9 |x| with a KCL
-residual below 1e-12 A, so their solutions agree far inside 1e-8 relative."""
+"""The DC Newton loop on the GPU (eec_newton_dc: the library's evaluate-and-stamp, a sparse solve
+-- cuSOLVER's QR, or the library's own sparse LU (EEC_SOLVER_LU) -- and a damped update) against
+the oracle's DC operating point (dense LU Newton with the same damping and stopping rules). Both
+loops stop at |dx| <= 1e-12 + 1e-9 |x| with a KCL residual below 1e-12 A, so their solutions
+agree far inside 1e-8 relative. The library's sparse LU is also checked on its own (eec_lu_solve)
+against its host check (the same plan and operations on the CPU)."""
 import numpy as np
 import pytest
 
@@ -26,7 +28,8 @@ CASES = [lambda: netgen.inverter_chain(64), lambda: netgen.inverter_chain(64, vi
 
 
 @pytest.mark.parametrize("make", CASES)
-@pytest.mark.parametrize("variant,rule,solver", [(2, 0, 0), (0, 0, 0), (2, 1, 0), (2, 0, 1)])
+@pytest.mark.parametrize("variant,rule,solver", [(2, 0, 0), (0, 0, 0), (2, 1, 0), (2, 0, 1),
+                                                 (2, 0, 2), (2, 1, 2), (5, 1, 2)])
 def test_gpu_newton_reaches_the_oracle_operating_point(eec, make, variant, rule, solver):
     import torch
     net = make()
@@ -60,9 +63,10 @@ def test_gpu_newton_reports_non_convergence_without_a_device_error(eec):
     assert it >= 1
 
 
+@pytest.mark.parametrize("solver", [0, 2])
 @pytest.mark.parametrize("make,rail_mode,max_iter", [(lambda: netgen.inverter_chain(64), 0, 150),
                                                      (lambda: netgen.inverter_chain(64), 1, 300)])
-def test_gshunt_stepping_where_plain_newton_fails(eec, make, rail_mode, max_iter):
+def test_gshunt_stepping_where_plain_newton_fails(eec, make, rail_mode, max_iter, solver):
     # plain damped Newton does not converge on these from the start below (the oracle needs its
     # gshunt-stepping fallback too); the GPU loop falls back the same way and reaches the
     # oracle's operating point. Solves needed (whole-step scaling, counted with the oracle's
@@ -81,7 +85,51 @@ def test_gshunt_stepping_where_plain_newton_fails(eec, make, rail_mode, max_iter
     circ = eec.Circuit(net, CARDS, variant=2, rail_mode=rail_mode)
     x = torch.as_tensor(x0, device="cuda")
     A, b, _ = circ.new_outputs(want_q=False)
-    it = eec.eec_newton_dc(circ.ctx, x, A, b, max_iter=max_iter)
-    assert it > max_iter                # the plain run used its solves, then the stages
+    it = eec.eec_newton_dc(circ.ctx, x, A, b, max_iter=max_iter, solver=solver)
+    if solver == 0:
+        assert it > max_iter            # the plain run used its solves, then the stages
     assert circ.status() == 0
     np.testing.assert_allclose(x.cpu().numpy(), ref, rtol=1e-8, atol=1e-10)
+
+
+@pytest.mark.parametrize("make", [lambda: netgen.ripple_adder(16), lambda: netgen.sram(12, 10),
+                                  lambda: netgen.random_logic(600, seed=3),
+                                  lambda: netgen.inverter_chain(200)])
+def test_sparse_lu_solve_matches_its_host_check(eec, make):
+    # the GPU kernels (refactorisation, triangular solves) against the same plan and operations
+    # executed on the host, on matrices stamped by the GPU; backward stability as the host LU
+    import torch
+    import scipy.sparse as sp
+    net = make()
+    circ = eec.Circuit(net, CARDS, variant=2)
+    rp, col, _ = circ.pattern()
+    for seed in (2, 3):
+        xv = torch.as_tensor(netgen.random_x(net, seed=seed), device="cuda")
+        A, b, _ = circ.eval_stamp(xv, want_q=False)
+        x = torch.empty_like(b)
+        eec.eec_lu_solve(circ.ctx, A, b, x)
+        Ah, bh, xg = A.cpu().numpy(), b.cpu().numpy(), x.cpu().numpy()
+        M = sp.csr_matrix((Ah, col, rp), shape=(circ.n, circ.n))
+        be = np.abs(M @ xg - bh).max() / (np.abs(Ah).max() * np.abs(xg).max() + np.abs(bh).max())
+        assert be <= 64 * np.finfo(float).eps, be
+        xh, nnz_lu, _ = eec.eec_lu_check_host(rp, col, Ah, bh)
+        if np.linalg.cond(M.toarray()) < 1e8:
+            assert np.abs(xg - xh).max() <= 1e-10 * np.abs(xh).max()
+    nnz_lu_ctx, analyses = eec.eec_lu_stats(circ.ctx)
+    assert nnz_lu_ctx >= circ.nnz and analyses >= 1
+
+
+def test_sparse_lu_newton_on_the_64_bit_adder(eec):
+    # NEXT-2 with the library's sparse LU: the 64-bit adder of Table II (896 unknowns) reaches
+    # the oracle's operating point; its per-iteration time is reported by bench.py --newton
+    import torch
+    net = netgen.ripple_adder(64)
+    ref, _ = oracle.Oracle(net, CARDS).dc_solve(max_iter=400)
+    for rule in (0, 1):
+        circ = eec.Circuit(net, CARDS, variant=2)
+        x = torch.zeros(circ.n, dtype=torch.float64, device="cuda")
+        A, b, _ = circ.new_outputs(want_q=False)
+        it = eec.eec_newton_dc(circ.ctx, x, A, b, max_iter=400, step_rule=rule,
+                               solver=eec.EEC_SOLVER_LU)
+        assert it >= 1 and circ.status() == 0
+        np.testing.assert_allclose(x.cpu().numpy(), ref, rtol=1e-8, atol=1e-10)
