@@ -44,8 +44,13 @@ UNIT = "device evals+stamps/s"
 # traffic until they are counted again.
 KERNEL_SOURCES = ("eec_model.cuh", "eec_fastmath.cuh", "eec_tables.h", "eec_internal.h",
                   "eec_kernels.cu")
-COUNTED_SOURCES_SHA16 = None
-COUNTS = {}   # (workload, kernel) -> (FP64 flop per device, DRAM bytes per device)
+COUNTED_SOURCES_SHA16 = "10e5aafe4fa86581"
+COUNTS = {    # (workload, kernel) -> (FP64 flop per device, DRAM bytes per device)
+    ("logic1m", "eval_cost"): (261.02, 292.61),
+    ("batch", "eval_cost"): (240.78, 377.13),
+    ("sram", "eval_cost"): (271.20, 186.07),
+    ("logic1m", "pipe"): (264.80, 284.81),
+}
 # GB300: 152 SMs x 2 FP64 FMA per clock per SM x 2 flop x 2070 MHz maximum SM clock.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
@@ -66,8 +71,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["sram", "logic", "logic1m", "batch", "chain"],
-                    default="logic1m")
+    ap.add_argument("--workload", choices=["sram", "logic", "logic1m", "logic120k", "batch", "chain"],
+                    default="logic1m",
+                    help="logic120k: 120,000 gates (~430k FETs), a profiling case whose inputs "
+                         "still exceed L2")
     ap.add_argument("--variant", default="auto")
     ap.add_argument("--eval-order", choices=["auto", "cost", "layout"], default="auto",
                     help="evaluation launch order of the order-free schedules (auto: the "
@@ -102,6 +109,8 @@ def workload(name, world=1, rank=0):
     if name == "logic1m":
         return (netgen.random_logic(277_778, seed), None,
                 "random_logic_277778_gates (~1M MOSFETs)")
+    if name == "logic120k":
+        return netgen.random_logic(120_000, seed), None, "random_logic_120000_gates"
     return netgen.inverter_chain(64, seed), None, "inverter_chain_64"
 
 
@@ -621,15 +630,14 @@ def extras(eec, circ, net, x, xt, A, b, q, args, dev):
     eec.eec_set_variant(circ.ctx, v0)
     res["phases_ungraphed"] = phases
 
-    # HBM roofline of the stamp-only kernel (the segmented-reduction gather from the buffer):
-    # per contribution 8 B of buffer + 4 B of source index, per A/b entry 8 B written, 8 B of
-    # its linear part, 4 B of offset and 4 B of list index
+    # HBM roofline of the stamp-only kernel (the segmented-reduction gather from the buffer in
+    # entry order): per contribution its 8 B value, per A/b entry 8 B written, 8 B of its linear
+    # part and 4 B of run offset
     _, _, unk = circ.pattern()
     free = unk[net.dev_nodes] >= 0
     contrib = int((free[:, [0, 2, 3]].sum(axis=1) * (1 + free.sum(axis=1))).sum())
     entries = circ.nnz + circ.n
-    gbytes = 12 * contrib + 20 * entries   # value + index per contribution; linear part,
-                                            # 32-bit pointer and output per entry
+    gbytes = 8 * contrib + 20 * entries
     st_ms = phases["segreduce"]["stamp_ms"]
     hbm = hbm_peak_gbs()
     res["stamp_roofline"] = {

@@ -14,8 +14,8 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "_libeec.so")
-SOURCES = ["eec_capi.cpp", "eec_kernels.cu", "eec_bwd.cu", "eec_color.cu", "eec_newton.cu",
-           "eec_lu.cu"]
+SOURCES = ["eec_capi.cpp", "eec_kernels.cu", "eec_gather.cu", "eec_bwd.cu", "eec_color.cu",
+           "eec_newton.cu", "eec_lu.cu"]
 LIBS = ["-lcusolver", "-lcusparse"]   # the sparse solve of eec_newton_dc
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

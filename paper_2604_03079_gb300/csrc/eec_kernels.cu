@@ -9,9 +9,10 @@
 //               parallel region);
 //   MODE_ATOMIC uncoloured, FP64 atomicAdd (the lock-based stamping the paper avoids, in its
 //               GPU form);
-//   MODE_BUFFER evaluate into a per-device buffer ("loadomp"/"Color" buffer), then either a
-//               per-entry gather (segmented reduction, deterministic, no colours) or one store-add
-//               launch per colour.
+//   MODE_BUFFER evaluate into a per-device buffer ("loadomp"/"Color" buffer), then a stamp of
+//               the buffer in colour order;
+//   MODE_SORTED evaluate into a contribution buffer laid out in entry order, then the per-entry
+//               gather of eec_gather.cu (segmented reduction, deterministic, no colours).
 // The evaluation is FP64-pipe bound on GB300 (FP64 issues at about 1/64 of the FP32 rate), so
 // the kernels aim at a saturated FP64 pipe: one device per thread, few warps per SM suffice;
 // parameters are precomputed per device so that no division on W or L is repeated per call.
@@ -362,52 +363,6 @@ __global__ void k_params(DevTopo T, const double* __restrict__ Wo, const double*
   T.prm[P_ISATVTG * N + k] = P.IsatVtG;
 }
 
-// Segmented reduction: entry e of [A ; b] = linear part + its contributions (deterministic, no
-// colours needed). The evaluation has written every entry's contributions contiguously, in
-// original-device order, at cbuf[gat_ptr[e] .. gat_ptr[e+1]), so the gather streams cbuf: light
-// entries (< kHeavy contributions, nearly all) take one thread each, in entry order (the warp's
-// runs are adjacent, so its loads cover a contiguous stretch of cbuf), and sum in order; heavy
-// entries (diagonals of word and bit lines) are skipped there and take one warp each:
-// lane-strided partial sums, then a fixed butterfly reduction. Blocks [0, nbl) cover the
-// entries, the rest the heavy ones, in one launch.
-constexpr int kGatherBlock = 256;
-
-__global__ void __launch_bounds__(kGatherBlock) k_gather(DevTopo T, double* A, double* b, int nbl) {
-  const long long E = T.nnz + T.n;
-  if ((int)blockIdx.x < nbl) {
-    const long long e = (long long)blockIdx.x * kGatherBlock + threadIdx.x;
-    if (e >= E) return;
-    const int p0 = __ldg(T.gat_ptr + e), p1 = __ldg(T.gat_ptr + e + 1);
-    if (p1 - p0 >= kHeavy) return;   // a warp of the heavy blocks sums this one
-    double s = e < T.nnz ? __ldg(T.Alin + e) : __ldg(T.blin + (e - T.nnz));
-    // the first four contributions loaded together, then summed in the loop's order
-    const int cnt = p1 - p0;
-    double v[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) v[j] = j < cnt ? __ldcs(T.cbuf + p0 + j) : 0.0;
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-      if (j < cnt) s += v[j];
-    for (int p = p0 + 4; p < p1; ++p) s += __ldcs(T.cbuf + p);
-    if (e < T.nnz) A[e] = s;
-    else b[e - T.nnz] = s;
-    return;
-  }
-  const int w = (blockIdx.x - nbl) * (kGatherBlock / 32) + (threadIdx.x >> 5);
-  if (w >= T.n_heavy) return;   // whole warp leaves together
-  const int lane = threadIdx.x & 31;
-  const long long e = __ldg(T.gat_heavy + w);
-  const int p0 = __ldg(T.gat_ptr + e), p1 = __ldg(T.gat_ptr + e + 1);
-  double s = 0.0;
-  for (int p = p0 + lane; p < p1; p += 32) s += __ldcs(T.cbuf + p);
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-  if (lane == 0) {
-    if (e < T.nnz) A[e] = __ldg(T.Alin + e) + s;
-    else b[e - T.nnz] = __ldg(T.blin + (e - T.nnz)) + s;
-  }
-}
-
 // One colour's stamp from the buffer (positions begin..end-1 share no row).
 // Add device k's buffered contributions to A and b. Callers stamp one colour at a time, so no
 // other thread adds to the same entries meanwhile; the additions are fire-and-forget atomics
@@ -716,16 +671,16 @@ struct PipeDC {
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
       const int row = idx[term[r]];
+      si[(kNSlot + r) * kPipeBlock + tid] = row;
+      if (row < 0) continue;   // rows of held terminals are not stamped: nothing to form
       double s = -o.I[term[r]];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         sv[(4 * r + u) * kPipeBlock + tid] = o.G[r][u];
-        si[(4 * r + u) * kPipeBlock + tid] =
-            (row >= 0 && idx[u] >= 0) ? __ldg(T.slot + (4 * r + u) * N + k) : -1;
+        si[(4 * r + u) * kPipeBlock + tid] = idx[u] >= 0 ? __ldg(T.slot + (4 * r + u) * N + k) : -1;
         if (idx[u] >= 0) s = fma(o.G[r][u], V[u], s);
       }
       sv[(kNSlot + r) * kPipeBlock + tid] = s;
-      si[(kNSlot + r) * kPipeBlock + tid] = row;
     }
     if (WANT_Q) {
       const int od = __ldg(T.orig + k);
@@ -787,6 +742,8 @@ struct PipeTran {
                         (ta.iprev ? ta.beta * __ldg(ta.iprev + at) : 0.0);
       ta.q[at] = o.Q[t];
       if (ta.icap) ta.icap[at] = ic;
+      si[(16 + t) * kPipeBlock + tid] = idx[t];
+      if (idx[t] < 0) continue;   // rows of held terminals are not stamped
       const int r = t == 0 ? 0 : (t == 2 ? 1 : 2);   // row of G (gate row of G is zero)
       double s = -(t == 1 ? 0.0 : o.I[t]) - ic;
 #pragma unroll
@@ -794,13 +751,11 @@ struct PipeTran {
         const double v = fma(ta.alpha, o.C[t][u], t == 1 ? 0.0 : o.G[r][u]);
         sv[(4 * t + u) * kPipeBlock + tid] = v;
         si[(4 * t + u) * kPipeBlock + tid] =
-            (idx[t] >= 0 && idx[u] >= 0)
-                ? (t == 1 ? __ldg(T.slot_g + u * N + k) : __ldg(T.slot + (4 * r + u) * N + k))
-                : -1;
+            idx[u] >= 0 ? (t == 1 ? __ldg(T.slot_g + u * N + k) : __ldg(T.slot + (4 * r + u) * N + k))
+                        : -1;
         if (idx[u] >= 0) s = fma(v, V[u], s);
       }
       sv[(16 + t) * kPipeBlock + tid] = s;
-      si[(16 + t) * kPipeBlock + tid] = idx[t];
     }
   }
 
@@ -1042,14 +997,6 @@ cudaError_t launch_init_lin(const DevTopo& T, double* A, double* b, cudaStream_t
   long long g = (total + 255) / 256;
   if (g > 152LL * 16) g = 152LL * 16;   // grid-stride beyond 16 blocks per SM
   k_init_lin<<<(int)g, 256, 0, s>>>(T.Alin, T.blin, A, b, T.nnz, T.n);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_gather(const DevTopo& T, double* A, double* b, cudaStream_t s) {
-  const int nbl = (int)((T.nnz + T.n + kGatherBlock - 1) / kGatherBlock);
-  const int nbh = (T.n_heavy + kGatherBlock / 32 - 1) / (kGatherBlock / 32);
-  if (nbl + nbh == 0) return cudaSuccess;
-  k_gather<<<nbl + nbh, kGatherBlock, 0, s>>>(T, A, b, nbl);
   return cudaGetLastError();
 }
 
