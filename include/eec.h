@@ -263,7 +263,13 @@ EEC_API int eec_eval_stamp_host(eec_ctx* ctx, const double* x_host, double* A_ho
  * fails (a singular matrix, a non-finite step), the loop restarts from the starting point with
  * gshunt stepping: a shunt conductance g from every node
  * to ground, g = 1e-3 S, converged, then g / 10 from that solution, down to the netlist's
- * gshunt, then the circuit itself (each stage with max_iter solves).
+ * gshunt, then the circuit itself (each stage with max_iter solves). When that fails too, a
+ * relaxation start: from the starting point, nonlinear Jacobi sweeps (every node moves to the
+ * zero of its own KCL residual with the other voltages held, the move clipped to 5 vstep; up to
+ * min(4 n + 1024, 65536) sweeps, until no node moved more than 1 uV in 32 sweeps), then Newton
+ * from the relaxed point, then gshunt stepping from there. A chain of gates settles one stage
+ * per sweep; from a poor start Newton's exact step on a long chain grows like the stage gain to
+ * the power of its length and overflows. eec_newton_info reports which path converged.
  *  x_dev       [n] in: starting point (free-node voltages), out: the last iterate.
  *  A_dev, b_dev  [nnz], [n] workspace; out: the stamp at the returned x.
  *  iters_out   (nullable) solves performed, over all stages.
@@ -277,6 +283,14 @@ EEC_API int eec_newton_dc(eec_ctx* ctx, double* x_dev, double* A_values_dev, dou
                           int32_t max_iter, double vstep, int32_t step_rule, int32_t solver,
                           double tol_abs, double tol_rel, double tol_f, int32_t* iters_out,
                           void* cuda_stream);
+
+/*
+ * The last eec_newton_dc call on this context: info[0] = solves (as iters_out), info[1] = gshunt
+ * stepping stages run, info[2] = relaxation sweeps, info[3] = the path that ended the call:
+ * 0 plain Newton, 1 gshunt stepping, 2 relaxation start then Newton, 3 relaxation start then
+ * gshunt stepping. info [4] host, out.
+ */
+EEC_API int eec_newton_info(const eec_ctx* ctx, int32_t* info);
 
 /*
  * x = A^-1 b on the context's pattern with the library's sparse LU (the solver EEC_SOLVER_LU of

@@ -98,6 +98,7 @@ _SIG = {
     "eec_batch_capture_graph": (ctypes.c_int, [_P, _P]),
     "eec_fp64_peak": (ctypes.c_int, [_I32, _I32, ctypes.POINTER(_F64)]),
     "eec_lu_stats": (ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I32)]),
+    "eec_newton_info": (ctypes.c_int, [_P, ctypes.POINTER(_I32)]),
     "eec_lu_solve": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "eec_lu_check_host": (ctypes.c_int, [_I32, _P, _P, _P, _P, _P, ctypes.POINTER(_I64),
                                          ctypes.POINTER(_I32)]),
@@ -401,6 +402,19 @@ def eec_lu_stats(ctx):
     return int(nnz.value), int(an.value)
 
 
+NEWTON_PATHS = ("plain Newton", "gshunt stepping", "relaxation start then Newton",
+                "relaxation start then gshunt stepping")
+
+
+def eec_newton_info(ctx):
+    """The last eec_newton_dc call: -> dict(solves, stages (gshunt stepping), sweeps
+    (relaxation), path (index into NEWTON_PATHS))."""
+    info = (_I32 * 4)()
+    _check(ctx, _load().eec_newton_info(ctx, info))
+    return {"solves": int(info[0]), "stages": int(info[1]), "sweeps": int(info[2]),
+            "path": int(info[3])}
+
+
 def eec_lu_check_host(row_ptr, col, a, b):
     """Host check of the sparse LU (no GPU): -> (x solving A x = b, entries of L and U, first
     column whose refactorised pivot degraded or -1)."""
@@ -426,7 +440,8 @@ def eec_lu_check_host(row_ptr, col, a, b):
 def eec_newton_dc(ctx, x, A, b, max_iter=200, vstep=0.2, step_rule=0, solver=0, tol_abs=1e-12,
                   tol_rel=1e-9, tol_f=1e-12, stream=None) -> int:
     """DC Newton on the GPU from x (updated in place), with gshunt stepping when it does not
-    converge; returns the number of solves.
+    converge and then a relaxation start (eec_newton_info tells which path converged); returns
+    the number of solves.
     step_rule 0: the whole step scaled to vstep; 1: every node's move clipped to vstep.
     solver 0: batched sparse QR, analysis reused; 1: sparse QR after an AMD ordering;
     2 (EEC_SOLVER_LU): the library's sparse LU, host analysis once, GPU refactorisation."""

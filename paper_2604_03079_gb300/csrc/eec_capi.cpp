@@ -117,6 +117,8 @@ struct eec_ctx {
   double* d_y = nullptr;
   double* d_x0 = nullptr;        // starting point, kept for the gshunt-stepping restart
   int* d_diag = nullptr;         // CSR position of the diagonal of every node row
+  int* d_rail_unk = nullptr;     // unknown of every rail node (rails as MNA unknowns)
+  int newton_info[4] = {0, 0, 0, 0};   // last eec_newton_dc: solves, gshunt stages, sweeps, path
   void* sp_buf = nullptr;
   unsigned long long* d_nstats = nullptr;
   // eec_newton_dc solver 2 (sparse LU): the column order (pattern only), the plan of the last
@@ -191,6 +193,7 @@ void free_topology(eec_ctx* c) {
   c->d_y = nullptr;
   c->d_x0 = nullptr;
   c->d_diag = nullptr;
+  c->d_rail_unk = nullptr;
   c->sp_buf = nullptr;
   c->d_nstats = nullptr;
   if (c->lu_ibuf) cudaFree(c->lu_ibuf);
@@ -1450,10 +1453,13 @@ int newton_common(eec_ctx* c) {
   for (int i = 0; i < n_node; ++i)
     diag[i] = (int)(std::lower_bound(c->col.begin() + c->row_ptr[i],
                                      c->col.begin() + c->row_ptr[i + 1], i) - c->col.begin());
+  std::vector<int> rail_unk(c->rail.size());
+  for (size_t r = 0; r < c->rail.size(); ++r) rail_unk[r] = c->unk[c->rail[r]];
   int rc;
   if ((rc = dupload(c, &c->d_rp, c->row_ptr)) || (rc = dupload(c, &c->d_col, c->col)) ||
       (rc = dalloc(c, &c->d_y, c->n)) || (rc = dalloc(c, &c->d_x0, c->n)) ||
-      (rc = dupload(c, &c->d_diag, diag)) || (rc = dalloc(c, &c->d_nstats, 4)))
+      (rc = dupload(c, &c->d_diag, diag)) || (rc = dalloc(c, &c->d_nstats, 4)) ||
+      (!rail_unk.empty() && (rc = dupload(c, &c->d_rail_unk, rail_unk))))
     return rc;
   return EEC_OK;
 }
@@ -1658,6 +1664,37 @@ int newton_run(eec_ctx* c, double* x, double* A, double* b, int max_iter, double
   return EEC_ENOCONV;
 }
 
+// Relaxation start: nonlinear Jacobi sweeps (every node to the zero of its own KCL residual,
+// the others held; moves clipped to vmax) from x until no node moved more than tol within 32
+// sweeps, or max_sweeps. A chain of n stages settles in about n sweeps (one stage per sweep),
+// where Newton from the same start needs the chain's gain to the n-th power in its linear solve.
+// Returns EEC_OK (settled or not: Newton takes over either way) or an error; *sweeps counts.
+int relax_run(eec_ctx* c, double* x, double* A, double* b, double vmax, int max_sweeps, double tol,
+              int* sweeps, cudaStream_t s) {
+  const int v = effective_variant(c), n = c->n;
+  const int n_rail = (int)c->rail.size(), n_node = n - n_rail;
+  unsigned long long hs[4];
+  int rc;
+  *sweeps = 0;
+  for (int k = 0; k < max_sweeps; ++k) {
+    if ((k & 31) == 0) CUDA_TRY(c, cudaMemsetAsync(c->d_nstats, 0, 4 * sizeof(unsigned long long), s));
+    if ((rc = eval_with(c, v, x, A, b, nullptr, s))) return rc;
+    CUDA_TRY(c, launch_relax_step(c->d_rp, c->d_col, A, x, b, c->d_diag, n_node, n, vmax,
+                                  c->d_rail_unk, n_rail, c->d_y, c->d_nstats, s));
+    c->n_kernels += 1 + (n_rail > 0);
+    CUDA_TRY(c, cudaMemcpyAsync(x, c->d_y, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    *sweeps = k + 1;
+    if ((k & 31) == 31 || k == max_sweeps - 1) {
+      CUDA_TRY(c, cudaMemcpyAsync(hs, c->d_nstats, sizeof hs, cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(c, cudaStreamSynchronize(s));
+      const double m = bits_to_double(hs[1]);
+      if (!std::isfinite(m)) return fail(c, EEC_ENUMERIC, "non-finite relaxation sweep");
+      if (m <= tol) return EEC_OK;
+    }
+  }
+  return EEC_OK;
+}
+
 int eec_newton_dc(eec_ctx* c, double* x, double* A, double* b, int32_t max_iter, double vstep,
                   int32_t step_rule, int32_t solver, double tol_abs, double tol_rel,
                   double tol_f, int32_t* iters_out, void* stream) {
@@ -1671,6 +1708,7 @@ int eec_newton_dc(eec_ctx* c, double* x, double* A, double* b, int32_t max_iter,
     return fail(c, EEC_EINVAL, "bad eec_newton_dc arguments");
   if (c->nnz > 0x7fffffffLL) return fail(c, EEC_EINVAL, "pattern too large for the sparse solver");
   if (iters_out) *iters_out = 0;
+  for (int k = 0; k < 4; ++k) c->newton_info[k] = 0;
   if (c->n == 0) return EEC_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (solver == EEC_SOLVER_LU) {
@@ -1681,32 +1719,62 @@ int eec_newton_dc(eec_ctx* c, double* x, double* A, double* b, int32_t max_iter,
       return fail(c, EEC_ECUDA, "cusolverSpSetStream failed");
   }
   CUDA_TRY(c, cudaMemcpyAsync(c->d_x0, x, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, s));
-  int its = 0, total = 0;
+  int its = 0, total = 0, stages = 0, sweeps = 0, path = 0;
+  // gshunt stepping (the oracle's fallback, taken as there both when plain Newton runs out of
+  // iterations and when a step fails: a singular matrix or a non-finite step): from x, a shunt
+  // of g = 1e-3 S on every node, converge, divide g by 10 and continue from that solution down
+  // to the circuit's own gshunt, then solve the circuit itself from there
+  auto stepping = [&]() {
+    int r = EEC_OK;
+    for (double g = 1e-3; r == EEC_OK && g > c->gshunt * 1.0000001; g *= 0.1) {
+      r = newton_run(c, x, A, b, max_iter, vstep, step_rule, solver, tol_abs, tol_rel, tol_f,
+                     g - c->gshunt, &its, s);
+      total += its;
+      ++stages;
+    }
+    if (r == EEC_OK) {
+      r = newton_run(c, x, A, b, max_iter, vstep, step_rule, solver, tol_abs, tol_rel, tol_f,
+                     0.0, &its, s);
+      total += its;
+    }
+    return r;
+  };
+  auto failed = [](int r) { return r == EEC_ENOCONV || r == EEC_ENUMERIC; };
   rc = newton_run(c, x, A, b, max_iter, vstep, step_rule, solver, tol_abs, tol_rel, tol_f, 0.0,
                   &its, s);
   total += its;
-  if (rc == EEC_ENOCONV || rc == EEC_ENUMERIC) {
-    // gshunt stepping (the oracle's fallback, taken as there both when plain Newton runs out of
-    // iterations and when a step fails: a singular matrix or a non-finite step): restart from
-    // the starting point with a shunt of
-    // g = 1e-3 S on every node, converge, divide g by 10 and continue from that solution down
-    // to the circuit's own gshunt, then solve the circuit itself from there
+  if (failed(rc)) {
+    path = 1;
     CUDA_TRY(c, cudaMemcpyAsync(x, c->d_x0, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, s));
-    rc = EEC_OK;
-    for (double g = 1e-3; rc == EEC_OK && g > c->gshunt * 1.0000001; g *= 0.1) {
-      rc = newton_run(c, x, A, b, max_iter, vstep, step_rule, solver, tol_abs, tol_rel, tol_f,
-                      g - c->gshunt, &its, s);
-      total += its;
-    }
-    if (rc == EEC_OK) {
-      rc = newton_run(c, x, A, b, max_iter, vstep, step_rule, solver, tol_abs, tol_rel, tol_f,
-                      0.0, &its, s);
-      total += its;
+    rc = stepping();
+  }
+  if (failed(rc)) {
+    // relaxation start (beyond the oracle's fallbacks): from the starting point, Jacobi sweeps
+    // until the nodes settle, then Newton, then gshunt stepping from the relaxed point. Long
+    // chains of gates need it: from a poor start the exact Newton step grows like the stage
+    // gain to the power of the chain length and leaves the range of doubles.
+    path = 2;
+    CUDA_TRY(c, cudaMemcpyAsync(x, c->d_x0, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, s));
+    const int max_sweeps = (int)std::min<long long>(4LL * c->n + 1024, 1 << 16);
+    if ((rc = relax_run(c, x, A, b, 5.0 * vstep, max_sweeps, 1e-6, &sweeps, s))) return rc;
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_x0, x, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, s));
+    rc = newton_run(c, x, A, b, max_iter, vstep, step_rule, solver, tol_abs, tol_rel, tol_f, 0.0,
+                    &its, s);
+    total += its;
+    if (failed(rc)) {
+      path = 3;
+      CUDA_TRY(c, cudaMemcpyAsync(x, c->d_x0, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, s));
+      rc = stepping();
     }
   }
+  c->newton_info[0] = total;
+  c->newton_info[1] = stages;
+  c->newton_info[2] = sweeps;
+  c->newton_info[3] = path;
   if (iters_out) *iters_out = total;
   if (rc == EEC_ENOCONV)
-    return fail(c, EEC_ENOCONV, "no convergence within max_iter iterations (gshunt stepping included)");
+    return fail(c, EEC_ENOCONV, "no convergence within max_iter iterations (gshunt stepping "
+                                "and relaxation start included)");
   return rc;
 }
 
@@ -2010,6 +2078,12 @@ int eec_lu_stats(const eec_ctx* c, int64_t* nnz_lu, int32_t* analyses) {
   if (!c) return EEC_EINVAL;
   if (nnz_lu) *nnz_lu = c->lu_ready ? c->lu.cptr[c->lu.n] : 0;
   if (analyses) *analyses = c->lu_analyses;
+  return EEC_OK;
+}
+
+int eec_newton_info(const eec_ctx* c, int32_t* info) {
+  if (!c || !info) return EEC_EINVAL;
+  for (int k = 0; k < 4; ++k) info[k] = c->newton_info[k];
   return EEC_OK;
 }
 

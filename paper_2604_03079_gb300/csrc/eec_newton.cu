@@ -81,6 +81,45 @@ __global__ void __launch_bounds__(kNewtonBlock) k_add_diag(double* __restrict__ 
   if (i < n) A[diag[i]] += g;
 }
 
+// One sweep of nonlinear Jacobi relaxation (the relaxation start of eec_newton_dc): every node
+// row i moves its own voltage to the zero of its linearised KCL residual with all other
+// voltages held, y_i = x_i - F_i(x) / A_ii, the move clipped to [-vmax, vmax]; a row whose
+// diagonal is not positive moves nothing. The other rows (rail source currents under modified
+// nodal analysis) are copied. Reads x, writes y: every row sees the same iterate, so the sweep
+// does not depend on the order of the threads. stats[1] = max |move|.
+__global__ void __launch_bounds__(kNewtonBlock) k_relax_step(const int* __restrict__ rp,
+                                                             const int* __restrict__ col,
+                                                             const double* __restrict__ A,
+                                                             const double* __restrict__ x,
+                                                             const double* __restrict__ b,
+                                                             const int* __restrict__ diag,
+                                                             int n_node, int n, double vmax,
+                                                             double* __restrict__ y,
+                                                             unsigned long long* stats) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double dx = 0.0;
+  if (i < n) {
+    if (i < n_node) {
+      double r = -b[i];
+      for (int p = rp[i]; p < rp[i + 1]; ++p) r = fma(A[p], x[col[p]], r);
+      const double d = A[diag[i]];
+      dx = d > 0.0 ? -r / d : 0.0;
+      // comparisons, not fmin/fmax: a NaN move stays NaN and the host sees it
+      dx = dx > vmax ? vmax : (dx < -vmax ? -vmax : dx);
+    }
+    y[i] = x[i] + dx;
+  }
+  max_abs_into(stats + 1, dx);
+}
+
+// Rails as MNA unknowns: rail node rail_unk[r] takes its source's voltage, the right-hand side
+// of its source equation (row n_node + r).
+__global__ void k_rail_fix(double* __restrict__ y, const double* __restrict__ b,
+                           const int* __restrict__ rail_unk, int n_node, int n_rail) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n_rail) y[rail_unk[r]] = b[n_node + r];
+}
+
 int blocks_for(int n) { return n > 0 ? (n + kNewtonBlock - 1) / kNewtonBlock : 1; }
 
 }  // namespace
@@ -96,6 +135,16 @@ cudaError_t launch_residual_norm(const int* rp, const int* col, const double* A,
                                  const double* b, int n, unsigned long long* stats,
                                  cudaStream_t s) {
   k_residual_norm<<<blocks_for(n), kNewtonBlock, 0, s>>>(rp, col, A, x, b, n, stats);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_relax_step(const int* rp, const int* col, const double* A, const double* x,
+                              const double* b, const int* diag, int n_node, int n, double vmax,
+                              const int* rail_unk, int n_rail, double* y,
+                              unsigned long long* stats, cudaStream_t s) {
+  k_relax_step<<<blocks_for(n), kNewtonBlock, 0, s>>>(rp, col, A, x, b, diag, n_node, n, vmax, y,
+                                                      stats);
+  if (n_rail > 0) k_rail_fix<<<blocks_for(n_rail), kNewtonBlock, 0, s>>>(y, b, rail_unk, n_node, n_rail);
   return cudaGetLastError();
 }
 

@@ -50,8 +50,10 @@ def test_gpu_newton_reaches_the_oracle_operating_point(eec, make, variant, rule,
 
 
 def test_gpu_newton_reports_non_convergence_without_a_device_error(eec):
+    # one solve per stage: plain Newton, gshunt stepping, and Newton after the relaxation start
+    # all stop short (the ring's Jacobi sweeps oscillate instead of settling)
     import torch
-    net = netgen.inverter_chain(64, vin=0.45)
+    net = netgen.ring_oscillator(11)
     circ = eec.Circuit(net, CARDS)
     x = torch.zeros(circ.n, dtype=torch.float64, device="cuda")
     A, b, _ = circ.new_outputs(want_q=False)
@@ -59,6 +61,7 @@ def test_gpu_newton_reports_non_convergence_without_a_device_error(eec):
         eec.eec_newton_dc(circ.ctx, x, A, b, max_iter=1)
     assert e.value.code == eec.EEC_ENOCONV
     assert circ.status() == 0
+    assert eec.eec_newton_info(circ.ctx)["path"] == 3
     it = eec.eec_newton_dc(circ.ctx, x, A, b)    # continues from the last iterate
     assert it >= 1
 
@@ -133,3 +136,31 @@ def test_sparse_lu_newton_on_the_64_bit_adder(eec):
                                solver=eec.EEC_SOLVER_LU)
         assert it >= 1 and circ.status() == 0
         np.testing.assert_allclose(x.cpu().numpy(), ref, rtol=1e-8, atol=1e-10)
+
+
+@pytest.mark.parametrize("n_stages,rail_mode", [(1024, 0), (4096, 0), (1024, 1)])
+def test_long_chain_converges_through_the_relaxation_start(eec, n_stages, rail_mode):
+    # From x = 0 the exact Newton step of a long inverter chain grows like the stage gain to the
+    # power of the chain length (inf in doubles beyond a few hundred stages); plain Newton and
+    # gshunt stepping both fail, and the relaxation start (Jacobi sweeps, one stage settled per
+    # sweep) hands Newton a start from which it converges. The oracle's own DC solve fails on
+    # these chains (its dense LU meets a zero pivot at 4096 stages), so its model checks the
+    # result instead: the oracle's KCL residual at the returned x is at the level of rounding,
+    # and the chain's unique operating point alternates between the rails (input at 0 V).
+    import torch
+    net = netgen.inverter_chain(n_stages)
+    o = oracle.Oracle(net, CARDS, rail_mode=rail_mode)
+    x0 = np.zeros(o.n)
+    circ = eec.Circuit(net, CARDS, variant=2, rail_mode=rail_mode)
+    x = torch.as_tensor(x0, device="cuda")
+    A, b, _ = circ.new_outputs(want_q=False)
+    it = eec.eec_newton_dc(circ.ctx, x, A, b, max_iter=100, step_rule=1, solver=eec.EEC_SOLVER_LU)
+    info = eec.eec_newton_info(circ.ctx)
+    assert circ.status() == 0 and it == info["solves"] >= 1
+    if rail_mode == 0:
+        assert info["path"] >= 2 and n_stages <= info["sweeps"] <= 4 * o.n + 1024
+    xh = x.cpu().numpy()
+    assert np.abs(o.kcl_residual(xh)).max() <= 1e-11
+    _, _, unk = circ.pattern()
+    v = xh[unk[3:3 + n_stages]]            # stage outputs: nodes 3, 4, ... (0 ground, 1 vdd, 2 in)
+    assert np.abs(v - (np.arange(n_stages) % 2 == 0)).max() < 0.05
