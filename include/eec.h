@@ -253,8 +253,8 @@ EEC_API int eec_eval_stamp_host(eec_ctx* ctx, const double* x_host, double* A_ho
  * L and U; every iteration then refactors the numbers on that pattern and solves on the GPU
  * (one single-block kernel, with one step of iterative refinement once the steps are below
  * 1 mV), and analyses again on the host if a pivot falls below 1e-4 of the
- * largest entry of its column (eec_lu_stats counts the
- * analyses) — then
+ * largest entry of its column (1e-10 for the unrefined solves of steps above 1 mV;
+ * eec_lu_stats counts the analyses) — then
  * a damped step: step_rule 0 scales the whole step, x += s (y - x) with s = min(1, vstep /
  * max|y - x|); step_rule 1 clips every node's move to [-vstep, vstep] on its own (long chains of
  * gates converge in far fewer iterations).

@@ -1530,15 +1530,20 @@ int lu_prepare(eec_ctx* c, const double* A, cudaStream_t s) {
 
 // Solver 2: factor A on the fixed plan and solve A y = b; analyses again
 // (once) when a pivot has fallen below kLuTiny of the largest entry of its column's L part --
-// the static pivots no longer make a stable factorisation of this matrix.
+// the static pivots no longer make a stable factorisation of this matrix. The unrefined solves
+// (Newton steps above 1 mV, where the step is clipped and only its direction counts) accept
+// growth up to 1 / kLuTinyFar: a host analysis of a large matrix costs far more than a solve,
+// and the bias moves the pivots' sizes on almost every early iteration.
 constexpr double kLuTiny = 1e-4;   // a fresh analysis keeps scaled L entries <= 1e3 (kLuDiagPref)
+constexpr double kLuTinyFar = 1e-10;
 int lu_factor_solve(eec_ctx* c, const double* A, const double* b, double* y, int refine,
                     cudaStream_t s) {
   int rc;
   if (!c->lu_ready && (rc = lu_prepare(c, A, s))) return rc;
   for (int attempt = 0; attempt < 2; ++attempt) {
     CUDA_TRY(c, cudaMemsetAsync(c->lud.flag, 0, 3 * sizeof(int), s));
-    CUDA_TRY(c, launch_lu_factor_solve(c->lud, A, c->d_rp, c->d_col, b, y, kLuTiny, refine, s));
+    CUDA_TRY(c, launch_lu_factor_solve(c->lud, A, c->d_rp, c->d_col, b, y,
+                                       refine ? kLuTiny : kLuTinyFar, refine, s));
     c->n_kernels += 1;
     int fl[3] = {0, 0, 0};
     CUDA_TRY(c, cudaMemcpyAsync(fl, c->lud.flag, sizeof fl, cudaMemcpyDeviceToHost, s));
@@ -1665,31 +1670,40 @@ int newton_run(eec_ctx* c, double* x, double* A, double* b, int max_iter, double
 }
 
 // Relaxation start: nonlinear Jacobi sweeps (every node to the zero of its own KCL residual,
-// the others held; moves clipped to vmax) from x until no node moved more than tol within 32
-// sweeps, or max_sweeps. A chain of n stages settles in about n sweeps (one stage per sweep),
-// where Newton from the same start needs the chain's gain to the n-th power in its linear solve.
+// the others held; moves clipped to vmax) from x, in windows of 32 sweeps, until no node moved
+// more than tol within a window, or the number of nodes still moving (by more than 1 mV, in a
+// window's last sweep) has not fallen over the last four windows, or max_sweeps. A chain of n
+// stages settles one stage per sweep (the nodes past the settled front toggle until it reaches
+// them, so their count falls by one per sweep), where Newton from the same start needs the
+// chain's gain to the n-th power in its linear solve; cross-coupled pairs (latches, memory
+// cells) toggle together forever under Jacobi sweeps, which the count detects.
 // Returns EEC_OK (settled or not: Newton takes over either way) or an error; *sweeps counts.
 int relax_run(eec_ctx* c, double* x, double* A, double* b, double vmax, int max_sweeps, double tol,
               int* sweeps, cudaStream_t s) {
   const int v = effective_variant(c), n = c->n;
   const int n_rail = (int)c->rail.size(), n_node = n - n_rail;
   unsigned long long hs[4];
+  std::vector<unsigned long long> moving;   // per window
   int rc;
   *sweeps = 0;
   for (int k = 0; k < max_sweeps; ++k) {
+    const bool last = (k & 31) == 31 || k == max_sweeps - 1;
     if ((k & 31) == 0) CUDA_TRY(c, cudaMemsetAsync(c->d_nstats, 0, 4 * sizeof(unsigned long long), s));
     if ((rc = eval_with(c, v, x, A, b, nullptr, s))) return rc;
     CUDA_TRY(c, launch_relax_step(c->d_rp, c->d_col, A, x, b, c->d_diag, n_node, n, vmax,
-                                  c->d_rail_unk, n_rail, c->d_y, c->d_nstats, s));
+                                  c->d_rail_unk, n_rail, c->d_y, c->d_nstats, last ? 1 : 0, s));
     c->n_kernels += 1 + (n_rail > 0);
     CUDA_TRY(c, cudaMemcpyAsync(x, c->d_y, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     *sweeps = k + 1;
-    if ((k & 31) == 31 || k == max_sweeps - 1) {
+    if (last) {
       CUDA_TRY(c, cudaMemcpyAsync(hs, c->d_nstats, sizeof hs, cudaMemcpyDeviceToHost, s));
       CUDA_TRY(c, cudaStreamSynchronize(s));
       const double m = bits_to_double(hs[1]);
       if (!std::isfinite(m)) return fail(c, EEC_ENUMERIC, "non-finite relaxation sweep");
       if (m <= tol) return EEC_OK;
+      moving.push_back(hs[0]);
+      const size_t w = moving.size();
+      if (w > 4 && moving[w - 1] >= moving[w - 5]) return EEC_OK;   // no progress: toggling
     }
   }
   return EEC_OK;

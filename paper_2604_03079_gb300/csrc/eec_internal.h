@@ -149,11 +149,12 @@ cudaError_t launch_residual_norm(const int* rp, const int* col, const double* A,
                                  const double* b, int n, unsigned long long* stats,
                                  cudaStream_t s);
 // One nonlinear Jacobi sweep from x into y (node rows; rail nodes set to their source voltage
-// when rails are MNA unknowns); stats[1] = max |move|.
+// when rails are MNA unknowns); stats[1] = max |move|, stats[0] += rows moved more than 1 mV
+// (when count is set).
 cudaError_t launch_relax_step(const int* rp, const int* col, const double* A, const double* x,
                               const double* b, const int* diag, int n_node, int n, double vmax,
                               const int* rail_unk, int n_rail, double* y,
-                              unsigned long long* stats, cudaStream_t s);
+                              unsigned long long* stats, int count, cudaStream_t s);
 // A[diag[i]] += g, i < n (the gshunt-stepping homotopy of eec_newton_dc)
 cudaError_t launch_add_diag(double* A, const int* diag, int n, double g, cudaStream_t s);
 // Transient companion stamp (mode MODE_RMW over one colour range, MODE_ATOMIC over all, or

@@ -86,7 +86,8 @@ __global__ void __launch_bounds__(kNewtonBlock) k_add_diag(double* __restrict__ 
 // voltages held, y_i = x_i - F_i(x) / A_ii, the move clipped to [-vmax, vmax]; a row whose
 // diagonal is not positive moves nothing. The other rows (rail source currents under modified
 // nodal analysis) are copied. Reads x, writes y: every row sees the same iterate, so the sweep
-// does not depend on the order of the threads. stats[1] = max |move|.
+// does not depend on the order of the threads. stats[1] = max |move|; stats[0] += the number of
+// rows that moved more than 1 mV (when count is set).
 __global__ void __launch_bounds__(kNewtonBlock) k_relax_step(const int* __restrict__ rp,
                                                              const int* __restrict__ col,
                                                              const double* __restrict__ A,
@@ -95,7 +96,8 @@ __global__ void __launch_bounds__(kNewtonBlock) k_relax_step(const int* __restri
                                                              const int* __restrict__ diag,
                                                              int n_node, int n, double vmax,
                                                              double* __restrict__ y,
-                                                             unsigned long long* stats) {
+                                                             unsigned long long* stats,
+                                                             int count) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double dx = 0.0;
   if (i < n) {
@@ -110,6 +112,10 @@ __global__ void __launch_bounds__(kNewtonBlock) k_relax_step(const int* __restri
     y[i] = x[i] + dx;
   }
   max_abs_into(stats + 1, dx);
+  if (count) {
+    const unsigned moved = __ballot_sync(0xffffffffu, fabs(dx) > 1e-3);
+    if ((threadIdx.x & 31) == 0 && moved) atomicAdd(stats, (unsigned long long)__popc(moved));
+  }
 }
 
 // Rails as MNA unknowns: rail node rail_unk[r] takes its source's voltage, the right-hand side
@@ -141,9 +147,9 @@ cudaError_t launch_residual_norm(const int* rp, const int* col, const double* A,
 cudaError_t launch_relax_step(const int* rp, const int* col, const double* A, const double* x,
                               const double* b, const int* diag, int n_node, int n, double vmax,
                               const int* rail_unk, int n_rail, double* y,
-                              unsigned long long* stats, cudaStream_t s) {
+                              unsigned long long* stats, int count, cudaStream_t s) {
   k_relax_step<<<blocks_for(n), kNewtonBlock, 0, s>>>(rp, col, A, x, b, diag, n_node, n, vmax, y,
-                                                      stats);
+                                                      stats, count);
   if (n_rail > 0) k_rail_fix<<<blocks_for(n_rail), kNewtonBlock, 0, s>>>(y, b, rail_unk, n_node, n_rail);
   return cudaGetLastError();
 }
