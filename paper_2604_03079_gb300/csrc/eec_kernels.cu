@@ -153,12 +153,14 @@ __device__ __forceinline__ void eval_one(const DevTopo& T, int k, const double* 
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
       if (idx[term[r]] < 0) continue;
-      double s = -o.I[term[r]];
+      double s = -i_entry(o, term[r]);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         if (idx[u] < 0) continue;
-        s = fma(o.G[r][u], V[u], s);
-        T.cbuf[__ldg(T.gat_pos + (4 * r + u) * N + k)] = o.G[r][u];
+        const double g = g_entry(o, r, u);
+        s = fma(g, V[u], s);
+        T.cbuf[__ldg(T.gat_pos + (4 * r + u) * N + k)] = g;
+        if (dbg) bc_ok = bc_ok && isfinite(g);
       }
       T.cbuf[__ldg(T.gat_pos + (kNSlot + r) * N + k)] = s;
       if (dbg) bc_ok = bc_ok && isfinite(s);   // FP64 compares: debug checks only
@@ -169,30 +171,34 @@ __device__ __forceinline__ void eval_one(const DevTopo& T, int k, const double* 
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
       if (idx[term[r]] < 0) continue;
-      double s = -o.I[term[r]];
+      double s = -i_entry(o, term[r]);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         if (idx[u] < 0) continue;
-        s = fma(o.G[r][u], V[u], s);
-        T.buf[(4 * r + u) * N + k] = o.G[r][u];
+        const double g = g_entry(o, r, u);
+        s = fma(g, V[u], s);
+        T.buf[(4 * r + u) * N + k] = g;
+        if (dbg) bc_ok = bc_ok && isfinite(g);
       }
       T.buf[(kNSlot + r) * N + k] = s;
       if (dbg) bc_ok = bc_ok && isfinite(s);   // FP64 compares: debug checks only
     }
   } else {
-    // rows of source-held terminals are not stamped: their b entries are not formed
+    // rows of source-held terminals are not stamped: their entries are not formed
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
       const int row = idx[term[r]];
       if (row < 0) continue;
-      double s = -o.I[term[r]];
+      double s = -i_entry(o, term[r]);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         if (idx[u] < 0) continue;
-        s = fma(o.G[r][u], V[u], s);
+        const double g = g_entry(o, r, u);
+        s = fma(g, V[u], s);
         const int sl = __ldg(T.slot + (4 * r + u) * N + k);
-        if (MODE == MODE_ATOMIC) atomicAdd(A + sl, o.G[r][u]);
-        else A[sl] += o.G[r][u];
+        if (MODE == MODE_ATOMIC) atomicAdd(A + sl, g);
+        else A[sl] += g;
+        if (dbg) bc_ok = bc_ok && isfinite(g);
       }
       if (MODE == MODE_ATOMIC) atomicAdd(b + row, s);
       else b[row] += s;
@@ -204,14 +210,7 @@ __device__ __forceinline__ void eval_one(const DevTopo& T, int k, const double* 
 #pragma unroll
     for (int t = 0; t < 4; ++t) q[t * N + od] = o.Q[t];
   }
-  if (dbg) {
-    bool ok = bc_ok;
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-      for (int u = 0; u < 4; ++u) ok = ok && isfinite(o.G[r][u]);
-    if (!ok) atomicOr(T.status, kStatusNumeric);
-  }
+  if (dbg && !bc_ok) atomicOr(T.status, kStatusNumeric);   // a formed entry is not finite
 }
 
 // Transient: evaluate with charges and their Jacobian, then stamp all four terminal rows
@@ -673,12 +672,17 @@ struct PipeDC {
       const int row = idx[term[r]];
       si[(kNSlot + r) * kPipeBlock + tid] = row;
       if (row < 0) continue;   // rows of held terminals are not stamped: nothing to form
-      double s = -o.I[term[r]];
+      double s = -i_entry(o, term[r]);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        sv[(4 * r + u) * kPipeBlock + tid] = o.G[r][u];
-        si[(4 * r + u) * kPipeBlock + tid] = idx[u] >= 0 ? __ldg(T.slot + (4 * r + u) * N + k) : -1;
-        if (idx[u] >= 0) s = fma(o.G[r][u], V[u], s);
+        if (idx[u] < 0) {
+          si[(4 * r + u) * kPipeBlock + tid] = -1;
+          continue;
+        }
+        const double g = g_entry(o, r, u);
+        sv[(4 * r + u) * kPipeBlock + tid] = g;
+        si[(4 * r + u) * kPipeBlock + tid] = __ldg(T.slot + (4 * r + u) * N + k);
+        s = fma(g, V[u], s);
       }
       sv[(kNSlot + r) * kPipeBlock + tid] = s;
     }
@@ -691,9 +695,11 @@ struct PipeDC {
       bool ok = true;
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
-        ok = ok && (idx[term[r]] < 0 || isfinite(sv[(kNSlot + r) * kPipeBlock + tid]));
+        if (idx[term[r]] < 0) continue;
+        ok = ok && isfinite(sv[(kNSlot + r) * kPipeBlock + tid]);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) ok = ok && isfinite(o.G[r][u]);
+        for (int u = 0; u < 4; ++u)
+          ok = ok && (idx[u] < 0 || isfinite(sv[(4 * r + u) * kPipeBlock + tid]));
       }
       if (!ok) atomicOr(T.status, kStatusNumeric);
     }

@@ -81,7 +81,29 @@ struct EvalOut {
   S G[3][4];   // rows d, s, b of dI_t / dV_u, u = d, g, s, b (gate row is zero in DC)
   S Q[4];      // terminal charges (only when requested)
   S C[4][4];   // dQ_t / dV_u, rows d, g, s, b (transient only)
+  // the parts I and G are formed from (see i_entry, g_entry): channel row of the physical
+  // drain, junction currents and conductances, polarity sign bit
+  S cdd, cdg, cds, cdb, gjd, gjs, Ichd, Ijd, Ijs;
+  unsigned long long psb;
 };
+
+// Entry (r, u) of G and entry t of I, formed from their parts. The DC stamps call these inside
+// their tests for free rows and columns, so that entries of held terminals cost no FP64 issue
+// slot (two thirds of a logic netlist's devices have source and body on a rail); I and G as
+// stored by ees_l1 are the same expressions.
+template <class S>
+__device__ __forceinline__ S g_entry(const EvalOut<S>& o, int r, int u) {
+  if (r == 0) return u == 0 ? o.cdd + o.gjd : u == 1 ? o.cdg : u == 2 ? o.cds : o.cdb - o.gjd;
+  if (r == 1) return u == 0 ? -o.cdd : u == 1 ? -o.cdg : u == 2 ? o.gjs - o.cds : -o.cdb - o.gjs;
+  return u == 0 ? -o.gjd : u == 1 ? S(0.0) : u == 2 ? -o.gjs : o.gjd + o.gjs;
+}
+template <class S>
+__device__ __forceinline__ S i_entry(const EvalOut<S>& o, int t) {
+  if (t == 0) return o.Ichd - flip(o.Ijd, o.psb);
+  if (t == 2) return -o.Ichd - flip(o.Ijs, o.psb);
+  if (t == 3) return flip(o.Ijd + o.Ijs, o.psb);
+  return S(0.0);
+}
 
 // Junction current and conductance: Ij(v) = Isat (explim(v/Vt) - 1) + GMIN v with
 // explim(z) = exp(z) for z <= 40 and e^40 (1 + z - 40) above; gj = dIj/dv
@@ -317,13 +339,22 @@ __device__ __forceinline__ void ees_l1(const CardK& c, unsigned long long psb, c
     junction<S>(c, P, flip(V[3] - V[2], psb), Ijs, gjs);
   }
 
-  o.I[0] = Ichd - flip(Ijd, psb);
-  o.I[1] = S(0.0);
-  o.I[2] = -Ichd - flip(Ijs, psb);
-  o.I[3] = flip(Ijd + Ijs, psb);
-  o.G[0][0] = cdd + gjd;  o.G[0][1] = cdg;   o.G[0][2] = cds;        o.G[0][3] = cdb - gjd;
-  o.G[1][0] = -cdd;       o.G[1][1] = -cdg;  o.G[1][2] = gjs - cds;  o.G[1][3] = -cdb - gjs;
-  o.G[2][0] = -gjd;       o.G[2][1] = S(0.0); o.G[2][2] = -gjs;      o.G[2][3] = gjd + gjs;
+  o.cdd = cdd;
+  o.cdg = cdg;
+  o.cds = cds;
+  o.cdb = cdb;
+  o.gjd = gjd;
+  o.gjs = gjs;
+  o.Ichd = Ichd;
+  o.Ijd = Ijd;
+  o.Ijs = Ijs;
+  o.psb = psb;
+#pragma unroll
+  for (int t = 0; t < 4; ++t) o.I[t] = i_entry(o, t);
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) o.G[r][u] = g_entry(o, r, u);
 
   if (WANT_Q) {
     // (11) charges: depletion, inversion partitioned to the mode drain by
