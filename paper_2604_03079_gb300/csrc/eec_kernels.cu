@@ -235,11 +235,11 @@ __device__ __forceinline__ void eval_one_tran(const DevTopo& T, int k, const dou
     const int row = idx[t];
     if (row < 0) continue;
     const int r = t == 0 ? 0 : (t == 2 ? 1 : 2);   // row of G (gate row of G is zero)
-    double rhs = -(t == 1 ? 0.0 : o.I[t]) - ic;
+    double rhs = -i_entry(o, t) - ic;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      if (idx[u] < 0) continue;
-      const double a = fma(ta.alpha, o.C[t][u], t == 1 ? 0.0 : o.G[r][u]);
+      if (idx[u] < 0) continue;   // entries of held columns are not formed
+      const double a = fma(ta.alpha, c_entry(o, t, u), t == 1 ? 0.0 : g_entry(o, r, u));
       if (MODE == MODE_BUFFER) {
         T.buf_tran[(4 * t + u) * N + k] = a;
       } else {
@@ -751,15 +751,18 @@ struct PipeTran {
       si[(16 + t) * kPipeBlock + tid] = idx[t];
       if (idx[t] < 0) continue;   // rows of held terminals are not stamped
       const int r = t == 0 ? 0 : (t == 2 ? 1 : 2);   // row of G (gate row of G is zero)
-      double s = -(t == 1 ? 0.0 : o.I[t]) - ic;
+      double s = -i_entry(o, t) - ic;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const double v = fma(ta.alpha, o.C[t][u], t == 1 ? 0.0 : o.G[r][u]);
+        if (idx[u] < 0) {   // entries of held columns are not formed
+          si[(4 * t + u) * kPipeBlock + tid] = -1;
+          continue;
+        }
+        const double v = fma(ta.alpha, c_entry(o, t, u), t == 1 ? 0.0 : g_entry(o, r, u));
         sv[(4 * t + u) * kPipeBlock + tid] = v;
         si[(4 * t + u) * kPipeBlock + tid] =
-            idx[u] >= 0 ? (t == 1 ? __ldg(T.slot_g + u * N + k) : __ldg(T.slot + (4 * r + u) * N + k))
-                        : -1;
-        if (idx[u] >= 0) s = fma(v, V[u], s);
+            t == 1 ? __ldg(T.slot_g + u * N + k) : __ldg(T.slot + (4 * r + u) * N + k);
+        s = fma(v, V[u], s);
       }
       sv[(16 + t) * kPipeBlock + tid] = s;
     }

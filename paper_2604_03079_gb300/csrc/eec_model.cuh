@@ -85,6 +85,11 @@ struct EvalOut {
   // drain, junction currents and conductances, polarity sign bit
   S cdd, cdg, cds, cdb, gjd, gjs, Ichd, Ijd, Ijs;
   unsigned long long psb;
+  // the parts C is formed from (see c_entry): mode-frame derivatives of the inversion charge,
+  // of its drain share and of the depletion charge, by physical terminal; the overlap
+  // capacitances; the mode
+  S MQi[4], MQD[4], MQb[4], CovS, CovD;
+  bool fwd;
 };
 
 // Entry (r, u) of G and entry t of I, formed from their parts. The DC stamps call these inside
@@ -96,6 +101,25 @@ __device__ __forceinline__ S g_entry(const EvalOut<S>& o, int r, int u) {
   if (r == 0) return u == 0 ? o.cdd + o.gjd : u == 1 ? o.cdg : u == 2 ? o.cds : o.cdb - o.gjd;
   if (r == 1) return u == 0 ? -o.cdd : u == 1 ? -o.cdg : u == 2 ? o.gjs - o.cds : -o.cdb - o.gjs;
   return u == 0 ? -o.gjd : u == 1 ? S(0.0) : u == 2 ? -o.gjs : o.gjd + o.gjs;
+}
+// Entry (t, u) of C, formed from its parts: physical d carries the drain share QD in forward
+// mode and QS = Qinv - QD in reverse mode; the gate row is minus the sum of the others; then the
+// overlaps, q_g += CovS (Vg - Vs) + CovD (Vg - Vd), q_s -= CovS (Vg - Vs), q_d -= CovD (Vg - Vd).
+template <class S>
+__device__ __forceinline__ S c_entry(const EvalOut<S>& o, int t, int u) {
+  if (t == 0) {
+    const S base = o.fwd ? o.MQD[u] : o.MQi[u] - o.MQD[u];
+    return u == 0 ? base + o.CovD : u == 1 ? base - o.CovD : base;
+  }
+  if (t == 1) {
+    const S base = -(o.MQb[u] + o.MQi[u]);
+    return u == 1 ? base + (o.CovS + o.CovD) : u == 0 ? base - o.CovD : u == 2 ? base - o.CovS : base;
+  }
+  if (t == 2) {
+    const S base = o.fwd ? o.MQi[u] - o.MQD[u] : o.MQD[u];
+    return u == 2 ? base + o.CovS : u == 1 ? base - o.CovS : base;
+  }
+  return o.MQb[u];
 }
 template <class S>
 __device__ __forceinline__ S i_entry(const EvalOut<S>& o, int t) {
@@ -422,23 +446,19 @@ __device__ __forceinline__ void ees_l1(const CardK& c, unsigned long long psb, c
       MQb[iD] = S(0.0);
       MQb[3] = Qb_vbs;
       MQb[iS] = -Qb_vbs;
-      // physical d carries QD in forward mode, QS = Qinv - QD in reverse mode
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const S MQS = MQi[u] - MQD[u];
-        o.C[1][u] = -(MQb[u] + MQi[u]);
-        o.C[0][u] = fwd ? MQD[u] : MQS;
-        o.C[2][u] = fwd ? MQS : MQD[u];
-        o.C[3][u] = MQb[u];
+        o.MQi[u] = MQi[u];
+        o.MQD[u] = MQD[u];
+        o.MQb[u] = MQb[u];
       }
-      // overlaps: q_g += CovS (Vg - Vs) + CovD (Vg - Vd), q_s -= CovS (Vg - Vs), q_d -= CovD (Vg - Vd)
-      o.C[1][1] = o.C[1][1] + (P.CovS + P.CovD);
-      o.C[1][0] = o.C[1][0] - P.CovD;
-      o.C[1][2] = o.C[1][2] - P.CovS;
-      o.C[0][0] = o.C[0][0] + P.CovD;
-      o.C[0][1] = o.C[0][1] - P.CovD;
-      o.C[2][2] = o.C[2][2] + P.CovS;
-      o.C[2][1] = o.C[2][1] - P.CovS;
+      o.CovS = P.CovS;
+      o.CovD = P.CovD;
+      o.fwd = fwd;
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) o.C[t][u] = c_entry(o, t, u);
     }
   }
 }
