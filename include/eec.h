@@ -11,7 +11,8 @@
  *
  * Conventions shared by every entry point
  *  - Return value: 0 on success, a negative EEC_E* code on failure. No C++ exception crosses the
- *    ABI. eec_last_error() returns a message for the last failure on that context.
+ *    ABI: host memory running out inside a call returns EEC_ENOMEM. eec_last_error() returns a
+ *    message for the last failure on that context.
  *  - Pointers named *_dev are CUDA device pointers; all others are host pointers. The caller owns
  *    every pointer it passes; the library copies host inputs during the call and keeps no pointer
  *    to them, never frees caller memory, and owns only the device arrays it allocates itself
@@ -275,7 +276,10 @@ EEC_API int eec_eval_stamp_host(eec_ctx* ctx, const double* x_host, double* A_ho
  *  iters_out   (nullable) solves performed, over all stages.
  * Returns EEC_OK, EEC_ENOCONV (a stage ran max_iter solves without meeting both tests: x holds
  * its last iterate), EEC_ENUMERIC (a non-finite step or residual, or a singular matrix),
- * EEC_ETIMEOUT (a bounded wait of the sparse LU's kernels ran out) or EEC_ENOMEM. Meant for netlists up to tens of thousands of unknowns (solver 0 checks its
+ * EEC_ETIMEOUT (a bounded wait of the sparse LU's kernels ran out) or EEC_ENOMEM (solver 2: the
+ * pattern fills in too much for a direct solve, as randomly wired logic does: its elimination
+ * graph or factor would exceed 32 nnz + 4 Mi entries, or its update list 128 nnz + 16 Mi; the
+ * 256 x 256 SRAM needs 1.2 nnz and 39 nnz). Meant for netlists up to tens of thousands of unknowns (solver 0 checks its
  * factor's size before allocating). Synchronises cuda_stream once per iteration.
  */
 #define EEC_SOLVER_LU 2
@@ -299,7 +303,8 @@ EEC_API int eec_newton_info(const eec_ctx* ctx, int32_t* info);
  * kernel (with one step of iterative refinement), analysing again if a pivot has fallen below 1e-4 of its column's
  * largest L entry.
  *  A_values_dev [nnz], b_dev [n] in (device, unchanged); x_dev [n] out (device).
- * Returns EEC_ENUMERIC for a singular matrix, EEC_ETIMEOUT if a bounded device wait ran out.
+ * Returns EEC_ENUMERIC for a singular matrix, EEC_ETIMEOUT if a bounded device wait ran out,
+ * EEC_ENOMEM when the pattern fills in too much (as for eec_newton_dc's solver 2).
  * Synchronises the stream once per call (the pivot check).
  */
 EEC_API int eec_lu_solve(eec_ctx* ctx, const double* A_values_dev, const double* b_dev,
@@ -320,7 +325,8 @@ EEC_API int eec_lu_stats(const eec_ctx* ctx, int64_t* nnz_lu, int32_t* analyses)
  * solution of A x = b. *nnz_lu (nullable) = entries of L and U; *bad_col
  * (nullable) = the first column whose refactorised pivot fell below 1e-4 of its column's
  * largest L entry, or -1.
- * Returns EEC_EINVAL for a malformed matrix, EEC_ENUMERIC for a singular one.
+ * Returns EEC_EINVAL for a malformed matrix, EEC_ENUMERIC for a singular one, EEC_ENOMEM when the
+ * pattern fills in too much (as for eec_newton_dc's solver 2).
  */
 EEC_API int eec_lu_check_host(int32_t n, const int32_t* row_ptr, const int32_t* col, const double* a,
                               const double* b, double* x, int64_t* nnz_lu, int32_t* bad_col);

@@ -15,10 +15,12 @@
 #include <cstring>
 #include <new>
 #include <numeric>
+#include <stdexcept>
 #include <string>
 #include <vector>
 
 #include "eec_internal.h"
+#include "eec_lu.h"
 
 using namespace eec;
 
@@ -140,6 +142,31 @@ namespace {
 
 int fail(eec_ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;
+  return code;
+}
+
+// No C++ exception crosses the C ABI: every entry point runs its body inside a try block and
+// reports an exception as an error code (host memory exhausted: EEC_ENOMEM). Called from the
+// catch block, so the exception being handled is rethrown here to be told apart.
+int abi_exception(eec_ctx* c) noexcept {
+  int code = EEC_EINVAL;
+  const char* msg = "internal error";
+  try {
+    throw;
+  } catch (const std::bad_alloc&) {
+    code = EEC_ENOMEM;
+    msg = "out of host memory";
+  } catch (const std::length_error&) {
+    code = EEC_ENOMEM;
+    msg = "a host array would exceed its maximum size";
+  } catch (...) {
+  }
+  if (c) {
+    try {
+      c->err = msg;
+    } catch (...) {
+    }
+  }
   return code;
 }
 
@@ -687,7 +714,7 @@ eec_options eec_default_options(void) {
   return o;
 }
 
-int eec_create(eec_ctx** out, const eec_options* opt) {
+static int eec_create_body(eec_ctx** out, const eec_options* opt) {
   if (!out) return EEC_EINVAL;
   *out = nullptr;
   eec_ctx* c = new (std::nothrow) eec_ctx;
@@ -704,6 +731,13 @@ int eec_create(eec_ctx** out, const eec_options* opt) {
   }
   *out = c;  // no CUDA call: host-side steps work without a device
   return EEC_OK;
+}
+int eec_create(eec_ctx** out, const eec_options* opt) {
+  try {
+    return eec_create_body(out, opt);
+  } catch (...) {
+    return abi_exception(nullptr);
+  }
 }
 
 void eec_destroy(eec_ctx* c) {
@@ -722,18 +756,32 @@ void eec_destroy(eec_ctx* c) {
 
 const char* eec_last_error(const eec_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
+static int eec_upload_netlist_body(eec_ctx* c, int32_t n_nodes, const uint8_t* node_fixed,
+                                   const double* node_vfix, int32_t n_dev, const int32_t* dev_nodes,
+                                   const int8_t* dev_type, const double* W, const double* L,
+                                   const int32_t* model_id, int32_t n_res, const int32_t* res_nodes,
+                                   const double* res_G, int32_t n_isrc, const int32_t* isrc_nodes,
+                                   const double* isrc_val, double gshunt) {
+  if (!c) return EEC_EINVAL;
+  return store_netlist(c, n_nodes, node_fixed, node_vfix, n_dev, dev_nodes, dev_type, W, L,
+                       model_id, n_res, res_nodes, res_G, n_isrc, isrc_nodes, isrc_val, gshunt);
+}
 int eec_upload_netlist(eec_ctx* c, int32_t n_nodes, const uint8_t* node_fixed,
                        const double* node_vfix, int32_t n_dev, const int32_t* dev_nodes,
                        const int8_t* dev_type, const double* W, const double* L,
                        const int32_t* model_id, int32_t n_res, const int32_t* res_nodes,
                        const double* res_G, int32_t n_isrc, const int32_t* isrc_nodes,
                        const double* isrc_val, double gshunt) {
-  if (!c) return EEC_EINVAL;
-  return store_netlist(c, n_nodes, node_fixed, node_vfix, n_dev, dev_nodes, dev_type, W, L,
-                       model_id, n_res, res_nodes, res_G, n_isrc, isrc_nodes, isrc_val, gshunt);
+  try {
+    return eec_upload_netlist_body(c, n_nodes, node_fixed, node_vfix, n_dev, dev_nodes, dev_type, W,
+                                   L, model_id, n_res, res_nodes, res_G, n_isrc, isrc_nodes,
+                                   isrc_val, gshunt);
+  } catch (...) {
+    return abi_exception(c);
+  }
 }
 
-int eec_upload_batch(eec_ctx* c, int32_t n_circ, const eec_netlist* nets, double gshunt) {
+static int eec_upload_batch_body(eec_ctx* c, int32_t n_circ, const eec_netlist* nets, double gshunt) {
   if (!c) return EEC_EINVAL;
   if (n_circ < 1 || !nets) return fail(c, EEC_EINVAL, "empty batch");
   if (c->opt.rail_mode != EEC_RAIL_ELIMINATE)
@@ -805,8 +853,15 @@ int eec_upload_batch(eec_ctx* c, int32_t n_circ, const eec_netlist* nets, double
   c->circ_dev_off = dev_off;
   return EEC_OK;
 }
+int eec_upload_batch(eec_ctx* c, int32_t n_circ, const eec_netlist* nets, double gshunt) {
+  try {
+    return eec_upload_batch_body(c, n_circ, nets, gshunt);
+  } catch (...) {
+    return abi_exception(c);
+  }
+}
 
-int eec_set_model_cards(eec_ctx* c, int32_t n_cards, const double* cards) {
+static int eec_set_model_cards_body(eec_ctx* c, int32_t n_cards, const double* cards) {
   if (!c) return EEC_EINVAL;
   if (n_cards < 1 || !cards) return fail(c, EEC_EINVAL, "need at least one card");
   for (int i = 0; i < n_cards; ++i)
@@ -823,9 +878,16 @@ int eec_set_model_cards(eec_ctx* c, int32_t n_cards, const double* cards) {
   }
   return EEC_OK;
 }
+int eec_set_model_cards(eec_ctx* c, int32_t n_cards, const double* cards) {
+  try {
+    return eec_set_model_cards_body(c, n_cards, cards);
+  } catch (...) {
+    return abi_exception(c);
+  }
+}
 
-int eec_color(eec_ctx* c, const int32_t* order, int32_t algo, int32_t* colors_out,
-              int32_t* n_colors) {
+static int eec_color_body(eec_ctx* c, const int32_t* order, int32_t algo, int32_t* colors_out,
+                          int32_t* n_colors) {
   if (!c) return EEC_EINVAL;
   if (!c->has_net) return fail(c, EEC_ESTATE, "upload a netlist first");
   if (!n_colors) return fail(c, EEC_EINVAL, "n_colors is NULL");
@@ -880,8 +942,16 @@ int eec_color(eec_ctx* c, const int32_t* order, int32_t algo, int32_t* colors_ou
   *n_colors = C;
   return EEC_OK;
 }
+int eec_color(eec_ctx* c, const int32_t* order, int32_t algo, int32_t* colors_out,
+              int32_t* n_colors) {
+  try {
+    return eec_color_body(c, order, algo, colors_out, n_colors);
+  } catch (...) {
+    return abi_exception(c);
+  }
+}
 
-int eec_build_scatter(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_out) {
+static int eec_build_scatter_body(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_out) {
   if (!c) return EEC_EINVAL;
   if (!c->has_net || !c->has_cards) return fail(c, EEC_ESTATE, "upload a netlist and model cards first");
   for (int k = 0; k < c->n_dev; ++k)
@@ -1235,8 +1305,15 @@ int eec_build_scatter(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_out) {
   c->built = true;
   return EEC_OK;
 }
+int eec_build_scatter(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_out) {
+  try {
+    return eec_build_scatter_body(c, n_unknowns, nnz_out);
+  } catch (...) {
+    return abi_exception(c);
+  }
+}
 
-int eec_verify_coloring(const eec_ctx* cc, int32_t with_gate_rows) {
+static int eec_verify_coloring_body(const eec_ctx* cc, int32_t with_gate_rows) {
   eec_ctx* c = const_cast<eec_ctx*>(cc);
   int rc = check_pattern(c);
   if (rc) return rc;
@@ -1272,8 +1349,15 @@ int eec_verify_coloring(const eec_ctx* cc, int32_t with_gate_rows) {
   }
   return EEC_OK;
 }
+int eec_verify_coloring(const eec_ctx* cc, int32_t with_gate_rows) {
+  try {
+    return eec_verify_coloring_body(cc, with_gate_rows);
+  } catch (...) {
+    return abi_exception(const_cast<eec_ctx*>(cc));
+  }
+}
 
-int eec_get_pattern(const eec_ctx* cc, int32_t* row_ptr, int32_t* col_idx, int32_t* unk_of_node) {
+static int eec_get_pattern_body(const eec_ctx* cc, int32_t* row_ptr, int32_t* col_idx, int32_t* unk_of_node) {
   eec_ctx* c = const_cast<eec_ctx*>(cc);
   int rc = check_pattern(c);
   if (rc) return rc;
@@ -1282,8 +1366,15 @@ int eec_get_pattern(const eec_ctx* cc, int32_t* row_ptr, int32_t* col_idx, int32
   if (unk_of_node) std::copy(c->unk.begin(), c->unk.end(), unk_of_node);
   return EEC_OK;
 }
+int eec_get_pattern(const eec_ctx* cc, int32_t* row_ptr, int32_t* col_idx, int32_t* unk_of_node) {
+  try {
+    return eec_get_pattern_body(cc, row_ptr, col_idx, unk_of_node);
+  } catch (...) {
+    return abi_exception(const_cast<eec_ctx*>(cc));
+  }
+}
 
-int eec_get_color_offsets(const eec_ctx* cc, int32_t* off) {
+static int eec_get_color_offsets_body(const eec_ctx* cc, int32_t* off) {
   eec_ctx* c = const_cast<eec_ctx*>(cc);
   int rc = check_pattern(c);
   if (rc) return rc;
@@ -1292,9 +1383,16 @@ int eec_get_color_offsets(const eec_ctx* cc, int32_t* off) {
   std::copy(c->color_off.begin(), c->color_off.end(), off);
   return EEC_OK;
 }
+int eec_get_color_offsets(const eec_ctx* cc, int32_t* off) {
+  try {
+    return eec_get_color_offsets_body(cc, off);
+  } catch (...) {
+    return abi_exception(const_cast<eec_ctx*>(cc));
+  }
+}
 
-int eec_get_sizes(const eec_ctx* cc, int32_t* n_dev, int32_t* n_unknowns, int64_t* nnz,
-                  int32_t* n_colors) {
+static int eec_get_sizes_body(const eec_ctx* cc, int32_t* n_dev, int32_t* n_unknowns, int64_t* nnz,
+                              int32_t* n_colors) {
   eec_ctx* c = const_cast<eec_ctx*>(cc);
   int rc = check_pattern(c);
   if (rc) return rc;
@@ -1304,8 +1402,16 @@ int eec_get_sizes(const eec_ctx* cc, int32_t* n_dev, int32_t* n_unknowns, int64_
   if (n_colors) *n_colors = c->colored ? c->C : 0;
   return EEC_OK;
 }
+int eec_get_sizes(const eec_ctx* cc, int32_t* n_dev, int32_t* n_unknowns, int64_t* nnz,
+                  int32_t* n_colors) {
+  try {
+    return eec_get_sizes_body(cc, n_dev, n_unknowns, nnz, n_colors);
+  } catch (...) {
+    return abi_exception(const_cast<eec_ctx*>(cc));
+  }
+}
 
-int eec_get_batch_offsets(const eec_ctx* cc, int32_t* row_off, int64_t* nnz_off, int32_t* dev_off) {
+static int eec_get_batch_offsets_body(const eec_ctx* cc, int32_t* row_off, int64_t* nnz_off, int32_t* dev_off) {
   eec_ctx* c = const_cast<eec_ctx*>(cc);
   int rc = check_pattern(c);
   if (rc) return rc;
@@ -1315,8 +1421,15 @@ int eec_get_batch_offsets(const eec_ctx* cc, int32_t* row_off, int64_t* nnz_off,
   if (dev_off) std::copy(c->circ_dev_off.begin(), c->circ_dev_off.end(), dev_off);
   return EEC_OK;
 }
+int eec_get_batch_offsets(const eec_ctx* cc, int32_t* row_off, int64_t* nnz_off, int32_t* dev_off) {
+  try {
+    return eec_get_batch_offsets_body(cc, row_off, nnz_off, dev_off);
+  } catch (...) {
+    return abi_exception(const_cast<eec_ctx*>(cc));
+  }
+}
 
-int eec_update_params(eec_ctx* c, const double* W_dev, const double* L_dev, void* stream) {
+static int eec_update_params_body(eec_ctx* c, const double* W_dev, const double* L_dev, void* stream) {
   int rc = check_built(c);
   if (rc) return rc;
   if (!W_dev || !L_dev) return fail(c, EEC_EINVAL, "NULL W or L");
@@ -1324,36 +1437,71 @@ int eec_update_params(eec_ctx* c, const double* W_dev, const double* L_dev, void
   c->params_dirty = true;
   return EEC_OK;
 }
+int eec_update_params(eec_ctx* c, const double* W_dev, const double* L_dev, void* stream) {
+  try {
+    return eec_update_params_body(c, W_dev, L_dev, stream);
+  } catch (...) {
+    return abi_exception(c);
+  }
+}
 
-int eec_set_variant(eec_ctx* c, int32_t v) {
+static int eec_set_variant_body(eec_ctx* c, int32_t v) {
   if (!c) return EEC_EINVAL;
   if (v < EEC_VARIANT_AUTO || v >= EEC_N_VARIANTS) return fail(c, EEC_EINVAL, "unknown variant");
   c->opt.variant = v;
   return EEC_OK;
 }
+int eec_set_variant(eec_ctx* c, int32_t v) {
+  try {
+    return eec_set_variant_body(c, v);
+  } catch (...) {
+    return abi_exception(c);
+  }
+}
 
-int eec_set_eval_order(eec_ctx* c, int32_t cost_order) {
+static int eec_set_eval_order_body(eec_ctx* c, int32_t cost_order) {
   if (!c) return EEC_EINVAL;
   if (cost_order != 0 && cost_order != 1) return fail(c, EEC_EINVAL, "cost_order must be 0 or 1");
   c->eval_ordered = cost_order == 1;
   return EEC_OK;
 }
+int eec_set_eval_order(eec_ctx* c, int32_t cost_order) {
+  try {
+    return eec_set_eval_order_body(c, cost_order);
+  } catch (...) {
+    return abi_exception(c);
+  }
+}
 
-int eec_get_variant(const eec_ctx* c, int32_t* v) {
+static int eec_get_variant_body(const eec_ctx* c, int32_t* v) {
   if (!c || !v) return EEC_EINVAL;
   *v = effective_variant(c);
   return EEC_OK;
 }
+int eec_get_variant(const eec_ctx* c, int32_t* v) {
+  try {
+    return eec_get_variant_body(c, v);
+  } catch (...) {
+    return abi_exception(const_cast<eec_ctx*>(c));
+  }
+}
 
-int eec_eval_stamp(eec_ctx* c, const double* x, double* A, double* b, double* q, void* stream) {
+static int eec_eval_stamp_body(eec_ctx* c, const double* x, double* A, double* b, double* q, void* stream) {
   int rc = check_built(c);
   if (rc) return rc;
   if (!x || !A || !b) return fail(c, EEC_EINVAL, "NULL x, A or b");
   return eval_with(c, effective_variant(c), x, A, b, q, static_cast<cudaStream_t>(stream));
 }
+int eec_eval_stamp(eec_ctx* c, const double* x, double* A, double* b, double* q, void* stream) {
+  try {
+    return eec_eval_stamp_body(c, x, A, b, q, stream);
+  } catch (...) {
+    return abi_exception(c);
+  }
+}
 
-int eec_eval_stamp_host(eec_ctx* c, const double* x_host, double* A_host, double* b_host,
-                        double* q_host, void* stream) {
+static int eec_eval_stamp_host_body(eec_ctx* c, const double* x_host, double* A_host, double* b_host,
+                                    double* q_host, void* stream) {
   NvtxRange range("eec/eval_stamp_host");
   int rc = check_built(c);
   if (rc) return rc;
@@ -1437,6 +1585,14 @@ int eec_eval_stamp_host(eec_ctx* c, const double* x_host, double* A_host, double
   CUDA_TRY(c, cudaStreamWaitEvent(s, c->hev[K], 0));
   return EEC_OK;
 }
+int eec_eval_stamp_host(eec_ctx* c, const double* x_host, double* A_host, double* b_host,
+                        double* q_host, void* stream) {
+  try {
+    return eec_eval_stamp_host_body(c, x_host, A_host, b_host, q_host, stream);
+  } catch (...) {
+    return abi_exception(c);
+  }
+}
 
 // Solver state of eec_newton_dc, on its first call: the pattern on the device, the sparse QR's
 // analysis (reused by every later factorisation: the pattern never changes) and its workspace.
@@ -1472,10 +1628,14 @@ int lu_prepare(eec_ctx* c, const double* A, cudaStream_t s) {
   std::vector<double> a(c->nnz);
   CUDA_TRY(c, cudaMemcpyAsync(a.data(), A, sizeof(double) * c->nnz, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(c, cudaStreamSynchronize(s));
-  if (c->lu_order.empty()) c->lu_order = lu_min_degree_order(c->n, c->row_ptr, c->col);
+  if (c->lu_order.empty() && !lu_min_degree_order(c->n, c->row_ptr, c->col, c->lu_order))
+    return fail(c, EEC_ENOMEM, "sparse LU: the elimination graph of this pattern would exceed " +
+                                   std::to_string(lu_entry_budget(c->nnz)) +
+                                   " entries: too much fill for a direct solve");
   LuPlan P;
   std::string err;
-  if (!lu_analyze(c->n, c->row_ptr, c->col, a, c->lu_order, P, err)) return fail(c, EEC_ENUMERIC, err);
+  int rc = lu_analyze(c->n, c->row_ptr, c->col, a, c->lu_order, P, err);
+  if (rc) return fail(c, rc, err);
   const std::vector<int>* parts[] = {&P.cptr, &P.cdiag, &P.a2lu, &P.uptr, &P.uk, &P.upos,
                                      &P.mptr, &P.msrc, &P.mdst, &P.lrptr, &P.lrcol, &P.lrpos,
                                      &P.urptr, &P.urcol, &P.urpos, &P.prow, &P.pcol};
@@ -1709,9 +1869,9 @@ int relax_run(eec_ctx* c, double* x, double* A, double* b, double vmax, int max_
   return EEC_OK;
 }
 
-int eec_newton_dc(eec_ctx* c, double* x, double* A, double* b, int32_t max_iter, double vstep,
-                  int32_t step_rule, int32_t solver, double tol_abs, double tol_rel,
-                  double tol_f, int32_t* iters_out, void* stream) {
+static int eec_newton_dc_body(eec_ctx* c, double* x, double* A, double* b, int32_t max_iter, double vstep,
+                              int32_t step_rule, int32_t solver, double tol_abs, double tol_rel,
+                              double tol_f, int32_t* iters_out, void* stream) {
   NvtxRange range("eec/newton_dc");
   int rc = check_built(c);
   if (rc) return rc;
@@ -1791,10 +1951,20 @@ int eec_newton_dc(eec_ctx* c, double* x, double* A, double* b, int32_t max_iter,
                                 "and relaxation start included)");
   return rc;
 }
+int eec_newton_dc(eec_ctx* c, double* x, double* A, double* b, int32_t max_iter, double vstep,
+                  int32_t step_rule, int32_t solver, double tol_abs, double tol_rel,
+                  double tol_f, int32_t* iters_out, void* stream) {
+  try {
+    return eec_newton_dc_body(c, x, A, b, max_iter, vstep, step_rule, solver, tol_abs, tol_rel,
+                              tol_f, iters_out, stream);
+  } catch (...) {
+    return abi_exception(c);
+  }
+}
 
-int eec_eval_stamp_tran(eec_ctx* c, const double* x, const double* q_prev, const double* i_prev,
-                        double alpha, double beta, double* A, double* b, double* q, double* icap,
-                        void* stream) {
+static int eec_eval_stamp_tran_body(eec_ctx* c, const double* x, const double* q_prev, const double* i_prev,
+                                    double alpha, double beta, double* A, double* b, double* q, double* icap,
+                                    void* stream) {
   NvtxRange range("eec/eval_stamp_tran");
   int rc = check_built(c);
   if (rc) return rc;
@@ -1836,9 +2006,18 @@ int eec_eval_stamp_tran(eec_ctx* c, const double* x, const double* q_prev, const
   }
   return EEC_OK;
 }
+int eec_eval_stamp_tran(eec_ctx* c, const double* x, const double* q_prev, const double* i_prev,
+                        double alpha, double beta, double* A, double* b, double* q, double* icap,
+                        void* stream) {
+  try {
+    return eec_eval_stamp_tran_body(c, x, q_prev, i_prev, alpha, beta, A, b, q, icap, stream);
+  } catch (...) {
+    return abi_exception(c);
+  }
+}
 
-int eec_eval_stamp_bwd(eec_ctx* c, const double* x, const double* gA, const double* gb,
-                       double* gx, double* gW, double* gL, void* stream) {
+static int eec_eval_stamp_bwd_body(eec_ctx* c, const double* x, const double* gA, const double* gb,
+                                   double* gx, double* gW, double* gL, void* stream) {
   NvtxRange range("eec/eval_stamp_bwd");
   int rc = check_built(c);
   if (rc) return rc;
@@ -1847,9 +2026,17 @@ int eec_eval_stamp_bwd(eec_ctx* c, const double* x, const double* gA, const doub
   CUDA_TRY(c, launch_bwd(c->d, x, gA, gb, gx, gW, gL, c->opt.block, static_cast<cudaStream_t>(stream)));
   return EEC_OK;
 }
+int eec_eval_stamp_bwd(eec_ctx* c, const double* x, const double* gA, const double* gb,
+                       double* gx, double* gW, double* gL, void* stream) {
+  try {
+    return eec_eval_stamp_bwd_body(c, x, gA, gb, gx, gW, gL, stream);
+  } catch (...) {
+    return abi_exception(c);
+  }
+}
 
-int eec_eval_stamp_bwd_noalloc(eec_ctx* c, const double* x, const double* gA, const double* gb,
-                               double* gx, double* gW, double* gL, void* stream) {
+static int eec_eval_stamp_bwd_noalloc_body(eec_ctx* c, const double* x, const double* gA, const double* gb,
+                                           double* gx, double* gW, double* gL, void* stream) {
   int rc = check_built(c);
   if (rc) return rc;
   if (!x || !gA || !gb || !gx || !gW || !gL) return fail(c, EEC_EINVAL, "NULL argument");
@@ -1860,8 +2047,16 @@ int eec_eval_stamp_bwd_noalloc(eec_ctx* c, const double* x, const double* gA, co
   CUDA_TRY(c, launch_bwd_noalloc(c->d, x, gA, gb, gx, gW, gL, static_cast<cudaStream_t>(stream)));
   return EEC_OK;
 }
+int eec_eval_stamp_bwd_noalloc(eec_ctx* c, const double* x, const double* gA, const double* gb,
+                               double* gx, double* gW, double* gL, void* stream) {
+  try {
+    return eec_eval_stamp_bwd_noalloc_body(c, x, gA, gb, gx, gW, gL, stream);
+  } catch (...) {
+    return abi_exception(c);
+  }
+}
 
-int eec_graph_capture(eec_ctx* c, const double* x, double* A, double* b, double* q, void* stream) {
+static int eec_graph_capture_body(eec_ctx* c, const double* x, double* A, double* b, double* q, void* stream) {
   int rc = check_built(c);
   if (rc) return rc;
   if (!x || !A || !b) return fail(c, EEC_EINVAL, "NULL x, A or b");
@@ -1871,9 +2066,16 @@ int eec_graph_capture(eec_ctx* c, const double* x, double* A, double* b, double*
   if (stream) CUDA_TRY(c, cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
   return capture(c, effective_variant(c), x, A, b, q, &c->user_exec, &c->user_kernels);
 }
+int eec_graph_capture(eec_ctx* c, const double* x, double* A, double* b, double* q, void* stream) {
+  try {
+    return eec_graph_capture_body(c, x, A, b, q, stream);
+  } catch (...) {
+    return abi_exception(c);
+  }
+}
 
-int eec_batch_create(eec_ctx** out, int32_t n_circ, const eec_netlist* const* nets,
-                     double gshunt, const eec_options* opt) {
+static int eec_batch_create_body(eec_ctx** out, int32_t n_circ, const eec_netlist* const* nets,
+                                 double gshunt, const eec_options* opt) {
   if (!out) return EEC_EINVAL;
   *out = nullptr;
   if (n_circ < 1 || !nets) return EEC_EINVAL;
@@ -1892,16 +2094,31 @@ int eec_batch_create(eec_ctx** out, int32_t n_circ, const eec_netlist* const* ne
   *out = c;
   return EEC_OK;
 }
+int eec_batch_create(eec_ctx** out, int32_t n_circ, const eec_netlist* const* nets,
+                     double gshunt, const eec_options* opt) {
+  try {
+    return eec_batch_create_body(out, n_circ, nets, gshunt, opt);
+  } catch (...) {
+    return abi_exception(nullptr);
+  }
+}
 
-int eec_batch_capture_graph(eec_ctx* c, void* stream) {
+static int eec_batch_capture_graph_body(eec_ctx* c, void* stream) {
   if (!c) return EEC_EINVAL;
   // no launch of the context may be in flight on the caller's stream while the mode changes
   if (stream) CUDA_TRY(c, cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
   c->graph_all = true;
   return EEC_OK;
 }
+int eec_batch_capture_graph(eec_ctx* c, void* stream) {
+  try {
+    return eec_batch_capture_graph_body(c, stream);
+  } catch (...) {
+    return abi_exception(c);
+  }
+}
 
-int eec_graph_launch(eec_ctx* c, void* stream) {
+static int eec_graph_launch_body(eec_ctx* c, void* stream) {
   int rc = check_built(c);
   if (rc) return rc;
   if (!c->user_exec) return fail(c, EEC_ESTATE, "no graph captured");
@@ -1909,8 +2126,15 @@ int eec_graph_launch(eec_ctx* c, void* stream) {
   c->n_kernels += c->user_kernels;
   return EEC_OK;
 }
+int eec_graph_launch(eec_ctx* c, void* stream) {
+  try {
+    return eec_graph_launch_body(c, stream);
+  } catch (...) {
+    return abi_exception(c);
+  }
+}
 
-int eec_profile_enable(eec_ctx* c, int32_t enable) {
+static int eec_profile_enable_body(eec_ctx* c, int32_t enable) {
   if (!c) return EEC_EINVAL;
   if (c->prof && !enable && c->ev_used) cudaDeviceSynchronize();
   c->prof = enable != 0;
@@ -1918,9 +2142,16 @@ int eec_profile_enable(eec_ctx* c, int32_t enable) {
   c->prof_calls = 0;
   return EEC_OK;
 }
+int eec_profile_enable(eec_ctx* c, int32_t enable) {
+  try {
+    return eec_profile_enable_body(c, enable);
+  } catch (...) {
+    return abi_exception(c);
+  }
+}
 
-int eec_profile_read(eec_ctx* c, double* ms_init, double* ms_eval, double* ms_stamp,
-                     int64_t* n_calls, int64_t* n_kernels) {
+static int eec_profile_read_body(eec_ctx* c, double* ms_init, double* ms_eval, double* ms_stamp,
+                                 int64_t* n_calls, int64_t* n_kernels) {
   if (!c) return EEC_EINVAL;
   double t[3] = {0.0, 0.0, 0.0};
   if (c->ev_used) {
@@ -1944,9 +2175,17 @@ int eec_profile_read(eec_ctx* c, double* ms_init, double* ms_eval, double* ms_st
   c->n_kernels = 0;
   return EEC_OK;
 }
+int eec_profile_read(eec_ctx* c, double* ms_init, double* ms_eval, double* ms_stamp,
+                     int64_t* n_calls, int64_t* n_kernels) {
+  try {
+    return eec_profile_read_body(c, ms_init, ms_eval, ms_stamp, n_calls, n_kernels);
+  } catch (...) {
+    return abi_exception(c);
+  }
+}
 
-int eec_autotune(eec_ctx* c, const double* x, double* A, double* b, double* q, int32_t reps,
-                 void* stream, float* ms_out) {
+static int eec_autotune_body(eec_ctx* c, const double* x, double* A, double* b, double* q, int32_t reps,
+                             void* stream, float* ms_out) {
   int rc = check_built(c);
   if (rc) return rc;
   if (!x || !A || !b || reps < 1) return fail(c, EEC_EINVAL, "bad autotune arguments");
@@ -2007,16 +2246,31 @@ int eec_autotune(eec_ctx* c, const double* x, double* A, double* b, double* q, i
   c->eval_ordered = best_o;
   return EEC_OK;
 }
+int eec_autotune(eec_ctx* c, const double* x, double* A, double* b, double* q, int32_t reps,
+                 void* stream, float* ms_out) {
+  try {
+    return eec_autotune_body(c, x, A, b, q, reps, stream, ms_out);
+  } catch (...) {
+    return abi_exception(c);
+  }
+}
 
-int eec_get_tuning(const eec_ctx* c, int32_t* variant, int32_t* block, int32_t* eval_order) {
+static int eec_get_tuning_body(const eec_ctx* c, int32_t* variant, int32_t* block, int32_t* eval_order) {
   if (!c) return EEC_EINVAL;
   if (variant) *variant = effective_variant(c);
   if (block) *block = c->opt.block ? c->opt.block : c->tuned_block;
   if (eval_order) *eval_order = (c->eval_nr >= 2 && c->eval_ordered) ? 1 : 0;
   return EEC_OK;
 }
+int eec_get_tuning(const eec_ctx* c, int32_t* variant, int32_t* block, int32_t* eval_order) {
+  try {
+    return eec_get_tuning_body(c, variant, block, eval_order);
+  } catch (...) {
+    return abi_exception(const_cast<eec_ctx*>(c));
+  }
+}
 
-int eec_status(eec_ctx* c, void* stream) {
+static int eec_status_body(eec_ctx* c, void* stream) {
   if (!c) return EEC_EINVAL;
   if (!c->d_status) return fail(c, EEC_ESTATE, "no device state yet");
   CUDA_TRY(c, cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
@@ -2027,16 +2281,31 @@ int eec_status(eec_ctx* c, void* stream) {
   if (st & kStatusNumeric) return fail(c, EEC_ENUMERIC, "non-finite value in an evaluated device");
   return EEC_OK;
 }
+int eec_status(eec_ctx* c, void* stream) {
+  try {
+    return eec_status_body(c, stream);
+  } catch (...) {
+    return abi_exception(c);
+  }
+}
 
-int eec_math_check(int32_t fn, int64_t n, const double* x, double* ours, double* ref,
-                   void* stream) {
+static int eec_math_check_body(int32_t fn, int64_t n, const double* x, double* ours, double* ref,
+                               void* stream) {
   if (fn < 0 || fn > 4 || n < 0 || (n > 0 && (!x || !ours || !ref))) return EEC_EINVAL;
   return math_check(fn, n, x, ours, ref, static_cast<cudaStream_t>(stream)) == cudaSuccess
              ? EEC_OK
              : EEC_ECUDA;
 }
+int eec_math_check(int32_t fn, int64_t n, const double* x, double* ours, double* ref,
+                   void* stream) {
+  try {
+    return eec_math_check_body(fn, n, x, ours, ref, stream);
+  } catch (...) {
+    return abi_exception(nullptr);
+  }
+}
 
-int eec_test_barrier_timeout(eec_ctx* c, const double* x, double* A, double* b, void* stream) {
+static int eec_test_barrier_timeout_body(eec_ctx* c, const double* x, double* A, double* b, void* stream) {
   int rc = check_built(c);
   if (rc) return rc;
   if (!c->colored || c->C < 2) return fail(c, EEC_ESTATE, "needs a coloured context with >= 2 colours");
@@ -2053,9 +2322,16 @@ int eec_test_barrier_timeout(eec_ctx* c, const double* x, double* A, double* b, 
                                 /*absent_block=*/0));
   return EEC_OK;
 }
+int eec_test_barrier_timeout(eec_ctx* c, const double* x, double* A, double* b, void* stream) {
+  try {
+    return eec_test_barrier_timeout_body(c, x, A, b, stream);
+  } catch (...) {
+    return abi_exception(c);
+  }
+}
 
-int eec_lu_check_host(int32_t n, const int32_t* row_ptr, const int32_t* col, const double* a,
-                      const double* b, double* x, int64_t* nnz_lu, int32_t* bad_col) {
+static int eec_lu_check_host_body(int32_t n, const int32_t* row_ptr, const int32_t* col, const double* a,
+                                  const double* b, double* x, int64_t* nnz_lu, int32_t* bad_col) {
   if (n < 1 || !row_ptr || !col || !a || !b || !x) return EEC_EINVAL;
   const std::vector<int> rp(row_ptr, row_ptr + n + 1);
   if (rp[0] != 0) return EEC_EINVAL;
@@ -2065,10 +2341,12 @@ int eec_lu_check_host(int32_t n, const int32_t* row_ptr, const int32_t* col, con
   for (int v : cl)
     if (v < 0 || v >= n) return EEC_EINVAL;
   const std::vector<double> av(a, a + rp[n]), bv(b, b + n);
-  const std::vector<int> q = lu_min_degree_order(n, rp, cl);
+  std::vector<int> q;
+  if (!lu_min_degree_order(n, rp, cl, q)) return EEC_ENOMEM;
   LuPlan P;
   std::string err;
-  if (!lu_analyze(n, rp, cl, av, q, P, err)) return EEC_ENUMERIC;
+  const int rc = lu_analyze(n, rp, cl, av, q, P, err);
+  if (rc) return rc;
   std::vector<double> xv;
   int bad = -1;
   lu_refactor_solve_host(P, av, bv, kLuTiny, xv, &bad);
@@ -2077,8 +2355,16 @@ int eec_lu_check_host(int32_t n, const int32_t* row_ptr, const int32_t* col, con
   if (bad_col) *bad_col = bad;
   return EEC_OK;
 }
+int eec_lu_check_host(int32_t n, const int32_t* row_ptr, const int32_t* col, const double* a,
+                      const double* b, double* x, int64_t* nnz_lu, int32_t* bad_col) {
+  try {
+    return eec_lu_check_host_body(n, row_ptr, col, a, b, x, nnz_lu, bad_col);
+  } catch (...) {
+    return abi_exception(nullptr);
+  }
+}
 
-int eec_lu_solve(eec_ctx* c, const double* A, const double* b, double* x, void* stream) {
+static int eec_lu_solve_body(eec_ctx* c, const double* A, const double* b, double* x, void* stream) {
   NvtxRange range("eec/lu_solve");
   int rc = check_built(c);
   if (rc) return rc;
@@ -2087,23 +2373,51 @@ int eec_lu_solve(eec_ctx* c, const double* A, const double* b, double* x, void* 
   if ((rc = newton_common(c))) return rc;
   return lu_factor_solve(c, A, b, x, 1, static_cast<cudaStream_t>(stream));
 }
+int eec_lu_solve(eec_ctx* c, const double* A, const double* b, double* x, void* stream) {
+  try {
+    return eec_lu_solve_body(c, A, b, x, stream);
+  } catch (...) {
+    return abi_exception(c);
+  }
+}
 
-int eec_lu_stats(const eec_ctx* c, int64_t* nnz_lu, int32_t* analyses) {
+static int eec_lu_stats_body(const eec_ctx* c, int64_t* nnz_lu, int32_t* analyses) {
   if (!c) return EEC_EINVAL;
   if (nnz_lu) *nnz_lu = c->lu_ready ? c->lu.cptr[c->lu.n] : 0;
   if (analyses) *analyses = c->lu_analyses;
   return EEC_OK;
 }
+int eec_lu_stats(const eec_ctx* c, int64_t* nnz_lu, int32_t* analyses) {
+  try {
+    return eec_lu_stats_body(c, nnz_lu, analyses);
+  } catch (...) {
+    return abi_exception(const_cast<eec_ctx*>(c));
+  }
+}
 
-int eec_newton_info(const eec_ctx* c, int32_t* info) {
+static int eec_newton_info_body(const eec_ctx* c, int32_t* info) {
   if (!c || !info) return EEC_EINVAL;
   for (int k = 0; k < 4; ++k) info[k] = c->newton_info[k];
   return EEC_OK;
 }
+int eec_newton_info(const eec_ctx* c, int32_t* info) {
+  try {
+    return eec_newton_info_body(c, info);
+  } catch (...) {
+    return abi_exception(const_cast<eec_ctx*>(c));
+  }
+}
 
-int eec_fp64_peak(int32_t iters, int32_t blocks_per_sm, double* flops) {
+static int eec_fp64_peak_body(int32_t iters, int32_t blocks_per_sm, double* flops) {
   if (iters < 1 || blocks_per_sm < 1 || !flops) return EEC_EINVAL;
   return fp64_peak(iters, blocks_per_sm, flops) == cudaSuccess ? EEC_OK : EEC_ECUDA;
+}
+int eec_fp64_peak(int32_t iters, int32_t blocks_per_sm, double* flops) {
+  try {
+    return eec_fp64_peak_body(iters, blocks_per_sm, flops);
+  } catch (...) {
+    return abi_exception(nullptr);
+  }
 }
 
 }  // extern "C"

@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "eec_internal.h"
+#include "eec_lu.h"
 
 namespace eec {
 
@@ -37,7 +38,18 @@ namespace eec {
 // eliminate a node of least current degree (ties: the lowest index) and join its remaining
 // neighbours into a clique, as elimination does. Explicit adjacency; the netlists this serves
 // have small degrees away from the rails, which the rule leaves to the end.
-std::vector<int> lu_min_degree_order(int n, const std::vector<int>& rp, const std::vector<int>& col) {
+long long lu_entry_budget(long long nnz) { return 32 * nnz + (4LL << 20); }
+
+// The update list (one entry per multiply-add of the factorisation) of a pattern of nnz entries
+// may hold 128 nnz + 16 Mi entries (the 256 x 256 SRAM: 39 nnz, from the dense block its word
+// and bit lines leave at the end of the order), and at most what 32-bit offsets address.
+static long long lu_update_budget(long long nnz) {
+  return std::min<long long>(128 * nnz + (16LL << 20), 0x7fffffffLL);
+}
+
+bool lu_min_degree_order(int n, const std::vector<int>& rp, const std::vector<int>& col,
+                         std::vector<int>& order) {
+  const long long budget = lu_entry_budget(rp[n]);
   std::vector<std::vector<int>> adj(n);
   for (int i = 0; i < n; ++i)
     for (int e = rp[i]; e < rp[i + 1]; ++e) {
@@ -51,8 +63,12 @@ std::vector<int> lu_min_degree_order(int n, const std::vector<int>& rp, const st
     a.erase(std::unique(a.begin(), a.end()), a.end());
   }
   std::set<std::pair<int, int>> by_deg;   // (degree, node) of the nodes not yet eliminated
-  for (int i = 0; i < n; ++i) by_deg.insert({(int)adj[i].size(), i});
-  std::vector<int> order;
+  long long total = 0;                      // entries of the elimination graph
+  for (int i = 0; i < n; ++i) {
+    by_deg.insert({(int)adj[i].size(), i});
+    total += (long long)adj[i].size();
+  }
+  order.clear();
   order.reserve(n);
   std::vector<int> merged;
   while (!by_deg.empty()) {
@@ -61,8 +77,10 @@ std::vector<int> lu_min_degree_order(int n, const std::vector<int>& rp, const st
     order.push_back(v);
     const std::vector<int> nb = std::move(adj[v]);
     adj[v].clear();
+    total -= (long long)nb.size();
     for (int a : nb) {
       by_deg.erase({(int)adj[a].size(), a});
+      total -= (long long)adj[a].size();
       // adj[a] := (adj[a] without v) joined with the other neighbours of v
       merged.clear();
       std::set_union(adj[a].begin(), adj[a].end(), nb.begin(), nb.end(), std::back_inserter(merged));
@@ -71,19 +89,27 @@ std::vector<int> lu_min_degree_order(int n, const std::vector<int>& rp, const st
                    merged.end());
       adj[a].swap(merged);
       by_deg.insert({(int)adj[a].size(), a});
+      total += (long long)adj[a].size();
+    }
+    if (total > budget) {   // the fill of this pattern outgrows any useful factor
+      order.clear();
+      return false;
     }
   }
-  return order;
+  return true;
 }
 
 constexpr double kLuDiagPref = 1e-3;
 
 // Left-looking LU with threshold partial pivoting of B = A(:, q) (A in CSR, symmetric pattern
-// not required); plan out. Returns false (with err) for a numerically singular column.
-bool lu_analyze(int n, const std::vector<int>& rp, const std::vector<int>& col,
-                const std::vector<double>& a, const std::vector<int>& q, LuPlan& P,
-                std::string& err) {
+// not required); plan out. Returns 0, EEC_ENUMERIC for a numerically singular column or
+// EEC_ENOMEM when the factor or its update list outgrows lu_entry_budget (err set).
+int lu_analyze(int n, const std::vector<int>& rp, const std::vector<int>& col,
+               const std::vector<double>& a, const std::vector<int>& q, LuPlan& P,
+               std::string& err) {
   const int nnz = rp[n];
+  const long long budget = lu_entry_budget(nnz), update_budget = lu_update_budget(nnz);
+  long long n_factor = 0;   // entries of L and U so far
   // CSC of A: column c lists (row, CSR position)
   std::vector<int> cp(n + 1, 0), ci(nnz), cpos(nnz);
   for (int e = 0; e < nnz; ++e) cp[col[e] + 1]++;
@@ -163,7 +189,7 @@ bool lu_analyze(int n, const std::vector<int>& rp, const std::vector<int>& col,
     if (piv < 0 || !(best > 0.0) || !std::isfinite(best)) {
       err = "sparse LU: matrix singular at column " + std::to_string(j);
       for (int i : pat) { x[i] = 0.0; mark[i] = 0; }
-      return false;
+      return EEC_ENUMERIC;
     }
     if (pinv[c] < 0 && mark[c] && std::fabs(x[c]) >= kLuDiagPref * best) piv = c;
     const double pv = x[piv];
@@ -176,6 +202,12 @@ bool lu_analyze(int n, const std::vector<int>& rp, const std::vector<int>& col,
       mark[i] = 0;
     }
     std::sort(Uk[j].begin(), Uk[j].end());
+    n_factor += (long long)Uk[j].size() + 1 + (long long)Lc[j].size();
+    if (n_factor > budget) {
+      err = "sparse LU: the factor of this pattern would exceed " + std::to_string(budget) +
+            " entries (32 per nonzero of A plus 4 Mi): too much fill for a direct solve";
+      return EEC_ENOMEM;
+    }
   }
   // plan: column storage of P A Q (rows in pivot-step numbering)
   P.n = n;
@@ -216,7 +248,7 @@ bool lu_analyze(int n, const std::vector<int>& rp, const std::vector<int>& col,
       P.a2lu[e] = find(pinv[i], qinv[col[e]]);
       if (P.a2lu[e] < 0) {
         err = "sparse LU: an entry of A outside the factor pattern";
-        return false;
+        return EEC_ENUMERIC;
       }
     }
   // updates of column j: for every k of U(:, j) (ascending), the entries of L(:, k) go to the
@@ -236,10 +268,15 @@ bool lu_analyze(int n, const std::vector<int>& rp, const std::vector<int>& col,
         const int d = find(P.crow[s], j);
         if (d < 0) {
           err = "sparse LU: an update outside the factor pattern";
-          return false;
+          return EEC_ENUMERIC;
         }
         P.msrc.push_back(s);
         P.mdst.push_back(d);
+      }
+      if ((long long)P.msrc.size() > update_budget) {
+        err = "sparse LU: the update list of this pattern would exceed " +
+              std::to_string(update_budget) + " entries: too much fill for a direct solve";
+        return EEC_ENOMEM;
       }
       P.mptr.push_back((int)P.msrc.size());
     }
@@ -265,7 +302,7 @@ bool lu_analyze(int n, const std::vector<int>& rp, const std::vector<int>& col,
     P.lrptr[r + 1] = (int)P.lrcol.size();
     P.urptr[r + 1] = (int)P.urcol.size();
   }
-  return true;
+  return 0;
 }
 
 // The GPU's refactorisation and substitutions executed on the host in the same order (column by

@@ -95,3 +95,16 @@ def test_singular_and_malformed_inputs_are_rejected(eec):
     with pytest.raises(eec.EECError) as e:
         eec.eec_lu_check_host(np.array([0, 1, 2]), np.array([0, 5]), np.ones(2), np.ones(2))
     assert e.value.code == eec.EEC_EINVAL
+
+
+def test_too_much_fill_is_refused_before_memory_runs_out(eec):
+    # randomly wired logic has no good elimination order: its factor would fill towards a dense
+    # matrix (a 20,000-gate netlist: ~36,000 unknowns). The analysis stops at its entry budget
+    # and reports EEC_ENOMEM within a second instead of exhausting host memory.
+    import time
+    rp, col, A, b = _system(netgen.random_logic(20_000, seed=3))
+    t0 = time.perf_counter()
+    with pytest.raises(eec.EECError) as e:
+        eec.eec_lu_check_host(rp, col, A, b)
+    assert e.value.code == eec.EEC_ENOMEM
+    assert time.perf_counter() - t0 < 30
