@@ -135,6 +135,7 @@ struct eec_ctx {
   double* lu_dbuf = nullptr;    // factor values, work vector and inverse diagonal
   size_t lu_dcap = 0;
   int* lu_flag = nullptr;
+  int* lu_gwork = nullptr;      // progress words and barrier of the multi-block LU kernel
   std::vector<cudaEvent_t> hev;  // chunk done (K) + side stream done (1) + start of the chunks (1)
 };
 
@@ -226,6 +227,8 @@ void free_topology(eec_ctx* c) {
   if (c->lu_ibuf) cudaFree(c->lu_ibuf);
   if (c->lu_dbuf) cudaFree(c->lu_dbuf);
   if (c->lu_flag) cudaFree(c->lu_flag);
+  if (c->lu_gwork) cudaFree(c->lu_gwork);
+  c->lu_gwork = nullptr;
   c->lu_ibuf = nullptr;
   c->lu_dbuf = nullptr;
   c->lu_flag = nullptr;
@@ -1667,6 +1670,11 @@ int lu_prepare(eec_ctx* c, const double* A, cudaStream_t s) {
   }
   if (!c->lu_flag && cudaMalloc(&c->lu_flag, 3 * sizeof(int)) != cudaSuccess)
     return fail(c, EEC_ENOMEM, "sparse LU: out of memory");
+  if (!c->lu_gwork) {
+    const int words = lu_grid_words();
+    if (words > 0 && cudaMalloc(&c->lu_gwork, sizeof(int) * (size_t)words) != cudaSuccess)
+      return fail(c, EEC_ENOMEM, "sparse LU: out of memory");
+  }
   CUDA_TRY(c, cudaMemcpyAsync(c->lu_ibuf, packed.data(), sizeof(int) * packed.size(),
                               cudaMemcpyHostToDevice, s));
   CUDA_TRY(c, cudaStreamSynchronize(s));   // the host vector dies with this call
@@ -1681,6 +1689,7 @@ int lu_prepare(eec_ctx* c, const double* A, cudaStream_t s) {
   d.vals = c->lu_dbuf;
   d.y = d.vals + d.nnz_lu;
   d.flag = c->lu_flag;
+  d.gwork = c->lu_gwork;
   c->lu = std::move(P);
   c->lud = d;
   c->lu_ready = true;

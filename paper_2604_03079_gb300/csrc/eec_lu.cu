@@ -522,6 +522,216 @@ __global__ void __launch_bounds__(kLuWarps * 32, 1) k_lu_factor_solve(LuDev L, c
   for (int i = threadIdx.x; i < L.n; i += blockDim.x) x[i] += d[i];
 }
 
+// ---- the same on every SM: one cooperative kernel ------------------------------------------
+//
+// When the factor does not fit in one block's shared memory it lives in global memory, and the
+// single block's 32 warps spend most of their time waiting for L2 (the 256 x 256 SRAM: 75 ms per
+// solve). Here the columns (rows in the substitutions) are dealt round robin to every warp of a
+// co-resident grid; a warp publishes its progress in global memory (a fence, then a release
+// store), waiters poll it with acquire loads, and grid barriers separate the phases. Values that
+// other SMs write (the factor, the inverse diagonal, the work vectors, x) are read and written
+// through L2 only (.cg), so no SM reads a stale line from its L1. All waits are bounded as in the
+// single-block kernel; after one gives up, every later wait returns at once and the host reports
+// the timeout.
+constexpr int kLuGridBlock = 256;
+constexpr int kLuGridBar = 8;   // gwork[0..1]: barrier count and generation; progress from 8
+
+__device__ __forceinline__ int lu_ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void lu_st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ bool lu_gwait(const int* prog, int W, int k, int* flag) {
+  long long spins = 0;
+  while (lu_ld_acquire(prog + (k % W)) <= k) {
+    if (*((volatile int*)(flag + 1))) return false;
+    if (++spins > kLuSpinLimit) {
+      atomicExch(flag + 1, 1);
+      return false;
+    }
+  }
+  return true;
+}
+
+// Bounded grid barrier (every block of the co-resident grid calls it the same number of times).
+__device__ __forceinline__ void lu_grid_sync(int* bar, int* flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const int gen = lu_ld_acquire(bar + 1);
+    if (atomicAdd(bar, 1) == (int)gridDim.x - 1) {
+      atomicExch(bar, 0);
+      __threadfence();
+      lu_st_release(bar + 1, gen + 1);
+    } else {
+      long long spins = 0;
+      while (lu_ld_acquire(bar + 1) == gen) {
+        if (*((volatile int*)(flag + 1))) break;
+        if (++spins > kLuSpinLimit) {
+          atomicExch(flag + 1, 1);
+          break;
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Row-times-vector of the substitutions (as lu_row_dot), all values through L2.
+__device__ __forceinline__ double lu_grow_dot(const int* __restrict__ cols, const int* __restrict__ pos,
+                                              int p0, int p1, const double* v, const double* u,
+                                              const int* prog, int W, int* flag, bool reversed,
+                                              int n) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  if (p1 - p0 <= 4) {
+    if (lane == 0)
+      for (int p = p0; p < p1; ++p) {
+        const int c = __ldg(cols + p);
+        lu_gwait(prog, W, reversed ? n - 1 - c : c, flag);
+        s = fma(__ldcg(v + __ldg(pos + p)), __ldcg(u + c), s);
+      }
+    return s;   // meaningful in lane 0
+  }
+  for (int p = p0 + lane; p < p1; p += 32) {
+    const int c = __ldg(cols + p);
+    lu_gwait(prog, W, reversed ? n - 1 - c : c, flag);
+    s = fma(__ldcg(v + __ldg(pos + p)), __ldcg(u + c), s);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  return s;
+}
+
+__device__ __forceinline__ void lu_gsubstitute(const LuDev& L, const double* v, const double* dinv,
+                                               double* y, int* prog, int* bar, int W, int gw,
+                                               const double* b, double* x) {
+  const int lane = threadIdx.x & 31;
+  const int n = L.n;
+  if (lane == 0) lu_st_release(prog + gw, gw);
+  lu_grid_sync(bar, L.flag);
+  for (int r = gw; r < n; r += W) {
+    const double s = lu_grow_dot(L.lrcol, L.lrpos, __ldg(L.lrptr + r), __ldg(L.lrptr + r + 1), v,
+                                 y, prog, W, L.flag, false, n);
+    if (lane == 0) {
+      __stcg(y + r, __ldcg(b + __ldg(L.prow + r)) - s);
+      __threadfence();
+      lu_st_release(prog + gw, r + W);
+    }
+    __syncwarp();
+  }
+  lu_grid_sync(bar, L.flag);
+  if (lane == 0) lu_st_release(prog + gw, gw);
+  lu_grid_sync(bar, L.flag);
+  for (int m = gw; m < n; m += W) {
+    const int r = n - 1 - m;
+    const double s = lu_grow_dot(L.urcol, L.urpos, __ldg(L.urptr + r), __ldg(L.urptr + r + 1), v,
+                                 y, prog, W, L.flag, true, n);
+    if (lane == 0) {
+      __stcg(y + r, (__ldcg(y + r) - s) * __ldcg(dinv + r));
+      __threadfence();
+      lu_st_release(prog + gw, m + W);
+    }
+    __syncwarp();
+  }
+  lu_grid_sync(bar, L.flag);
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x)
+    __stcg(x + __ldg(L.pcol + r), __ldcg(y + r));
+}
+
+__global__ void __launch_bounds__(kLuGridBlock, 4) k_lu_factor_solve_grid(LuDev L,
+                                                                       const double* __restrict__ A,
+                                                                       const int* __restrict__ rp,
+                                                                       const int* __restrict__ col,
+                                                                       const double* __restrict__ b,
+                                                                       double* x, double tiny,
+                                                                       int refine) {
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * (kLuGridBlock / 32) + (threadIdx.x >> 5);
+  const int W = gridDim.x * (kLuGridBlock / 32);
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x, GT = gridDim.x * blockDim.x;
+  int* bar = L.gwork;
+  int* prog = L.gwork + kLuGridBar;
+  double* v = L.vals;
+  double* y = L.y;
+  double* dinv = L.y + L.n;
+  if (lane == 0) lu_st_release(prog + gw, gw);
+  for (int p = gt; p < L.nnz_lu; p += GT) __stcg(v + p, 0.0);
+  lu_grid_sync(bar, L.flag);
+  for (int e = gt; e < L.nnz_a; e += GT) __stcg(v + __ldg(L.a2lu + e), __ldg(A + e));
+  lu_grid_sync(bar, L.flag);
+  for (int j = gw; j < L.n; j += W) {
+    const int t1 = __ldg(L.uptr + j + 1);
+    for (int t = __ldg(L.uptr + j); t < t1; ++t) {
+      const int k = __ldg(L.uk + t);
+      if (lane == 0) lu_gwait(prog, W, k, L.flag);
+      __syncwarp();   // orders lane 0's observation before every lane's loads of column k
+      const double ukj = __ldcg(v + __ldg(L.upos + t));
+      const int m1 = __ldg(L.mptr + t + 1);
+      for (int m = __ldg(L.mptr + t) + lane; m < m1; m += 32) {
+        const int d = __ldg(L.mdst + m);
+        __stcg(v + d, fma(-__ldcg(v + __ldg(L.msrc + m)), ukj, __ldcg(v + d)));
+      }
+      __threadfence_block();
+      __syncwarp();
+    }
+    const int pd = __ldg(L.cdiag + j), p1 = __ldg(L.cptr + j + 1);
+    const double inv = lu_rcp(__ldcg(v + pd));
+    for (int p = pd + 1 + lane; p < p1; p += 32) __stcg(v + p, __ldcg(v + p) * inv);
+    if (lane == 0) __stcg(dinv + j, inv);
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) lu_st_release(prog + gw, j + W);
+  }
+  lu_grid_sync(bar, L.flag);
+  const double lim = 1.0 / tiny;
+  for (int j = gt; j < L.n; j += GT) {
+    const double di = __ldcg(dinv + j);
+    if (!isfinite(di) || di == 0.0) {
+      atomicCAS(L.flag + 2, 0, j + 1);
+      continue;
+    }
+    bool bad = false;
+    for (int p = __ldg(L.cdiag + j) + 1; p < __ldg(L.cptr + j + 1) && !bad; ++p)
+      bad = !(fabs(__ldcg(v + p)) < lim);
+    if (bad) atomicCAS(L.flag, 0, j + 1);
+  }
+  lu_gsubstitute(L, v, dinv, y, prog, bar, W, gw, b, x);
+  if (!refine) return;
+  lu_grid_sync(bar, L.flag);
+  double* r = L.y + 2 * L.n;   // residual, then the correction
+  for (int i = gt; i < L.n; i += GT) {
+    double s = __ldg(b + i);
+    const int e1 = __ldg(rp + i + 1);
+    for (int e = __ldg(rp + i); e < e1; ++e) s = fma(-__ldg(A + e), __ldcg(x + __ldg(col + e)), s);
+    __stcg(r + i, s);
+  }
+  lu_grid_sync(bar, L.flag);
+  double* d = r + L.n;
+  lu_gsubstitute(L, v, dinv, y, prog, bar, W, gw, r, d);
+  lu_grid_sync(bar, L.flag);
+  for (int i = gt; i < L.n; i += GT) __stcg(x + i, __ldcg(x + i) + __ldcg(d + i));
+}
+
+// Blocks of the cooperative grid on this device (0 until the first query).
+int lu_grid_blocks() {
+  static int blocks = 0;
+  if (!blocks) {
+    int dev = 0, nsm = 0, occ = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lu_factor_solve_grid, kLuGridBlock,
+                                                      0) != cudaSuccess)
+      return 0;
+    blocks = nsm * std::min(occ, 4);
+  }
+  return blocks;
+}
+
 }  // namespace
 
 size_t lu_smem_bytes(const LuDev& L) { return sizeof(double) * ((size_t)L.nnz_lu + 2 * (size_t)L.n); }
@@ -539,6 +749,23 @@ cudaError_t launch_lu_factor_solve(const LuDev& L, const double* A, const int* r
   const size_t fixed = sizeof(int) * kLuWarps;
   const int smem = need + fixed <= (size_t)max_optin ? 1 : 0;
   const size_t dyn = smem ? need : 0;
+  const int grid = smem ? 0 : lu_grid_blocks();
+  if (grid > 0 && L.gwork) {
+    // the factor in global memory: the cooperative kernel over every SM (co-resident blocks,
+    // or the launch fails), its barrier and progress words cleared first
+    const int W = grid * (kLuGridBlock / 32);
+    e = cudaMemsetAsync(L.gwork, 0, sizeof(int) * (size_t)(kLuGridBar + W), s);
+    if (e != cudaSuccess) return e;
+    LuDev Lc = L;
+    const double* pA = A;
+    const int* prp = rp;
+    const int* pcol = col;
+    const double* pb = b;
+    double* px = x;
+    void* args[] = {&Lc, &pA, &prp, &pcol, &pb, &px, &tiny, &refine};
+    return cudaLaunchCooperativeKernel((const void*)k_lu_factor_solve_grid, dim3(grid),
+                                       dim3(kLuGridBlock), args, 0, s);
+  }
   if (smem) {
     e = cudaFuncSetAttribute(k_lu_factor_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)dyn);
@@ -546,6 +773,14 @@ cudaError_t launch_lu_factor_solve(const LuDev& L, const double* A, const int* r
   }
   k_lu_factor_solve<<<1, kLuWarps * 32, dyn, s>>>(L, A, rp, col, b, x, tiny, smem, refine);
   return cudaGetLastError();
+}
+
+int lu_grid_words() {
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 0;
+  return kLuGridBar + 32 * nsm;   // up to 4 blocks of 8 warps per SM
 }
 
 }  // namespace eec

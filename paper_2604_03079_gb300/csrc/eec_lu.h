@@ -32,7 +32,11 @@ struct LuDev {
   double* y;     // [4n] work vector and inverse diagonal (when the factor is not in shared
                  // memory), then the refinement's residual and correction
   int* flag;
+  int* gwork;    // [lu_grid_words()] progress words and barrier of the multi-block kernel
 };
+// Words of LuDev::gwork: a grid barrier and one progress word per warp of the largest grid the
+// multi-block kernel launches on this device.
+int lu_grid_words();
 // Entries the host analysis may create for a pattern of nnz entries in the order's elimination
 // graph and in the factor: 32 nnz + 4 Mi (its update list has a budget of its own, in
 // eec_lu.cu). Circuit matrices with locality stay far below (the 256 x 256 SRAM: 1.2 nnz);
@@ -53,7 +57,8 @@ bool lu_refactor_solve_host(const LuPlan& P, const std::vector<double>& a,
                             const std::vector<double>& b, double tiny, std::vector<double>& x,
                             int* bad_col);
 // Refactor A (CSR values, pattern rp/col) on the plan and solve A x = b, with refine one step of
-// iterative refinement, in one single-block kernel (the factor in shared memory when it fits).
+// iterative refinement: in one single-block kernel when the factor fits in shared memory, else in
+// one cooperative kernel over every SM (the factor in global memory).
 cudaError_t launch_lu_factor_solve(const LuDev& L, const double* A, const int* rp, const int* col,
                                    const double* b, double* x, double tiny, int refine,
                                    cudaStream_t s);
