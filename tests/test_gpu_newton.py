@@ -166,3 +166,23 @@ def test_long_chain_converges_through_the_relaxation_start(eec, n_stages, rail_m
     _, _, unk = circ.pattern()
     v = xh[unk[3:3 + n_stages]]            # stage outputs: nodes 3, 4, ... (0 ground, 1 vdd, 2 in)
     assert np.abs(v - (np.arange(n_stages) % 2 == 0)).max() < 0.05
+
+
+def test_sram_dc_point_through_the_multi_block_lu(eec):
+    # the 64 x 64 SRAM's factor (78,080 entries) does not fit in one block's shared memory, so
+    # every solve runs the cooperative kernel over all SMs; plain Newton and gshunt stepping from
+    # x = 0 fail on the array of bistable cells and the relaxation start hands Newton a point
+    # from which it converges. The oracle's dense LU is too slow at 8,384 unknowns, so its
+    # model checks the result: its KCL residual at the returned point is at rounding level.
+    import torch
+    net = netgen.sram(64, 64)
+    circ = eec.Circuit(net, CARDS, variant=2)
+    x = torch.zeros(circ.n, dtype=torch.float64, device="cuda")
+    A, b, _ = circ.new_outputs(want_q=False)
+    it = eec.eec_newton_dc(circ.ctx, x, A, b, max_iter=100, step_rule=1, solver=eec.EEC_SOLVER_LU)
+    info = eec.eec_newton_info(circ.ctx)
+    assert circ.status() == 0 and it == info["solves"] >= 1
+    nnz_lu, _ = eec.eec_lu_stats(circ.ctx)
+    assert 8 * nnz_lu > 227 * 1024            # the factor lives in global memory
+    F = oracle.Oracle(net, CARDS).kcl_residual(x.cpu().numpy())
+    assert np.abs(F).max() <= 1e-11
