@@ -252,7 +252,8 @@ EEC_API int eec_eval_stamp_host(eec_ctx* ctx, const double* x_host, double* A_ho
  * on the host, once per context, a minimum-degree column order and one factorisation of the
  * first iterate's matrix with threshold partial pivoting fix the row pivots and the patterns of
  * L and U; every iteration then refactors the numbers on that pattern and solves on the GPU
- * (one single-block kernel, with one step of iterative refinement once the steps are below
+ * (one single-block kernel when the factor fits in shared memory, else one cooperative kernel
+ * over every SM; with one step of iterative refinement once the steps are below
  * 1 mV), and analyses again on the host if a pivot falls below 1e-4 of the
  * largest entry of its column (1e-10 for the unrefined solves of steps above 1 mV;
  * eec_lu_stats counts the analyses) — then
@@ -267,7 +268,8 @@ EEC_API int eec_eval_stamp_host(eec_ctx* ctx, const double* x_host, double* A_ho
  * gshunt, then the circuit itself (each stage with max_iter solves). When that fails too, a
  * relaxation start: from the starting point, nonlinear Jacobi sweeps (every node moves to the
  * zero of its own KCL residual with the other voltages held, the move clipped to 5 vstep; up to
- * min(4 n + 1024, 65536) sweeps, until no node moved more than 1 uV in 32 sweeps), then Newton
+ * min(4 n + 1024, 65536) sweeps, until no node moved more than 1 uV in 32 sweeps or the count of
+ * nodes moving more than 1 mV stopped falling over 128 sweeps), then Newton
  * from the relaxed point, then gshunt stepping from there. A chain of gates settles one stage
  * per sweep; from a poor start Newton's exact step on a long chain grows like the stage gain to
  * the power of its length and overflows. eec_newton_info reports which path converged.
@@ -279,8 +281,10 @@ EEC_API int eec_eval_stamp_host(eec_ctx* ctx, const double* x_host, double* A_ho
  * EEC_ETIMEOUT (a bounded wait of the sparse LU's kernels ran out) or EEC_ENOMEM (solver 2: the
  * pattern fills in too much for a direct solve, as randomly wired logic does: its elimination
  * graph or factor would exceed 32 nnz + 4 Mi entries, or its update list 128 nnz + 16 Mi; the
- * 256 x 256 SRAM needs 1.2 nnz and 39 nnz). Meant for netlists up to tens of thousands of unknowns (solver 0 checks its
- * factor's size before allocating). Synchronises cuda_stream once per iteration.
+ * 256 x 256 SRAM needs 1.2 nnz and 39 nnz). Solvers 0 and 1 are meant for netlists up to tens of
+ * thousands of unknowns (solver 0 checks its factor's size before allocating); solver 2 has
+ * solved the 131,840-unknown SRAM. Synchronises cuda_stream once per iteration (and once per
+ * 32 relaxation sweeps).
  */
 #define EEC_SOLVER_LU 2
 EEC_API int eec_newton_dc(eec_ctx* ctx, double* x_dev, double* A_values_dev, double* b_dev,
