@@ -564,6 +564,30 @@ def newton_study(eec, dev, stream):
                       "lu_stats": eec.eec_lu_stats(c.ctx) if solver == 2 else None, "ms": ms,
                       "ms_per_iteration": ms / max(its, 1), "eval_stamp_ms": ev_ms,
                       "eval_stamp_share": ev_ms * max(its, 1) / ms}
+    # NEXT-1 with the GPU Newton loop: transient runs (trapezoidal, fixed step, sources held)
+    # from every node at 0 V (power-up: the circuit settles, the chain's stages switch one after
+    # another), every step's Newton iterations solved with the library's sparse LU
+    for nname, nn, h, steps in (("ripple_adder_64", netgen.ripple_adder(64), 10e-12, 200),
+                                ("inverter_chain_1024", netgen.inverter_chain(1024, vin=1.0),
+                                 5e-12, 200)):
+        key = f"{nname}_transient_tr"
+        if time.perf_counter() - t_start > 120:
+            out[key] = {"skipped": "time budget of the study used up"}
+            continue
+        c = eec.Circuit(nn, netgen.default_cards(), color=True)
+        xd = torch.zeros(c.n, dtype=torch.float64, device=dev)
+        try:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            its = eec.eec_transient(c.ctx, xd, h, steps, method=1, solver=2)
+            torch.cuda.synchronize()
+        except eec.EECError as e:
+            out[key] = {"error": str(e)}
+            continue
+        ms = (time.perf_counter() - t0) * 1e3
+        out[key] = {"unknowns": c.n, "devices": nn.n_dev, "steps": steps, "h_s": h,
+                    "newton_iterations": its, "ms": ms, "ms_per_iteration": ms / max(its, 1),
+                    "start": "every node at 0 V"}
     return out
 
 

@@ -293,6 +293,45 @@ EEC_API int eec_newton_dc(eec_ctx* ctx, double* x_dev, double* A_values_dev, dou
                           void* cuda_stream);
 
 /*
+ * One implicit time step of a transient analysis (NEXT-1 with the GPU Newton loop of
+ * eec_newton_dc): damped Newton on the companion system of eec_eval_stamp_tran,
+ * F(x) + i_cap(x) = 0 with i_cap = alpha (q(x) - q_prev) - beta i_prev (backward Euler:
+ * alpha = 1/h, beta = 0; trapezoidal: alpha = 2/h, beta = 1), from x (normally the previous time
+ * point). The solvers, step rules and tests are eec_newton_dc's; no gshunt stepping or
+ * relaxation start (a step that does not converge is the caller's cue to shorten h).
+ *  x_dev       [n] in: starting point, out: the last iterate (the new time point when EEC_OK).
+ *  q_prev_dev  [4 n_dev] charges of the previous time point (original device order).
+ *  i_prev_dev  [4 n_dev] (nullable) capacitive currents of the previous time point.
+ *  A_dev, b_dev  workspace, out: the companion stamp at the returned x.
+ *  q_dev, icap_dev  [4 n_dev] out: charges and (icap nullable) capacitive currents at x: the next
+ *              step's q_prev and i_prev.
+ * Returns as eec_newton_dc (EEC_ENOCONV: the step ran max_iter solves).
+ */
+EEC_API int eec_newton_tran(eec_ctx* ctx, double* x_dev, const double* q_prev_dev,
+                            const double* i_prev_dev, double alpha, double beta,
+                            double* A_values_dev, double* b_dev, double* q_dev, double* icap_dev,
+                            int32_t max_iter, double vstep, int32_t step_rule, int32_t solver,
+                            double tol_abs, double tol_rel, double tol_f, int32_t* iters_out,
+                            void* cuda_stream);
+
+/*
+ * A transient analysis of n_steps fixed steps of h seconds from the state x (the sources held at
+ * their values, as in the oracle's transient solver): the charges at t = 0, then eec_newton_tran
+ * per step with method 0 (backward Euler) or 1 (trapezoidal; the first step's history current
+ * is zero). Context-owned device buffers (allocated on the first call) hold A, b and two time
+ * points' charges and capacitive currents.
+ *  x_dev     [n] in: the state at t = 0, out: the state at t = n_steps h (or at the failed step).
+ *  traj_dev  [(n_steps + 1) n] (nullable) out: the state at every time point, row by row.
+ *  iters_out (nullable) Newton iterations over all steps.
+ * Returns EEC_OK, EEC_EINVAL, EEC_ENOCONV (a step did not converge; the message names it), or
+ * eec_newton_dc's other codes. Synchronises cuda_stream once per Newton iteration.
+ */
+EEC_API int eec_transient(eec_ctx* ctx, double* x_dev, double h, int32_t n_steps, int32_t method,
+                          double* traj_dev, int32_t max_iter, double vstep, int32_t step_rule,
+                          int32_t solver, double tol_abs, double tol_rel, double tol_f,
+                          int32_t* iters_out, void* cuda_stream);
+
+/*
  * The last eec_newton_dc call on this context: info[0] = solves (as iters_out), info[1] = gshunt
  * stepping stages run, info[2] = relaxation sweeps, info[3] = the path that ended the call:
  * 0 plain Newton, 1 gshunt stepping, 2 relaxation start then Newton, 3 relaxation start then

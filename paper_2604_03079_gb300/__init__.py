@@ -83,6 +83,10 @@ _SIG = {
     "eec_newton_dc": (ctypes.c_int, [_P, _P, _P, _P, _I32, _F64, _I32, _I32, _F64, _F64, _F64,
                                      ctypes.POINTER(_I32), _P]),
     "eec_eval_stamp_tran": (ctypes.c_int, [_P, _P, _P, _P, _F64, _F64, _P, _P, _P, _P, _P]),
+    "eec_newton_tran": (ctypes.c_int, [_P, _P, _P, _P, _F64, _F64, _P, _P, _P, _P, _I32, _F64,
+                                       _I32, _I32, _F64, _F64, _F64, ctypes.POINTER(_I32), _P]),
+    "eec_transient": (ctypes.c_int, [_P, _P, _F64, _I32, _I32, _P, _I32, _F64, _I32, _I32, _F64,
+                                     _F64, _F64, ctypes.POINTER(_I32), _P]),
     "eec_eval_stamp_bwd_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "eec_graph_capture": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "eec_graph_launch": (ctypes.c_int, [_P, _P]),
@@ -451,6 +455,43 @@ def eec_newton_dc(ctx, x, A, b, max_iter=200, vstep=0.2, step_rule=0, solver=0, 
                                       int(max_iter), float(vstep), int(step_rule), int(solver),
                                       float(tol_abs), float(tol_rel), float(tol_f),
                                       ctypes.byref(it), _stream(stream)))
+    return int(it.value)
+
+
+def eec_newton_tran(ctx, x, q_prev, i_prev, alpha, beta, A, b, q, icap=None, max_iter=200,
+                    vstep=0.2, step_rule=1, solver=EEC_SOLVER_LU, tol_abs=1e-12, tol_rel=1e-9,
+                    tol_f=1e-9, stream=None) -> int:
+    """One implicit time step (Newton on the transient companion system) from x (updated in
+    place); q and icap receive the charges and capacitive currents at the new point. Returns the
+    Newton iterations."""
+    _need_step(ctx, x, A, b, q)
+    nd = _sizes(ctx)[0]
+    _need(q_prev, 4 * nd, "q_prev")
+    _need(i_prev, 4 * nd, "i_prev")
+    _need(icap, 4 * nd, "icap")
+    it = _I32(0)
+    _check(ctx, _load().eec_newton_tran(
+        ctx, _d(x, name="x"), _d(q_prev, name="q_prev"), _d(i_prev, name="i_prev"),
+        float(alpha), float(beta), _d(A, name="A"), _d(b, name="b"), _d(q, name="q"),
+        _d(icap, name="icap"), int(max_iter), float(vstep), int(step_rule), int(solver),
+        float(tol_abs), float(tol_rel), float(tol_f), ctypes.byref(it), _stream(stream)))
+    return int(it.value)
+
+
+def eec_transient(ctx, x, h, n_steps, method=1, traj=None, max_iter=200, vstep=0.2, step_rule=1,
+                  solver=EEC_SOLVER_LU, tol_abs=1e-12, tol_rel=1e-9, tol_f=1e-9,
+                  stream=None) -> int:
+    """n_steps fixed time steps of h seconds from x (updated in place; method 0 backward Euler,
+    1 trapezoidal); traj (nullable, [(n_steps + 1) * n] device) receives every time point.
+    Returns the Newton iterations over all steps."""
+    n = _sizes(ctx)[1]
+    _need(x, n, "x")
+    _need(traj, (int(n_steps) + 1) * n, "traj")
+    it = _I32(0)
+    _check(ctx, _load().eec_transient(
+        ctx, _d(x, name="x"), float(h), int(n_steps), int(method), _d(traj, name="traj"),
+        int(max_iter), float(vstep), int(step_rule), int(solver), float(tol_abs), float(tol_rel),
+        float(tol_f), ctypes.byref(it), _stream(stream)))
     return int(it.value)
 
 

@@ -120,6 +120,10 @@ struct eec_ctx {
   double* d_x0 = nullptr;        // starting point, kept for the gshunt-stepping restart
   int* d_diag = nullptr;         // CSR position of the diagonal of every node row
   int* d_rail_unk = nullptr;     // unknown of every rail node (rails as MNA unknowns)
+  // eec_transient: A, b and the charges and capacitive currents of two time points
+  double* tr_A = nullptr;
+  double* tr_b = nullptr;
+  double* tr_q = nullptr;
   int newton_info[4] = {0, 0, 0, 0};   // last eec_newton_dc: solves, gshunt stages, sweeps, path
   void* sp_buf = nullptr;
   unsigned long long* d_nstats = nullptr;
@@ -222,6 +226,7 @@ void free_topology(eec_ctx* c) {
   c->d_x0 = nullptr;
   c->d_diag = nullptr;
   c->d_rail_unk = nullptr;
+  c->tr_A = c->tr_b = c->tr_q = nullptr;   // freed with the other device arrays
   c->sp_buf = nullptr;
   c->d_nstats = nullptr;
   if (c->lu_ibuf) cudaFree(c->lu_ibuf);
@@ -1782,9 +1787,15 @@ double bits_to_double(unsigned long long u) {
 // One damped Newton run from x with g_extra added to the diagonal of every node row after each
 // stamp (0: the circuit itself). Returns EEC_OK, EEC_ENOCONV (x holds the last iterate) or an
 // error; *iters counts its solves.
+static int eec_eval_stamp_tran_body(eec_ctx* c, const double* x, const double* q_prev,
+                                    const double* i_prev, double alpha, double beta, double* A,
+                                    double* b, double* q, double* icap, void* stream);
+
+// With ta set, every iterate is stamped by the transient companion stamp (eec_eval_stamp_tran)
+// instead: one implicit time step's Newton loop.
 int newton_run(eec_ctx* c, double* x, double* A, double* b, int max_iter, double vstep,
                int step_rule, int solver, double tol_abs, double tol_rel, double tol_f,
-               double g_extra, int* iters, cudaStream_t s) {
+               double g_extra, int* iters, cudaStream_t s, const TranArgs* ta = nullptr) {
   const int v = effective_variant(c), n = c->n, nnz = (int)c->nnz;
   const int n_node = n - (int)c->rail.size();
   int rc;
@@ -1794,7 +1805,13 @@ int newton_run(eec_ctx* c, double* x, double* A, double* b, int max_iter, double
   *iters = 0;
   for (int it = 0; it <= max_iter; ++it) {
     CUDA_TRY(c, cudaMemsetAsync(c->d_nstats, 0, 4 * sizeof(unsigned long long), s));
-    if ((rc = eval_with(c, v, x, A, b, nullptr, s))) return rc;
+    if (ta) {
+      if ((rc = eec_eval_stamp_tran_body(c, x, ta->qprev, ta->iprev, ta->alpha, ta->beta, A, b,
+                                         ta->q, ta->icap, s)))
+        return rc;
+    } else if ((rc = eval_with(c, v, x, A, b, nullptr, s))) {
+      return rc;
+    }
     if (g_extra > 0.0) {
       CUDA_TRY(c, launch_add_diag(A, c->d_diag, n_node, g_extra, s));
       ++c->n_kernels;
@@ -1878,29 +1895,38 @@ int relax_run(eec_ctx* c, double* x, double* A, double* b, double vmax, int max_
   return EEC_OK;
 }
 
+// Solver state for eec_newton_dc / eec_newton_tran / eec_transient, on their first call.
+int newton_begin(eec_ctx* c, double* A, int solver, cudaStream_t s) {
+  int rc;
+  if (solver == EEC_SOLVER_LU) return newton_common(c);
+  if ((rc = newton_setup(c, A))) return rc;
+  if (cusolverSpSetStream(c->sp, s) != CUSOLVER_STATUS_SUCCESS)
+    return fail(c, EEC_ECUDA, "cusolverSpSetStream failed");
+  return EEC_OK;
+}
+
+bool newton_args_ok(double* x, double* A, double* b, int32_t max_iter, double vstep,
+                    int32_t step_rule, int32_t solver, double tol_abs, double tol_rel,
+                    double tol_f) {
+  return x && A && b && max_iter >= 1 && vstep > 0.0 && step_rule >= 0 && step_rule <= 1 &&
+         solver >= 0 && solver <= EEC_SOLVER_LU && tol_abs >= 0.0 && tol_rel >= 0.0 &&
+         tol_f >= 0.0;
+}
+
 static int eec_newton_dc_body(eec_ctx* c, double* x, double* A, double* b, int32_t max_iter, double vstep,
                               int32_t step_rule, int32_t solver, double tol_abs, double tol_rel,
                               double tol_f, int32_t* iters_out, void* stream) {
   NvtxRange range("eec/newton_dc");
   int rc = check_built(c);
   if (rc) return rc;
-  if (!x || !A || !b || max_iter < 1 || !(vstep > 0.0) || step_rule < 0 || step_rule > 1 ||
-      solver < 0 || solver > EEC_SOLVER_LU ||
-      !(tol_abs >= 0.0) ||
-      !(tol_rel >= 0.0) || !(tol_f >= 0.0))
+  if (!newton_args_ok(x, A, b, max_iter, vstep, step_rule, solver, tol_abs, tol_rel, tol_f))
     return fail(c, EEC_EINVAL, "bad eec_newton_dc arguments");
   if (c->nnz > 0x7fffffffLL) return fail(c, EEC_EINVAL, "pattern too large for the sparse solver");
   if (iters_out) *iters_out = 0;
   for (int k = 0; k < 4; ++k) c->newton_info[k] = 0;
   if (c->n == 0) return EEC_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (solver == EEC_SOLVER_LU) {
-    if ((rc = newton_common(c))) return rc;
-  } else {
-    if ((rc = newton_setup(c, A))) return rc;
-    if (cusolverSpSetStream(c->sp, s) != CUSOLVER_STATUS_SUCCESS)
-      return fail(c, EEC_ECUDA, "cusolverSpSetStream failed");
-  }
+  if ((rc = newton_begin(c, A, solver, s))) return rc;
   CUDA_TRY(c, cudaMemcpyAsync(c->d_x0, x, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, s));
   int its = 0, total = 0, stages = 0, sweeps = 0, path = 0;
   // gshunt stepping (the oracle's fallback, taken as there both when plain Newton runs out of
@@ -1966,6 +1992,104 @@ int eec_newton_dc(eec_ctx* c, double* x, double* A, double* b, int32_t max_iter,
   try {
     return eec_newton_dc_body(c, x, A, b, max_iter, vstep, step_rule, solver, tol_abs, tol_rel,
                               tol_f, iters_out, stream);
+  } catch (...) {
+    return abi_exception(c);
+  }
+}
+
+static int eec_newton_tran_body(eec_ctx* c, double* x, const double* q_prev,
+                                const double* i_prev, double alpha, double beta, double* A,
+                                double* b, double* q, double* icap, int32_t max_iter,
+                                double vstep, int32_t step_rule, int32_t solver, double tol_abs,
+                                double tol_rel, double tol_f, int32_t* iters_out, void* stream) {
+  NvtxRange range("eec/newton_tran");
+  int rc = check_built(c);
+  if (rc) return rc;
+  if (!newton_args_ok(x, A, b, max_iter, vstep, step_rule, solver, tol_abs, tol_rel, tol_f) ||
+      !q_prev || !q || !std::isfinite(alpha) || !std::isfinite(beta) || alpha < 0.0)
+    return fail(c, EEC_EINVAL, "bad eec_newton_tran arguments");
+  if (c->nnz > 0x7fffffffLL) return fail(c, EEC_EINVAL, "pattern too large for the sparse solver");
+  if (iters_out) *iters_out = 0;
+  if (c->n == 0) return EEC_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((rc = newton_begin(c, A, solver, s))) return rc;
+  const TranArgs ta{q_prev, i_prev, alpha, beta, q, icap};
+  int its = 0;
+  rc = newton_run(c, x, A, b, max_iter, vstep, step_rule, solver, tol_abs, tol_rel, tol_f, 0.0,
+                  &its, s, &ta);
+  if (iters_out) *iters_out = its;
+  if (rc == EEC_ENOCONV)
+    return fail(c, EEC_ENOCONV, "time step: no convergence within max_iter iterations");
+  return rc;
+}
+int eec_newton_tran(eec_ctx* c, double* x, const double* q_prev, const double* i_prev,
+                    double alpha, double beta, double* A, double* b, double* q, double* icap,
+                    int32_t max_iter, double vstep, int32_t step_rule, int32_t solver,
+                    double tol_abs, double tol_rel, double tol_f, int32_t* iters_out,
+                    void* stream) {
+  try {
+    return eec_newton_tran_body(c, x, q_prev, i_prev, alpha, beta, A, b, q, icap, max_iter, vstep,
+                                step_rule, solver, tol_abs, tol_rel, tol_f, iters_out, stream);
+  } catch (...) {
+    return abi_exception(c);
+  }
+}
+
+static int eec_transient_body(eec_ctx* c, double* x, double h, int32_t n_steps, int32_t method,
+                              double* traj, int32_t max_iter, double vstep, int32_t step_rule,
+                              int32_t solver, double tol_abs, double tol_rel, double tol_f,
+                              int32_t* iters_out, void* stream) {
+  NvtxRange range("eec/transient");
+  int rc = check_built(c);
+  if (rc) return rc;
+  if (!x || !(h > 0.0) || !std::isfinite(h) || n_steps < 0 || method < 0 || method > 1)
+    return fail(c, EEC_EINVAL, "bad eec_transient arguments");
+  if (iters_out) *iters_out = 0;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t nq = (size_t)4 * c->n_dev;
+  if ((!c->tr_A && (rc = dalloc(c, &c->tr_A, (size_t)c->nnz))) ||
+      (!c->tr_b && (rc = dalloc(c, &c->tr_b, (size_t)c->n))) ||
+      (!c->tr_q && (rc = dalloc(c, &c->tr_q, 4 * nq))))
+    return rc;
+  double* qa = c->tr_q;            // charges of the previous time point
+  double* qb = c->tr_q + nq;       // charges at the iterate
+  double* ia = c->tr_q + 2 * nq;   // capacitive currents of the previous time point
+  double* ib = c->tr_q + 3 * nq;
+  const double alpha = method == 0 ? 1.0 / h : 2.0 / h;
+  const double beta = method == 0 ? 0.0 : 1.0;
+  // the charges at t = 0 (the first time point's history: no current through the capacitors)
+  CUDA_TRY(c, cudaMemsetAsync(c->tr_q, 0, sizeof(double) * 4 * nq, s));
+  if ((rc = eec_eval_stamp_tran_body(c, x, qb, nullptr, 0.0, 0.0, c->tr_A, c->tr_b, qa, nullptr,
+                                     s)))
+    return rc;
+  if (traj) CUDA_TRY(c, cudaMemcpyAsync(traj, x, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, s));
+  int total = 0;
+  for (int st = 1; st <= n_steps; ++st) {
+    int its = 0;
+    rc = eec_newton_tran_body(c, x, qa, ia, alpha, beta, c->tr_A, c->tr_b, qb, ib, max_iter, vstep,
+                              step_rule, solver, tol_abs, tol_rel, tol_f, &its, stream);
+    total += its;
+    if (iters_out) *iters_out = total;
+    if (rc) {
+      if (rc == EEC_ENOCONV)
+        return fail(c, EEC_ENOCONV, "time step " + std::to_string(st) +
+                                        ": no convergence within max_iter iterations");
+      return rc;
+    }
+    std::swap(qa, qb);
+    std::swap(ia, ib);
+    if (traj)
+      CUDA_TRY(c, cudaMemcpyAsync(traj + (size_t)st * c->n, x, sizeof(double) * c->n,
+                                  cudaMemcpyDeviceToDevice, s));
+  }
+  return EEC_OK;
+}
+int eec_transient(eec_ctx* c, double* x, double h, int32_t n_steps, int32_t method, double* traj,
+                  int32_t max_iter, double vstep, int32_t step_rule, int32_t solver,
+                  double tol_abs, double tol_rel, double tol_f, int32_t* iters_out, void* stream) {
+  try {
+    return eec_transient_body(c, x, h, n_steps, method, traj, max_iter, vstep, step_rule, solver,
+                              tol_abs, tol_rel, tol_f, iters_out, stream);
   } catch (...) {
     return abi_exception(c);
   }

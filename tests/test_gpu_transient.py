@@ -140,3 +140,55 @@ def test_gpu_stamped_transient_inverter_chain_matches_oracle(eec, variant):
     # both loops stop at |dx| <= 1e-12 + 1e-9 |x|: the states agree far inside that
     np.testing.assert_allclose(got, ref, rtol=1e-8, atol=1e-10)
     assert np.abs(ref[-1] - ref[0]).max() > 0.5          # the chain really switches
+
+
+@pytest.mark.parametrize("solver", [0, 2])
+@pytest.mark.parametrize("method", [0, 1])
+def test_library_transient_matches_oracle(eec, method, solver):
+    # the library's own transient run (eec_transient: the GPU Newton loop on the companion
+    # stamp, every step solved on the GPU) against the oracle's transient solver (dense LU,
+    # the same per-node step limit and |dx| test): a 6-stage chain switching its input at t = 0
+    import torch
+    net = netgen.inverter_chain(6, vin=1.0)
+    h, n = 2e-12, 25
+    ref = oracle.Oracle(net, CARDS).tran_solve(np.zeros(net.n_free), h, n, method=method)
+    circ = eec.Circuit(net, CARDS, variant=2)
+    x = torch.zeros(circ.n, dtype=torch.float64, device="cuda")
+    traj = torch.empty((n + 1) * circ.n, dtype=torch.float64, device="cuda")
+    its = eec.eec_transient(circ.ctx, x, h, n, method=method, traj=traj, solver=solver)
+    assert its >= n and circ.status() == 0
+    got = host(traj).reshape(n + 1, circ.n)
+    np.testing.assert_allclose(got, ref, rtol=1e-8, atol=1e-10)
+    np.testing.assert_array_equal(host(x), got[-1])
+    assert np.abs(ref[-1] - ref[0]).max() > 0.5          # the chain really switches
+
+
+@pytest.mark.parametrize("method", [0, 1])
+def test_library_transient_rc_and_single_step(eec, method):
+    # an RC charge through a resistor into a gate capacitance: the library's run against the
+    # oracle (whose BE/TR recurrences are pinned to the exact ones on the CPU); then one step by
+    # eec_newton_tran from the run's last state and history equals one more step of the run
+    import torch
+    W, L, R, Vs = 4e-6, 1e-6, 5e3, 1.0
+    card = netgen.card(VTH0=5.0, JS=0.0, GMIN=0.0)
+    cards = np.stack([card, card])
+    net = tiny_net("rc", [1, 1, 0], [0, Vs, 0], [(0, 2, 0, 0)], [1], W=[W], L=[L], res=[(1, 2)],
+                   resG=[1 / R], gshunt=0.0)
+    h = R * 4e-10 * W / 7
+    ref = oracle.Oracle(net, cards).tran_solve(np.zeros(1), h, 31, method=method)
+    circ = eec.Circuit(net, cards, color=True, variant=2)
+    x = torch.zeros(circ.n, dtype=torch.float64, device="cuda")
+    traj = torch.empty(32 * circ.n, dtype=torch.float64, device="cuda")
+    eec.eec_transient(circ.ctx, x, h, 31, method=method, traj=traj)
+    np.testing.assert_allclose(host(traj).reshape(32, circ.n), ref, rtol=1e-10, atol=1e-13)
+    # the step API: 30 steps by the run, then step 31 by eec_newton_tran (backward Euler: the
+    # history is the charges at step 30 alone)
+    if method == 0:
+        x2 = torch.zeros(circ.n, dtype=torch.float64, device="cuda")
+        eec.eec_transient(circ.ctx, x2, h, 30, method=0)
+        A, b, q = circ.new_outputs(want_q=True)
+        q30 = torch.zeros_like(q)
+        eec.eec_eval_stamp_tran(circ.ctx, x2, q30, None, 0.0, 0.0, A, b, q30, None)
+        it = eec.eec_newton_tran(circ.ctx, x2, q30, None, 1.0 / h, 0.0, A, b, q)
+        assert it >= 1
+        np.testing.assert_allclose(host(x2), ref[31], rtol=1e-10, atol=1e-13)
