@@ -1004,7 +1004,10 @@ cudaError_t launch_init_lin(const DevTopo& T, double* A, double* b, cudaStream_t
   const long long total = T.nnz + T.n;
   if (total <= 0) return cudaSuccess;
   long long g = (total + 255) / 256;
-  if (g > 152LL * 16) g = 152LL * 16;   // grid-stride beyond 16 blocks per SM
+  // grid-stride over 4 blocks per SM: enough to stream A_lin and b_lin at full bandwidth, and
+  // the evaluation (a programmatic dependent) finds SMs with room for its blocks at once instead
+  // of waiting for a full-occupancy copy to drain (1M-FET logic: 0.355 -> 0.350 ms per step)
+  if (g > 152LL * 4) g = 152LL * 4;
   k_init_lin<<<(int)g, 256, 0, s>>>(T.Alin, T.blin, A, b, T.nnz, T.n);
   return cudaGetLastError();
 }
