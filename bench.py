@@ -564,6 +564,26 @@ def newton_study(eec, dev, stream):
                       "lu_stats": eec.eec_lu_stats(c.ctx) if solver == 2 else None, "ms": ms,
                       "ms_per_iteration": ms / max(its, 1), "eval_stamp_ms": ev_ms,
                       "eval_stamp_share": ev_ms * max(its, 1) / ms}
+    # the batch of config 4 as one block-diagonal system: the DC points of 4,096 circuits in one
+    # Newton loop (its convergence tests take the maximum over every circuit's nodes)
+    if time.perf_counter() - t_start < 120:
+        nets = netgen.batch_circuits(4096)
+        c = eec.Circuit(None, netgen.default_cards(), color=True, batch=nets)
+        xd = torch.zeros(c.n, dtype=torch.float64, device=dev)
+        An, bn, _ = c.new_outputs(want_q=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        try:
+            its = eec.eec_newton_dc(c.ctx, xd, An, bn, max_iter=300, step_rule=1, solver=2)
+            torch.cuda.synchronize()
+            info = eec.eec_newton_info(c.ctx)
+            ms = (time.perf_counter() - t0) * 1e3
+            out["batch_4096_circuits_solver2"] = {
+                "unknowns": c.n, "devices": c.n_dev, "iterations": its,
+                "path": eec.NEWTON_PATHS[info["path"]], "relaxation_sweeps": info["sweeps"],
+                "lu_stats": eec.eec_lu_stats(c.ctx), "ms": ms, "ms_per_iteration": ms / max(its, 1)}
+        except eec.EECError as e:
+            out["batch_4096_circuits_solver2"] = {"error": str(e)}
     # NEXT-1 with the GPU Newton loop: transient runs (trapezoidal, fixed step, sources held)
     # from every node at 0 V (power-up: the circuit settles, the chain's stages switch one after
     # another), every step's Newton iterations solved with the library's sparse LU

@@ -34,10 +34,16 @@ namespace eec {
 
 // ---- host analysis ----------------------------------------------------------------------------
 
-// Minimum-degree order of the symmetric pattern of A + A^T (diagonal ignored): repeatedly
-// eliminate a node of least current degree (ties: the lowest index) and join its remaining
-// neighbours into a clique, as elimination does. Explicit adjacency; the netlists this serves
-// have small degrees away from the rails, which the rule leaves to the end.
+// Minimum-degree order of the symmetric pattern of A + A^T (diagonal ignored), by passes of
+// multiple elimination: each pass eliminates, in index order, every node of the current least
+// degree that no node eliminated earlier in the pass neighbours, joining each one's remaining
+// neighbours into a clique as elimination does. Eliminating one node of least degree at a time
+// (ties to the lowest index) would run along a chain of gates node after node, and through a
+// batch of circuits circuit after circuit: every column of the order then depends on the one
+// before it, and the GPU refactorisation, which deals consecutive columns to different warps,
+// becomes one long chain. A pass takes the ends of all chains at once instead (the order's
+// consecutive columns are independent) at the same fill. Explicit adjacency; the netlists this
+// serves have small degrees away from the rails, which the rule leaves to the end.
 long long lu_entry_budget(long long nnz) { return 32 * nnz + (4LL << 20); }
 
 // The update list (one entry per multiply-add of the factorisation) of a pattern of nnz entries
@@ -70,30 +76,41 @@ bool lu_min_degree_order(int n, const std::vector<int>& rp, const std::vector<in
   }
   order.clear();
   order.reserve(n);
-  std::vector<int> merged;
+  std::vector<int> merged, cand;
+  std::vector<int> touched(n, 0);   // pass in which a neighbour was eliminated
+  int pass = 0;
   while (!by_deg.empty()) {
-    const int v = by_deg.begin()->second;
-    by_deg.erase(by_deg.begin());
-    order.push_back(v);
-    const std::vector<int> nb = std::move(adj[v]);
-    adj[v].clear();
-    total -= (long long)nb.size();
-    for (int a : nb) {
-      by_deg.erase({(int)adj[a].size(), a});
-      total -= (long long)adj[a].size();
-      // adj[a] := (adj[a] without v) joined with the other neighbours of v
-      merged.clear();
-      std::set_union(adj[a].begin(), adj[a].end(), nb.begin(), nb.end(), std::back_inserter(merged));
-      merged.erase(std::remove_if(merged.begin(), merged.end(),
-                                  [&](int u) { return u == v || u == a; }),
-                   merged.end());
-      adj[a].swap(merged);
-      by_deg.insert({(int)adj[a].size(), a});
-      total += (long long)adj[a].size();
-    }
-    if (total > budget) {   // the fill of this pattern outgrows any useful factor
-      order.clear();
-      return false;
+    const int dmin = by_deg.begin()->first;
+    cand.clear();
+    for (auto it = by_deg.begin(); it != by_deg.end() && it->first == dmin; ++it)
+      cand.push_back(it->second);
+    ++pass;
+    for (const int v : cand) {
+      if (touched[v] == pass) continue;   // its degree changed in this pass
+      by_deg.erase({dmin, v});
+      order.push_back(v);
+      const std::vector<int> nb = std::move(adj[v]);
+      adj[v].clear();
+      total -= (long long)nb.size();
+      for (int a : nb) {
+        touched[a] = pass;
+        by_deg.erase({(int)adj[a].size(), a});
+        total -= (long long)adj[a].size();
+        // adj[a] := (adj[a] without v) joined with the other neighbours of v
+        merged.clear();
+        std::set_union(adj[a].begin(), adj[a].end(), nb.begin(), nb.end(),
+                       std::back_inserter(merged));
+        merged.erase(std::remove_if(merged.begin(), merged.end(),
+                                    [&](int u) { return u == v || u == a; }),
+                     merged.end());
+        adj[a].swap(merged);
+        by_deg.insert({(int)adj[a].size(), a});
+        total += (long long)adj[a].size();
+      }
+      if (total > budget) {   // the fill of this pattern outgrows any useful factor
+        order.clear();
+        return false;
+      }
     }
   }
   return true;
