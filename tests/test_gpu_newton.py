@@ -186,3 +186,22 @@ def test_sram_dc_point_through_the_multi_block_lu(eec):
     assert 8 * nnz_lu > 227 * 1024            # the factor lives in global memory
     F = oracle.Oracle(net, CARDS).kcl_residual(x.cpu().numpy())
     assert np.abs(F).max() <= 1e-11
+
+
+def test_batch_of_circuits_dc_points_in_one_newton_loop(eec):
+    # 48 circuits of config 4's mix as one block-diagonal system: one Newton loop (its tests take
+    # the maximum over every circuit's nodes) reaches every circuit's operating point. Each block
+    # is checked with the oracle's model on its own circuit: the KCL residual of its nodes at the
+    # returned point is at rounding level.
+    import torch
+    nets = netgen.batch_circuits(48, seed=11)
+    circ = eec.Circuit(None, CARDS, color=True, batch=nets)
+    x = torch.zeros(circ.n, dtype=torch.float64, device="cuda")
+    A, b, _ = circ.new_outputs(want_q=False)
+    it = eec.eec_newton_dc(circ.ctx, x, A, b, max_iter=300, step_rule=1, solver=eec.EEC_SOLVER_LU)
+    assert it >= 1 and circ.status() == 0
+    ro, _, _ = eec.eec_get_batch_offsets(circ.ctx, len(nets))
+    xh = x.cpu().numpy()
+    for k, net in enumerate(nets):
+        F = oracle.Oracle(net, CARDS).kcl_residual(xh[ro[k]:ro[k + 1]])
+        assert np.abs(F).max() <= 1e-11, k
