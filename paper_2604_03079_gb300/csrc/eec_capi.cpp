@@ -1695,6 +1695,8 @@ int lu_prepare(eec_ctx* c, const double* A, cudaStream_t s) {
   d.y = d.vals + d.nnz_lu;
   d.flag = c->lu_flag;
   d.gwork = c->lu_gwork;
+  d.ibase = c->lu_ibuf;
+  d.ilen = (long long)packed.size();
   c->lu = std::move(P);
   c->lud = d;
   c->lu_ready = true;

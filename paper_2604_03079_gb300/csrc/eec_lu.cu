@@ -407,16 +407,16 @@ __device__ __forceinline__ double lu_row_dot(const int* __restrict__ cols, const
   if (p1 - p0 <= 4) {
     if (lane == 0)
       for (int p = p0; p < p1; ++p) {
-        const int c = __ldg(cols + p);
+        const int c = cols[p];
         lu_wait(prog, reversed ? n - 1 - c : c, flag);
-        s = fma(v[__ldg(pos + p)], u[c], s);
+        s = fma(v[pos[p]], u[c], s);
       }
     return s;   // meaningful in lane 0
   }
   for (int p = p0 + lane; p < p1; p += 32) {
-    const int c = __ldg(cols + p);
+    const int c = cols[p];
     lu_wait(prog, reversed ? n - 1 - c : c, flag);
-    s = fma(v[__ldg(pos + p)], u[c], s);
+    s = fma(v[pos[p]], u[c], s);
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
@@ -434,10 +434,10 @@ __device__ __forceinline__ void lu_substitute(const LuDev& L, const double* v, c
   if (lane == 0) prog[w] = w;
   __syncthreads();
   for (int r = w; r < n; r += kLuWarps) {
-    const double s = lu_row_dot(L.lrcol, L.lrpos, __ldg(L.lrptr + r), __ldg(L.lrptr + r + 1), v,
+    const double s = lu_row_dot(L.lrcol, L.lrpos, L.lrptr[r], L.lrptr[r + 1], v,
                                 y, prog, L.flag, false, n);
     if (lane == 0) {
-      y[r] = b[__ldg(L.prow + r)] - s;
+      y[r] = b[L.prow[r]] - s;
       __threadfence_block();
       prog[w] = r + kLuWarps;
     }
@@ -450,7 +450,7 @@ __device__ __forceinline__ void lu_substitute(const LuDev& L, const double* v, c
   __syncthreads();
   for (int m = w; m < n; m += kLuWarps) {
     const int r = n - 1 - m;
-    const double s = lu_row_dot(L.urcol, L.urpos, __ldg(L.urptr + r), __ldg(L.urptr + r + 1), v,
+    const double s = lu_row_dot(L.urcol, L.urpos, L.urptr[r], L.urptr[r + 1], v,
                                 y, prog, L.flag, true, n);
     if (lane == 0) {
       y[r] = (y[r] - s) * dinv[r];
@@ -460,7 +460,13 @@ __device__ __forceinline__ void lu_substitute(const LuDev& L, const double* v, c
     __syncwarp();
   }
   __syncthreads();
-  for (int r = threadIdx.x; r < n; r += blockDim.x) x[__ldg(L.pcol + r)] = y[r];
+  for (int r = threadIdx.x; r < n; r += blockDim.x) x[L.pcol[r]] = y[r];
+}
+
+// Doubles of the shared-memory values region: factor, inverse diagonal, work vector; an even
+// count, so that the index arrays after it start on 16 bytes.
+__host__ __device__ __forceinline__ long long lu_vals_doubles(const LuDev& L) {
+  return ((long long)L.nnz_lu + 2LL * L.n + 1) & ~1LL;
 }
 
 // Refactorisation of A on the plan, then x = A^-1 b, in one block; with refine, one step of
@@ -476,30 +482,56 @@ __global__ void __launch_bounds__(kLuWarps * 32, 1) k_lu_factor_solve(LuDev L, c
                                                                       const double* __restrict__ b,
                                                                       double* x, double tiny,
                                                                       int smem, int refine) {
-  extern __shared__ double lu_dyn[];
+  extern __shared__ __align__(16) double lu_dyn[];
   __shared__ volatile int prog[kLuWarps];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   double* v = smem ? lu_dyn : L.vals;
   double* dinv = smem ? lu_dyn + L.nnz_lu : L.y + L.n;
   double* y = smem ? lu_dyn + L.nnz_lu + L.n : L.y;
+  if (smem == 2) {
+    // the plan's index arrays too (one packed, 16-byte aligned buffer), after the values: the
+    // column chain then reads every index from shared memory instead of L2
+    int* sidx = reinterpret_cast<int*>(lu_dyn + lu_vals_doubles(L));
+    const int4* src = reinterpret_cast<const int4*>(L.ibase);
+    int4* dst = reinterpret_cast<int4*>(sidx);
+    for (long long i = threadIdx.x; i < L.ilen / 4; i += blockDim.x) dst[i] = __ldg(src + i);
+    L.cptr = sidx + (L.cptr - L.ibase);
+    L.cdiag = sidx + (L.cdiag - L.ibase);
+    L.a2lu = sidx + (L.a2lu - L.ibase);
+    L.uptr = sidx + (L.uptr - L.ibase);
+    L.uk = sidx + (L.uk - L.ibase);
+    L.upos = sidx + (L.upos - L.ibase);
+    L.mptr = sidx + (L.mptr - L.ibase);
+    L.msrc = sidx + (L.msrc - L.ibase);
+    L.mdst = sidx + (L.mdst - L.ibase);
+    L.lrptr = sidx + (L.lrptr - L.ibase);
+    L.lrcol = sidx + (L.lrcol - L.ibase);
+    L.lrpos = sidx + (L.lrpos - L.ibase);
+    L.urptr = sidx + (L.urptr - L.ibase);
+    L.urcol = sidx + (L.urcol - L.ibase);
+    L.urpos = sidx + (L.urpos - L.ibase);
+    L.prow = sidx + (L.prow - L.ibase);
+    L.pcol = sidx + (L.pcol - L.ibase);
+    __syncthreads();
+  }
   if (lane == 0) prog[w] = w;
   for (int p = threadIdx.x; p < L.nnz_lu; p += blockDim.x) v[p] = 0.0;
   __syncthreads();
-  for (int e = threadIdx.x; e < L.nnz_a; e += blockDim.x) v[__ldg(L.a2lu + e)] = __ldg(A + e);
+  for (int e = threadIdx.x; e < L.nnz_a; e += blockDim.x) v[L.a2lu[e]] = __ldg(A + e);
   __syncthreads();
   for (int j = w; j < L.n; j += kLuWarps) {
-    const int t1 = __ldg(L.uptr + j + 1);
-    for (int t = __ldg(L.uptr + j); t < t1; ++t) {
-      const int k = __ldg(L.uk + t);
+    const int t1 = L.uptr[j + 1];
+    for (int t = L.uptr[j]; t < t1; ++t) {
+      const int k = L.uk[t];
       if (lane == 0) lu_wait(prog, k, L.flag);
       __syncwarp();   // orders lane 0's observation before every lane's loads of column k
-      const double ukj = v[__ldg(L.upos + t)];
-      const int m1 = __ldg(L.mptr + t + 1);
-      for (int m = __ldg(L.mptr + t) + lane; m < m1; m += 32)
-        v[__ldg(L.mdst + m)] -= v[__ldg(L.msrc + m)] * ukj;
+      const double ukj = v[L.upos[t]];
+      const int m1 = L.mptr[t + 1];
+      for (int m = L.mptr[t] + lane; m < m1; m += 32)
+        v[L.mdst[m]] -= v[L.msrc[m]] * ukj;
       __syncwarp();
     }
-    const int pd = __ldg(L.cdiag + j), p1 = __ldg(L.cptr + j + 1);
+    const int pd = L.cdiag[j], p1 = L.cptr[j + 1];
     const double inv = lu_rcp(v[pd]);
     for (int p = pd + 1 + lane; p < p1; p += 32) v[p] *= inv;
     if (lane == 0) dinv[j] = inv;
@@ -518,7 +550,7 @@ __global__ void __launch_bounds__(kLuWarps * 32, 1) k_lu_factor_solve(LuDev L, c
       continue;
     }
     bool bad = false;
-    for (int p = __ldg(L.cdiag + j) + 1; p < __ldg(L.cptr + j + 1) && !bad; ++p)
+    for (int p = L.cdiag[j] + 1; p < L.cptr[j + 1] && !bad; ++p)
       bad = !(fabs(v[p]) < lim);
     if (bad) atomicCAS(L.flag, 0, j + 1);
   }
@@ -752,7 +784,7 @@ int lu_grid_blocks() {
 
 }  // namespace
 
-size_t lu_smem_bytes(const LuDev& L) { return sizeof(double) * ((size_t)L.nnz_lu + 2 * (size_t)L.n); }
+size_t lu_smem_bytes(const LuDev& L) { return sizeof(double) * (size_t)lu_vals_doubles(L); }
 
 cudaError_t launch_lu_factor_solve(const LuDev& L, const double* A, const int* rp, const int* col,
                                    const double* b, double* x, double tiny, int refine,
@@ -764,9 +796,11 @@ cudaError_t launch_lu_factor_solve(const LuDev& L, const double* A, const int* r
   e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
   const size_t need = lu_smem_bytes(L);
+  const size_t need_idx = need + sizeof(int) * (size_t)L.ilen;
   const size_t fixed = sizeof(int) * kLuWarps;
-  const int smem = need + fixed <= (size_t)max_optin ? 1 : 0;
-  const size_t dyn = smem ? need : 0;
+  const int smem = (L.ibase && need_idx + fixed <= (size_t)max_optin) ? 2
+                   : (need + fixed <= (size_t)max_optin ? 1 : 0);
+  const size_t dyn = smem == 2 ? need_idx : (smem ? need : 0);
   const int grid = smem ? 0 : lu_grid_blocks();
   if (grid > 0 && L.gwork) {
     // the factor in global memory: the cooperative kernel over every SM (co-resident blocks,

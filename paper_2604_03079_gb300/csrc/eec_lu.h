@@ -33,6 +33,8 @@ struct LuDev {
                  // memory), then the refinement's residual and correction
   int* flag;
   int* gwork;    // [lu_grid_words()] progress words and barrier of the multi-block kernel
+  const int* ibase;   // the packed buffer every index array above lives in (16-byte aligned
+  long long ilen;     // parts), and its length in ints (a multiple of 4)
 };
 // Words of LuDev::gwork: a grid barrier and one progress word per warp of the largest grid the
 // multi-block kernel launches on this device.
