@@ -766,20 +766,21 @@ __global__ void __launch_bounds__(kLuGridBlock, 4) k_lu_factor_solve_grid(LuDev 
   for (int i = gt; i < L.n; i += GT) __stcg(x + i, __ldcg(x + i) + __ldcg(d + i));
 }
 
-// Blocks of the cooperative grid on this device (0 until the first query).
+// Blocks of the cooperative grid on the current device (0 if the query fails), cached per device.
 int lu_grid_blocks() {
-  static int blocks = 0;
-  if (!blocks) {
-    int dev = 0, nsm = 0, occ = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lu_factor_solve_grid, kLuGridBlock,
-                                                      0) != cudaSuccess)
-      return 0;
-    blocks = nsm * std::min(occ, 2);   // 1, 2 and 4 per SM measured within 5 %: the chain of
-                                       // dependent columns sets the time, not the warps
-  }
-  return blocks;
+  static int blocks[64] = {};
+  int dev = 0, nsm = 0, occ = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 0;
+  if (dev < 64 && blocks[dev]) return blocks[dev];
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lu_factor_solve_grid, kLuGridBlock,
+                                                    0) != cudaSuccess)
+    return 0;
+  // 1, 2 and 4 per SM measured within 5 %: the chain of dependent columns sets the time, not
+  // the warps
+  const int b = nsm * std::min(occ, 2);
+  if (dev < 64) blocks[dev] = b;
+  return b;
 }
 
 }  // namespace
