@@ -249,7 +249,7 @@ EEC_API int eec_eval_stamp_host(eec_ctx* ctx, const double* x_host, double* A_ho
  * batched sparse QR, its pattern analysis done once per context and reused by every iteration,
  * no fill-reducing order; solver 1: cuSOLVER's sparse QR after a symmetric approximate-minimum-
  * degree ordering, analysed on every call; solver EEC_SOLVER_LU (2): the library's sparse LU —
- * on the host, once per context, a minimum-degree column order and one factorisation of the
+ * on the host, once per context, a multiple-minimum-degree column order and one factorisation of the
  * first iterate's matrix with threshold partial pivoting fix the row pivots and the patterns of
  * L and U; every iteration then refactors the numbers on that pattern and solves on the GPU
  * (one single-block kernel when the factor fits in shared memory, else one cooperative kernel
@@ -362,7 +362,7 @@ EEC_API int eec_lu_stats(const eec_ctx* ctx, int64_t* nnz_lu, int32_t* analyses)
 
 /*
  * Host check of the sparse LU (no GPU; the paper has no counterpart): for an n x n matrix in CSR
- * (row_ptr [n+1], col [nnz], a [nnz], host), the minimum-degree order, the host factorisation
+ * (row_ptr [n+1], col [nnz], a [nnz], host), the multiple-minimum-degree order, the host factorisation
  * with threshold partial pivoting, then the GPU kernel's refactorisation and triangular solves
  * executed on the host in the GPU's order, for the right-hand side b [n]; x [n] receives the
  * solution of A x = b. *nnz_lu (nullable) = entries of L and U; *bad_col

@@ -5,7 +5,7 @@
 // host. Here the pattern of A never changes between iterations, so the expensive symbolic work is
 // done once and only the numbers are recomputed on the GPU every iteration:
 //  * host, once per pattern (again only if a pivot degrades): a fill-reducing column order
-//    (approximate minimum degree on the symmetric pattern), then one left-looking sparse LU of
+//    (multiple minimum degree on the symmetric pattern), then one left-looking sparse LU of
 //    the first iterate's matrix with threshold partial pivoting (Gilbert-Peierls: the pattern of
 //    every column is the set reached in the graph of the L columns before it, so it does not
 //    depend on the values). It fixes the row pivot sequence and the structural patterns of L and

@@ -44,7 +44,7 @@ int lu_grid_words();
 // eec_lu.cu). Circuit matrices with locality stay far below (the 256 x 256 SRAM: 1.2 nnz);
 // randomly wired netlists have no good elimination order and would fill towards a dense factor.
 long long lu_entry_budget(long long nnz);
-// Host: minimum-degree column order of the symmetric pattern of A + A^T; false (order left
+// Host: multiple-minimum-degree column order of the symmetric pattern of A + A^T; false (order left
 // empty) when the elimination graph would outgrow lu_entry_budget.
 bool lu_min_degree_order(int n, const std::vector<int>& rp, const std::vector<int>& col,
                          std::vector<int>& order);

@@ -1,5 +1,5 @@
 """The sparse LU of eec_newton_dc (solver EEC_SOLVER_LU), checked on the CPU through the C ABI's
-host check (no GPU): the minimum-degree order, the host factorisation with threshold partial
+host check (no GPU): the multiple-minimum-degree order, the host factorisation with threshold partial
 pivoting, and the GPU kernels' refactorisation and triangular solves executed on the host in the
 GPU's order. Matrices are the oracle's MNA matrices of several netlist families.
 
