@@ -142,9 +142,9 @@ def test_gpu_stamped_transient_inverter_chain_matches_oracle(eec, variant):
     assert np.abs(ref[-1] - ref[0]).max() > 0.5          # the chain really switches
 
 
-@pytest.mark.parametrize("solver", [0, 2])
+@pytest.mark.parametrize("solver,variant", [(0, 2), (2, 2), (2, 5)])
 @pytest.mark.parametrize("method", [0, 1])
-def test_library_transient_matches_oracle(eec, method, solver):
+def test_library_transient_matches_oracle(eec, method, solver, variant):
     # the library's own transient run (eec_transient: the GPU Newton loop on the companion
     # stamp, every step solved on the GPU) against the oracle's transient solver (dense LU,
     # the same per-node step limit and |dx| test): a 6-stage chain switching its input at t = 0
@@ -152,7 +152,7 @@ def test_library_transient_matches_oracle(eec, method, solver):
     net = netgen.inverter_chain(6, vin=1.0)
     h, n = 2e-12, 25
     ref = oracle.Oracle(net, CARDS).tran_solve(np.zeros(net.n_free), h, n, method=method)
-    circ = eec.Circuit(net, CARDS, variant=2)
+    circ = eec.Circuit(net, CARDS, variant=variant)   # 5: the pipelined colour schedule
     x = torch.zeros(circ.n, dtype=torch.float64, device="cuda")
     traj = torch.empty((n + 1) * circ.n, dtype=torch.float64, device="cuda")
     its = eec.eec_transient(circ.ctx, x, h, n, method=method, traj=traj, solver=solver)
