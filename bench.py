@@ -44,12 +44,12 @@ UNIT = "device evals+stamps/s"
 # traffic until they are counted again.
 KERNEL_SOURCES = ("eec_model.cuh", "eec_fastmath.cuh", "eec_tables.h", "eec_internal.h",
                   "eec_kernels.cu")
-COUNTED_SOURCES_SHA16 = "42ababb81038a999"
+COUNTED_SOURCES_SHA16 = "ea3295f251db3176"
 COUNTS = {    # (workload, kernel) -> (FP64 flop per device, DRAM bytes per device)
-    ("logic1m", "eval_cost"): (255.46, 293.48),
-    ("batch", "eval_cost"): (234.78, 377.08),
-    ("sram", "eval_cost"): (265.86, 186.06),
-    ("logic1m", "pipe"): (258.24, 285.87),
+    ("logic1m", "eval_cost"): (255.46, 291.86),
+    ("batch", "eval_cost"): (234.78, 376.15),
+    ("sram", "eval_cost"): (265.86, 185.19),
+    ("logic1m", "pipe"): (258.24, 285.01),
 }
 # GB300: 152 SMs x 2 FP64 FMA per clock per SM x 2 flop x 2070 MHz maximum SM clock.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
@@ -678,13 +678,14 @@ def extras(eec, circ, net, x, xt, A, b, q, args, dev):
     res["phases_ungraphed"] = phases
 
     # HBM roofline of the stamp-only kernel (the segmented-reduction gather from the buffer in
-    # entry order): per contribution its 8 B value, per A/b entry 8 B written, 8 B of its linear
-    # part and 4 B of run offset
+    # entry order): per contribution its 8 B value, per A/b entry 8 B of its linear part and 8 B
+    # written (the chunk descriptors, 16 B per 64 items, and the unused ends of chunks not
+    # counted)
     _, _, unk = circ.pattern()
     free = unk[net.dev_nodes] >= 0
     contrib = int((free[:, [0, 2, 3]].sum(axis=1) * (1 + free.sum(axis=1))).sum())
     entries = circ.nnz + circ.n
-    gbytes = 8 * contrib + 20 * entries
+    gbytes = 8 * contrib + 16 * entries
     st_ms = phases["segreduce"]["stamp_ms"]
     hbm = hbm_peak_gbs()
     res["stamp_roofline"] = {

@@ -81,7 +81,7 @@ struct eec_ctx {
   int stamp_mode = 0;          // colour-buffered stamp: 0 per-colour launches, 1 grid, 2 cluster
   int pipe_grid = 0;           // blocks of the pipelined colour schedule (resident blocks)
   int pipe_colors = 0;         // non-empty colours (counters of the pipelined schedule)
-  long long n_contrib = 0;     // contributions of the segmented reduction (cbuf length)
+  long long n_stream = 0;     // items of the segmented reduction's cbuf
   // phase timing and launch counting
   bool prof = false;
   bool graph_all = false;      // eec_batch_capture_graph: every schedule replays a cached graph
@@ -368,10 +368,16 @@ int ensure_buf(eec_ctx* c) {
   return dalloc(c, &c->d.buf, (size_t)kNContrib * c->n_dev);
 }
 
-// The segmented reduction's contribution buffer, in entry order (gat_ptr's last value long).
+// The segmented reduction's buffer: every entry's run, its linear part written here once (the
+// evaluation overwrites only the contributions).
 int ensure_cbuf(eec_ctx* c) {
   if (c->d.cbuf) return EEC_OK;
-  return dalloc(c, &c->d.cbuf, std::max<size_t>((size_t)c->n_contrib, 1));
+  int rc = dalloc(c, &c->d.cbuf, std::max<size_t>((size_t)c->n_stream, 1));
+  if (rc) return rc;
+  CUDA_TRY(c, cudaMemset(c->d.cbuf, 0, std::max<size_t>((size_t)c->n_stream, 1) * sizeof(double)));
+  CUDA_TRY(c, launch_gather_init(c->d, 0));
+  CUDA_TRY(c, cudaStreamSynchronize(0));
+  return EEC_OK;
 }
 
 int ensure_gv(eec_ctx* c) {
@@ -1097,9 +1103,13 @@ static int eec_build_scatter_body(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_
     Alin[find(jr[r], a)] += 1.0;     // source equation: v_rail = its voltage
     blin[jr[r]] += c->vfix[c->rail[r]];
   }
-  // segmented-reduction map: contributions per entry in original device order
+  // segmented-reduction map. Entry e is its linear part, then its contributions in original
+  // device order. Per window of kGatherWin entries, the light ones (< kHeavy contributions) are
+  // sorted by their count and dealt to groups of 32, each stored column-major (the gather then
+  // adds one item of 32 entries per instruction, and each entry's sum keeps the serial order);
+  // heavy entries' runs follow, contiguous.
   const long long E = c->nnz + n;
-  std::vector<long long> gptr(E + 1, 0);
+  std::vector<int> gcnt(E, 0);
   for (int k = 0; k < N; ++k) {
     const int p = pos_of[k];
     const int4 t4 = tidx[p];
@@ -1109,17 +1119,54 @@ static int eec_build_scatter_body(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_
       if (row < 0) continue;
       for (int u = 0; u < 4; ++u) {
         const int s = slot[(size_t)(4 * r + u) * N + p];
-        if (s >= 0) gptr[s + 1]++;
+        if (s >= 0) gcnt[s]++;
       }
-      gptr[c->nnz + row + 1]++;
+      gcnt[c->nnz + row]++;
     }
   }
-  for (long long e = 0; e < E; ++e) gptr[e + 1] += gptr[e];
-  // position in entry order of every contribution (j, p): the evaluation writes it there
+  const long long n_win = (E + kGatherWin - 1) / kGatherWin;
+  std::vector<long long> ghead(E);   // item of the linear part
+  std::vector<int> gwoff((size_t)n_win * (kGatherGroups + 1));
+  std::vector<unsigned short> gloc((size_t)n_win * kGatherWin, 0xffff);
+  std::vector<int4> gheavy;
+  long long gitems = 0;
+  {
+    std::vector<long long> order;
+    for (long long w = 0; w < n_win; ++w) {
+      const long long e0 = w * kGatherWin, e1 = std::min(E, e0 + kGatherWin);
+      order.clear();
+      for (long long e = e0; e < e1; ++e)
+        if (gcnt[e] < kHeavy) order.push_back(e);
+      std::stable_sort(order.begin(), order.end(),
+                       [&](long long x, long long y) { return gcnt[x] < gcnt[y]; });
+      for (int g = 0; g < kGatherGroups; ++g) {
+        gwoff[(size_t)w * (kGatherGroups + 1) + g] = (int)std::min(gitems, 0x7fffffffLL);
+        const size_t s0 = (size_t)32 * g, s1 = std::min(order.size(), s0 + 32);
+        if (s0 >= s1) continue;
+        for (size_t i = s0; i < s1; ++i) {
+          ghead[order[i]] = gitems + (long long)(i - s0);
+          gloc[(size_t)w * kGatherWin + i] = (unsigned short)(order[i] - e0);
+        }
+        gitems += 32LL * (1 + gcnt[order[s1 - 1]]);   // the group's rows: its largest run
+      }
+      gwoff[(size_t)w * (kGatherGroups + 1) + kGatherGroups] = (int)std::min(gitems, 0x7fffffffLL);
+    }
+    for (long long e = 0; e < E; ++e) {
+      if (gcnt[e] < kHeavy) continue;
+      ghead[e] = gitems;
+      if (gitems + 1 + gcnt[e] <= 0x7fffffffLL)
+        gheavy.push_back(make_int4((int)e, (int)gitems, 1 + gcnt[e], 0));
+      gitems += 1 + gcnt[e];
+    }
+    if (gitems > 0x7fffffffLL) return fail(c, EEC_EINVAL, "too many contributions");
+    c->n_stream = gitems;
+  }
+  // position in cbuf of every contribution (j, p): the evaluation writes it there
   if ((long long)N * kNContrib > 0x7fffffffLL) return fail(c, EEC_EINVAL, "too many devices");
   std::vector<int> gpos((size_t)kNContrib * N, -1);
   {
-    std::vector<long long> fill(gptr.begin(), gptr.end() - 1);
+    std::vector<long long> fill(E);   // next item of entry e, and the step between its items
+    for (long long e = 0; e < E; ++e) fill[e] = ghead[e] + (gcnt[e] < kHeavy ? 32 : 1);
     for (int k = 0; k < N; ++k) {
       const int p = pos_of[k];
       const int4 t4 = tidx[p];
@@ -1129,18 +1176,17 @@ static int eec_build_scatter_body(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_
         if (row < 0) continue;
         for (int u = 0; u < 4; ++u) {
           const int s = slot[(size_t)(4 * r + u) * N + p];
-          if (s >= 0) gpos[(size_t)(4 * r + u) * N + p] = (int)fill[s]++;
+          if (s >= 0) {
+            gpos[(size_t)(4 * r + u) * N + p] = (int)fill[s];
+            fill[s] += gcnt[s] < kHeavy ? 32 : 1;
+          }
         }
-        gpos[(size_t)(kNSlot + r) * N + p] = (int)fill[c->nnz + row]++;
+        const long long eb = c->nnz + row;
+        gpos[(size_t)(kNSlot + r) * N + p] = (int)fill[eb];
+        fill[eb] += gcnt[eb] < kHeavy ? 32 : 1;
       }
     }
   }
-  std::vector<int> gheavy;
-  for (long long e = 0; e < E; ++e)
-    if (gptr[e + 1] - gptr[e] >= kHeavy) gheavy.push_back((int)e);
-  if (gptr[E] > 0x7fffffffLL) return fail(c, EEC_EINVAL, "too many contributions");
-  c->n_contrib = gptr[E];
-  const std::vector<int> gptr32(gptr.begin(), gptr.end());
   // backward incidence: unknown -> (terminal, position) in original device order
   std::vector<int> iptr(n + 1, 0);
   for (int k = 0; k < N; ++k)
@@ -1197,6 +1243,7 @@ static int eec_build_scatter_body(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_
   d.N = N;
   d.n = n;
   d.nnz = c->nnz;
+  d.n_win = (int)n_win;
   d.n_heavy = (int)gheavy.size();
   d.n_inc_light = (int)ilight.size();
   d.n_inc_heavy = (int)iheavy.size();
@@ -1208,7 +1255,7 @@ static int eec_build_scatter_body(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_
       (rc = dalloc(c, &d.prm, (size_t)kNPrm * N)) || (rc = dalloc(c, &d.bodyk, (size_t)kNBody * N)) ||
       (rc = dupload(c, &d.vfix, vtab)) ||
       (rc = dupload(c, &d.cards, c->cardk)) || (rc = dupload(c, &d.Alin, Alin)) ||
-      (rc = dupload(c, &d.blin, blin)) || (rc = dupload(c, &d.gat_ptr, gptr32)) ||
+      (rc = dupload(c, &d.blin, blin)) || (rc = dupload(c, &d.gat_woff, gwoff)) || (rc = dupload(c, &d.gat_loc, gloc)) ||
       (rc = dupload(c, &d.gat_pos, gpos)) ||
       (rc = dupload(c, &d.gat_heavy, gheavy)) || (rc = dupload(c, &d.inc_ptr, iptr)) ||
       (rc = dupload(c, &d.inc_light, ilight)) || (rc = dupload(c, &d.inc_heavy, iheavy)) ||

@@ -61,14 +61,20 @@ struct DevTopo {
   double* Alin;     // [nnz]
   double* blin;     // [n]
   // segmented reduction: the evaluation writes contribution j of the device at position k to
-  // cbuf[gat_pos[j * N + k]] (-1: not formed), so that entry e (A entries 0..nnz-1, then b rows)
-  // is the linear part plus cbuf[gat_ptr[e] .. gat_ptr[e+1]), its contributions in
-  // original-device order, read as one contiguous run
-  int* gat_ptr;        // [nnz + n + 1] (at most kNContrib N < 2^31 contributions)
-  int* gat_pos;        // [kNContrib][N] position of each contribution in cbuf, or -1
-  int* gat_heavy;      // entries with kHeavy or more contributions (one warp each)
+  // cbuf[gat_pos[j * N + k]] (-1: not formed). Entry e (A entries 0..nnz-1, then b rows) is its
+  // linear part (written once, when cbuf is allocated), then its contributions in original
+  // device order. The entries of window w (kGatherWin consecutive ones) with fewer than kHeavy
+  // contributions, sorted by their count (ties in entry order), form groups of 32; group g keeps
+  // its items column-major from cbuf[gat_woff[w (kGatherGroups + 1) + g]]: item k of its i-th
+  // entry at 32 k + i (item 0 the linear part; zeros past an entry's end). Heavy entries' runs
+  // follow, contiguous
+  int* gat_woff;           // [n_win (kGatherGroups + 1)] first item of every group, then the end
+  unsigned short* gat_loc; // [n_win kGatherWin] slot 32 g + i -> entry - w kGatherWin (0xffff: none)
+  int n_win;
+  int4* gat_heavy;     // [n_heavy] {entry, first item, items, 0} (one warp each)
   int n_heavy;
-  double* cbuf;        // [gat_ptr[nnz + n]] contributions in entry order (allocated on first use)
+  int* gat_pos;        // [kNContrib][N] position of each contribution in cbuf, or -1
+  double* cbuf;        // (allocated on first use)
   double* buf;         // [kNContrib][N] (allocated on first use)
   double* buf_tran;    // [kNContribTran][N]: transient values G + alpha C (4 x 4) and 4 rhs
   // backward: unknown u gathers gv[src] over inc_src[inc_ptr[u] .. inc_ptr[u+1])
@@ -95,6 +101,8 @@ constexpr int kPipeItem = 128;   // devices per work item of the pipelined colou
 constexpr int kPipeHdr = 4;
 
 constexpr int kHeavy = 32;  // contributions from which an entry gets a whole warp in the gather
+constexpr int kGatherWin = 1024;  // entries per window of the gather (one block)
+constexpr int kGatherGroups = kGatherWin / 32;
 
 constexpr int kStatusTimeout = 1;
 constexpr int kStatusNumeric = 2;
@@ -126,6 +134,8 @@ cudaError_t launch_persistent(const DevTopo& T, const int* color_off_dev, int n_
                               int grid, int dbg, cudaStream_t s, int absent_block = -1);
 int persistent_max_blocks_per_sm(int block, bool want_q);
 cudaError_t launch_gather(const DevTopo& T, double* A, double* b, cudaStream_t s);
+// writes every entry's linear part to the head of its run in a new cbuf
+cudaError_t launch_gather_init(const DevTopo& T, cudaStream_t s);
 // A <- A_lin, b <- b_lin (the linear part), one kernel.
 cudaError_t launch_init_lin(const DevTopo& T, double* A, double* b, cudaStream_t s);
 // Buffered contributions of every colour, in colour order, in one cooperative launch of `grid`
