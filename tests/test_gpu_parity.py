@@ -102,6 +102,36 @@ def test_edge_cases(eec, variant):
             check_against_oracle(eec, circ, o, x, variant)
 
 
+def _fan_net(k):
+    # k transistors with their drains on one free node (2), each gate on a free node of its own,
+    # sources and bodies on the rails: entry (2, 2) and row 2 of b receive k contributions, the
+    # gate rows none (their diagonals keep only gshunt)
+    from helpers import tiny_net
+    fixed = [1, 1] + [0] * (1 + k)
+    vfix = [0.0, 1.0] + [0.0] * (1 + k)
+    types = [1 if i % 3 else -1 for i in range(k)]
+    devs = [(2, 3 + i, 0 if t > 0 else 1, 0 if t > 0 else 1) for i, t in enumerate(types)]
+    W = [1e-6 * (1 + (i % 7)) for i in range(k)]
+    return tiny_net(f"fan{k}", fixed, vfix, devs, types, W=W, res=[(1, 2)], resG=[1e-4])
+
+
+@pytest.mark.parametrize("k", [1, 30, 31, 32, 33, 100, 1500])
+def test_fan_in_around_the_heavy_entry_bound(eec, k):
+    # The segmented reduction's gather sums an entry with fewer than 32 contributions in a group
+    # of 32 entries sorted by their count (up to 32 items per lane: the linear part and 31
+    # contributions), and one with 32 or more in a warp of its own; 1,500 spreads the pattern
+    # over several windows of 1,024 entries.
+    net = _fan_net(k)
+    o = oracle.Oracle(net, CARDS)
+    circ = eec.Circuit(net, CARDS, color=True)
+    for s in range(2):
+        x = netgen.random_x(net, seed=70 + s, lo=-0.2, hi=1.2)
+        ref = o.eval_stamp(x, want_q=True, want_scale=True)
+        outs = {v: check_against_oracle(eec, circ, o, x, v, ref=ref) for v in (2, 3)}
+        again = circ.eval_stamp(dev(x))
+        assert np.array_equal(host(again[0]), outs[3][0]) and np.array_equal(host(again[1]), outs[3][1])
+
+
 @pytest.mark.parametrize("variant", [0, 2, 3, 5])
 @pytest.mark.parametrize("make", [lambda: netgen.sram(16, 16), netgen.ota5t,
                                   lambda: netgen.random_logic(500, seed=2)])
