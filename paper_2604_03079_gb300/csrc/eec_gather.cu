@@ -1,10 +1,10 @@
 // The stamp half of the segmented-reduction schedule (EEC_VARIANT_SEGREDUCE): the per-entry
-// gather of the contributions that the evaluation (MODE_SORTED) wrote in entry order.
+// gather of the contributions that the evaluation (MODE_SORTED) wrote to each entry's items.
 //
 // Sec. II: stamping accumulates every device's contributions into A and b; the colour order
 // makes that lock-free on the CPU. Here the same sums are formed without colours and without
-// atomics: each entry of [A ; b] is its linear part plus its own contiguous run of
-// contributions, summed in one fixed order, so the result is the same bit for bit on every call.
+// atomics: each entry of [A ; b] is its linear part plus its own contributions, summed in one
+// fixed order, so the result is the same bit for bit on every call.
 #include <cuda_runtime.h>
 
 #include "eec_internal.h"
