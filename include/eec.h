@@ -375,6 +375,34 @@ EEC_API int eec_lu_check_host(int32_t n, const int32_t* row_ptr, const int32_t* 
                               const double* b, double* x, int64_t* nnz_lu, int32_t* bad_col);
 
 /*
+ * Host check of the segmented-reduction schedule's gather plan (no GPU; the paper has no
+ * counterpart): the layout eec_build_scatter gives the buffer between EEC_VARIANT_SEGREDUCE's
+ * evaluation and its per-entry gather, for n_entries A/b entries (A values, then b rows) with
+ * cnt[e] >= 0 device contributions each. Entry e occupies 1 + cnt[e] items: its linear part,
+ * then its contributions in original device order. Per window of EEC_GATHER_WINDOW entries, the
+ * entries with fewer than EEC_GATHER_HEAVY contributions are sorted by their count (ties in entry
+ * order) and dealt to groups of 32, each group stored column-major over 32 x (1 + its largest
+ * count) items (zeros past an entry's end); the other entries' runs follow all windows,
+ * contiguous. Outputs (each nullable, host):
+ *  item_of [n_entries]   item of entry e's linear part
+ *  step_of [n_entries]   distance between entry e's consecutive items (32 or 1)
+ *  woff    [n_win * 33]  n_win = ceil(n_entries / EEC_GATHER_WINDOW): per window the first item
+ *                        of each of its 32 groups, then the window's end
+ *  loc     [n_win * EEC_GATHER_WINDOW]  per window and slot 32 g + i: entry - w * EEC_GATHER_WINDOW,
+ *                        or 0xffff for an empty slot
+ *  heavy   [3 * n_heavy] per entry with EEC_GATHER_HEAVY or more contributions, in entry order:
+ *                        entry, first item, items
+ *  *n_items              the buffer's length in items
+ * Returns EEC_EINVAL for a negative count, more than 2^31 - 1 entries, or a plan longer than
+ * 2^31 - 1 items.
+ */
+#define EEC_GATHER_WINDOW 1024
+#define EEC_GATHER_HEAVY 32
+EEC_API int eec_gather_plan_host(int64_t n_entries, const int32_t* cnt, int64_t* item_of,
+                                 int32_t* step_of, int32_t* woff, uint16_t* loc, int32_t* heavy,
+                                 int64_t* n_items);
+
+/*
  * Transient companion stamp of one Newton iterate of a time step (the transient loop of Sec. II,
  * Fig. 1, re-forms A x = b at every Newton iteration of every step). The terminal charges q_t
  * are integrated by a one-step rule: the capacitive current into the device is

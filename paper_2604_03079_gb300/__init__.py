@@ -37,6 +37,8 @@ EEC_COLOR_GREEDY_SEQ, EEC_COLOR_JP_INDEX, EEC_COLOR_JP_RANDOM = 0, 1, 2
 EEC_RAIL_ELIMINATE, EEC_RAIL_MNA_BRANCH = 0, 1
 EEC_SOLVER_LU = 2
 EEC_CARD_LEN = 21
+EEC_GATHER_WINDOW = 1024   # the gather plan's window and heavy-entry bound (eec.h)
+EEC_GATHER_HEAVY = 32
 
 
 
@@ -107,6 +109,7 @@ _SIG = {
     "eec_lu_check_host": (ctypes.c_int, [_I32, _P, _P, _P, _P, _P, ctypes.POINTER(_I64),
                                          ctypes.POINTER(_I32)]),
     "eec_math_check": (ctypes.c_int, [_I32, _I64, _P, _P, _P, _P]),
+    "eec_gather_plan_host": (ctypes.c_int, [_I64, _P, _P, _P, _P, _P, _P, ctypes.POINTER(_I64)]),
     "eec_test_barrier_timeout": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "eec_profile_enable": (ctypes.c_int, [_P, _I32]),
     "eec_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(_F64), ctypes.POINTER(_F64),
@@ -417,6 +420,30 @@ def eec_newton_info(ctx):
     _check(ctx, _load().eec_newton_info(ctx, info))
     return {"solves": int(info[0]), "stages": int(info[1]), "sweeps": int(info[2]),
             "path": int(info[3])}
+
+
+def eec_gather_plan_host(cnt):
+    """Host check of the segmented reduction's gather plan (no GPU) for entries with cnt[e]
+    contributions: -> dict of item_of, step_of, woff [n_win, 33], loc [n_win, 1024], heavy
+    [n_heavy, 3] (entry, first item, items) and n_items."""
+    import numpy as np
+    c = np.ascontiguousarray(cnt, np.int32)
+    E = c.size
+    n_win = -(-E // EEC_GATHER_WINDOW)
+    n_heavy = int(np.count_nonzero(c >= EEC_GATHER_HEAVY))
+    item_of = np.zeros(E, np.int64)
+    step_of = np.zeros(E, np.int32)
+    woff = np.zeros((n_win, 33), np.int32)
+    loc = np.zeros((n_win, EEC_GATHER_WINDOW), np.uint16)
+    heavy = np.zeros((n_heavy, 3), np.int32)
+    n_items = _I64(0)
+    rc = _load().eec_gather_plan_host(E, c.ctypes.data, item_of.ctypes.data, step_of.ctypes.data,
+                                      woff.ctypes.data, loc.ctypes.data, heavy.ctypes.data,
+                                      ctypes.byref(n_items))
+    if rc != EEC_OK:
+        raise EECError(rc, "eec_gather_plan_host failed")
+    return {"item_of": item_of, "step_of": step_of, "woff": woff, "loc": loc, "heavy": heavy,
+            "n_items": n_items.value}
 
 
 def eec_lu_check_host(row_ptr, col, a, b):

@@ -363,6 +363,58 @@ bool valid_card(const double* a) {
          a[10] >= 0 && a[18] >= 0 && a[13] >= 0 && a[14] >= 0;
 }
 
+// The segmented reduction's gather plan for entries with gcnt[e] contributions each. Per window
+// of kGatherWin entries, the light ones (< kHeavy contributions) are sorted by their count (ties
+// in entry order) and dealt to groups of 32, each stored column-major: the gather then adds one
+// item of 32 entries per instruction, and each entry's sum keeps the serial order. A group takes
+// 32 x (1 + its largest count) items. Heavy entries' runs follow, contiguous. ghead[e] = item of
+// entry e's linear part (its contributions follow 32 items apart when light, 1 when heavy);
+// gwoff[w (kGatherGroups + 1) + g] = first item of group g of window w, then the window's end;
+// gloc[w kGatherWin + slot] = entry - w kGatherWin or 0xffff; gheavy = {entry, first item, items,
+// 0}. False when the plan would exceed 2^31 - 1 items.
+static_assert(EEC_GATHER_WINDOW == kGatherWin && EEC_GATHER_HEAVY == kHeavy,
+              "the gather plan's constants in eec.h");
+bool gather_plan(const std::vector<int>& gcnt, std::vector<long long>& ghead,
+                 std::vector<int>& gwoff, std::vector<unsigned short>& gloc,
+                 std::vector<int4>& gheavy, long long& n_items) {
+  const long long E = (long long)gcnt.size();
+  const long long n_win = (E + kGatherWin - 1) / kGatherWin;
+  ghead.assign(E, 0);
+  gwoff.assign((size_t)n_win * (kGatherGroups + 1), 0);
+  gloc.assign((size_t)n_win * kGatherWin, 0xffff);
+  gheavy.clear();
+  long long gitems = 0;
+  std::vector<long long> order;
+  for (long long w = 0; w < n_win; ++w) {
+    const long long e0 = w * kGatherWin, e1 = std::min(E, e0 + kGatherWin);
+    order.clear();
+    for (long long e = e0; e < e1; ++e)
+      if (gcnt[e] < kHeavy) order.push_back(e);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](long long x, long long y) { return gcnt[x] < gcnt[y]; });
+    for (int g = 0; g < kGatherGroups; ++g) {
+      gwoff[(size_t)w * (kGatherGroups + 1) + g] = (int)std::min(gitems, 0x7fffffffLL);
+      const size_t s0 = (size_t)32 * g, s1 = std::min(order.size(), s0 + 32);
+      if (s0 >= s1) continue;
+      for (size_t i = s0; i < s1; ++i) {
+        ghead[order[i]] = gitems + (long long)(i - s0);
+        gloc[(size_t)w * kGatherWin + i] = (unsigned short)(order[i] - e0);
+      }
+      gitems += 32LL * (1 + gcnt[order[s1 - 1]]);   // the group's rows: its largest run
+    }
+    gwoff[(size_t)w * (kGatherGroups + 1) + kGatherGroups] = (int)std::min(gitems, 0x7fffffffLL);
+  }
+  for (long long e = 0; e < E; ++e) {
+    if (gcnt[e] < kHeavy) continue;
+    ghead[e] = gitems;
+    if (gitems + 1 + gcnt[e] <= 0x7fffffffLL)
+      gheavy.push_back(make_int4((int)e, (int)gitems, 1 + gcnt[e], 0));
+    gitems += 1 + gcnt[e];
+  }
+  n_items = gitems;
+  return gitems <= 0x7fffffffLL;
+}
+
 int ensure_buf(eec_ctx* c) {
   if (c->d.buf) return EEC_OK;
   return dalloc(c, &c->d.buf, (size_t)kNContrib * c->n_dev);
@@ -1103,11 +1155,7 @@ static int eec_build_scatter_body(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_
     Alin[find(jr[r], a)] += 1.0;     // source equation: v_rail = its voltage
     blin[jr[r]] += c->vfix[c->rail[r]];
   }
-  // segmented-reduction map. Entry e is its linear part, then its contributions in original
-  // device order. Per window of kGatherWin entries, the light ones (< kHeavy contributions) are
-  // sorted by their count and dealt to groups of 32, each stored column-major (the gather then
-  // adds one item of 32 entries per instruction, and each entry's sum keeps the serial order);
-  // heavy entries' runs follow, contiguous.
+  // segmented-reduction map: contributions per entry, then the gather plan (gather_plan)
   const long long E = c->nnz + n;
   std::vector<int> gcnt(E, 0);
   for (int k = 0; k < N; ++k) {
@@ -1124,43 +1172,13 @@ static int eec_build_scatter_body(eec_ctx* c, int32_t* n_unknowns, int64_t* nnz_
       gcnt[c->nnz + row]++;
     }
   }
-  const long long n_win = (E + kGatherWin - 1) / kGatherWin;
-  std::vector<long long> ghead(E);   // item of the linear part
-  std::vector<int> gwoff((size_t)n_win * (kGatherGroups + 1));
-  std::vector<unsigned short> gloc((size_t)n_win * kGatherWin, 0xffff);
+  std::vector<long long> ghead;
+  std::vector<int> gwoff;
+  std::vector<unsigned short> gloc;
   std::vector<int4> gheavy;
-  long long gitems = 0;
-  {
-    std::vector<long long> order;
-    for (long long w = 0; w < n_win; ++w) {
-      const long long e0 = w * kGatherWin, e1 = std::min(E, e0 + kGatherWin);
-      order.clear();
-      for (long long e = e0; e < e1; ++e)
-        if (gcnt[e] < kHeavy) order.push_back(e);
-      std::stable_sort(order.begin(), order.end(),
-                       [&](long long x, long long y) { return gcnt[x] < gcnt[y]; });
-      for (int g = 0; g < kGatherGroups; ++g) {
-        gwoff[(size_t)w * (kGatherGroups + 1) + g] = (int)std::min(gitems, 0x7fffffffLL);
-        const size_t s0 = (size_t)32 * g, s1 = std::min(order.size(), s0 + 32);
-        if (s0 >= s1) continue;
-        for (size_t i = s0; i < s1; ++i) {
-          ghead[order[i]] = gitems + (long long)(i - s0);
-          gloc[(size_t)w * kGatherWin + i] = (unsigned short)(order[i] - e0);
-        }
-        gitems += 32LL * (1 + gcnt[order[s1 - 1]]);   // the group's rows: its largest run
-      }
-      gwoff[(size_t)w * (kGatherGroups + 1) + kGatherGroups] = (int)std::min(gitems, 0x7fffffffLL);
-    }
-    for (long long e = 0; e < E; ++e) {
-      if (gcnt[e] < kHeavy) continue;
-      ghead[e] = gitems;
-      if (gitems + 1 + gcnt[e] <= 0x7fffffffLL)
-        gheavy.push_back(make_int4((int)e, (int)gitems, 1 + gcnt[e], 0));
-      gitems += 1 + gcnt[e];
-    }
-    if (gitems > 0x7fffffffLL) return fail(c, EEC_EINVAL, "too many contributions");
-    c->n_stream = gitems;
-  }
+  if (!gather_plan(gcnt, ghead, gwoff, gloc, gheavy, c->n_stream))
+    return fail(c, EEC_EINVAL, "too many contributions");
+  const long long n_win = (long long)gwoff.size() / (kGatherGroups + 1);
   // position in cbuf of every contribution (j, p): the evaluation writes it there
   if ((long long)N * kNContrib > 0x7fffffffLL) return fail(c, EEC_EINVAL, "too many devices");
   std::vector<int> gpos((size_t)kNContrib * N, -1);
@@ -2541,6 +2559,43 @@ int eec_lu_check_host(int32_t n, const int32_t* row_ptr, const int32_t* col, con
                       const double* b, double* x, int64_t* nnz_lu, int32_t* bad_col) {
   try {
     return eec_lu_check_host_body(n, row_ptr, col, a, b, x, nnz_lu, bad_col);
+  } catch (...) {
+    return abi_exception(nullptr);
+  }
+}
+
+static int eec_gather_plan_host_body(int64_t n_entries, const int32_t* cnt, int64_t* item_of,
+                                     int32_t* step_of, int32_t* woff, uint16_t* loc,
+                                     int32_t* heavy, int64_t* n_items) {
+  if (n_entries < 0 || n_entries > 0x7fffffffLL || (n_entries > 0 && !cnt)) return EEC_EINVAL;
+  const std::vector<int> gcnt(cnt, cnt + n_entries);
+  for (int v : gcnt)
+    if (v < 0) return EEC_EINVAL;
+  std::vector<long long> ghead;
+  std::vector<int> gwoff;
+  std::vector<unsigned short> gloc;
+  std::vector<int4> gheavy;
+  long long items = 0;
+  if (!gather_plan(gcnt, ghead, gwoff, gloc, gheavy, items)) return EEC_EINVAL;
+  for (long long e = 0; e < n_entries; ++e) {
+    if (item_of) item_of[e] = ghead[e];
+    if (step_of) step_of[e] = gcnt[e] < kHeavy ? 32 : 1;
+  }
+  if (woff) std::copy(gwoff.begin(), gwoff.end(), woff);
+  if (loc) std::copy(gloc.begin(), gloc.end(), loc);
+  if (heavy)
+    for (size_t h = 0; h < gheavy.size(); ++h) {
+      heavy[3 * h] = gheavy[h].x;
+      heavy[3 * h + 1] = gheavy[h].y;
+      heavy[3 * h + 2] = gheavy[h].z;
+    }
+  if (n_items) *n_items = items;
+  return EEC_OK;
+}
+int eec_gather_plan_host(int64_t n_entries, const int32_t* cnt, int64_t* item_of, int32_t* step_of,
+                         int32_t* woff, uint16_t* loc, int32_t* heavy, int64_t* n_items) {
+  try {
+    return eec_gather_plan_host_body(n_entries, cnt, item_of, step_of, woff, loc, heavy, n_items);
   } catch (...) {
     return abi_exception(nullptr);
   }
