@@ -109,7 +109,8 @@ constexpr int kStatusNumeric = 2;
 
 // ---- kernels (eec_kernels.cu) ----
 // MODE_BUFFER: contributions into buf (layout position-major, read by the colour-ordered stamps);
-// MODE_SORTED: contributions into cbuf in entry order (read by the segmented-reduction gather).
+// MODE_SORTED: contributions into cbuf at gat_pos, each entry's items in device order (read by
+// the segmented-reduction gather).
 enum StampMode : int { MODE_RMW = 0, MODE_ATOMIC = 1, MODE_BUFFER = 2, MODE_SORTED = 3 };
 
 cudaError_t launch_params(const DevTopo& T, cudaStream_t s);

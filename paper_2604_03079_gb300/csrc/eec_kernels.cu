@@ -11,8 +11,9 @@
 //               GPU form);
 //   MODE_BUFFER evaluate into a per-device buffer ("loadomp"/"Color" buffer), then a stamp of
 //               the buffer in colour order;
-//   MODE_SORTED evaluate into a contribution buffer laid out in entry order, then the per-entry
-//               gather of eec_gather.cu (segmented reduction, deterministic, no colours).
+//   MODE_SORTED evaluate into a contribution buffer laid out by entry (windows of entries sorted
+//               by their contribution count), then the per-entry gather of eec_gather.cu
+//               (segmented reduction, deterministic, no colours).
 // The evaluation is FP64-pipe bound on GB300 (FP64 issues at about 1/64 of the FP32 rate), so
 // the kernels aim at a saturated FP64 pipe: one device per thread, few warps per SM suffice;
 // parameters are precomputed per device so that no division on W or L is repeated per call.
@@ -148,8 +149,8 @@ __device__ __forceinline__ void eval_one(const DevTopo& T, int k, const double* 
   const int term[3] = {0, 2, 3};
   bool bc_ok = true;
   if (MODE == MODE_SORTED) {
-    // the same contributions as MODE_BUFFER, each written to its place in entry order (the
-    // gather then reads every entry's contributions as one contiguous run)
+    // the same contributions as MODE_BUFFER, each written to its item in the gather's buffer
+    // (gat_pos: the entry's items, in original device order)
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
       if (idx[term[r]] < 0) continue;
