@@ -190,11 +190,42 @@ def sum_over_ranks(value, device=None):
     return float(t.item())
 
 
-def cpu_baseline(net, x, budget_s=10.0):
-    """The oracle as it stands, single-threaded, on the host: full workload, repeated."""
+def parity_vs_oracle(o, x, A, b, q, tol=1e-12):
+    """Full-size parity of one GPU step (host copies of A, b, q) against the oracle, untimed:
+    per entry the cancellation-aware error |gpu - oracle| / max(|oracle|, S_e), S_e the sum of
+    |contributions| into the entry (the tests' criterion, at most tol), beside the plain relative
+    error |gpu - oracle| / |oracle| over the entries where the oracle is not zero; charges
+    relative to each device's largest terminal charge."""
+    r = o.eval_stamp(x, want_q=True, want_scale=True)
+    rec = {"tol": tol}
+    ok = True
+    for k, got, ref, sc in (("A", A, r["A"], r["A_scale"]), ("b", b, r["b"], r["b_scale"])):
+        den = np.maximum(np.abs(ref), sc)
+        den = np.where(den == 0, 1.0, den)
+        err = np.abs(got - ref) / den
+        nz = ref != 0
+        plain = np.abs(got[nz] - ref[nz]) / np.abs(ref[nz])
+        rec[k] = {"entries": int(ref.size), "max_err": float(err.max(initial=0.0)),
+                  "max_plain": float(plain.max(initial=0.0)),
+                  "p99_plain": float(np.quantile(plain, 0.99)) if plain.size else 0.0,
+                  "median_plain": float(np.median(plain)) if plain.size else 0.0}
+        ok = ok and rec[k]["max_err"] <= tol
+    if r["q"].size:
+        qg = q.reshape(4, -1)
+        scale = np.maximum(np.abs(r["q"]).max(axis=0, keepdims=True), 1e-300)
+        rec["q"] = {"max_err": float((np.abs(qg - r["q"]) / scale).max())}
+    rec["pass"] = bool(ok)
+    return rec
+
+
+def cpu_baseline(net, x, budget_s=10.0, gpu_step=None):
+    """The oracle as it stands, single-threaded, on the host: full workload, repeated. With
+    gpu_step = (A, b, q) from the GPU at the same x, also the full-size parity record (one
+    untimed oracle call with the error scales)."""
     import netgen
     import oracle
     o = oracle.Oracle(net, netgen.default_cards())
+    parity = parity_vs_oracle(o, x, *gpu_step) if gpu_step is not None else None
     reps, t0 = 0, time.perf_counter()
     while True:
         o.eval_stamp(x, want_q=True)
@@ -202,10 +233,11 @@ def cpu_baseline(net, x, budget_s=10.0):
         el = time.perf_counter() - t0
         if el >= budget_s or (reps >= 1 and el * (reps + 1) / reps > 3 * budget_s):
             break
-    return {"value": net.n_dev * reps / el, "unit": UNIT, "cores": 1,
-            "host_cores_available": len(os.sched_getaffinity(0)), "kind": "oracle",
-            "sample": f"whole workload ({net.n_dev} devices) x {reps} eval_stamp calls, "
-                      f"{el:.1f} s, 1 thread"}
+    out = {"value": net.n_dev * reps / el, "unit": UNIT, "cores": 1,
+           "host_cores_available": len(os.sched_getaffinity(0)), "kind": "oracle",
+           "sample": f"whole workload ({net.n_dev} devices) x {reps} eval_stamp calls, "
+                     f"{el:.1f} s, 1 thread"}
+    return out, parity
 
 
 def _merged(net, nets):
@@ -420,7 +452,12 @@ def run_ours(args):
             if world == 1 and not args.no_extras:
                 out["extras"] = extras(eec, circ, mnet, x, xt, A, b, q, args, dev)
             if world == 1:
-                out["cpu_baseline"] = cpu_baseline(mnet, x)
+                # one more step of the timed schedule at the same x (the extras reuse A and b),
+                # for the parity record
+                circ.eval_stamp(xt, A, b, q)
+                torch.cuda.synchronize()
+                step = tuple(t.cpu().numpy() for t in (A, b, q))
+                out["cpu_baseline"], out["parity"] = cpu_baseline(mnet, x, gpu_step=step)
                 out["gpu_over_oracle"] = value / out["cpu_baseline"]["value"]
             print(json.dumps(out))
     if world > 1:

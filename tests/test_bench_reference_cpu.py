@@ -34,3 +34,26 @@ def test_reference_arm_prints_one_json_line():
 def test_reference_arm_other_ranks_exit_without_work():
     out = _run({"RANK": "1", "WORLD_SIZE": "2"})
     assert out.returncode == 0 and out.stdout.strip() == ""
+
+
+def test_bench_parity_record_on_the_oracle_itself():
+    # the bench's full-size parity record, fed the oracle's own step: zero error; one entry
+    # moved by 1e-9 of its size: the cancellation-aware error sees it and the record fails
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    import netgen
+    import oracle
+    net = netgen.random_logic(300, seed=3)
+    x = netgen.random_x(net)
+    o = oracle.Oracle(net, netgen.default_cards())
+    r = o.eval_stamp(x, want_q=True)
+    rec = bench.parity_vs_oracle(o, x, r["A"].copy(), r["b"].copy(), r["q"].reshape(-1).copy())
+    assert rec["pass"] and rec["A"]["max_err"] == 0 and rec["b"]["max_plain"] == 0
+    assert rec["q"]["max_err"] == 0 and rec["A"]["entries"] == r["A"].size
+    A = r["A"].copy()
+    k = int(np.argmax(np.abs(A)))
+    A[k] *= 1 + 1e-9
+    bad = bench.parity_vs_oracle(o, x, A, r["b"].copy(), r["q"].reshape(-1).copy())
+    assert not bad["pass"] and 1e-10 < bad["A"]["max_err"] <= 1e-9 * (1 + 1e-6)
+    assert abs(bad["A"]["max_plain"] - 1e-9) < 1e-12
