@@ -375,6 +375,30 @@ EEC_API int eec_lu_check_host(int32_t n, const int32_t* row_ptr, const int32_t* 
                               const double* b, double* x, int64_t* nnz_lu, int32_t* bad_col);
 
 /*
+ * The same host check with a choice of column order, and what the plan implies for the GPU:
+ *  order   EEC_LU_ORDER_MMD: the multiple-minimum-degree order of A + A^T that eec_newton_dc's
+ *          solver EEC_SOLVER_LU uses (eec_lu_check_host); EEC_LU_ORDER_BTF: block triangular
+ *          form, the strongly connected components of A's directed graph (an edge i -> j for
+ *          every off-diagonal A(i, j)), each placed after every component its edges reach,
+ *          with multiple minimum degree inside each component (with A's diagonal present the
+ *          permuted matrix is block lower triangular). Host check only: eec_newton_dc does not
+ *          use this order yet.
+ *  q_out   [n] (nullable): the column order (the plan eliminates column q_out[k] k-th)
+ *  depth   [3] (nullable): the longest chains of dependent steps of the plan, which bound the
+ *          GPU's steps however many warps it has: [0] the refactorisation (column j waits for
+ *          every column of U(:, j)), [1] the forward substitution (row i waits for the columns
+ *          of L(i, :)), [2] the backward substitution (row i waits for those of U(i, :))
+ * The other arguments and the errors are those of eec_lu_check_host; EEC_EINVAL for an unknown
+ * order.
+ */
+#define EEC_LU_ORDER_MMD 0
+#define EEC_LU_ORDER_BTF 1
+EEC_API int eec_lu_check_host_ex(int32_t n, const int32_t* row_ptr, const int32_t* col,
+                                 const double* a, const double* b, int32_t order, double* x,
+                                 int32_t* q_out, int64_t* nnz_lu, int32_t* bad_col,
+                                 int32_t* depth);
+
+/*
  * Host check of the segmented-reduction schedule's gather plan (no GPU; the paper has no
  * counterpart): the layout eec_build_scatter gives the buffer between EEC_VARIANT_SEGREDUCE's
  * evaluation and its per-entry gather, for n_entries A/b entries (A values, then b rows) with

@@ -36,6 +36,8 @@ EEC_CONFLICT_FREE_NODE, EEC_CONFLICT_ANY_NONGROUND, EEC_CONFLICT_WRITE_ROWS = 0,
 EEC_COLOR_GREEDY_SEQ, EEC_COLOR_JP_INDEX, EEC_COLOR_JP_RANDOM = 0, 1, 2
 EEC_RAIL_ELIMINATE, EEC_RAIL_MNA_BRANCH = 0, 1
 EEC_SOLVER_LU = 2
+EEC_LU_ORDER_MMD = 0   # column orders of eec_lu_check_host_ex
+EEC_LU_ORDER_BTF = 1
 EEC_CARD_LEN = 21
 EEC_GATHER_WINDOW = 1024   # the gather plan's window and heavy-entry bound (eec.h)
 EEC_GATHER_HEAVY = 32
@@ -108,6 +110,8 @@ _SIG = {
     "eec_lu_solve": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "eec_lu_check_host": (ctypes.c_int, [_I32, _P, _P, _P, _P, _P, ctypes.POINTER(_I64),
                                          ctypes.POINTER(_I32)]),
+    "eec_lu_check_host_ex": (ctypes.c_int, [_I32, _P, _P, _P, _P, _I32, _P, _P,
+                                            ctypes.POINTER(_I64), ctypes.POINTER(_I32), _P]),
     "eec_math_check": (ctypes.c_int, [_I32, _I64, _P, _P, _P, _P]),
     "eec_gather_plan_host": (ctypes.c_int, [_I64, _P, _P, _P, _P, _P, _P, ctypes.POINTER(_I64)]),
     "eec_test_barrier_timeout": (ctypes.c_int, [_P, _P, _P, _P, _P]),
@@ -466,6 +470,32 @@ def eec_lu_check_host(row_ptr, col, a, b):
     if rc != EEC_OK:
         raise EECError(rc, "eec_lu_check_host failed")
     return x, int(nnz.value), int(bad.value)
+
+
+def eec_lu_check_host_ex(row_ptr, col, a, b, order=EEC_LU_ORDER_MMD):
+    """Host check of the sparse LU with a choice of column order (no GPU): -> (x solving A x = b,
+    the column order q, entries of L and U, first column whose refactorised pivot degraded or
+    -1, the longest chains of dependent steps of the plan: (refactorisation, forward
+    substitution, backward substitution))."""
+    import numpy as np
+    rp = np.ascontiguousarray(row_ptr, np.int32)
+    cl = np.ascontiguousarray(col, np.int32)
+    av = np.ascontiguousarray(a, np.float64)
+    bv = np.ascontiguousarray(b, np.float64)
+    n = rp.size - 1
+    if cl.size != rp[-1] or av.size != rp[-1] or bv.size != n:
+        raise ValueError("eec_lu_check_host_ex: inconsistent sizes")
+    x = np.zeros(n)
+    q = np.zeros(n, np.int32)
+    nnz = _I64(0)
+    bad = _I32(0)
+    depth = np.zeros(3, np.int32)
+    rc = _load().eec_lu_check_host_ex(n, rp.ctypes.data, cl.ctypes.data, av.ctypes.data,
+                                      bv.ctypes.data, int(order), x.ctypes.data, q.ctypes.data,
+                                      ctypes.byref(nnz), ctypes.byref(bad), depth.ctypes.data)
+    if rc != EEC_OK:
+        raise EECError(rc, "eec_lu_check_host_ex failed")
+    return x, q, int(nnz.value), int(bad.value), tuple(int(v) for v in depth)
 
 
 def eec_newton_dc(ctx, x, A, b, max_iter=200, vstep=0.2, step_rule=0, solver=0, tol_abs=1e-12,

@@ -2530,9 +2530,12 @@ int eec_test_barrier_timeout(eec_ctx* c, const double* x, double* A, double* b, 
   }
 }
 
-static int eec_lu_check_host_body(int32_t n, const int32_t* row_ptr, const int32_t* col, const double* a,
-                                  const double* b, double* x, int64_t* nnz_lu, int32_t* bad_col) {
+static int eec_lu_check_host_ex_body(int32_t n, const int32_t* row_ptr, const int32_t* col,
+                                     const double* a, const double* b, int32_t order, double* x,
+                                     int32_t* q_out, int64_t* nnz_lu, int32_t* bad_col,
+                                     int32_t* depth) {
   if (n < 1 || !row_ptr || !col || !a || !b || !x) return EEC_EINVAL;
+  if (order != EEC_LU_ORDER_MMD && order != EEC_LU_ORDER_BTF) return EEC_EINVAL;
   const std::vector<int> rp(row_ptr, row_ptr + n + 1);
   if (rp[0] != 0) return EEC_EINVAL;
   for (int i = 0; i < n; ++i)
@@ -2542,7 +2545,9 @@ static int eec_lu_check_host_body(int32_t n, const int32_t* row_ptr, const int32
     if (v < 0 || v >= n) return EEC_EINVAL;
   const std::vector<double> av(a, a + rp[n]), bv(b, b + n);
   std::vector<int> q;
-  if (!lu_min_degree_order(n, rp, cl, q)) return EEC_ENOMEM;
+  const bool ok = order == EEC_LU_ORDER_BTF ? lu_btf_order(n, rp, cl, q)
+                                            : lu_min_degree_order(n, rp, cl, q);
+  if (!ok) return EEC_ENOMEM;
   LuPlan P;
   std::string err;
   const int rc = lu_analyze(n, rp, cl, av, q, P, err);
@@ -2551,14 +2556,27 @@ static int eec_lu_check_host_body(int32_t n, const int32_t* row_ptr, const int32
   int bad = -1;
   lu_refactor_solve_host(P, av, bv, kLuTiny, xv, &bad);
   std::copy(xv.begin(), xv.end(), x);
+  if (q_out) std::copy(q.begin(), q.end(), q_out);
   if (nnz_lu) *nnz_lu = P.cptr[n];
   if (bad_col) *bad_col = bad;
+  if (depth) lu_plan_depth(P, depth);
   return EEC_OK;
+}
+int eec_lu_check_host_ex(int32_t n, const int32_t* row_ptr, const int32_t* col, const double* a,
+                         const double* b, int32_t order, double* x, int32_t* q_out,
+                         int64_t* nnz_lu, int32_t* bad_col, int32_t* depth) {
+  try {
+    return eec_lu_check_host_ex_body(n, row_ptr, col, a, b, order, x, q_out, nnz_lu, bad_col,
+                                     depth);
+  } catch (...) {
+    return abi_exception(nullptr);
+  }
 }
 int eec_lu_check_host(int32_t n, const int32_t* row_ptr, const int32_t* col, const double* a,
                       const double* b, double* x, int64_t* nnz_lu, int32_t* bad_col) {
   try {
-    return eec_lu_check_host_body(n, row_ptr, col, a, b, x, nnz_lu, bad_col);
+    return eec_lu_check_host_ex_body(n, row_ptr, col, a, b, EEC_LU_ORDER_MMD, x, nullptr, nnz_lu,
+                                     bad_col, nullptr);
   } catch (...) {
     return abi_exception(nullptr);
   }

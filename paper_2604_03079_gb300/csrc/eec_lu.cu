@@ -116,6 +116,130 @@ bool lu_min_degree_order(int n, const std::vector<int>& rp, const std::vector<in
   return true;
 }
 
+// Block triangular order: the strongly connected components of the directed graph of A (an
+// edge i -> j for every off-diagonal A(i, j)), each component after every component its edges
+// lead to, and each component's columns in the multiple-minimum-degree order of its own
+// symmetric pattern. Tarjan's algorithm completes a component only after every component it
+// reaches, so its completion order is such an order. With A's diagonal present the permuted
+// matrix is block lower triangular: elimination fills only inside the diagonal blocks and the
+// rows below them, and a column waits only on columns it reaches. A netlist whose gates are
+// wired without loops (a DAG, components of one gate) then factors with almost no fill and a
+// chain of dependent columns as long as its logic depth; a minimum-degree order of the
+// symmetric pattern ignores the direction and fills. False when a component's minimum-degree
+// order outgrows its budget.
+bool lu_btf_order(int n, const std::vector<int>& rp, const std::vector<int>& col,
+                  std::vector<int>& order) {
+  std::vector<int> index(n, -1), low(n, 0), comp(n, -1);
+  std::vector<char> on_stack(n, 0);
+  std::vector<int> stack, members;          // Tarjan's stack; nodes by component, in order
+  std::vector<int> comp_start{0};
+  std::vector<std::pair<int, int>> call;    // (node, next edge) of the depth-first search
+  int next_index = 0;
+  for (int s = 0; s < n; ++s) {
+    if (index[s] >= 0) continue;
+    index[s] = low[s] = next_index++;
+    stack.push_back(s);
+    on_stack[s] = 1;
+    call.push_back({s, rp[s]});
+    while (!call.empty()) {
+      const int v = call.back().first;
+      const int e = call.back().second;
+      if (e < rp[v + 1]) {
+        call.back().second = e + 1;
+        const int w = col[e];
+        if (w == v) continue;
+        if (index[w] < 0) {
+          index[w] = low[w] = next_index++;
+          stack.push_back(w);
+          on_stack[w] = 1;
+          call.push_back({w, rp[w]});
+        } else if (on_stack[w]) {
+          low[v] = std::min(low[v], index[w]);
+        }
+        continue;
+      }
+      if (low[v] == index[v]) {   // v roots a component: pop it
+        const int c = (int)comp_start.size() - 1;
+        int w;
+        do {
+          w = stack.back();
+          stack.pop_back();
+          on_stack[w] = 0;
+          comp[w] = c;
+          members.push_back(w);
+        } while (w != v);
+        comp_start.push_back((int)members.size());
+      }
+      call.pop_back();
+      if (!call.empty()) {
+        const int u = call.back().first;
+        low[u] = std::min(low[u], low[v]);
+      }
+    }
+  }
+  order.clear();
+  order.reserve(n);
+  std::vector<int> local(n, -1), srp, scol, sub;
+  for (size_t c = 0; c + 1 < comp_start.size(); ++c) {
+    const int b0 = comp_start[c], b1 = comp_start[c + 1], m = b1 - b0;
+    if (m == 1) {
+      order.push_back(members[b0]);
+      continue;
+    }
+    std::vector<int> nodes(members.begin() + b0, members.begin() + b1);
+    std::sort(nodes.begin(), nodes.end());
+    for (int i = 0; i < m; ++i) local[nodes[i]] = i;
+    srp.assign(1, 0);
+    scol.clear();
+    for (int i = 0; i < m; ++i) {
+      const int r = nodes[i];
+      for (int e = rp[r]; e < rp[r + 1]; ++e)
+        if (comp[col[e]] == (int)c) scol.push_back(local[col[e]]);
+      srp.push_back((int)scol.size());
+    }
+    if (!lu_min_degree_order(m, srp, scol, sub)) {
+      order.clear();
+      return false;
+    }
+    for (int i : sub) order.push_back(nodes[i]);
+  }
+  return true;
+}
+
+// Longest chains of dependent steps of a plan, which the GPU can take in no fewer steps however
+// many warps it has: depth[0] of the refactorisation (column j waits for every column k of
+// U(:, j)), depth[1] of the forward substitution (row i waits for the columns of L(i, :)),
+// depth[2] of the backward substitution (row i waits for the columns of U(i, :)).
+void lu_plan_depth(const LuPlan& P, int depth[3]) {
+  const int n = P.n;
+  std::vector<int> d(n, 0);
+  int best = 0;
+  for (int j = 0; j < n; ++j) {
+    int m = 0;
+    for (int t = P.uptr[j]; t < P.uptr[j + 1]; ++t)
+      if (P.uk[t] != j) m = std::max(m, d[P.uk[t]]);
+    d[j] = m + 1;
+    best = std::max(best, d[j]);
+  }
+  depth[0] = best;
+  best = 0;
+  for (int i = 0; i < n; ++i) {
+    int m = 0;
+    for (int t = P.lrptr[i]; t < P.lrptr[i + 1]; ++t) m = std::max(m, d[P.lrcol[t]]);
+    d[i] = m + 1;
+    best = std::max(best, d[i]);
+  }
+  depth[1] = best;
+  best = 0;
+  for (int i = n - 1; i >= 0; --i) {
+    int m = 0;
+    for (int t = P.urptr[i]; t < P.urptr[i + 1]; ++t) m = std::max(m, d[P.urcol[t]]);
+    d[i] = m + 1;
+    best = std::max(best, d[i]);
+  }
+  depth[2] = best;
+}
+
 constexpr double kLuDiagPref = 1e-3;
 
 // Left-looking LU with threshold partial pivoting of B = A(:, q) (A in CSR, symmetric pattern

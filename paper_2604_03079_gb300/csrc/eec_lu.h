@@ -48,6 +48,14 @@ long long lu_entry_budget(long long nnz);
 // empty) when the elimination graph would outgrow lu_entry_budget.
 bool lu_min_degree_order(int n, const std::vector<int>& rp, const std::vector<int>& col,
                          std::vector<int>& order);
+// Host: block triangular order (strongly connected components of A's directed graph, each
+// after the components it reaches; multiple minimum degree inside each); false when a
+// component's order outgrows the budget.
+bool lu_btf_order(int n, const std::vector<int>& rp, const std::vector<int>& col,
+                  std::vector<int>& order);
+// Host: longest chains of dependent steps of a plan: refactorisation, forward and backward
+// substitution.
+void lu_plan_depth(const LuPlan& P, int depth[3]);
 // Host: plan of A (CSR) in column order q from one factorisation with threshold partial
 // pivoting. Returns 0, EEC_ENUMERIC (a numerically singular column) or EEC_ENOMEM (the factor
 // or its update list would outgrow its budget), with err set.

@@ -108,3 +108,78 @@ def test_too_much_fill_is_refused_before_memory_runs_out(eec):
         eec.eec_lu_check_host(rp, col, A, b)
     assert e.value.code == eec.EEC_ENOMEM
     assert time.perf_counter() - t0 < 30
+
+
+def _dc_pruned(net, seed=2, shift=0.0):
+    """The DC system at random node voltages, with the pattern's entries that no DC stamp writes
+    dropped (the gate rows: in DC only their diagonal's gshunt is nonzero)."""
+    import scipy.sparse as sp
+    rp, col, A, b = _system(net, seed=seed, shift=shift)
+    n = len(rp) - 1
+    M = sp.csr_matrix((A, col, rp), shape=(n, n))
+    full = M.copy()
+    M.eliminate_zeros()
+    M.sort_indices()
+    return full, M, b
+
+
+def _backward_error(M, x, b):
+    return np.abs(M @ x - b).max() / (np.abs(M.data).max() * np.abs(x).max() + np.abs(b).max())
+
+
+def test_dc_pruned_pattern_shortens_the_lu_chains(eec):
+    # The symmetric pattern keeps the gate rows, which DC never writes. Symbolically the word
+    # lines then couple every bit line through the cells, and the factor's last columns form
+    # a chain as long as the array is wide. Without those entries, the same minimum-degree
+    # order leaves short chains in the refactorisation and in both substitutions.
+    full, M, b = _dc_pruned(netgen.sram(64, 64))
+    _, _, nnz_full, bad_f, d_full = eec.eec_lu_check_host_ex(full.indptr, full.indices, full.data, b)
+    x, _, nnz_dc, bad_d, d_dc = eec.eec_lu_check_host_ex(M.indptr, M.indices, M.data, b)
+    assert min(d_full) >= 60 and max(d_dc) <= 8, (d_full, d_dc)
+    assert nnz_dc < 0.8 * nnz_full and bad_f == bad_d == -1
+    assert _backward_error(M, x, b) <= 64 * np.finfo(float).eps
+
+
+def test_dc_pruned_pattern_of_random_logic_factors(eec):
+    # randomly wired logic: the full pattern's fill is refused; without the gate rows it factors
+    full, M, b = _dc_pruned(netgen.random_logic(2000, seed=3))
+    with pytest.raises(eec.EECError) as e:
+        eec.eec_lu_check_host_ex(full.indptr, full.indices, full.data, b)
+    assert e.value.code == eec.EEC_ENOMEM
+    x, _, nnz, bad, _ = eec.eec_lu_check_host_ex(M.indptr, M.indices, M.data, b)
+    assert nnz <= 8 * M.nnz and bad == -1
+    assert _backward_error(M, x, b) <= 64 * np.finfo(float).eps
+
+
+@pytest.mark.parametrize("make", [lambda: netgen.random_logic(600, seed=3),
+                                  lambda: netgen.sram(12, 10), lambda: netgen.ripple_adder(8),
+                                  lambda: netgen.concat(netgen.batch_circuits(16))])
+def test_block_triangular_order(eec, make):
+    # the order lists the strongly connected components of A's directed graph, each after every
+    # component its edges reach: A(q, q) is block lower triangular
+    from scipy.sparse.csgraph import connected_components
+    _, M, b = _dc_pruned(make(), shift=1e-3)   # a shunt keeps long chains well conditioned
+    x, q, nnz, bad, depth = eec.eec_lu_check_host_ex(M.indptr, M.indices, M.data, b,
+                                                     order=eec.EEC_LU_ORDER_BTF)
+    n = M.shape[0]
+    assert np.array_equal(np.sort(q), np.arange(n))
+    _, lab = connected_components(M, directed=True, connection="strong")
+    pos = np.empty(n, np.int64)
+    pos[q] = np.arange(n)
+    first = {}
+    for k in range(n):                      # each component's columns are consecutive in q
+        first.setdefault(lab[q[k]], k)
+    comp_pos = np.array([first[lab[i]] for i in range(n)])
+    sizes = np.bincount(lab)
+    for c, k0 in first.items():
+        assert set(lab[q[k0:k0 + sizes[c]]]) == {c}
+    C = M.tocoo()
+    assert np.all(comp_pos[C.col] <= comp_pos[C.row])   # row i's columns in earlier components
+    assert bad == -1 and _backward_error(M, x, b) <= 64 * np.finfo(float).eps
+
+
+def test_unknown_order_is_rejected(eec):
+    _, M, b = _dc_pruned(netgen.inverter_chain(8))
+    with pytest.raises(eec.EECError) as e:
+        eec.eec_lu_check_host_ex(M.indptr, M.indices, M.data, b, order=7)
+    assert e.value.code == eec.EEC_EINVAL
